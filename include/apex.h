@@ -1,0 +1,207 @@
+/*
+ * apex.h -- C ABI of the B300 (sm_103a) exhaustive CSL enumeration library.
+ *
+ * The library answers the retrieval problem of Sec. 3 (Eq. orig_topk, relaxed to the
+ * factorized surrogate in Eq. apex_topk): among all compounds of a combinatorial synthesis
+ * library (reactions -> R-group slots -> synthons, Sec. 3.2 / App. A.1), return the k with
+ * the largest objective sum_j w_j o_j whose constrained outputs lie in [lower_i, upper_i].
+ * A compound's outputs are o = head(g) with g = sum over its slots of the synthon embedding
+ * u_{t,j,s} (Eq. factorizer); the first layer is applied per synthon once at load
+ * (P_{t,j,s} = W_1 u_{t,j,s}, the substitution of Eq. apex_subtitution..apex generalized to a
+ * matrix), so enumeration only sums rows of P and runs the remaining layers.
+ *
+ * Conventions for every entry point:
+ *   - returns apex_status: APEX_OK (0) or a negative code; no C++ exception crosses the ABI;
+ *     apex_last_error() returns a thread-local message for the last failure on this thread.
+ *   - "host" pointers are ordinary CPU memory owned by the caller, read (or written) only
+ *     during the call unless stated otherwise; the caller may free them when the call returns.
+ *   - device memory the library allocates is owned by the library and released by
+ *     apex_free_library (per-query state: when the query is fetched or cancelled).
+ *   - global compound id: off_t + mixed radix of (s_1..s_n), slot 1 most significant, where
+ *     off_t = number of compounds of the reactions before t (library order).
+ *   - all device work of a library runs on one CUDA stream (the one given at load, or one the
+ *     library creates) from a host worker thread owned by the library.
+ */
+#ifndef APEX_H
+#define APEX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t apex_status;
+#define APEX_OK 0
+#define APEX_EINVAL (-1)        /* malformed descriptor or argument */
+#define APEX_ENOMEM (-2)        /* device memory budget or allocation exhausted */
+#define APEX_EBUSY (-3)         /* no query slot can ever admit this request */
+#define APEX_EAGAIN (-4)        /* query not finished within timeout_ms */
+#define APEX_ETIMEDOUT (-5)     /* a device-side bounded wait gave up (kernel status word) */
+#define APEX_ECANCELED (-6)     /* the query was cancelled */
+#define APEX_ECUDA (-7)         /* a CUDA runtime call failed */
+#define APEX_ENOTFOUND (-8)     /* unknown query id */
+#define APEX_EUNSUPPORTED (-9)  /* shape/precision combination this build does not implement */
+
+#define APEX_ACT_IDENTITY 0
+#define APEX_ACT_RELU 1
+#define APEX_ACT_SILU 2
+
+/* Query precision of the enumeration pass. FP32: every layer in FP32 on the CUDA cores.
+ * BF16: layers 2.. on tcgen05 tensor cores (BF16 operands, FP32 accumulators in TMEM); the
+ * candidates are then rescored in FP32 and the top-k boundary band in FP64, so the returned
+ * set equals the FP64 top-k when the calibrated error bounds hold. */
+#define APEX_FP32 0
+#define APEX_BF16 1
+
+#define APEX_MAX_SLOTS 4          /* slots per reaction */
+#define APEX_MAX_OUTPUTS 32       /* head outputs */
+#define APEX_MAX_OBJECTIVES 16
+#define APEX_MAX_CONSTRAINTS 16
+#define APEX_MAX_ACTIVE 64        /* queries sharing one enumeration pass */
+
+typedef struct apex_library apex_library;
+typedef int64_t apex_query_id;
+
+/* Library descriptor (Sec. 3.2 hierarchy + head). Read during apex_load_library only. */
+typedef struct {
+  int32_t n_reactions;          /* >= 1 */
+  const int32_t *n_slots;       /* host [n_reactions], each in 1..APEX_MAX_SLOTS */
+  const int64_t *slot_sizes;    /* host [sum n_slots], reaction-major, each >= 1 */
+  int32_t d;                    /* embedding width, == dims[0] */
+  const float *U;               /* [sum slot_sizes x d] row-major float32, rows reaction -> slot ->
+                                   synthon; host memory, or device memory when U_on_device != 0
+                                   (then 16-byte aligned; the library copies it either way) */
+  int32_t U_on_device;
+  int32_t n_layers;             /* >= 1 */
+  const int32_t *dims;          /* host [n_layers + 1]; hidden widths <= 256; dims[n_layers] <= 32 */
+  const float *const *W;        /* host [n_layers] of host float32 [dims[l+1] x dims[l]] row-major */
+  const float *const *b;        /* host [n_layers] of host float32 [dims[l+1]] */
+  int32_t activation;           /* APEX_ACT_*, applied after every layer but the last */
+  int32_t n_objectives;         /* outputs [0, n_objectives) may carry objective weight */
+  int32_t n_properties;         /* n_objectives + n_properties == dims[n_layers] */
+  uint32_t precisions;          /* bit (1 << APEX_BF16) builds the tensor-core tables; FP32 always */
+  uint64_t device_mem_budget;   /* bytes the library may hold on the device; 0 = unlimited */
+  void *cuda_stream;            /* cudaStream_t to run on; NULL = the library creates one */
+  int32_t device;               /* CUDA device ordinal */
+  uint64_t seed;                /* seed of the calibration sample */
+} apex_library_desc;
+
+/* Query descriptor (Eq. orig_topk: objective weights, constraint boxes, k). Copied by
+ * apex_query; the caller may free it when the call returns. */
+typedef struct {
+  int32_t precision;            /* APEX_FP32 or APEX_BF16 */
+  const float *objective_weights; /* host [n_objectives]; the objective is maximized */
+  int32_t n_constraints;        /* 0..APEX_MAX_CONSTRAINTS */
+  const int32_t *output_index;  /* host [n_constraints], any output index */
+  const double *lower;          /* host [n_constraints]; inclusive; -INFINITY allowed */
+  const double *upper;          /* host [n_constraints]; inclusive; +INFINITY allowed; lower <= upper */
+  int64_t k;                    /* >= 1 */
+  int32_t n_reaction_subset;    /* 0 = every reaction */
+  const int32_t *reactions;     /* host [n_reaction_subset], distinct reaction indices */
+} apex_query_desc;
+
+typedef struct {
+  int64_t n_compounds;          /* N = sum_t prod_j |slot_{t,j}| (App. A.1) */
+  int64_t n_synthon_rows;       /* sum of slot sizes */
+  int32_t max_slots;
+  int32_t n_outputs;
+  uint64_t device_bytes;        /* device memory held by the library tables */
+  uint32_t precisions;          /* tables built */
+  int32_t n_calibration;        /* compounds in the calibration sample */
+  double err_bf16[APEX_MAX_OUTPUTS]; /* per-output admission margin of the BF16 pass */
+  double err_fp32[APEX_MAX_OUTPUTS]; /* per-output margin of the FP32 rescore */
+  double rms[APEX_MAX_OUTPUTS];      /* output RMS over the calibration sample */
+} apex_library_info_t;
+
+typedef struct {
+  int64_t n_scope;              /* compounds in the query's reaction subset */
+  int64_t n_scored;             /* head evaluations of enumeration launches that served it */
+  int64_t n_candidates;         /* first-pass candidates rescored in FP32 */
+  int64_t n_rescored_fp64;      /* compounds rescored in FP64 */
+  int64_t n_feasible_lower;     /* results found (<= k) */
+  int32_t n_restarts;           /* reruns after a candidate buffer overflow or a failed start guess */
+  int32_t n_launches;           /* enumeration launches that served this query */
+  double queue_ms;              /* host wall time from apex_query to admission */
+  double latency_ms;            /* host wall time from apex_query until the results were ready */
+  double gpu_ms;                /* device time (CUDA events) from its first to its last kernel */
+  double enumerate_ms;          /* device time of the enumeration launches that served it */
+} apex_query_stats_t;
+
+/* Pure host: N = sum_t prod_j slot_sizes (App. A.1). EINVAL on bad shapes or int64 overflow. */
+apex_status apex_count_compounds(int32_t n_reactions, const int32_t *n_slots, const int64_t *slot_sizes,
+                                 int64_t *n_out);
+
+/* Validates desc (before touching the GPU), uploads U and the head, builds P = W_1 U^T (+ b_1
+ * folded into slot 1 rows) in FP32 and, if requested, the BF16 tables and tensor-core weight
+ * images, calibrates the error margins on a seeded sample, and starts the worker thread.
+ * EINVAL bad desc; ENOMEM over budget; EUNSUPPORTED e.g. BF16 with hidden widths != 256;
+ * ECUDA on a CUDA failure. On error *out is NULL and nothing is leaked. */
+apex_status apex_load_library(const apex_library_desc *desc, apex_library **out);
+
+/* Stops the worker (pending queries end as ECANCELED), frees every device buffer. NULL is OK. */
+apex_status apex_free_library(apex_library *lib);
+
+apex_status apex_library_info(const apex_library *lib, apex_library_info_t *out);
+
+/* Submits a query (Eq. apex_topk) and returns at once with its id. The worker admits it
+ * when a slot (APEX_MAX_ACTIVE) and device memory for its candidate state are free, and
+ * serves it from the shared enumeration pass (continuous batching); queries that arrive
+ * while others run join the pass at its current position and leave after one revolution
+ * over their own reactions. EINVAL bad desc (NaN bound, lower > upper, index out of range,
+ * k < 1, duplicate or out-of-range reaction); EUNSUPPORTED precision not built. */
+apex_status apex_query(apex_library *lib, const apex_query_desc *desc, apex_query_id *out);
+
+/* Waits up to timeout_ms (< 0: forever) for the query, then copies min(capacity, n) results,
+ * n = min(k, feasible compounds in scope), ordered by (objective desc, id asc):
+ *   ids [cap], reaction [cap], synthons [cap x APEX_MAX_SLOTS] (-1 padded),
+ *   objective [cap], outputs [cap x n_outputs]   -- host buffers; any may be NULL.
+ * Objectives and outputs are the FP32 rescore, replaced by FP64 for every compound in the
+ * top-k boundary band or tied with a neighbour within the FP32 margin. *n_out = n.
+ * EAGAIN: not done yet (the query stays alive); otherwise the query is released. */
+apex_status apex_topk_fetch(apex_library *lib, apex_query_id id, int64_t capacity, int64_t *ids,
+                            int32_t *reaction, int64_t *synthons, double *objective, double *outputs,
+                            int64_t *n_out, int32_t timeout_ms);
+
+/* Cancels a queued or running query; a later fetch returns ECANCELED. */
+apex_status apex_cancel(apex_library *lib, apex_query_id id);
+
+/* Statistics of a finished (not yet fetched) query, or of the last fetched one when id < 0. */
+apex_status apex_query_stats(apex_library *lib, apex_query_id id, apex_query_stats_t *out);
+
+/* Scores given compounds (host ids [n]) through the gather kernels: precision APEX_FP32
+ * (CUDA cores) or 2 (= FP64 plain form g = sum u, then the head). outputs: host [n x n_outputs].
+ * Synchronous. Used for calibration checks and parity tests. */
+apex_status apex_score_ids(apex_library *lib, int32_t precision, int64_t n, const int64_t *ids,
+                           double *outputs);
+
+/* Runs the production enumeration kernel of the given precision over one reaction and
+ * writes the raw outputs of every compound, in id order: host float [N_t x n_outputs].
+ * capacity is the number of rows of outputs. Synchronous; meant for tests of raw scores. */
+apex_status apex_dump_outputs(apex_library *lib, int32_t precision, int32_t reaction, float *outputs,
+                              int64_t capacity);
+
+/* Decodes global ids into (reaction, synthon indices); host buffers; pure host work. */
+apex_status apex_decode_ids(const apex_library *lib, int64_t n, const int64_t *ids, int32_t *reaction,
+                            int64_t *synthons);
+
+/* Top-k selection step on device data (Sec. 3.3 queue, realised as a radix select): among n
+ * keys (device float [n]) with ids (device int64 [n]), writes the k largest keys, ties by
+ * smaller id, in (key desc, id asc) order to out_keys / out_ids (device [k]) and *n_out =
+ * min(k, n) (host). Scratch comes from cudaMalloc inside the call. cuda_stream may be NULL. */
+apex_status apex_topk_select(const float *keys, const int64_t *ids, int64_t n, int64_t k, float *out_keys,
+                             int64_t *out_ids, int64_t *n_out, void *cuda_stream);
+
+/* Number of kernel launches this process has issued through the library so far (all
+ * libraries, all entry points). Pure host counter. */
+apex_status apex_kernel_launches(int64_t *out);
+
+/* Thread-local message describing the last error returned on this thread ("" if none). */
+const char *apex_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APEX_H */

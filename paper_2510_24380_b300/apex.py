@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libapex_b300.so (include/apex.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module only converts numpy arrays and
+Python values into the C structs and back. It fails loudly when the library is missing.
+The functions keep the C names; ``Library`` wraps them for csl_gen inputs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libapex_b300.so")
+
+APEX_OK = 0
+STATUS = {0: "APEX_OK", -1: "APEX_EINVAL", -2: "APEX_ENOMEM", -3: "APEX_EBUSY", -4: "APEX_EAGAIN",
+          -5: "APEX_ETIMEDOUT", -6: "APEX_ECANCELED", -7: "APEX_ECUDA", -8: "APEX_ENOTFOUND",
+          -9: "APEX_EUNSUPPORTED"}
+APEX_EAGAIN = -4
+ACT = {"identity": 0, "relu": 1, "silu": 2}
+PREC = {"fp32": 0, "bf16": 1, "fp64": 2}
+MAX_SLOTS = 4
+MAX_OUTPUTS = 32
+
+
+class ApexError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class LibraryDesc(C.Structure):
+    _fields_ = [
+        ("n_reactions", C.c_int32), ("n_slots", C.POINTER(C.c_int32)), ("slot_sizes", C.POINTER(C.c_int64)),
+        ("d", C.c_int32), ("U", C.POINTER(C.c_float)), ("U_on_device", C.c_int32), ("n_layers", C.c_int32),
+        ("dims", C.POINTER(C.c_int32)), ("W", C.POINTER(C.POINTER(C.c_float))), ("b", C.POINTER(C.POINTER(C.c_float))),
+        ("activation", C.c_int32), ("n_objectives", C.c_int32), ("n_properties", C.c_int32),
+        ("precisions", C.c_uint32), ("device_mem_budget", C.c_uint64), ("cuda_stream", C.c_void_p),
+        ("device", C.c_int32), ("seed", C.c_uint64),
+    ]
+
+
+class QueryDesc(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32), ("objective_weights", C.POINTER(C.c_float)), ("n_constraints", C.c_int32),
+        ("output_index", C.POINTER(C.c_int32)), ("lower", C.POINTER(C.c_double)), ("upper", C.POINTER(C.c_double)),
+        ("k", C.c_int64), ("n_reaction_subset", C.c_int32), ("reactions", C.POINTER(C.c_int32)),
+    ]
+
+
+class LibraryInfo(C.Structure):
+    _fields_ = [
+        ("n_compounds", C.c_int64), ("n_synthon_rows", C.c_int64), ("max_slots", C.c_int32),
+        ("n_outputs", C.c_int32), ("device_bytes", C.c_uint64), ("precisions", C.c_uint32),
+        ("n_calibration", C.c_int32), ("err_bf16", C.c_double * MAX_OUTPUTS), ("err_fp32", C.c_double * MAX_OUTPUTS),
+        ("rms", C.c_double * MAX_OUTPUTS),
+    ]
+
+
+class QueryStats(C.Structure):
+    _fields_ = [
+        ("n_scope", C.c_int64), ("n_scored", C.c_int64), ("n_candidates", C.c_int64), ("n_rescored_fp64", C.c_int64),
+        ("n_feasible_lower", C.c_int64), ("n_restarts", C.c_int32), ("n_launches", C.c_int32),
+        ("queue_ms", C.c_double), ("latency_ms", C.c_double), ("gpu_ms", C.c_double), ("enumerate_ms", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_dll = None
+
+SYMBOLS = {
+    "apex_count_compounds": [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+    "apex_load_library": [C.POINTER(LibraryDesc), C.POINTER(C.c_void_p)],
+    "apex_free_library": [C.c_void_p],
+    "apex_library_info": [C.c_void_p, C.POINTER(LibraryInfo)],
+    "apex_query": [C.c_void_p, C.POINTER(QueryDesc), C.POINTER(C.c_int64)],
+    "apex_topk_fetch": [C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                        C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                        C.c_int32],
+    "apex_cancel": [C.c_void_p, C.c_int64],
+    "apex_query_stats": [C.c_void_p, C.c_int64, C.POINTER(QueryStats)],
+    "apex_score_ids": [C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+    "apex_dump_outputs": [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_float), C.c_int64],
+    "apex_decode_ids": [C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int64)],
+    "apex_topk_select": [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64),
+                         C.c_void_p],
+    "apex_kernel_launches": [C.POINTER(C.c_int64)],
+    "apex_last_error": [],
+}
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library (never falls back to anything else)."""
+    global _dll
+    if _dll is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with `python -m paper_2510_24380_b300.build`")
+        dll = C.CDLL(path)
+        for name, args in SYMBOLS.items():
+            fn = getattr(dll, name)
+            fn.argtypes = args
+            fn.restype = C.c_int32
+        dll.apex_last_error.restype = C.c_char_p
+        _dll = dll
+    return _dll
+
+
+def _check(code, what=""):
+    if code != APEX_OK:
+        msg = load().apex_last_error().decode(errors="replace")
+        raise ApexError(code, f"{what}: {msg}")
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+# ---------------------------------------------------------------- C-named thin wrappers
+def apex_count_compounds(n_slots, slot_sizes) -> int:
+    ns = np.ascontiguousarray(n_slots, np.int32)
+    ss = np.ascontiguousarray(slot_sizes, np.int64)
+    out = C.c_int64()
+    _check(load().apex_count_compounds(int(ns.shape[0]), _p(ns, C.c_int32), _p(ss, C.c_int64), C.byref(out)),
+           "apex_count_compounds")
+    return out.value
+
+
+class Library:
+    """A loaded library (apex_load_library) built from csl_gen's CSL and Head."""
+
+    def __init__(self, lib, head, precisions=("fp32", "bf16"), device: int = 0, stream=None, budget: int = 0,
+                 seed: int = 0, U_device=None):
+        dll = load()
+        self._keep = []
+        ns = np.ascontiguousarray(lib.n_slots, np.int32)
+        ss = np.ascontiguousarray(lib.slot_sizes, np.int64)
+        dims = np.asarray(head.dims, np.int32)
+        W = [np.ascontiguousarray(w, np.float32) for w in head.W]
+        b = [np.ascontiguousarray(x, np.float32) for x in head.b]
+        Wp = (C.POINTER(C.c_float) * len(W))(*[_p(w, C.c_float) for w in W])
+        bp = (C.POINTER(C.c_float) * len(b))(*[_p(x, C.c_float) for x in b])
+        self._keep += [ns, ss, dims, W, b, Wp, bp]
+        D = LibraryDesc()
+        D.n_reactions = int(ns.shape[0])
+        D.n_slots = _p(ns, C.c_int32)
+        D.slot_sizes = _p(ss, C.c_int64)
+        D.d = int(lib.d)
+        if U_device is not None:
+            D.U = C.cast(C.c_void_p(int(U_device)), C.POINTER(C.c_float))
+            D.U_on_device = 1
+        else:
+            U = np.ascontiguousarray(lib.U, np.float32)
+            self._keep.append(U)
+            D.U = _p(U, C.c_float)
+            D.U_on_device = 0
+        D.n_layers = len(W)
+        D.dims = _p(dims, C.c_int32)
+        D.W = C.cast(Wp, C.POINTER(C.POINTER(C.c_float)))
+        D.b = C.cast(bp, C.POINTER(C.POINTER(C.c_float)))
+        D.activation = ACT[head.activation]
+        D.n_objectives = int(head.n_objectives)
+        D.n_properties = int(head.n_properties)
+        D.precisions = sum(1 << PREC[p] for p in precisions)
+        D.device_mem_budget = int(budget)
+        D.cuda_stream = stream
+        D.device = int(device)
+        D.seed = int(seed)
+        h = C.c_void_p()
+        _check(dll.apex_load_library(C.byref(D), C.byref(h)), "apex_load_library")
+        self._keep = [dims]
+        self.h = h
+        self.n_outputs = int(head.dims[-1])
+        self.n_objectives = int(head.n_objectives)
+
+    def close(self):
+        if self.h:
+            load().apex_free_library(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> LibraryInfo:
+        out = LibraryInfo()
+        _check(load().apex_library_info(self.h, C.byref(out)), "apex_library_info")
+        return out
+
+    def query(self, q) -> int:
+        """apex_query for a csl_gen.Query; returns the query id."""
+        w = np.ascontiguousarray(q.weights, np.float32)
+        idx = np.ascontiguousarray(q.cons_idx, np.int32)
+        lo = np.ascontiguousarray(q.lo, np.float64)
+        hi = np.ascontiguousarray(q.hi, np.float64)
+        sub = None if q.subset is None else np.ascontiguousarray(q.subset, np.int32)
+        D = QueryDesc()
+        D.precision = PREC[q.precision]
+        D.objective_weights = _p(w, C.c_float)
+        D.n_constraints = int(idx.shape[0])
+        D.output_index = _p(idx, C.c_int32)
+        D.lower = _p(lo, C.c_double)
+        D.upper = _p(hi, C.c_double)
+        D.k = int(q.k)
+        D.n_reaction_subset = 0 if sub is None else int(sub.shape[0])
+        D.reactions = _p(sub, C.c_int32) if sub is not None else C.POINTER(C.c_int32)()
+        qid = C.c_int64()
+        _check(load().apex_query(self.h, C.byref(D), C.byref(qid)), "apex_query")
+        return qid.value
+
+    def fetch(self, qid: int, capacity: int, timeout_ms: int = -1):
+        """apex_topk_fetch into fresh host arrays; returns a dict (or None on EAGAIN)."""
+        cap = int(capacity)
+        ids = np.empty(cap, np.int64)
+        rxn = np.empty(cap, np.int32)
+        syn = np.empty((cap, MAX_SLOTS), np.int64)
+        obj = np.empty(cap, np.float64)
+        out = np.empty((cap, self.n_outputs), np.float64)
+        n = C.c_int64()
+        code = load().apex_topk_fetch(self.h, int(qid), cap, _p(ids, C.c_int64), _p(rxn, C.c_int32),
+                                      _p(syn, C.c_int64), _p(obj, C.c_double), _p(out, C.c_double), C.byref(n),
+                                      int(timeout_ms))
+        if code == APEX_EAGAIN:
+            return None
+        _check(code, "apex_topk_fetch")
+        m = min(n.value, cap)
+        return {"ids": ids[:m], "reaction": rxn[:m], "synthons": syn[:m], "objective": obj[:m],
+                "outputs": out[:m], "n": n.value}
+
+    def run(self, q, timeout_ms: int = -1):
+        qid = self.query(q)
+        return self.fetch(qid, int(q.k), timeout_ms)
+
+    def cancel(self, qid: int):
+        _check(load().apex_cancel(self.h, int(qid)), "apex_cancel")
+
+    def stats(self, qid: int = -1) -> dict:
+        s = QueryStats()
+        _check(load().apex_query_stats(self.h, int(qid), C.byref(s)), "apex_query_stats")
+        return s.as_dict()
+
+    def score_ids(self, ids, precision: str = "fp32"):
+        ids = np.ascontiguousarray(ids, np.int64)
+        out = np.empty((ids.shape[0], self.n_outputs), np.float64)
+        _check(load().apex_score_ids(self.h, PREC[precision], int(ids.shape[0]), _p(ids, C.c_int64),
+                                     _p(out, C.c_double)), "apex_score_ids")
+        return out
+
+    def dump_outputs(self, reaction: int, n_compounds: int, precision: str = "bf16"):
+        out = np.empty((int(n_compounds), self.n_outputs), np.float32)
+        _check(load().apex_dump_outputs(self.h, PREC[precision], int(reaction), _p(out, C.c_float),
+                                        int(n_compounds)), "apex_dump_outputs")
+        return out
+
+    def decode(self, ids):
+        ids = np.ascontiguousarray(ids, np.int64)
+        t = np.empty(ids.shape[0], np.int32)
+        s = np.empty((ids.shape[0], MAX_SLOTS), np.int64)
+        _check(load().apex_decode_ids(self.h, int(ids.shape[0]), _p(ids, C.c_int64), _p(t, C.c_int32),
+                                      _p(s, C.c_int64)), "apex_decode_ids")
+        return t, s
+
+
+def apex_kernel_launches() -> int:
+    out = C.c_int64()
+    _check(load().apex_kernel_launches(C.byref(out)), "apex_kernel_launches")
+    return out.value
+
+
+def apex_topk_select(keys_ptr: int, ids_ptr: int, n: int, k: int, out_keys_ptr: int, out_ids_ptr: int,
+                     stream: int | None = None) -> int:
+    """Device pointers in, device pointers out; returns n_out."""
+    n_out = C.c_int64()
+    _check(load().apex_topk_select(C.c_void_p(keys_ptr), C.c_void_p(ids_ptr), int(n), int(k), C.c_void_p(out_keys_ptr),
+                                   C.c_void_p(out_ids_ptr), C.byref(n_out), C.c_void_p(stream or 0)),
+           "apex_topk_select")
+    return n_out.value

@@ -1,0 +1,1363 @@
+// apex_lib.cu -- host side of the C ABI (include/apex.h).
+//
+//   load:   validate -> upload U and the head -> P32 = W_1 U^T (+ b_1 on slot-1 rows) ->
+//           BF16 tables and tensor-core weight images -> per-reaction work plans ->
+//           calibration of the pass margins -> worker thread.
+//   query:  apex_query queues a request; the worker admits it into one of APEX_MAX_ACTIVE slots
+//           when its candidate state fits the memory budget, estimates a starting threshold from
+//           a seeded FP32 sample of its scope, and serves it from the shared circular pass over
+//           the library (continuous batching: one enumeration launch serves every active query
+//           whose reactions it covers). When a query has seen all its items once, it is
+//           finalized: exact selection (FP32 rescore of the candidates, FP64 rescore of the
+//           boundary band and of near-ties), ordering by (objective desc, id asc), decode.
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <random>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+// ------------------------------------------------------------------ kernels (other files)
+cudaError_t apx_launch_fp32(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, const long long *ids,
+                            long long n_ids, float *out, int grid, cudaStream_t st);
+cudaError_t apx_launch_fp64(const DevTables &T, const long long *ids, long long n, double *out, cudaStream_t st);
+cudaError_t apx_launch_prep(const float *U, const float *W1, const float *b1, const unsigned char *bias_row,
+                            long long rows, int K, int N, float *P32, cudaStream_t st);
+cudaError_t apx_launch_p16(const float *P32, long long n, float scale, void *P16, cudaStream_t st);
+cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
+                          cudaStream_t st);
+void apx_make_sw128_image(const float *W, int rows_used, int rows, unsigned char *img);
+cudaError_t apx_launch_slot_select(QuerySlot *slots, const int *slot_list, int n_slots, int mode, cudaStream_t st);
+cudaError_t apx_launch_eval32(const EvalArgs &a, long long n, float *f32, unsigned char *maybe, unsigned char *sure,
+                              cudaStream_t st);
+cudaError_t apx_launch_kth(const float *keys, const unsigned char *flag, long long n, long long k, float *out_tau,
+                           int *out_ok, cudaStream_t st);
+cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
+                               const unsigned char *sure, float thr, RItem *R, unsigned *n_r, cudaStream_t st);
+cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64, cudaStream_t st);
+cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, int n_out,
+                               const QuerySlot *Q, const double *lo, const double *hi, double *out_rows,
+                               cudaStream_t st);
+cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st);
+cudaError_t apx_launch_mark(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked,
+                            cudaStream_t st);
+cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const DevTables &T, const float *out32,
+                            const double *out64_rows, long long *ids, int *rxn, long long *syn, double *obj,
+                            double *outs, cudaStream_t st);
+int apx_count_alive(const RItem *R, unsigned n, cudaStream_t st, unsigned *d_tmp, cudaError_t *e);
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+static apex_status fail(apex_status code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+static apex_status fail(apex_status code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+apex_status apx_fail(apex_status code, const char *msg) {
+  g_err = msg;
+  return code;
+}
+#define CU(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) throw CudaFail(e_, #call, __LINE__);                                     \
+  } while (0)
+struct CudaFail {
+  cudaError_t e;
+  const char *what;
+  int line;
+  CudaFail(cudaError_t e_, const char *w, int l) : e(e_), what(w), line(l) {}
+};
+struct BudgetFail {};
+
+static std::atomic<long long> g_launches{0};
+void apx_count_launch(long long n) { g_launches += n; }
+
+static double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------------ query record
+enum QState { Q_QUEUED, Q_ACTIVE, Q_DONE, Q_CANCELED, Q_FAILED };
+
+struct QueryRec {
+  apex_query_id id;
+  int precision;
+  std::vector<float> w;
+  std::vector<int> cidx;
+  std::vector<double> lo, hi;
+  long long k;
+  std::vector<int> subset;          // sorted reaction indices
+  std::vector<char> need;           // [n_rx]
+  long long scope_items = 0, remaining = 0, scope_n = 0;
+  QState state = Q_QUEUED;
+  int slot = -1;
+  apex_status err = APEX_OK;
+  std::string err_msg;
+  bool cancel = false;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  // device state
+  unsigned cap = 0;
+  float *keys = nullptr, *keys2 = nullptr;
+  long long *ids = nullptr, *ids2 = nullptr;
+  size_t dev_bytes = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool started = false;
+  int spec_rank = 0;                // rank used for the speculative start threshold (0 = none)
+  float tau_spec = -INFINITY;
+  // results
+  std::vector<long long> r_ids;
+  std::vector<int> r_rxn;
+  std::vector<long long> r_syn;
+  std::vector<double> r_obj, r_out;
+  apex_query_stats_t stats{};
+};
+
+// ------------------------------------------------------------------ library
+struct apex_library {
+  // shape
+  int T = 0, d = 0, n_layers = 0, act = 0, n_obj = 0, n_prop = 0, n_out = 0, max_slots = 0;
+  int dims[8] = {0};
+  std::vector<int> n_slots;
+  std::vector<long long> slot_sizes, slot_first, row_first, id_first;
+  long long N = 0, rows = 0;
+  uint32_t precisions = 1u;
+  bool tc_ok = false;
+  // device
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int n_sm = 148;
+  std::vector<void *> allocs;
+  size_t bytes = 0, budget = 0, query_bytes = 0;
+  DevTables T_{};
+  std::vector<RxnPlan> rx;
+  long long total_items = 0;
+  std::vector<long long> item_first;  // [T+1] prefix of items
+  QuerySlot *d_slots = nullptr;
+  int *d_err = nullptr;
+  int *d_slot_list = nullptr;
+  // calibration
+  double err16[APEX_MAX_OUTPUTS] = {0}, err32[APEX_MAX_OUTPUTS] = {0}, rms[APEX_MAX_OUTPUTS] = {0};
+  int n_calib = 0;
+  float *d_err32f = nullptr;  // per-output FP32 margin (float) for eval32
+  uint64_t seed = 0;
+  // engine
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv, cv_done;
+  bool stop = false;
+  std::deque<QueryRec *> queued;
+  std::map<apex_query_id, std::unique_ptr<QueryRec>> queries;
+  QueryRec *active[APEX_MAX_ACTIVE] = {nullptr};
+  std::atomic<long long> next_id{1};
+  long long cursor = 0;  // global item index of the circular pass
+  apex_query_stats_t last_stats{};
+  std::mt19937_64 rng;
+
+  void *dalloc(size_t n, bool count = true) {
+    if (count && budget && bytes + query_bytes + n > budget) throw BudgetFail();
+    void *p = nullptr;
+    CU(cudaMalloc(&p, n ? n : 16));
+    allocs.push_back(p);
+    if (count) bytes += n;
+    return p;
+  }
+  void release_all() {
+    for (void *p : allocs) cudaFree(p);
+    allocs.clear();
+  }
+  ~apex_library() {}
+};
+
+// ------------------------------------------------------------------ helpers
+static bool mul_ok(long long a, long long b, long long *out) {
+  if (a <= 0 || b <= 0) return false;
+  if (a > (long long)(INT64_MAX / b)) return false;
+  *out = a * b;
+  return true;
+}
+
+extern "C" apex_status apex_count_compounds(int32_t n_reactions, const int32_t *n_slots, const int64_t *slot_sizes,
+                                            int64_t *n_out) {
+  if (!n_slots || !slot_sizes || !n_out || n_reactions < 1) return fail(APEX_EINVAL, "bad arguments");
+  long long total = 0, s = 0;
+  for (int t = 0; t < n_reactions; ++t) {
+    if (n_slots[t] < 1) return fail(APEX_EINVAL, "reaction %d has %d slots", t, n_slots[t]);
+    long long n = 1;
+    for (int j = 0; j < n_slots[t]; ++j, ++s) {
+      if (slot_sizes[s] < 1) return fail(APEX_EINVAL, "slot %lld has size %lld", s, (long long)slot_sizes[s]);
+      if (!mul_ok(n, slot_sizes[s], &n)) return fail(APEX_EINVAL, "reaction %d overflows int64", t);
+    }
+    if (total > INT64_MAX - n) return fail(APEX_EINVAL, "library size overflows int64");
+    total += n;
+  }
+  *n_out = total;
+  return APEX_OK;
+}
+
+// Inner/outer split of reaction t (see common.cuh). The outer slot is slot 1 unless the
+// reaction has 2 slots and using slot 2 as the outer slot wastes fewer padded tile rows.
+static RxnPlan plan_reaction(const apex_library &L, int t, long long target_tiles_per_item) {
+  RxnPlan p{};
+  const int n = L.n_slots[t];
+  const long long *sz = &L.slot_sizes[L.slot_first[t]];
+  const long long *rf = &L.row_first[L.slot_first[t]];
+  p.id_first = L.id_first[t];
+  p.n_slots = n;
+  for (int j = 0; j < n; ++j) {
+    p.slot_row[j] = rf[j];
+    p.slot_size[j] = sz[j];
+  }
+  auto waste = [](long long m) { return (double)((m + APX_TILE - 1) / APX_TILE * APX_TILE) / (double)m; };
+  if (n == 1) {
+    p.n_inner = sz[0];
+    p.n_outer = 1;
+    p.inner_stride = 1;
+    p.outer_stride = 0;
+    p.outer_row = -1;
+    p.n_inner_slots = 1;
+    p.inner_row[0] = rf[0];
+    p.inner_size[0] = sz[0];
+  } else if (n == 2 && waste(sz[0]) < waste(sz[1])) {
+    // inner = slot 1 (stride |slot 2|), outer = slot 2 (stride 1)
+    p.n_inner = sz[0];
+    p.n_outer = sz[1];
+    p.inner_stride = sz[1];
+    p.outer_stride = 1;
+    p.outer_row = rf[1];
+    p.n_inner_slots = 1;
+    p.inner_row[0] = rf[0];
+    p.inner_size[0] = sz[0];
+  } else {
+    // outer = slot 1, inner = slots 2..n flattened (mixed radix, slot 2 most significant)
+    long long ni = 1;
+    for (int j = 1; j < n; ++j) ni *= sz[j];
+    p.n_inner = ni;
+    p.n_outer = sz[0];
+    p.inner_stride = 1;
+    p.outer_stride = ni;
+    p.outer_row = rf[0];
+    p.n_inner_slots = n - 1;
+    for (int j = 1; j < n; ++j) {
+      p.inner_row[j - 1] = rf[j];
+      p.inner_size[j - 1] = sz[j];
+    }
+  }
+  p.n_b = (int)((p.n_inner + APX_TILE - 1) / APX_TILE);
+  p.L_o = (int)std::max<long long>(1, std::min<long long>(p.n_outer, target_tiles_per_item));
+  p.n_oc = (int)((p.n_outer + p.L_o - 1) / p.L_o);
+  p.n_items = (long long)p.n_b * p.n_oc;
+  return p;
+}
+
+static DevTables upload_plans(apex_library &L) {
+  RxnPlan *d_rx = (RxnPlan *)L.dalloc(sizeof(RxnPlan) * L.rx.size());
+  CU(cudaMemcpy(d_rx, L.rx.data(), sizeof(RxnPlan) * L.rx.size(), cudaMemcpyHostToDevice));
+  long long *d_idf = (long long *)L.dalloc(sizeof(long long) * (L.T + 1));
+  CU(cudaMemcpy(d_idf, L.id_first.data(), sizeof(long long) * (L.T + 1), cudaMemcpyHostToDevice));
+  DevTables T = L.T_;
+  T.rx = d_rx;
+  T.id_first = d_idf;
+  return T;
+}
+
+// Builds a launch over [first item, ...) of the given reactions' items (a "chunk").
+struct PlanBuilder {
+  LaunchPlan P;
+  PlanBuilder() {
+    memset(&P, 0, sizeof(P));
+  }
+  bool add(int rxn, long long b, long long e, unsigned long long qmask) {
+    if (P.n_seg >= APX_MAX_SEG || e <= b) return false;
+    Segment &s = P.seg[P.n_seg];
+    s.rxn = rxn;
+    s.item_begin = b;
+    s.item_end = e;
+    s.qmask = qmask;
+    P.seg_first[P.n_seg + 1] = P.seg_first[P.n_seg] + (e - b);
+    P.n_seg++;
+    P.total_items = P.seg_first[P.n_seg];
+    return true;
+  }
+};
+
+static int grid_for(const apex_library &L, long long items) {
+  return (int)std::max<long long>(1, std::min<long long>(items, L.n_sm));
+}
+
+static void launch_enum(apex_library &L, const LaunchPlan &P, int precision) {
+  if (P.total_items == 0) return;
+  if (precision == APEX_BF16)
+    CU(apx_launch_tc(P, L.T_, L.d_slots, L.d_err, grid_for(L, P.total_items), L.st));
+  else
+    CU(apx_launch_fp32(P, L.T_, L.d_slots, nullptr, 0, nullptr, grid_for(L, P.total_items), L.st));
+}
+
+static void check_kernel_status(apex_library &L) {
+  int e = 0;
+  CU(cudaMemcpyAsync(&e, L.d_err, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+  CU(cudaStreamSynchronize(L.st));
+  if (e) {
+    int z = 0;
+    CU(cudaMemcpy(L.d_err, &z, sizeof(int), cudaMemcpyHostToDevice));
+    throw CudaFail(cudaErrorLaunchTimeout, "device-side bounded wait expired", e);
+  }
+}
+
+// ------------------------------------------------------------------ calibration
+// Margins of the reduced-precision pass and of the FP32 rescore, measured on a seeded sample:
+// the BF16 production kernel and the FP32 kernel score the same work items (dump mode); the
+// FP32 gather kernel and the FP64 kernel score the same sampled ids. margin = factor * max
+// |difference| + a floor relative to the output RMS. The sample bounds the error empirically;
+// there is no closed-form bound through bf16 rounding and tanh.approx.
+static void calibrate(apex_library &L) {
+  const int no = L.n_out;
+  std::mt19937_64 g(L.seed ^ 0x9e3779b97f4a7c15ull);
+  // FP32 vs FP64 on sampled ids
+  const long long ns = std::min<long long>(L.N, 4096);
+  std::vector<long long> ids(ns);
+  for (long long i = 0; i < ns; ++i) ids[i] = (long long)(g() % (unsigned long long)L.N);
+  long long *d_ids = (long long *)L.dalloc(sizeof(long long) * ns, false);
+  float *d_o32 = (float *)L.dalloc(sizeof(float) * ns * no, false);
+  double *d_o64 = (double *)L.dalloc(sizeof(double) * ns * no, false);
+  CU(cudaMemcpyAsync(d_ids, ids.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, L.st));
+  LaunchPlan dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  CU(apx_launch_fp32(dummy, L.T_, nullptr, d_ids, ns, d_o32, grid_for(L, (ns + APX_TILE - 1) / APX_TILE), L.st));
+  CU(apx_launch_fp64(L.T_, d_ids, ns, d_o64, L.st));
+  std::vector<float> o32(ns * no);
+  std::vector<double> o64(ns * no);
+  CU(cudaMemcpyAsync(o32.data(), d_o32, sizeof(float) * ns * no, cudaMemcpyDeviceToHost, L.st));
+  CU(cudaMemcpyAsync(o64.data(), d_o64, sizeof(double) * ns * no, cudaMemcpyDeviceToHost, L.st));
+  CU(cudaStreamSynchronize(L.st));
+  for (int p = 0; p < no; ++p) {
+    double m = 0, ss = 0;
+    for (long long i = 0; i < ns; ++i) {
+      m = std::max(m, std::fabs((double)o32[i * no + p] - o64[i * no + p]));
+      ss += o64[i * no + p] * o64[i * no + p];
+    }
+    L.rms[p] = std::sqrt(ss / (double)ns);
+    L.err32[p] = 8.0 * m + 1e-6 * L.rms[p] + 1e-9;
+  }
+  L.n_calib = (int)ns;
+  if (L.tc_ok) {
+    // BF16 vs FP32 on whole work items: the first item of up to 48 reactions, weighted by size
+    PlanBuilder pb;
+    std::vector<int> order(L.T);
+    for (int t = 0; t < L.T; ++t) order[t] = t;
+    std::shuffle(order.begin(), order.end(), g);
+    int max_lo = 1;
+    for (int t : order) {
+      if (pb.P.n_seg >= 48) break;
+      pb.add(t, 0, 1, 0);
+      max_lo = std::max(max_lo, L.rx[t].L_o);
+    }
+    const long long slots = pb.P.total_items * max_lo * APX_TILE;
+    float *d16 = (float *)L.dalloc(sizeof(float) * slots * no, false);
+    float *d32 = (float *)L.dalloc(sizeof(float) * slots * no, false);
+    long long *di16 = (long long *)L.dalloc(sizeof(long long) * slots, false);
+    long long *di32 = (long long *)L.dalloc(sizeof(long long) * slots, false);
+    LaunchPlan P = pb.P;
+    P.mode = 2;
+    P.dump_lo = max_lo;
+    P.dump_n = slots;
+    P.dump = d16;
+    P.dump_ids = di16;
+    CU(cudaMemsetAsync(di16, 0xff, sizeof(long long) * slots, L.st));
+    CU(cudaMemsetAsync(di32, 0xff, sizeof(long long) * slots, L.st));
+    CU(apx_launch_tc(P, L.T_, nullptr, L.d_err, grid_for(L, P.total_items), L.st));
+    P.dump = d32;
+    P.dump_ids = di32;
+    CU(apx_launch_fp32(P, L.T_, nullptr, nullptr, 0, nullptr, grid_for(L, P.total_items), L.st));
+    check_kernel_status(L);
+    std::vector<float> a(slots * no), b(slots * no);
+    std::vector<long long> ia(slots), ib(slots);
+    CU(cudaMemcpy(a.data(), d16, sizeof(float) * slots * no, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(b.data(), d32, sizeof(float) * slots * no, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(ia.data(), di16, sizeof(long long) * slots, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(ib.data(), di32, sizeof(long long) * slots, cudaMemcpyDeviceToHost));
+    long long cnt = 0;
+    double mx[APEX_MAX_OUTPUTS] = {0};
+    for (long long i = 0; i < slots; ++i) {
+      if (ia[i] < 0 || ia[i] != ib[i]) continue;
+      ++cnt;
+      for (int p = 0; p < no; ++p) mx[p] = std::max(mx[p], std::fabs((double)a[i * no + p] - (double)b[i * no + p]));
+    }
+    for (int p = 0; p < no; ++p) L.err16[p] = 4.0 * mx[p] + 1e-3 * L.rms[p] + L.err32[p];
+    L.n_calib += (int)cnt;
+  }
+  L.d_err32f = (float *)L.dalloc(sizeof(float) * APEX_MAX_OUTPUTS);
+  float e32[APEX_MAX_OUTPUTS] = {0};
+  for (int p = 0; p < no; ++p) e32[p] = (float)L.err32[p];
+  CU(cudaMemcpy(L.d_err32f, e32, sizeof(e32), cudaMemcpyHostToDevice));
+}
+
+// ------------------------------------------------------------------ load
+static void worker_main(apex_library *L);
+
+extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_library **out) {
+  if (!out) return fail(APEX_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!D) return fail(APEX_EINVAL, "desc is NULL");
+  if (D->n_reactions < 1 || !D->n_slots || !D->slot_sizes) return fail(APEX_EINVAL, "no reactions");
+  if (D->d < 1 || D->d > 1024) return fail(APEX_EINVAL, "d = %d outside 1..1024", D->d);
+  if (!D->U) return fail(APEX_EINVAL, "U is NULL");
+  if (D->n_layers < 1 || D->n_layers > 7 || !D->dims || !D->W || !D->b)
+    return fail(APEX_EINVAL, "n_layers must be 1..7 with dims, W and b");
+  if (D->dims[0] != D->d) return fail(APEX_EINVAL, "dims[0] (%d) != d (%d)", D->dims[0], D->d);
+  for (int l = 1; l <= D->n_layers; ++l) {
+    const int lim = (l == D->n_layers) ? APEX_MAX_OUTPUTS : 256;
+    if (D->dims[l] < 1 || D->dims[l] > lim) return fail(APEX_EINVAL, "dims[%d] = %d outside 1..%d", l, D->dims[l], lim);
+  }
+  for (int l = 0; l < D->n_layers; ++l)
+    if (!D->W[l] || !D->b[l]) return fail(APEX_EINVAL, "W[%d] or b[%d] is NULL", l, l);
+  if (D->activation < 0 || D->activation > 2) return fail(APEX_EINVAL, "unknown activation %d", D->activation);
+  if (D->n_objectives < 1 || D->n_objectives > APEX_MAX_OBJECTIVES || D->n_properties < 0 ||
+      D->n_objectives + D->n_properties != D->dims[D->n_layers])
+    return fail(APEX_EINVAL, "n_objectives + n_properties must equal the output width");
+  int64_t N = 0;
+  apex_status s = apex_count_compounds(D->n_reactions, D->n_slots, D->slot_sizes, &N);
+  if (s != APEX_OK) return s;
+  if (N >= (1LL << 62)) return fail(APEX_EINVAL, "library too large (ids must stay below 2^62)");
+  for (int t = 0; t < D->n_reactions; ++t)
+    if (D->n_slots[t] > APEX_MAX_SLOTS) return fail(APEX_EUNSUPPORTED, "reaction %d has more than %d slots", t, APEX_MAX_SLOTS);
+  const bool want_bf16 = (D->precisions >> APEX_BF16) & 1u;
+  const bool tc_shape = D->n_layers == 3 && D->dims[1] == 256 && D->dims[2] == 256 && D->dims[3] <= 16;
+  if (want_bf16 && !tc_shape)
+    return fail(APEX_EUNSUPPORTED, "the BF16 tensor-core path needs a d -> 256 -> 256 -> <=16 head");
+
+  std::unique_ptr<apex_library> L(new apex_library());
+  L->T = D->n_reactions;
+  L->d = D->d;
+  L->n_layers = D->n_layers;
+  for (int l = 0; l <= D->n_layers; ++l) L->dims[l] = D->dims[l];
+  L->act = D->activation;
+  L->n_obj = D->n_objectives;
+  L->n_prop = D->n_properties;
+  L->n_out = D->dims[D->n_layers];
+  L->N = N;
+  L->n_slots.assign(D->n_slots, D->n_slots + L->T);
+  L->slot_first.assign(L->T + 1, 0);
+  for (int t = 0; t < L->T; ++t) L->slot_first[t + 1] = L->slot_first[t] + L->n_slots[t];
+  const long long S = L->slot_first[L->T];
+  L->slot_sizes.assign(D->slot_sizes, D->slot_sizes + S);
+  L->row_first.assign(S + 1, 0);
+  for (long long j = 0; j < S; ++j) L->row_first[j + 1] = L->row_first[j] + L->slot_sizes[j];
+  L->rows = L->row_first[S];
+  L->id_first.assign(L->T + 1, 0);
+  for (int t = 0; t < L->T; ++t) {
+    long long n = 1;
+    for (long long j = L->slot_first[t]; j < L->slot_first[t + 1]; ++j) n *= L->slot_sizes[j];
+    L->id_first[t + 1] = L->id_first[t] + n;
+    L->max_slots = std::max(L->max_slots, L->n_slots[t]);
+  }
+  L->budget = D->device_mem_budget;
+  L->device = D->device;
+  L->seed = D->seed;
+  L->tc_ok = want_bf16;
+  L->precisions = 1u | (want_bf16 ? (1u << APEX_BF16) : 0u);
+  L->rng.seed(D->seed + 17);
+
+  try {
+    CU(cudaSetDevice(L->device));
+    cudaDeviceProp prop;
+    CU(cudaGetDeviceProperties(&prop, L->device));
+    L->n_sm = prop.multiProcessorCount;
+    if (D->cuda_stream) {
+      L->st = (cudaStream_t)D->cuda_stream;
+    } else {
+      CU(cudaStreamCreateWithFlags(&L->st, cudaStreamNonBlocking));
+      L->own_stream = true;
+    }
+    const int d = L->d, h1 = L->dims[1];
+    // U (kept for the FP64 plain rescore)
+    float *dU = (float *)L->dalloc(sizeof(float) * L->rows * d);
+    CU(cudaMemcpyAsync(dU, D->U, sizeof(float) * L->rows * d,
+                       D->U_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, L->st));
+    L->T_.U = dU;
+    L->T_.d = d;
+    L->T_.n_layers = L->n_layers;
+    for (int l = 0; l <= L->n_layers; ++l) L->T_.dims[l] = L->dims[l];
+    L->T_.act = L->act;
+    L->T_.n_out = L->n_out;
+    L->T_.n_rx = L->T;
+    L->T_.n_rows = L->rows;
+    // head: FP32 copies (transposed for layers >= 1) and FP64 transposed copies of every layer
+    for (int l = 0; l < L->n_layers; ++l) {
+      const int K = L->dims[l], Nn = L->dims[l + 1];
+      std::vector<float> wt((size_t)K * Nn);
+      std::vector<double> wt64((size_t)K * Nn), b64(Nn);
+      for (int n = 0; n < Nn; ++n) {
+        b64[n] = D->b[l][n];
+        for (int k = 0; k < K; ++k) {
+          wt[(size_t)k * Nn + n] = D->W[l][(size_t)n * K + k];
+          wt64[(size_t)k * Nn + n] = D->W[l][(size_t)n * K + k];
+        }
+      }
+      double *dw64 = (double *)L->dalloc(sizeof(double) * K * Nn);
+      double *db64 = (double *)L->dalloc(sizeof(double) * Nn);
+      CU(cudaMemcpy(dw64, wt64.data(), sizeof(double) * K * Nn, cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(db64, b64.data(), sizeof(double) * Nn, cudaMemcpyHostToDevice));
+      L->T_.WT64[l] = dw64;
+      L->T_.B64[l] = db64;
+      if (l >= 1) {
+        float *dw = (float *)L->dalloc(sizeof(float) * K * Nn);
+        float *db = (float *)L->dalloc(sizeof(float) * Nn);
+        CU(cudaMemcpy(dw, wt.data(), sizeof(float) * K * Nn, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(db, D->b[l], sizeof(float) * Nn, cudaMemcpyHostToDevice));
+        L->T_.WT[l] = dw;
+        L->T_.B[l] = db;
+      }
+    }
+    // P32 = W_1 u + b_1 on slot-1 rows
+    {
+      float *dW1 = (float *)L->dalloc(sizeof(float) * h1 * d, false);
+      float *db1 = (float *)L->dalloc(sizeof(float) * h1, false);
+      CU(cudaMemcpy(dW1, D->W[0], sizeof(float) * h1 * d, cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(db1, D->b[0], sizeof(float) * h1, cudaMemcpyHostToDevice));
+      std::vector<unsigned char> brow(L->rows, 0);
+      for (int t = 0; t < L->T; ++t) {
+        const long long j0 = L->slot_first[t];
+        for (long long r = L->row_first[j0]; r < L->row_first[j0 + 1]; ++r) brow[r] = 1;
+      }
+      unsigned char *dbrow = (unsigned char *)L->dalloc(L->rows, false);
+      CU(cudaMemcpy(dbrow, brow.data(), L->rows, cudaMemcpyHostToDevice));
+      float *P32 = (float *)L->dalloc(sizeof(float) * L->rows * h1);
+      CU(apx_launch_prep(dU, dW1, db1, dbrow, L->rows, d, h1, P32, L->st));
+      L->T_.P32 = P32;
+      if (L->tc_ok) {
+        const float scale = (L->act == APEX_ACT_SILU) ? 0.5f : 1.0f;
+        void *P16 = L->dalloc(sizeof(unsigned short) * L->rows * 256);
+        CU(apx_launch_p16(P32, L->rows * 256, scale, P16, L->st));
+        L->T_.P16 = (const unsigned short *)P16;
+        // W_2 (scaled into the activation's input space), W_3 padded to 16 rows
+        std::vector<float> w2((size_t)256 * 256), w3((size_t)16 * 256, 0.f);
+        for (size_t i = 0; i < w2.size(); ++i) w2[i] = scale * D->W[1][i];
+        for (int n = 0; n < L->n_out; ++n)
+          for (int k = 0; k < 256; ++k) w3[(size_t)n * 256 + k] = D->W[2][(size_t)n * 256 + k];
+        std::vector<unsigned char> img2(256 * 256 * 2), img3(16 * 256 * 2);
+        apx_make_sw128_image(w2.data(), 256, 256, img2.data());
+        apx_make_sw128_image(w3.data(), L->n_out, 16, img3.data());
+        unsigned char *d2 = (unsigned char *)L->dalloc(img2.size());
+        unsigned char *d3 = (unsigned char *)L->dalloc(img3.size());
+        CU(cudaMemcpy(d2, img2.data(), img2.size(), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d3, img3.data(), img3.size(), cudaMemcpyHostToDevice));
+        std::vector<float> b2s(256), b3(16, 0.f);
+        for (int n = 0; n < 256; ++n) b2s[n] = scale * D->b[1][n];
+        for (int n = 0; n < L->n_out; ++n) b3[n] = D->b[2][n];
+        float *db2 = (float *)L->dalloc(sizeof(float) * 256);
+        float *db3 = (float *)L->dalloc(sizeof(float) * 16);
+        CU(cudaMemcpy(db2, b2s.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(db3, b3.data(), sizeof(float) * 16, cudaMemcpyHostToDevice));
+        L->T_.w2img = d2;
+        L->T_.w3img = d3;
+        L->T_.b2s = db2;
+        L->T_.b3 = db3;
+      }
+    }
+    // work plans: outer runs sized for ~32 tiles per item, fewer when the library is small
+    {
+      long long tiles_total = 0;
+      for (int t = 0; t < L->T; ++t) {
+        RxnPlan p = plan_reaction(*L, t, 1);
+        tiles_total += (long long)p.n_b * p.n_outer;
+      }
+      const long long per_item = std::max<long long>(1, std::min<long long>(32, tiles_total / (L->n_sm * 16LL)));
+      L->rx.resize(L->T);
+      L->item_first.assign(L->T + 1, 0);
+      for (int t = 0; t < L->T; ++t) {
+        L->rx[t] = plan_reaction(*L, t, per_item);
+        L->item_first[t + 1] = L->item_first[t] + L->rx[t].n_items;
+      }
+      L->total_items = L->item_first[L->T];
+      L->T_ = upload_plans(*L);
+    }
+    L->d_slots = (QuerySlot *)L->dalloc(sizeof(QuerySlot) * APEX_MAX_ACTIVE);
+    CU(cudaMemset(L->d_slots, 0, sizeof(QuerySlot) * APEX_MAX_ACTIVE));
+    L->d_err = (int *)L->dalloc(sizeof(int));
+    CU(cudaMemset(L->d_err, 0, sizeof(int)));
+    L->d_slot_list = (int *)L->dalloc(sizeof(int) * APEX_MAX_ACTIVE);
+    CU(cudaStreamSynchronize(L->st));
+    calibrate(*L);
+    CU(cudaStreamSynchronize(L->st));
+  } catch (const CudaFail &f) {
+    apex_status code = (f.e == cudaErrorMemoryAllocation) ? APEX_ENOMEM : APEX_ECUDA;
+    if (f.e == cudaErrorLaunchTimeout) code = APEX_ETIMEDOUT;
+    L->release_all();
+    if (L->own_stream) cudaStreamDestroy(L->st);
+    return fail(code, "load: %s failed: %s (line %d)", f.what, cudaGetErrorString(f.e), f.line);
+  } catch (const BudgetFail &) {
+    L->release_all();
+    if (L->own_stream) cudaStreamDestroy(L->st);
+    return fail(APEX_ENOMEM, "load: library tables exceed device_mem_budget");
+  }
+  apex_library *lib = L.release();
+  lib->worker = std::thread(worker_main, lib);
+  *out = lib;
+  return APEX_OK;
+}
+
+extern "C" apex_status apex_free_library(apex_library *L) {
+  if (!L) return APEX_OK;
+  {
+    std::lock_guard<std::mutex> g(L->mu);
+    L->stop = true;
+  }
+  L->cv.notify_all();
+  if (L->worker.joinable()) L->worker.join();
+  cudaSetDevice(L->device);
+  cudaStreamSynchronize(L->st);
+  for (auto &kv : L->queries) {
+    QueryRec *q = kv.second.get();
+    if (q->ev0) cudaEventDestroy(q->ev0);
+    if (q->ev1) cudaEventDestroy(q->ev1);
+    if (q->keys) cudaFree(q->keys);
+    if (q->ids) cudaFree(q->ids);
+    if (q->keys2) cudaFree(q->keys2);
+    if (q->ids2) cudaFree(q->ids2);
+  }
+  L->release_all();
+  if (L->own_stream) cudaStreamDestroy(L->st);
+  delete L;
+  return APEX_OK;
+}
+
+extern "C" apex_status apex_library_info(const apex_library *L, apex_library_info_t *o) {
+  if (!L || !o) return fail(APEX_EINVAL, "NULL argument");
+  memset(o, 0, sizeof(*o));
+  o->n_compounds = L->N;
+  o->n_synthon_rows = L->rows;
+  o->max_slots = L->max_slots;
+  o->n_outputs = L->n_out;
+  o->device_bytes = L->bytes;
+  o->precisions = L->precisions;
+  o->n_calibration = L->n_calib;
+  for (int p = 0; p < L->n_out; ++p) {
+    o->err_bf16[p] = L->err16[p];
+    o->err_fp32[p] = L->err32[p];
+    o->rms[p] = L->rms[p];
+  }
+  return APEX_OK;
+}
+
+extern "C" apex_status apex_decode_ids(const apex_library *L, int64_t n, const int64_t *ids, int32_t *reaction,
+                                       int64_t *synthons) {
+  if (!L || n < 0 || (n > 0 && !ids)) return fail(APEX_EINVAL, "bad arguments");
+  for (int64_t i = 0; i < n; ++i) {
+    const long long id = ids[i];
+    if (id < 0 || id >= L->N) return fail(APEX_EINVAL, "id %lld outside [0, %lld)", id, L->N);
+    const int t = (int)(std::upper_bound(L->id_first.begin(), L->id_first.end(), id) - L->id_first.begin()) - 1;
+    long long rem = id - L->id_first[t];
+    long long s[APEX_MAX_SLOTS];
+    for (int j = APEX_MAX_SLOTS - 1; j >= 0; --j) {
+      if (j < L->n_slots[t]) {
+        const long long sz = L->slot_sizes[L->slot_first[t] + j];
+        s[j] = rem % sz;
+        rem /= sz;
+      } else {
+        s[j] = -1;
+      }
+    }
+    if (reaction) reaction[i] = t;
+    if (synthons)
+      for (int j = 0; j < APEX_MAX_SLOTS; ++j) synthons[i * APEX_MAX_SLOTS + j] = s[j];
+  }
+  return APEX_OK;
+}
+
+// ------------------------------------------------------------------ query submission
+extern "C" apex_status apex_query(apex_library *L, const apex_query_desc *Dq, apex_query_id *out) {
+  if (!L || !Dq || !out) return fail(APEX_EINVAL, "NULL argument");
+  if (Dq->precision != APEX_FP32 && Dq->precision != APEX_BF16)
+    return fail(APEX_EINVAL, "unknown precision %d", Dq->precision);
+  if (!((L->precisions >> Dq->precision) & 1u))
+    return fail(APEX_EUNSUPPORTED, "precision %d tables were not built at load", Dq->precision);
+  if (!Dq->objective_weights) return fail(APEX_EINVAL, "objective_weights is NULL");
+  if (Dq->k < 1) return fail(APEX_EINVAL, "k must be >= 1");
+  if (Dq->k > (1LL << 24)) return fail(APEX_EINVAL, "k must be <= 2^24");
+  if (Dq->n_constraints < 0 || Dq->n_constraints > APEX_MAX_CONSTRAINTS)
+    return fail(APEX_EINVAL, "n_constraints outside 0..%d", APEX_MAX_CONSTRAINTS);
+  if (Dq->n_constraints > 0 && (!Dq->output_index || !Dq->lower || !Dq->upper))
+    return fail(APEX_EINVAL, "constraint arrays are NULL");
+  std::unique_ptr<QueryRec> q(new QueryRec());
+  q->precision = Dq->precision;
+  q->w.assign(Dq->objective_weights, Dq->objective_weights + L->n_obj);
+  for (float x : q->w)
+    if (!std::isfinite(x)) return fail(APEX_EINVAL, "objective weight is not finite");
+  for (int i = 0; i < Dq->n_constraints; ++i) {
+    if (Dq->output_index[i] < 0 || Dq->output_index[i] >= L->n_out)
+      return fail(APEX_EINVAL, "constraint %d: output index %d outside 0..%d", i, Dq->output_index[i], L->n_out - 1);
+    if (std::isnan(Dq->lower[i]) || std::isnan(Dq->upper[i]))
+      return fail(APEX_EINVAL, "constraint %d: NaN bound", i);
+    if (Dq->lower[i] > Dq->upper[i]) return fail(APEX_EINVAL, "constraint %d: lower > upper", i);
+    q->cidx.push_back(Dq->output_index[i]);
+    q->lo.push_back(Dq->lower[i]);
+    q->hi.push_back(Dq->upper[i]);
+  }
+  q->k = Dq->k;
+  q->need.assign(L->T, 0);
+  if (Dq->n_reaction_subset > 0) {
+    if (!Dq->reactions) return fail(APEX_EINVAL, "reactions is NULL");
+    for (int i = 0; i < Dq->n_reaction_subset; ++i) {
+      const int t = Dq->reactions[i];
+      if (t < 0 || t >= L->T) return fail(APEX_EINVAL, "reaction %d outside 0..%d", t, L->T - 1);
+      if (q->need[t]) return fail(APEX_EINVAL, "reaction %d listed twice", t);
+      q->need[t] = 1;
+    }
+  } else if (Dq->n_reaction_subset < 0) {
+    return fail(APEX_EINVAL, "negative n_reaction_subset");
+  } else {
+    std::fill(q->need.begin(), q->need.end(), 1);
+  }
+  for (int t = 0; t < L->T; ++t)
+    if (q->need[t]) {
+      q->subset.push_back(t);
+      q->scope_items += L->rx[t].n_items;
+      q->scope_n += L->id_first[t + 1] - L->id_first[t];
+    }
+  q->remaining = q->scope_items;
+  q->t_submit = now_ms();
+  q->id = L->next_id++;
+  const apex_query_id id = q->id;
+  {
+    std::lock_guard<std::mutex> g(L->mu);
+    if (L->stop) return fail(APEX_ECANCELED, "library is shutting down");
+    L->queued.push_back(q.get());
+    L->queries[id] = std::move(q);
+  }
+  L->cv.notify_all();
+  *out = id;
+  return APEX_OK;
+}
+
+extern "C" apex_status apex_cancel(apex_library *L, apex_query_id id) {
+  if (!L) return fail(APEX_EINVAL, "NULL library");
+  std::lock_guard<std::mutex> g(L->mu);
+  auto it = L->queries.find(id);
+  if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found", (long long)id);
+  it->second->cancel = true;
+  L->cv.notify_all();
+  return APEX_OK;
+}
+
+// ------------------------------------------------------------------ worker: admission
+static size_t query_bytes_for(unsigned cap) { return (size_t)cap * (4 + 8) * 2; }
+
+static void free_query_device(apex_library &L, QueryRec *q) {
+  if (q->keys) cudaFree(q->keys);
+  if (q->ids) cudaFree(q->ids);
+  if (q->keys2) cudaFree(q->keys2);
+  if (q->ids2) cudaFree(q->ids2);
+  q->keys = q->keys2 = nullptr;
+  q->ids = q->ids2 = nullptr;
+  L.query_bytes -= q->dev_bytes;
+  q->dev_bytes = 0;
+}
+
+// Writes the query's slot parameters (boxes widened / shrunk by the pass margin).
+static void write_slot(apex_library &L, QueryRec *q, float admit) {
+  QuerySlot S;
+  memset(&S, 0, sizeof(S));
+  const double *err = (q->precision == APEX_BF16) ? L.err16 : L.err32;
+  for (int j = 0; j < L.n_obj; ++j) S.w[j] = q->w[j];
+  S.n_obj = L.n_obj;
+  S.n_cons = (int)q->cidx.size();
+  double df = 0;
+  for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
+  for (int c = 0; c < S.n_cons; ++c) {
+    const int p = q->cidx[c];
+    S.cons_idx[c] = p;
+    S.lo_w[c] = (float)(q->lo[c] - err[p]);
+    S.hi_w[c] = (float)(q->hi[c] + err[p]);
+    S.lo_s[c] = (float)(q->lo[c] + err[p]);
+    S.hi_s[c] = (float)(q->hi[c] - err[p]);
+  }
+  S.delta_f = (float)(df * 1.0001 + 1e-12);
+  S.admit = admit;
+  S.tau = -INFINITY;
+  S.tau_spec = q->tau_spec;
+  S.k = q->k;
+  S.cap = q->cap;
+  S.keys = q->keys;
+  S.ids = q->ids;
+  S.keys2 = q->keys2;
+  S.ids2 = q->ids2;
+  CU(cudaMemcpyAsync(L.d_slots + q->slot, &S, sizeof(S), cudaMemcpyHostToDevice, L.st));
+}
+
+// Start threshold guess: the rank-r best objective among surely feasible compounds of a seeded
+// FP32 sample of the query's scope, r chosen so that ~3k scope compounds are expected above it.
+// Only a guess: finalization verifies it (>= k sure entries at or above it) or restarts lower.
+static float speculative_start(apex_library &L, QueryRec *q) {
+  if (q->spec_rank < 0) return -INFINITY;
+  const long long S = std::min<long long>(16384, q->scope_n);
+  const double expect = (double)S * (double)q->k / (double)q->scope_n;
+  long long r = q->spec_rank > 0 ? q->spec_rank : (long long)std::ceil(3.0 * expect + 5.0);
+  q->spec_rank = (int)std::min<long long>(r, 1 << 30);
+  if (r >= S) {
+    q->spec_rank = -1;
+    return -INFINITY;
+  }
+  std::vector<long long> ids(S);
+  for (long long i = 0; i < S; ++i) {
+    long long u = (long long)(L.rng() % (unsigned long long)q->scope_n);
+    for (int t : q->subset) {
+      const long long nt = L.id_first[t + 1] - L.id_first[t];
+      if (u < nt) {
+        ids[i] = L.id_first[t] + u;
+        break;
+      }
+      u -= nt;
+    }
+  }
+  const int no = L.n_out;
+  long long *d_ids = nullptr;
+  float *d_out = nullptr;
+  CU(cudaMalloc(&d_ids, sizeof(long long) * S));
+  CU(cudaMalloc(&d_out, sizeof(float) * S * no));
+  CU(cudaMemcpyAsync(d_ids, ids.data(), sizeof(long long) * S, cudaMemcpyHostToDevice, L.st));
+  LaunchPlan dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  CU(apx_launch_fp32(dummy, L.T_, nullptr, d_ids, S, d_out, grid_for(L, (S + APX_TILE - 1) / APX_TILE), L.st));
+  std::vector<float> o(S * no);
+  CU(cudaMemcpyAsync(o.data(), d_out, sizeof(float) * S * no, cudaMemcpyDeviceToHost, L.st));
+  CU(cudaStreamSynchronize(L.st));
+  cudaFree(d_ids);
+  cudaFree(d_out);
+  std::vector<float> f;
+  f.reserve(S);
+  for (long long i = 0; i < S; ++i) {
+    bool ok = true;
+    for (size_t c = 0; c < q->cidx.size(); ++c) {
+      const double v = o[i * no + q->cidx[c]];
+      if (!(v >= q->lo[c] && v <= q->hi[c])) ok = false;
+    }
+    if (!ok) continue;
+    double s = 0;
+    for (int j = 0; j < L.n_obj; ++j) s += (double)q->w[j] * o[i * no + j];
+    f.push_back((float)s);
+  }
+  if ((long long)f.size() < r) return -INFINITY;
+  std::nth_element(f.begin(), f.begin() + (r - 1), f.end(), std::greater<float>());
+  return f[r - 1];
+}
+
+static void start_query(apex_library &L, QueryRec *q) {
+  const double *err = (q->precision == APEX_BF16) ? L.err16 : L.err32;
+  double df = 0;
+  for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
+  q->tau_spec = speculative_start(L, q);
+  const float admit = std::isfinite(q->tau_spec) ? (float)(q->tau_spec - 2.0 * df * 1.0001) : -INFINITY;
+  write_slot(L, q, admit);
+  q->remaining = q->scope_items;
+  q->started = true;
+}
+
+static bool admit_one(apex_library &L, QueryRec *q) {
+  int slot = -1;
+  for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+    if (!L.active[s]) {
+      slot = s;
+      break;
+    }
+  if (slot < 0) return false;
+  if (q->cap == 0) q->cap = (unsigned)std::min<long long>(std::max<long long>(1LL << 18, 8 * q->k), 1LL << 30);
+  const size_t need = query_bytes_for(q->cap);
+  if (L.budget && L.bytes + L.query_bytes + need > L.budget) return false;
+  CU(cudaMalloc(&q->keys, sizeof(float) * q->cap));
+  CU(cudaMalloc(&q->keys2, sizeof(float) * q->cap));
+  CU(cudaMalloc(&q->ids, sizeof(long long) * q->cap));
+  CU(cudaMalloc(&q->ids2, sizeof(long long) * q->cap));
+  q->dev_bytes = need;
+  L.query_bytes += need;
+  q->slot = slot;
+  L.active[slot] = q;
+  q->state = Q_ACTIVE;
+  q->t_admit = now_ms();
+  if (!q->ev0) {
+    CU(cudaEventCreate(&q->ev0));
+    CU(cudaEventCreate(&q->ev1));
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ worker: finalization
+struct DevBuf {
+  std::vector<void *> p;
+  void *get(size_t n) {
+    void *x = nullptr;
+    CU(cudaMalloc(&x, n ? n : 16));
+    p.push_back(x);
+    return x;
+  }
+  ~DevBuf() {
+    for (void *x : p) cudaFree(x);
+  }
+};
+
+// returns false when the query must restart (start guess too high or candidate overflow)
+static bool finalize(apex_library &L, QueryRec *q) {
+  const int no = L.n_out;
+  const int sl = q->slot;
+  CU(cudaMemcpyAsync(L.d_slot_list, &sl, sizeof(int), cudaMemcpyHostToDevice, L.st));
+  CU(apx_launch_slot_select(L.d_slots, L.d_slot_list, 1, 1, L.st));
+  QuerySlot S;
+  CU(cudaMemcpyAsync(&S, L.d_slots + sl, sizeof(S), cudaMemcpyDeviceToHost, L.st));
+  CU(cudaStreamSynchronize(L.st));
+  const bool spec_bad = std::isfinite(q->tau_spec) && (long long)S.n_sure_above_spec < q->k;
+  if (S.overflow || spec_bad) {
+    q->stats.n_restarts++;
+    if (S.overflow && !spec_bad && std::isfinite(S.tau)) {
+      q->tau_spec = S.tau;  // a valid lower bound: k real, surely feasible compounds reach it
+    } else if (S.overflow) {
+      free_query_device(L, q);
+      q->cap = (unsigned)std::min<unsigned long long>((unsigned long long)q->cap * 4ull, 1ull << 30);
+      q->dev_bytes = query_bytes_for(q->cap);
+      CU(cudaMalloc(&q->keys, sizeof(float) * q->cap));
+      CU(cudaMalloc(&q->keys2, sizeof(float) * q->cap));
+      CU(cudaMalloc(&q->ids, sizeof(long long) * q->cap));
+      CU(cudaMalloc(&q->ids2, sizeof(long long) * q->cap));
+      L.query_bytes += q->dev_bytes;
+      q->tau_spec = -INFINITY;
+      q->spec_rank = -1;
+    } else {
+      q->spec_rank = q->spec_rank > 0 ? q->spec_rank * 8 : -1;  // lower the guess
+      q->tau_spec = -INFINITY;
+    }
+    if (std::isfinite(q->tau_spec)) {
+      const double *err = (q->precision == APEX_BF16) ? L.err16 : L.err32;
+      double df = 0;
+      for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
+      write_slot(L, q, (float)(q->tau_spec - 2.0 * df * 1.0001));
+    } else {
+      const float tspec = q->spec_rank > 0 ? speculative_start(L, q) : -INFINITY;
+      q->tau_spec = tspec;
+      const double *err = (q->precision == APEX_BF16) ? L.err16 : L.err32;
+      double df = 0;
+      for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
+      write_slot(L, q, std::isfinite(tspec) ? (float)(tspec - 2.0 * df * 1.0001) : -INFINITY);
+    }
+    q->remaining = q->scope_items;
+    return false;
+  }
+  DevBuf B;
+  const long long nc = S.count;
+  q->stats.n_candidates = nc;
+  const long long k = q->k;
+  // FP32 rescore of the candidates
+  float *out32 = (float *)B.get(sizeof(float) * std::max<long long>(nc, 1) * no);
+  if (nc > 0) {
+    LaunchPlan dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    CU(apx_launch_fp32(dummy, L.T_, nullptr, q->ids, nc, out32, grid_for(L, (nc + APX_TILE - 1) / APX_TILE), L.st));
+  }
+  float *f32 = (float *)B.get(sizeof(float) * std::max<long long>(nc, 1));
+  unsigned char *maybe = (unsigned char *)B.get(std::max<long long>(nc, 1));
+  unsigned char *sure = (unsigned char *)B.get(std::max<long long>(nc, 1));
+  const int m = (int)q->cidx.size();
+  double *dlo = (double *)B.get(sizeof(double) * std::max(m, 1));
+  double *dhi = (double *)B.get(sizeof(double) * std::max(m, 1));
+  if (m > 0) {
+    CU(cudaMemcpyAsync(dlo, q->lo.data(), sizeof(double) * m, cudaMemcpyHostToDevice, L.st));
+    CU(cudaMemcpyAsync(dhi, q->hi.data(), sizeof(double) * m, cudaMemcpyHostToDevice, L.st));
+  }
+  double e32f = 0;
+  for (int j = 0; j < L.n_obj; ++j) e32f += std::fabs((double)q->w[j]) * L.err32[j];
+  EvalArgs ea{out32, no, L.d_slots + sl, L.d_err32f, (float)e32f, dlo, dhi};
+  CU(apx_launch_eval32(ea, nc, f32, maybe, sure, L.st));
+  float *d_tau = (float *)B.get(sizeof(float));
+  int *d_ok = (int *)B.get(sizeof(int));
+  CU(apx_launch_kth(f32, sure, nc, k, d_tau, d_ok, L.st));
+  float tau32;
+  CU(cudaMemcpyAsync(&tau32, d_tau, sizeof(float), cudaMemcpyDeviceToHost, L.st));
+  CU(cudaStreamSynchronize(L.st));
+  const float thr = std::isfinite(tau32) ? (float)(tau32 - 2.0 * e32f * 1.0001) : -INFINITY;
+  unsigned n_pow2 = 1;
+  while (n_pow2 < (unsigned)std::max<long long>(nc, 1)) n_pow2 <<= 1;
+  n_pow2 = std::max(n_pow2, 2u);
+  RItem *R = (RItem *)B.get(sizeof(RItem) * n_pow2);
+  unsigned *d_cnt = (unsigned *)B.get(sizeof(unsigned) * 4);
+  CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned) * 4, L.st));
+  CU(apx_launch_build_r(nc, q->ids, f32, maybe, sure, thr, R, d_cnt, L.st));
+  unsigned nr = 0;
+  CU(cudaMemcpyAsync(&nr, d_cnt, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
+  CU(cudaStreamSynchronize(L.st));
+  unsigned np = 1;
+  while (np < std::max(nr, 2u)) np <<= 1;
+  double *out64 = (double *)B.get(sizeof(double) * std::max<long long>(nc, 1) * no);
+  long long *ids64 = (long long *)B.get(sizeof(long long) * std::max(nr, 1u));
+  int *pos64 = (int *)B.get(sizeof(int) * std::max(nr, 1u));
+  double *o64 = (double *)B.get(sizeof(double) * std::max(nr, 1u) * no);
+  const double tol = 2.0 * e32f * 1.0001 + 1e-300;
+  long long n64_total = 0;
+  for (int round = 0; round < 8 && nr > 0; ++round) {
+    CU(cudaMemsetAsync(d_cnt + 1, 0, sizeof(unsigned) * 2, L.st));
+    CU(apx_launch_collect64(R, nr, ids64, pos64, d_cnt + 1, L.st));
+    unsigned n64 = 0;
+    CU(cudaMemcpyAsync(&n64, d_cnt + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
+    CU(cudaStreamSynchronize(L.st));
+    if (n64 > 0) {
+      CU(apx_launch_fp64(L.T_, ids64, n64, o64, L.st));
+      CU(apx_launch_apply64(R, pos64, o64, n64, no, L.d_slots + sl, dlo, dhi, out64, L.st));
+      n64_total += n64;
+    }
+    CU(apx_sort_r(R, nr, np, L.st));
+    CU(apx_launch_mark(R, nr, (unsigned)std::min<long long>(k + 1, nr), k, tol, d_cnt + 2, L.st));
+    unsigned marked = 0;
+    CU(cudaMemcpyAsync(&marked, d_cnt + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
+    CU(cudaStreamSynchronize(L.st));
+    if (marked == 0) break;
+  }
+  q->stats.n_rescored_fp64 = n64_total;
+  cudaError_t ce = cudaSuccess;
+  const int alive = nr > 0 ? apx_count_alive(R, nr, L.st, d_cnt + 3, &ce) : 0;
+  CU(ce);
+  const long long nf = std::min<long long>(k, alive);
+  q->r_ids.resize(nf);
+  q->r_rxn.resize(nf);
+  q->r_syn.resize(nf * APEX_MAX_SLOTS);
+  q->r_obj.resize(nf);
+  q->r_out.resize(nf * no);
+  if (nf > 0) {
+    long long *e_ids = (long long *)B.get(sizeof(long long) * nf);
+    int *e_rxn = (int *)B.get(sizeof(int) * nf);
+    long long *e_syn = (long long *)B.get(sizeof(long long) * nf * APEX_MAX_SLOTS);
+    double *e_obj = (double *)B.get(sizeof(double) * nf);
+    double *e_out = (double *)B.get(sizeof(double) * nf * no);
+    CU(apx_launch_emit(R, (unsigned)nf, L.T_, out32, out64, e_ids, e_rxn, e_syn, e_obj, e_out, L.st));
+    CU(cudaMemcpyAsync(q->r_ids.data(), e_ids, sizeof(long long) * nf, cudaMemcpyDeviceToHost, L.st));
+    CU(cudaMemcpyAsync(q->r_rxn.data(), e_rxn, sizeof(int) * nf, cudaMemcpyDeviceToHost, L.st));
+    CU(cudaMemcpyAsync(q->r_syn.data(), e_syn, sizeof(long long) * nf * APEX_MAX_SLOTS, cudaMemcpyDeviceToHost,
+                       L.st));
+    CU(cudaMemcpyAsync(q->r_obj.data(), e_obj, sizeof(double) * nf, cudaMemcpyDeviceToHost, L.st));
+    CU(cudaMemcpyAsync(q->r_out.data(), e_out, sizeof(double) * nf * no, cudaMemcpyDeviceToHost, L.st));
+  }
+  CU(cudaEventRecord(q->ev1, L.st));
+  CU(cudaStreamSynchronize(L.st));
+  q->stats.n_feasible_lower = nf;
+  return true;
+}
+
+// ------------------------------------------------------------------ worker: main loop
+static void finish(apex_library &L, QueryRec *q, QState st, apex_status err, const std::string &msg) {
+  if (q->slot >= 0) {
+    L.active[q->slot] = nullptr;
+    q->slot = -1;
+  }
+  free_query_device(L, q);
+  q->state = st;
+  q->err = err;
+  q->err_msg = msg;
+  q->t_done = now_ms();
+  q->stats.queue_ms = q->t_admit > 0 ? q->t_admit - q->t_submit : 0;
+  q->stats.latency_ms = q->t_done - q->t_submit;
+  q->stats.n_scope = q->scope_n;
+}
+
+// One step of the circular pass: a launch over the next chunk of items needed by any active
+// query (per precision), then the conditional select of the served queries.
+static void pass_step(apex_library &L) {
+  const long long chunk_compounds = 1LL << 25;
+  // build one plan (items from the cursor) with per-precision query masks
+  PlanBuilder pb[2];
+  long long served_compounds = 0;
+  long long cur = L.cursor;
+  long long visited = 0;
+  std::vector<long long> served(APEX_MAX_ACTIVE, 0);
+  while (visited < L.total_items && served_compounds < chunk_compounds) {
+    const int t = (int)(std::upper_bound(L.item_first.begin(), L.item_first.end(), cur) - L.item_first.begin()) - 1;
+    const long long b = cur - L.item_first[t];
+    const long long e = L.rx[t].n_items;
+    unsigned long long mask[2] = {0, 0};
+    for (int s = 0; s < APEX_MAX_ACTIVE; ++s) {
+      QueryRec *q = L.active[s];
+      if (q && q->remaining > 0 && q->need[t]) mask[q->precision] |= 1ull << s;
+    }
+    long long take = e - b;
+    if (mask[0] | mask[1]) {
+      const long long per_item = (long long)L.rx[t].L_o * APX_TILE;
+      const long long room = std::max<long long>(1, (chunk_compounds - served_compounds + per_item - 1) / per_item);
+      take = std::min(take, room);
+      bool ok = true;
+      for (int p = 0; p < 2; ++p)
+        if (mask[p] && pb[p].P.n_seg >= APX_MAX_SEG) ok = false;
+      if (!ok) break;
+      for (int p = 0; p < 2; ++p)
+        if (mask[p]) pb[p].add(t, b, b + take, mask[p]);
+      for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+        if ((mask[0] | mask[1]) >> s & 1ull) served[s] += take;
+      served_compounds += take * per_item;
+    }
+    visited += take;
+    cur += take;
+    if (cur >= L.total_items) cur = 0;
+  }
+  L.cursor = cur;
+  std::vector<int> list;
+  for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+    if (served[s] > 0) list.push_back(s);
+  for (int s : list) {
+    QueryRec *q = L.active[s];
+    if (q->stats.n_launches == 0 && q->stats.n_restarts == 0) CU(cudaEventRecord(q->ev0, L.st));
+  }
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, L.st));
+  for (int p = 0; p < 2; ++p) launch_enum(L, pb[p].P, p);
+  CU(cudaEventRecord(e1, L.st));
+  if (!list.empty()) {
+    CU(cudaMemcpyAsync(L.d_slot_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, L.st));
+    CU(apx_launch_slot_select(L.d_slots, L.d_slot_list, (int)list.size(), 0, L.st));
+  }
+  check_kernel_status(L);
+  float ms = 0;
+  CU(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int s : list) {
+    QueryRec *q = L.active[s];
+    q->remaining -= served[s];
+    q->stats.n_launches++;
+    q->stats.enumerate_ms += ms;
+    long long comp = 0;
+    for (int p = 0; p < 2; ++p)
+      for (int g = 0; g < pb[p].P.n_seg; ++g)
+        if (pb[p].P.seg[g].qmask >> s & 1ull) {
+          const RxnPlan &r = L.rx[pb[p].P.seg[g].rxn];
+          comp += (pb[p].P.seg[g].item_end - pb[p].P.seg[g].item_begin) * r.L_o * APX_TILE;
+        }
+    q->stats.n_scored += comp;
+  }
+}
+
+static void worker_main(apex_library *Lp) {
+  apex_library &L = *Lp;
+  cudaSetDevice(L.device);
+  for (;;) {
+    std::vector<QueryRec *> fresh;
+    {
+      std::unique_lock<std::mutex> lk(L.mu);
+      if (L.stop) break;
+      // cancellations
+      for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+        if (L.active[s] && L.active[s]->cancel) {
+          finish(L, L.active[s], Q_CANCELED, APEX_ECANCELED, "cancelled");
+          L.cv_done.notify_all();
+        }
+      for (auto it = L.queued.begin(); it != L.queued.end();) {
+        if ((*it)->cancel) {
+          finish(L, *it, Q_CANCELED, APEX_ECANCELED, "cancelled");
+          it = L.queued.erase(it);
+          L.cv_done.notify_all();
+        } else {
+          ++it;
+        }
+      }
+      // admission (FIFO while slots and memory allow)
+      try {
+        while (!L.queued.empty()) {
+          QueryRec *q = L.queued.front();
+          if (!admit_one(L, q)) {
+            bool none_active = true;
+            for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+              if (L.active[s]) none_active = false;
+            if (none_active) {  // cannot fit even alone
+              L.queued.pop_front();
+              finish(L, q, Q_FAILED, APEX_ENOMEM, "candidate state exceeds the device memory budget");
+              L.cv_done.notify_all();
+              continue;
+            }
+            break;
+          }
+          L.queued.pop_front();
+          fresh.push_back(q);
+        }
+      } catch (const CudaFail &f) {
+        QueryRec *q = L.queued.front();
+        L.queued.pop_front();
+        finish(L, q, Q_FAILED, APEX_ENOMEM, std::string("admission: ") + cudaGetErrorString(f.e));
+        L.cv_done.notify_all();
+      }
+      bool any = false;
+      for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+        if (L.active[s]) any = true;
+      if (!any) {
+        L.cv.wait_for(lk, std::chrono::milliseconds(20));
+        continue;
+      }
+    }
+    try {
+      for (QueryRec *q : fresh) start_query(L, q);
+      pass_step(L);
+      for (int s = 0; s < APEX_MAX_ACTIVE; ++s) {
+        QueryRec *q = L.active[s];
+        if (!q || q->remaining > 0) continue;
+        if (finalize(L, q)) {
+          float ms = 0;
+          if (cudaEventElapsedTime(&ms, q->ev0, q->ev1) == cudaSuccess) q->stats.gpu_ms = ms;
+          std::lock_guard<std::mutex> g(L.mu);
+          finish(L, q, Q_DONE, APEX_OK, "");
+          L.cv_done.notify_all();
+        }
+      }
+    } catch (const CudaFail &f) {
+      std::lock_guard<std::mutex> g(L.mu);
+      const apex_status code = (f.e == cudaErrorLaunchTimeout) ? APEX_ETIMEDOUT : APEX_ECUDA;
+      char buf[256];
+      snprintf(buf, sizeof(buf), "%s failed: %s (line %d)", f.what, cudaGetErrorString(f.e), f.line);
+      for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+        if (L.active[s]) finish(L, L.active[s], Q_FAILED, code, buf);
+      L.cv_done.notify_all();
+    }
+  }
+  // shutdown: everything still pending is cancelled
+  std::lock_guard<std::mutex> g(L.mu);
+  for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+    if (L.active[s]) finish(L, L.active[s], Q_CANCELED, APEX_ECANCELED, "library freed");
+  for (QueryRec *q : L.queued) finish(L, q, Q_CANCELED, APEX_ECANCELED, "library freed");
+  L.queued.clear();
+  L.cv_done.notify_all();
+}
+
+// ------------------------------------------------------------------ fetch / stats
+extern "C" apex_status apex_topk_fetch(apex_library *L, apex_query_id id, int64_t capacity, int64_t *ids,
+                                       int32_t *reaction, int64_t *synthons, double *objective, double *outputs,
+                                       int64_t *n_out, int32_t timeout_ms) {
+  if (!L) return fail(APEX_EINVAL, "NULL library");
+  if (capacity < 0) return fail(APEX_EINVAL, "negative capacity");
+  std::unique_lock<std::mutex> lk(L->mu);
+  auto it = L->queries.find(id);
+  if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found", (long long)id);
+  QueryRec *q = it->second.get();
+  auto done = [&] { return q->state == Q_DONE || q->state == Q_CANCELED || q->state == Q_FAILED; };
+  if (timeout_ms < 0)
+    L->cv_done.wait(lk, done);
+  else if (!L->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
+    return fail(APEX_EAGAIN, "query %lld not finished", (long long)id);
+  apex_status rc = q->err;
+  if (q->state == Q_DONE) {
+    const long long n = (long long)q->r_ids.size();
+    const long long c = std::min<long long>(n, capacity);
+    if (ids) memcpy(ids, q->r_ids.data(), sizeof(int64_t) * c);
+    if (reaction) memcpy(reaction, q->r_rxn.data(), sizeof(int32_t) * c);
+    if (synthons) memcpy(synthons, q->r_syn.data(), sizeof(int64_t) * c * APEX_MAX_SLOTS);
+    if (objective) memcpy(objective, q->r_obj.data(), sizeof(double) * c);
+    if (outputs) memcpy(outputs, q->r_out.data(), sizeof(double) * c * L->n_out);
+    if (n_out) *n_out = n;
+  } else {
+    if (n_out) *n_out = 0;
+    fail(rc, "query %lld: %s", (long long)id, q->err_msg.c_str());
+  }
+  if (q->ev0) cudaEventDestroy(q->ev0);
+  if (q->ev1) cudaEventDestroy(q->ev1);
+  L->last_stats = q->stats;
+  L->queries.erase(it);
+  return rc;
+}
+
+extern "C" apex_status apex_query_stats(apex_library *L, apex_query_id id, apex_query_stats_t *out) {
+  if (!L || !out) return fail(APEX_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> g(L->mu);
+  if (id < 0) {
+    *out = L->last_stats;
+    return APEX_OK;
+  }
+  auto it = L->queries.find(id);
+  if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found", (long long)id);
+  *out = it->second->stats;
+  return APEX_OK;
+}
+
+// ------------------------------------------------------------------ direct scoring (tests)
+extern "C" apex_status apex_score_ids(apex_library *L, int32_t precision, int64_t n, const int64_t *ids,
+                                      double *outputs) {
+  if (!L || n < 0 || (n > 0 && (!ids || !outputs))) return fail(APEX_EINVAL, "bad arguments");
+  if (precision != APEX_FP32 && precision != 2) return fail(APEX_EINVAL, "precision must be APEX_FP32 or 2 (FP64)");
+  for (int64_t i = 0; i < n; ++i)
+    if (ids[i] < 0 || ids[i] >= L->N) return fail(APEX_EINVAL, "id %lld out of range", (long long)ids[i]);
+  if (n == 0) return APEX_OK;
+  std::lock_guard<std::mutex> g(L->mu);  // keeps the worker from interleaving on the stream
+  const int no = L->n_out;
+  try {
+    CU(cudaSetDevice(L->device));
+    DevBuf B;
+    long long *d_ids = (long long *)B.get(sizeof(long long) * n);
+    CU(cudaMemcpyAsync(d_ids, ids, sizeof(long long) * n, cudaMemcpyHostToDevice, L->st));
+    if (precision == APEX_FP32) {
+      float *d = (float *)B.get(sizeof(float) * n * no);
+      LaunchPlan dummy;
+      memset(&dummy, 0, sizeof(dummy));
+      CU(apx_launch_fp32(dummy, L->T_, nullptr, d_ids, n, d, grid_for(*L, (n + APX_TILE - 1) / APX_TILE), L->st));
+      std::vector<float> h(n * no);
+      CU(cudaMemcpyAsync(h.data(), d, sizeof(float) * n * no, cudaMemcpyDeviceToHost, L->st));
+      CU(cudaStreamSynchronize(L->st));
+      for (long long i = 0; i < n * no; ++i) outputs[i] = h[i];
+    } else {
+      double *d = (double *)B.get(sizeof(double) * n * no);
+      CU(apx_launch_fp64(L->T_, d_ids, n, d, L->st));
+      CU(cudaMemcpyAsync(outputs, d, sizeof(double) * n * no, cudaMemcpyDeviceToHost, L->st));
+      CU(cudaStreamSynchronize(L->st));
+    }
+  } catch (const CudaFail &f) {
+    return fail(APEX_ECUDA, "score_ids: %s failed: %s", f.what, cudaGetErrorString(f.e));
+  }
+  return APEX_OK;
+}
+
+extern "C" apex_status apex_dump_outputs(apex_library *L, int32_t precision, int32_t reaction, float *outputs,
+                                         int64_t capacity) {
+  if (!L || !outputs || reaction < 0 || reaction >= L->T) return fail(APEX_EINVAL, "bad arguments");
+  if (precision != APEX_FP32 && precision != APEX_BF16) return fail(APEX_EINVAL, "unknown precision");
+  if (!((L->precisions >> precision) & 1u)) return fail(APEX_EUNSUPPORTED, "precision not built");
+  const long long nt = L->id_first[reaction + 1] - L->id_first[reaction];
+  if (capacity < nt) return fail(APEX_EINVAL, "capacity %lld < %lld compounds", (long long)capacity, nt);
+  std::lock_guard<std::mutex> g(L->mu);
+  const int no = L->n_out;
+  try {
+    CU(cudaSetDevice(L->device));
+    DevBuf B;
+    float *d = (float *)B.get(sizeof(float) * nt * no);
+    PlanBuilder pb;
+    const long long items = L->rx[reaction].n_items;
+    for (long long b = 0; b < items; b += 1LL << 30) pb.add(reaction, b, std::min(items, b + (1LL << 30)), 0);
+    LaunchPlan P = pb.P;
+    P.mode = 1;
+    P.dump = d;
+    P.dump_base = L->id_first[reaction];
+    P.dump_n = nt;
+    launch_enum(*L, P, precision);
+    check_kernel_status(*L);
+    CU(cudaMemcpy(outputs, d, sizeof(float) * nt * no, cudaMemcpyDeviceToHost));
+  } catch (const CudaFail &f) {
+    return fail(f.e == cudaErrorLaunchTimeout ? APEX_ETIMEDOUT : APEX_ECUDA, "dump: %s failed: %s", f.what,
+                cudaGetErrorString(f.e));
+  }
+  return APEX_OK;
+}
+
+extern "C" apex_status apex_kernel_launches(int64_t *out) {
+  if (!out) return fail(APEX_EINVAL, "NULL argument");
+  *out = g_launches.load();
+  return APEX_OK;
+}
+
+extern "C" const char *apex_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,207 @@
+// common.cuh -- structures shared by the host library and the kernels, and small device helpers.
+//
+// Work decomposition (the enumeration of Sec. 3.3 over each reaction's Cartesian product,
+// App. GPU implementation): every reaction's slots are split into one "outer" slot and the
+// "inner" slots (flattened, mixed radix). A work item is a block of APX_TILE consecutive inner
+// indices (one per tile row) times a run of L_o outer indices; each tile row keeps the sum of
+// its inner synthons' first-layer rows resident while the outer index advances, so a new tile
+// costs one broadcast row instead of APX_TILE gathers. Compound id = id_first + q *
+// inner_stride + o * outer_stride (the mixed radix split into its inner and outer parts).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/apex.h"
+
+#define APX_TILE 128
+#define APX_MAX_SEG 160
+#define APX_SIMT_THREADS 256
+
+struct RxnPlan {
+  long long id_first;
+  long long n_inner, n_outer;
+  long long inner_stride, outer_stride;
+  long long outer_row;                       // first table row of the outer slot, -1 = none
+  long long inner_row[APEX_MAX_SLOTS];       // first table row of each inner slot (most significant first)
+  long long inner_size[APEX_MAX_SLOTS];
+  long long n_items;                         // n_b * n_oc
+  long long slot_row[APEX_MAX_SLOTS];        // first table row of each slot, library order
+  long long slot_size[APEX_MAX_SLOTS];
+  int n_slots;
+  int n_inner_slots;
+  int n_b;                                   // inner tiles = ceil(n_inner / APX_TILE)
+  int L_o;                                   // outer indices per item
+  int n_oc;                                  // outer runs = ceil(n_outer / L_o)
+};
+
+struct Segment {
+  int rxn;
+  int pad;
+  long long item_begin, item_end;           // item range of this reaction
+  unsigned long long qmask;                 // query slots served by this segment
+};
+
+// One enumeration launch: a list of item ranges, passed by value as a kernel parameter.
+struct LaunchPlan {
+  int n_seg;
+  int mode;                                  // 0 = queries, 1 = dump by id, 2 = dump by tile slot
+  int dump_lo;                               // mode 2: slots per item = dump_lo * APX_TILE
+  long long total_items;
+  long long seg_first[APX_MAX_SEG + 1];      // prefix of items
+  Segment seg[APX_MAX_SEG];
+  // dump mode
+  float *dump;                               // [dump_n x n_out]
+  long long *dump_ids;                       // mode 2: [dump_n], -1 = padding row
+  long long dump_base, dump_n;
+};
+
+// Per-query device state (one per active slot).
+struct QuerySlot {
+  float w[APEX_MAX_OBJECTIVES];
+  int n_obj;
+  int n_cons;
+  int cons_idx[APEX_MAX_CONSTRAINTS];
+  float lo_w[APEX_MAX_CONSTRAINTS], hi_w[APEX_MAX_CONSTRAINTS];  // admission box (widened by the pass margin)
+  float lo_s[APEX_MAX_CONSTRAINTS], hi_s[APEX_MAX_CONSTRAINTS];  // sure box (shrunk by the margin)
+  float admit;        // admission threshold on the pass objective
+  float delta_f;      // objective margin of the pass
+  float tau;          // k-th largest sure key seen so far (-inf until k sure keys exist)
+  float tau_spec;     // speculative start threshold (validated at the end)
+  long long k;
+  unsigned cap;
+  unsigned count;     // appended entries (atomic)
+  unsigned overflow;
+  unsigned n_sure_above_spec;
+  float *keys;
+  long long *ids;     // bit 62 set = not surely feasible
+  float *keys2;
+  long long *ids2;
+};
+
+#define APX_UNSURE_BIT (1LL << 62)
+#define APX_ID_MASK ((1LL << 62) - 1)
+
+// Kernel status word values (device-side failures; never trap).
+#define APX_ERR_TIMEOUT 1
+#define APX_ERR_BOUNDS 2
+
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned apx_key_bits(float f) {
+  // order-preserving map float -> uint32 (larger float -> larger uint)
+  unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float apx_bits_key(unsigned u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+template <int N>
+__device__ __forceinline__ float apx_sel(const float (&o)[N], int idx) {
+  // o[idx] for a register array without dynamic indexing
+  float v = 0.f;
+#pragma unroll
+  for (int j = 0; j < N; ++j) v = (j == idx) ? o[j] : v;
+  return v;
+}
+
+// Applies every query of qmask to one compound (one row per lane; all 32 lanes call it).
+// Sec. 3 / Eq. apex_topk: objective sum_j w_j o_j; feasibility = every constrained output
+// inside its box. A compound is admitted when its pass objective reaches the slot's admission
+// threshold and it lies inside the widened box; it is marked "sure" if it also lies inside the
+// shrunk box (then its feasibility cannot change under the margin).
+template <int NOUT>
+__device__ __forceinline__ void apx_apply_queries(QuerySlot *__restrict__ slots, unsigned long long qmask, bool valid,
+                                                  long long id, const float (&o)[NOUT]) {
+  const unsigned lane = threadIdx.x & 31;
+  while (qmask) {
+    const int s = __ffsll((long long)qmask) - 1;
+    qmask &= qmask - 1;
+    QuerySlot *Q = slots + s;
+    const int n_obj = Q->n_obj;
+    float f = 0.f;
+#pragma unroll
+    for (int j = 0; j < APEX_MAX_OBJECTIVES && j < NOUT; ++j)
+      if (j < n_obj) f = fmaf(__ldg(&Q->w[j]), o[j], f);
+    bool pass = valid && (f >= *((volatile float *)&Q->admit));
+    if (__ballot_sync(0xffffffffu, pass) == 0u) continue;
+    bool sure = true;
+    const int nc = Q->n_cons;
+    for (int i = 0; i < nc; ++i) {
+      const float v = apx_sel<NOUT>(o, Q->cons_idx[i]);
+      pass = pass && (v >= Q->lo_w[i]) && (v <= Q->hi_w[i]);
+      sure = sure && (v >= Q->lo_s[i]) && (v <= Q->hi_s[i]);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, pass);
+    if (m == 0u) continue;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if ((int)lane == leader) base = atomicAdd(&Q->count, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pass) {
+      const unsigned pos = base + __popc(m & ((1u << lane) - 1u));
+      if (pos < Q->cap) {
+        Q->keys[pos] = f;
+        Q->ids[pos] = id | (sure ? 0LL : APX_UNSURE_BIT);
+      } else {
+        atomicExch(&Q->overflow, 1u);
+      }
+    }
+  }
+}
+
+// Host-side count of kernel launches issued by this library (all launch wrappers add to it).
+void apx_count_launch(long long n = 1);
+
+// Locates item `it` of a launch: segment (binary search) and local item index.
+__device__ __forceinline__ int apx_find_seg(const LaunchPlan &L, long long it) {
+  int lo = 0, hi = L.n_seg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L.seg_first[mid] <= it) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// FP32 candidate evaluation arguments (exact box, per-output FP32 margins).
+struct EvalArgs {
+  const float *out32;       // [n x n_out] FP32 outputs of the candidates
+  int n_out;
+  const QuerySlot *Q;       // objective weights and constrained output indices
+  const float *eps;         // per-output FP32 margin [n_out]
+  float eps_f;              // objective margin
+  const double *lo, *hi;    // exact box [n_cons]
+};
+
+// One member of the result set under exact selection.
+struct RItem {
+  double s;          // best score so far (FP32 rescore, or FP64 once rescored)
+  long long id;      // global id (no flag bits)
+  int src;           // index into the FP32 candidate arrays
+  unsigned char alive, is64, need64, pad;
+};
+
+// Device pointers and shapes of a loaded library (passed by value to the kernels).
+struct DevTables {
+  int n_layers;
+  int dims[8];
+  int act;                     // APEX_ACT_*
+  int n_out;
+  int d;
+  int n_rx;
+  long long n_rows;
+  const RxnPlan *rx;           // [n_rx]
+  const long long *id_first;   // [n_rx + 1]
+  // FP32 path
+  const float *P32;            // [n_rows x dims[1]]: W_1 u + b_1 on slot-1 rows
+  const float *WT[8];          // layer l >= 1, transposed: [dims[l] x dims[l+1]]
+  const float *B[8];           // layer l >= 1
+  // FP64 plain path
+  const float *U;              // [n_rows x d]
+  const double *WT64[8];       // every layer, transposed: [dims[l] x dims[l+1]]
+  const double *B64[8];
+  // BF16 tensor-core path (3-layer heads with dims[1] == dims[2] == 256, <= 16 outputs)
+  const unsigned short *P16;   // [n_rows x 256] bf16 bits, scaled into the activation's input space
+  const unsigned char *w2img;  // W_2 as the SW128 K-major shared-memory image (128 KB)
+  const unsigned char *w3img;  // W_3 padded to 16 rows, same layout (8 KB)
+  const float *b2s;            // b_2 in the same scaled space [256]
+  const float *b3;             // b_3 padded [16]
+};

@@ -1,0 +1,440 @@
+// k_select.cu -- streaming top-k state of the queries (the size-k priority queue of Sec. 3.3
+// realised as threshold-filtered candidate buffers), radix selection, candidate evaluation,
+// bitonic ordering by (objective desc, id asc), decode of the final ids (App. GPU impl.:
+// "index decoding"), and the standalone select entry point.
+#include <cfloat>
+#include <cmath>
+#include <algorithm>
+#include "common.cuh"
+
+#define SEL_THREADS 1024
+
+// ------------------------------------------------------------------ block radix select
+// k-th largest 32-bit key (order-preserving bits) among n entries; include(i) filters.
+// Returns true and *out_bits when at least k entries are included.
+struct SelSrc {
+  const float *keys;          // float keys
+  const long long *ids;       // optional: entries with APX_UNSURE_BIT are excluded
+  const unsigned char *flag;  // optional: entries with flag == 0 are excluded
+  __device__ __forceinline__ bool get(long long i, unsigned &bits) const {
+    if (ids && (ids[i] & APX_UNSURE_BIT)) return false;
+    if (flag && !flag[i]) return false;
+    bits = apx_key_bits(keys[i]);
+    return true;
+  }
+};
+
+__device__ bool block_kth_largest(const SelSrc &src, long long n, long long k, unsigned *out_bits,
+                                  unsigned long long *out_included) {
+  __shared__ unsigned long long hist[256];
+  __shared__ unsigned prefix_s;
+  __shared__ long long kk_s;
+  __shared__ unsigned long long total_s;
+  if (threadIdx.x == 0) {
+    prefix_s = 0;
+    kk_s = k;
+  }
+  unsigned prefix = 0, mask = 0;
+  for (int pass = 3; pass >= 0; --pass) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    prefix = prefix_s;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+      unsigned b;
+      if (src.get(i, b) && ((b & mask) == prefix)) atomicAdd(&hist[(b >> (8 * pass)) & 255u], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (pass == 3) {
+        unsigned long long t = 0;
+        for (int d = 0; d < 256; ++d) t += hist[d];
+        total_s = t;
+      }
+      long long kk = kk_s;
+      unsigned long long cum = 0;
+      int dsel = 0;
+      for (int d = 255; d >= 0; --d) {
+        if (cum + hist[d] >= (unsigned long long)kk) {
+          dsel = d;
+          break;
+        }
+        cum += hist[d];
+      }
+      kk_s = kk - (long long)cum;
+      prefix_s = prefix | ((unsigned)dsel << (8 * pass));
+    }
+    __syncthreads();
+    mask |= 255u << (8 * pass);
+    if (total_s < (unsigned long long)k) break;
+  }
+  if (out_included) *out_included = total_s;
+  *out_bits = prefix_s;
+  const bool ok = total_s >= (unsigned long long)k;
+  __syncthreads();
+  return ok;
+}
+
+// ------------------------------------------------------------------ per-slot select / compaction
+// mode 0: only when the buffer is more than half full; mode 1: always (end of the pass).
+// Raises tau (k-th largest sure key) and the admission threshold tau - 2 delta_f, then keeps
+// only entries at or above the admission threshold.
+__global__ void __launch_bounds__(SEL_THREADS) k_slot_select(QuerySlot *slots, const int *slot_list, int mode) {
+  QuerySlot *Q = slots + slot_list[blockIdx.x];
+  __shared__ unsigned kept;
+  __shared__ unsigned n_spec;
+  const unsigned n = min(*((volatile unsigned *)&Q->count), Q->cap);
+  if (mode == 0 && n <= Q->cap / 2) return;
+  SelSrc src{Q->keys, Q->ids, nullptr};
+  unsigned bits;
+  if (block_kth_largest(src, n, Q->k, &bits, nullptr)) {
+    if (threadIdx.x == 0) {
+      const float tau = apx_bits_key(bits);
+      if (!(tau <= Q->tau)) Q->tau = tau;
+      const float adm = Q->tau - 2.0f * Q->delta_f;
+      if (!(adm <= Q->admit)) Q->admit = adm;
+    }
+  }
+  if (threadIdx.x == 0) {
+    kept = 0;
+    n_spec = 0;
+  }
+  __syncthreads();
+  const float admit = Q->admit;
+  const float spec = Q->tau_spec;
+  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+    const float key = Q->keys[i];
+    const long long id = Q->ids[i];
+    if (mode == 1 && !(id & APX_UNSURE_BIT) && key >= spec) atomicAdd(&n_spec, 1u);
+    if (key >= admit) {
+      const unsigned p = atomicAdd(&kept, 1u);
+      Q->keys2[p] = key;
+      Q->ids2[p] = id;
+    }
+  }
+  __syncthreads();
+  const unsigned m = kept;
+  for (unsigned i = threadIdx.x; i < m; i += blockDim.x) {
+    Q->keys[i] = Q->keys2[i];
+    Q->ids[i] = Q->ids2[i];
+  }
+  if (threadIdx.x == 0) {
+    Q->count = m;
+    if (mode == 1) Q->n_sure_above_spec = n_spec;
+  }
+}
+
+cudaError_t apx_launch_slot_select(QuerySlot *slots, const int *slot_list, int n_slots, int mode, cudaStream_t st) {
+  if (n_slots <= 0) return cudaSuccess;
+  apx_count_launch();
+  k_slot_select<<<n_slots, SEL_THREADS, 0, st>>>(slots, slot_list, mode);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FP32 candidate evaluation
+// From FP32 outputs of the candidates: objective, maybe-feasible (box widened by the FP32
+// margin eps) and sure-feasible (box shrunk by eps).
+
+__global__ void k_eval32(EvalArgs a, long long n, float *f32, unsigned char *maybe, unsigned char *sure) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float *o = a.out32 + i * a.n_out;
+    float f = 0.f;
+    for (int j = 0; j < a.Q->n_obj; ++j) f = fmaf(a.Q->w[j], o[j], f);
+    bool mb = true, sr = true;
+    for (int c = 0; c < a.Q->n_cons; ++c) {
+      const int p = a.Q->cons_idx[c];
+      const float v = o[p];
+      const double lo = a.lo[c], hi = a.hi[c];
+      mb = mb && ((double)v >= lo - a.eps[p]) && ((double)v <= hi + a.eps[p]);
+      sr = sr && ((double)v >= lo + a.eps[p]) && ((double)v <= hi - a.eps[p]);
+    }
+    f32[i] = f;
+    maybe[i] = mb;
+    sure[i] = sr;
+  }
+}
+
+// tau32 = k-th largest f32 among sure entries (one CTA)
+__global__ void __launch_bounds__(SEL_THREADS) k_kth(const float *keys, const unsigned char *flag, long long n, long long k,
+                                                     float *out_tau, int *out_ok) {
+  SelSrc src{keys, nullptr, flag};
+  unsigned bits;
+  const bool ok = block_kth_largest(src, n, k, &bits, nullptr);
+  if (threadIdx.x == 0) {
+    *out_tau = ok ? apx_bits_key(bits) : -INFINITY;
+    *out_ok = ok;
+  }
+}
+
+// ------------------------------------------------------------------ result set R
+
+// R = {maybe && f32 >= thr}; need64 = !sure
+__global__ void k_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
+                          const unsigned char *sure, float thr, RItem *R, unsigned *n_r) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (maybe[i] && f32[i] >= thr) {
+      const unsigned p = atomicAdd(n_r, 1u);
+      RItem it;
+      it.s = (double)f32[i];
+      it.id = cand_ids[i] & APX_ID_MASK;
+      it.src = (int)i;
+      it.alive = 1;
+      it.is64 = 0;
+      it.need64 = sure[i] ? 0 : 1;
+      it.pad = 0;
+      R[p] = it;
+    }
+  }
+}
+
+// list of R positions whose FP64 rescore is pending
+__global__ void k_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (R[i].alive && R[i].need64 && !R[i].is64) {
+      const unsigned p = atomicAdd(n64, 1u);
+      ids64[p] = R[i].id;
+      pos64[p] = (int)i;
+    }
+  }
+}
+
+// apply FP64 outputs: exact objective and box; drop infeasible
+__global__ void k_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, int n_out, const QuerySlot *Q,
+                          const double *lo, const double *hi, double *out_rows /* [n_candidates x n_out], by src */) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n64; i += gridDim.x * blockDim.x) {
+    const double *o = out64 + (size_t)i * n_out;
+    double f = 0.0;
+    for (int j = 0; j < Q->n_obj; ++j) f += (double)Q->w[j] * o[j];
+    bool ok = true;
+    for (int c = 0; c < Q->n_cons; ++c) {
+      const double v = o[Q->cons_idx[c]];
+      ok = ok && (v >= lo[c]) && (v <= hi[c]);
+    }
+    RItem &it = R[pos64[i]];
+    it.s = f;
+    it.is64 = 1;
+    it.alive = ok ? 1 : 0;
+    for (int j = 0; j < n_out; ++j) out_rows[(size_t)it.src * n_out + j] = o[j];
+  }
+}
+
+// ------------------------------------------------------------------ bitonic sort of R
+// order: alive first, then s desc, then id asc
+__device__ __forceinline__ bool r_before(const RItem &a, const RItem &b) {
+  if (a.alive != b.alive) return a.alive > b.alive;
+  if (a.s != b.s) return a.s > b.s;
+  return a.id < b.id;
+}
+
+__global__ void k_bitonic_global(RItem *R, unsigned n, unsigned j, unsigned kk) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned l = i ^ j;
+    if (l > i) {
+      const bool up = ((i & kk) == 0);
+      RItem a = R[i], b = R[l];
+      const bool swap = up ? r_before(b, a) : r_before(a, b);
+      if (swap) {
+        R[i] = b;
+        R[l] = a;
+      }
+    }
+  }
+}
+
+#define BITONIC_SMEM 2048
+__global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned n, unsigned kk_from, unsigned kk_to) {
+  // handles every (kk, j) step with j < BITONIC_SMEM inside blocks of BITONIC_SMEM elements
+  __shared__ RItem s[BITONIC_SMEM];
+  const unsigned base = blockIdx.x * BITONIC_SMEM;
+  for (unsigned t = threadIdx.x; t < BITONIC_SMEM; t += blockDim.x) s[t] = R[base + t];
+  __syncthreads();
+  for (unsigned kk = kk_from; kk <= kk_to; kk <<= 1) {
+    for (unsigned j = min(kk >> 1, (unsigned)BITONIC_SMEM >> 1); j > 0; j >>= 1) {
+      for (unsigned t = threadIdx.x; t < BITONIC_SMEM; t += blockDim.x) {
+        const unsigned l = t ^ j;
+        if (l > t) {
+          const unsigned gi = base + t;
+          const bool up = ((gi & kk) == 0);
+          RItem a = s[t], b = s[l];
+          const bool swap = up ? r_before(b, a) : r_before(a, b);
+          if (swap) {
+            s[t] = b;
+            s[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (unsigned t = threadIdx.x; t < BITONIC_SMEM; t += blockDim.x) R[base + t] = s[t];
+}
+
+__global__ void k_pad_r(RItem *R, unsigned from, unsigned to) {
+  for (unsigned i = from + blockIdx.x * blockDim.x + threadIdx.x; i < to; i += gridDim.x * blockDim.x) {
+    RItem it;
+    it.s = -INFINITY;
+    it.id = 0x3fffffffffffffffLL;
+    it.src = -1;
+    it.alive = 0;
+    it.is64 = 1;
+    it.need64 = 0;
+    it.pad = 0;
+    R[i] = it;
+  }
+}
+
+// Sorts R[0, n_pow2) (n_pow2 a power of two >= BITONIC_SMEM or the padded size).
+cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st) {
+  if (n_pow2 < 2) return cudaSuccess;
+  apx_count_launch();
+  k_pad_r<<<64, 256, 0, st>>>(R, n_used, n_pow2);
+  if (n_pow2 <= BITONIC_SMEM) {
+    // small: global steps only (cheap at this size)
+    for (unsigned kk = 2; kk <= n_pow2; kk <<= 1)
+      for (unsigned j = kk >> 1; j > 0; j >>= 1) {
+        apx_count_launch();
+        k_bitonic_global<<<(n_pow2 + 255) / 256, 256, 0, st>>>(R, n_pow2, j, kk);
+      }
+    return cudaGetLastError();
+  }
+  const unsigned nb = n_pow2 / BITONIC_SMEM;
+  apx_count_launch();
+  k_bitonic_shared<<<nb, 1024, 0, st>>>(R, n_pow2, 2, BITONIC_SMEM);
+  for (unsigned kk = BITONIC_SMEM * 2; kk <= n_pow2; kk <<= 1) {
+    for (unsigned j = kk >> 1; j >= BITONIC_SMEM; j >>= 1) {
+      apx_count_launch();
+      k_bitonic_global<<<std::min<unsigned>(nb * 8, 148u * 16u), 256, 0, st>>>(R, n_pow2, j, kk);
+    }
+    apx_count_launch();
+    k_bitonic_shared<<<nb, 1024, 0, st>>>(R, n_pow2, kk, kk);
+  }
+  return cudaGetLastError();
+}
+
+// Marks for FP64 every alive, not-yet-FP64 item among the first kp1 sorted positions that is
+// within tol of a neighbour or of the k-th score (the tie-breaking / boundary band).
+__global__ void k_mark_ties(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked) {
+  __shared__ double sk;
+  if (threadIdx.x == 0) {
+    const unsigned kk = (unsigned)(k < (long long)n ? k : (long long)n) - 1u;
+    sk = (n > 0 && R[kk].alive) ? R[kk].s : -INFINITY;
+  }
+  __syncthreads();
+  const unsigned lim = min(kp1, n);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += gridDim.x * blockDim.x) {
+    RItem &it = R[i];
+    if (!it.alive || it.is64) continue;
+    bool m = fabs(it.s - sk) <= tol;
+    if (i > 0 && R[i - 1].alive && fabs(R[i - 1].s - it.s) <= tol) m = true;
+    if (i + 1 < n && R[i + 1].alive && fabs(R[i + 1].s - it.s) <= tol) m = true;
+    if (m) {
+      it.need64 = 1;
+      atomicAdd(n_marked, 1u);
+    }
+  }
+}
+
+// Final rows: ids, reaction, synthons, objective, outputs (FP64 where rescored, else FP32)
+__global__ void k_emit(const RItem *R, unsigned n_final, const __grid_constant__ DevTables T, const float *out32,
+                       const double *out64_rows, long long *ids, int *rxn, long long *syn, double *obj, double *outs) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_final; i += gridDim.x * blockDim.x) {
+    const RItem it = R[i];
+    const long long id = it.id;
+    int lo = 0, hi = T.n_rx - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (T.id_first[mid] <= id) lo = mid; else hi = mid - 1;
+    }
+    const RxnPlan *p = T.rx + lo;
+    long long rem = id - p->id_first;
+    long long s[APEX_MAX_SLOTS];
+    for (int j = APEX_MAX_SLOTS - 1; j >= 0; --j) {
+      if (j < p->n_slots) {
+        s[j] = rem % p->slot_size[j];
+        rem /= p->slot_size[j];
+      } else {
+        s[j] = -1;
+      }
+    }
+    ids[i] = id;
+    rxn[i] = lo;
+    for (int j = 0; j < APEX_MAX_SLOTS; ++j) syn[(size_t)i * APEX_MAX_SLOTS + j] = s[j];
+    obj[i] = it.s;
+    // outputs are kept per candidate (src), so the permutation of R by the sorts does not matter
+    for (int j = 0; j < T.n_out; ++j)
+      outs[(size_t)i * T.n_out + j] =
+          it.is64 ? out64_rows[(size_t)it.src * T.n_out + j] : (double)out32[(size_t)it.src * T.n_out + j];
+  }
+}
+
+cudaError_t apx_launch_eval32(const EvalArgs &a, long long n, float *f32, unsigned char *maybe, unsigned char *sure,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  apx_count_launch();
+  k_eval32<<<(unsigned)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0, st>>>(a, n, f32, maybe, sure);
+  return cudaGetLastError();
+}
+cudaError_t apx_launch_kth(const float *keys, const unsigned char *flag, long long n, long long k, float *out_tau,
+                           int *out_ok, cudaStream_t st) {
+  apx_count_launch();
+  k_kth<<<1, SEL_THREADS, 0, st>>>(keys, flag, n, k, out_tau, out_ok);
+  return cudaGetLastError();
+}
+cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
+                               const unsigned char *sure, float thr, RItem *R, unsigned *n_r, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  apx_count_launch();
+  k_build_r<<<(unsigned)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0, st>>>(n, cand_ids, f32, maybe, sure, thr, R,
+                                                                                 n_r);
+  return cudaGetLastError();
+}
+cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  apx_count_launch();
+  k_collect64<<<std::min<unsigned>((n + 255) / 256, 148u * 16u), 256, 0, st>>>(R, n, ids64, pos64, n64);
+  return cudaGetLastError();
+}
+cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, int n_out,
+                               const QuerySlot *Q, const double *lo, const double *hi, double *out_rows,
+                               cudaStream_t st) {
+  if (n64 == 0) return cudaSuccess;
+  apx_count_launch();
+  k_apply64<<<std::min<unsigned>((n64 + 255) / 256, 148u * 16u), 256, 0, st>>>(R, pos64, out64, n64, n_out, Q, lo, hi, out_rows);
+  return cudaGetLastError();
+}
+cudaError_t apx_launch_mark(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked,
+                            cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  apx_count_launch();
+  k_mark_ties<<<std::min<unsigned>((kp1 + 255) / 256 + 1, 148u * 16u), 256, 0, st>>>(R, n, kp1, k, tol, n_marked);
+  return cudaGetLastError();
+}
+cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const DevTables &T, const float *out32,
+                            const double *out64_rows, long long *ids, int *rxn, long long *syn, double *obj,
+                            double *outs, cudaStream_t st) {
+  if (n_final == 0) return cudaSuccess;
+  apx_count_launch();
+  k_emit<<<std::min<unsigned>((n_final + 127) / 128, 148u * 4u), 128, 0, st>>>(R, n_final, T, out32, out64_rows, ids, rxn, syn, obj,
+                                                               outs);
+  return cudaGetLastError();
+}
+
+__global__ void k_count_alive(const RItem *R, unsigned n, unsigned *out) {
+  unsigned c = 0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) c += R[i].alive;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+int apx_count_alive(const RItem *R, unsigned n, cudaStream_t st, unsigned *d_tmp, cudaError_t *e) {
+  unsigned h = 0;
+  *e = cudaMemsetAsync(d_tmp, 0, sizeof(unsigned), st);
+  if (*e != cudaSuccess) return 0;
+  apx_count_launch();
+  k_count_alive<<<std::min<unsigned>((n + 255) / 256, 148u * 4u), 256, 0, st>>>(R, n, d_tmp);
+  *e = cudaGetLastError();
+  if (*e != cudaSuccess) return 0;
+  *e = cudaMemcpyAsync(&h, d_tmp, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (*e != cudaSuccess) return 0;
+  *e = cudaStreamSynchronize(st);
+  return (int)h;
+}

