@@ -193,6 +193,21 @@ apex_status apex_decode_ids(const apex_library *lib, int64_t n, const int64_t *i
 apex_status apex_topk_select(const float *keys, const int64_t *ids, int64_t n, int64_t k, float *out_keys,
                              int64_t *out_ids, int64_t *n_out, void *cuda_stream);
 
+/* apex_topk_select for callers that cannot allocate device memory (a caller-owned memory
+ * pool or arena that forbids outside allocations, a host callback or latency-critical loop
+ * that must not pay cudaMalloc's synchronization, a plugin whose host framework owns every
+ * allocation). Same arguments, same result and order as apex_topk_select; no counterpart in
+ * the paper. Its scratch is one file-scope device array of fixed size (about 1.6 MB, held by
+ * every GPU that loads the library until the process exits), so it calls no cudaMalloc,
+ * cudaFree or allocating routine. min(k, n) must be <= APEX_SELECT_NOALLOC_MAX_K, else EINVAL.
+ * The first call on a device looks up the array's device address (with that device current);
+ * make that first call before any stream capture. All calls share the one array and it keeps
+ * the last call's contents: calls that overlap on the GPU (other streams, other host threads)
+ * race; each call clears the state it needs and synchronizes its stream before returning. */
+#define APEX_SELECT_NOALLOC_MAX_K 65536
+apex_status apex_topk_select_noalloc(const float *keys, const int64_t *ids, int64_t n, int64_t k, float *out_keys,
+                                     int64_t *out_ids, int64_t *n_out, void *cuda_stream);
+
 /* Number of kernel launches this process has issued through the library so far (all
  * libraries, all entry points). Pure host counter. */
 apex_status apex_kernel_launches(int64_t *out);

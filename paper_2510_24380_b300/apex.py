@@ -88,6 +88,8 @@ SYMBOLS = {
     "apex_decode_ids": [C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int64)],
     "apex_topk_select": [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64),
                          C.c_void_p],
+    "apex_topk_select_noalloc": [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                 C.POINTER(C.c_int64), C.c_void_p],
     "apex_kernel_launches": [C.POINTER(C.c_int64)],
     "apex_last_error": [],
 }
@@ -279,4 +281,17 @@ def apex_topk_select(keys_ptr: int, ids_ptr: int, n: int, k: int, out_keys_ptr: 
     _check(load().apex_topk_select(C.c_void_p(keys_ptr), C.c_void_p(ids_ptr), int(n), int(k), C.c_void_p(out_keys_ptr),
                                    C.c_void_p(out_ids_ptr), C.byref(n_out), C.c_void_p(stream or 0)),
            "apex_topk_select")
+    return n_out.value
+
+
+NOALLOC_MAX_K = 65536
+
+
+def apex_topk_select_noalloc(keys_ptr: int, ids_ptr: int, n: int, k: int, out_keys_ptr: int, out_ids_ptr: int,
+                             stream: int | None = None) -> int:
+    """apex_topk_select with static device scratch (no allocation); device pointers; returns n_out."""
+    n_out = C.c_int64()
+    _check(load().apex_topk_select_noalloc(C.c_void_p(keys_ptr), C.c_void_p(ids_ptr), int(n), int(k),
+                                           C.c_void_p(out_keys_ptr), C.c_void_p(out_ids_ptr), C.byref(n_out),
+                                           C.c_void_p(stream or 0)), "apex_topk_select_noalloc")
     return n_out.value

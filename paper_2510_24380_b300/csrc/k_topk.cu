@@ -10,6 +10,7 @@
 //   compaction of the members, then a bitonic sort of the k members.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include "common.cuh"
 
@@ -173,6 +174,63 @@ extern "C" apex_status apex_topk_select(const float *keys, const int64_t *ids, i
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(S);
   cudaFree(R);
+  if (e != cudaSuccess) return apx_fail(APEX_ECUDA, cudaGetErrorString(e));
+  *n_out = ke;
+  return APEX_OK;
+}
+
+// ------------------------------------------------------------------ variant without allocation
+// Some callers cannot allocate device memory at the point where they need a selection: code
+// that runs under a caller-owned memory pool or arena that forbids outside allocations, code
+// inside a host callback or a real-time loop where cudaMalloc's implicit synchronization and
+// latency are not acceptable, or plugins whose host framework owns every allocation. For them
+// the scratch of apex_topk_select (selection state + sort buffer) lives in this file-scope
+// device array instead, sized for k <= APEX_SELECT_NOALLOC_MAX_K. Every GPU that loads the
+// library holds it until the process exits.
+#define APX_SEL_STATE_SLOT 4096
+static_assert(sizeof(SelState) <= APX_SEL_STATE_SLOT, "selection state exceeds its slot");
+#define APX_NOALLOC_BYTES ((size_t)APX_SEL_STATE_SLOT + (size_t)APEX_SELECT_NOALLOC_MAX_K * sizeof(RItem))
+static __device__ __align__(256) unsigned char g_select_scratch[APX_NOALLOC_BYTES];
+
+#define APX_MAX_DEVICES 64
+static void *g_select_scratch_dev[APX_MAX_DEVICES] = {nullptr};
+static std::mutex g_select_scratch_mu;
+
+extern "C" apex_status apex_topk_select_noalloc(const float *keys, const int64_t *ids, int64_t n, int64_t k,
+                                                float *out_keys, int64_t *out_ids, int64_t *n_out, void *cuda_stream) {
+  if (n < 0 || k < 1 || !n_out || (n > 0 && (!keys || !ids || !out_keys || !out_ids)))
+    return apx_fail(APEX_EINVAL, "topk_select_noalloc: bad arguments");
+  const long long ke = std::min<long long>(k, n);
+  if (ke > APEX_SELECT_NOALLOC_MAX_K)
+    return apx_fail(APEX_EINVAL, "topk_select_noalloc: min(k, n) exceeds the static scratch limit "
+                                 "APEX_SELECT_NOALLOC_MAX_K (65536); use apex_topk_select");
+  *n_out = 0;
+  if (n == 0) return APEX_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= APX_MAX_DEVICES)
+    return apx_fail(APEX_ECUDA, "topk_select_noalloc: no current CUDA device");
+  void *base = nullptr;
+  {
+    // one-time set-up per device, with that device current: the device address of the array
+    // (its name in host code is only a host-side stand-in)
+    std::lock_guard<std::mutex> g(g_select_scratch_mu);
+    if (!g_select_scratch_dev[dev]) {
+      void *p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_select_scratch);
+      if (e != cudaSuccess || !p)
+        return apx_fail(APEX_ECUDA, "topk_select_noalloc: cudaGetSymbolAddress failed");
+      g_select_scratch_dev[dev] = p;
+    }
+    base = g_select_scratch_dev[dev];
+  }
+  unsigned np = 2;
+  while ((long long)np < ke) np <<= 1;
+  SelState *S = reinterpret_cast<SelState *>(base);
+  RItem *R = reinterpret_cast<RItem *>(static_cast<unsigned char *>(base) + APX_SEL_STATE_SLOT);
+  // k_sel_init clears the selection state; the sort buffer is fully rewritten by each call
+  cudaError_t e = apx_topk_select_run(keys, (const long long *)ids, n, ke, out_keys, (long long *)out_ids, S, R, np,
+                                      (cudaStream_t)cuda_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return apx_fail(APEX_ECUDA, cudaGetErrorString(e));
   *n_out = ke;
   return APEX_OK;
