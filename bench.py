@@ -296,7 +296,8 @@ def main():
                      "kernel_ms_per_step": mean_enum},
         "fp32_plain": {"value": fp32_rate, "unit": "compounds/s", "same_topk_set_as_bf16": bool(same) if fp32_rate else None},
         "query": {k: last_stats[k] for k in ("n_candidates", "n_rescored_fp64", "n_restarts", "n_launches",
-                                             "gpu_ms", "enumerate_ms")},
+                                             "gpu_ms", "enumerate_ms", "queue_ms", "latency_ms", "host_start_ms",
+                                             "host_pass_ms", "host_finalize_ms")},
         "clocks": clk,
     }
     if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):

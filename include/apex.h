@@ -127,6 +127,9 @@ typedef struct {
   double latency_ms;            /* host wall time from apex_query until the results were ready */
   double gpu_ms;                /* device time (CUDA events) from its first to its last kernel */
   double enumerate_ms;          /* device time of the enumeration launches that served it */
+  double host_start_ms;         /* worker wall time spent estimating the start threshold */
+  double host_pass_ms;          /* worker wall time of the pass steps that served it */
+  double host_finalize_ms;      /* worker wall time of exact selection, ordering and decode */
 } apex_query_stats_t;
 
 /* Pure host: N = sum_t prod_j slot_sizes (App. A.1). EINVAL on bad shapes or int64 overflow. */

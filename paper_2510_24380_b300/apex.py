@@ -64,6 +64,7 @@ class QueryStats(C.Structure):
         ("n_scope", C.c_int64), ("n_scored", C.c_int64), ("n_candidates", C.c_int64), ("n_rescored_fp64", C.c_int64),
         ("n_feasible_lower", C.c_int64), ("n_restarts", C.c_int32), ("n_launches", C.c_int32),
         ("queue_ms", C.c_double), ("latency_ms", C.c_double), ("gpu_ms", C.c_double), ("enumerate_ms", C.c_double),
+        ("host_start_ms", C.c_double), ("host_pass_ms", C.c_double), ("host_finalize_ms", C.c_double),
     ]
 
     def as_dict(self):

@@ -171,6 +171,18 @@ struct apex_library {
   long long cursor = 0;  // global item index of the circular pass
   apex_query_stats_t last_stats{};
   std::mt19937_64 rng;
+  // reusable device scratch: per-slot candidate buffers (grow-only) and a bump arena for
+  // finalization / sampling temporaries (grow-only), pinned host staging, events
+  struct SlotBuf {
+    float *keys = nullptr, *keys2 = nullptr;
+    long long *ids = nullptr, *ids2 = nullptr;
+    unsigned cap = 0;
+  } slotbuf[APEX_MAX_ACTIVE];
+  char *arena = nullptr;
+  size_t arena_cap = 0, arena_off = 0;
+  char *pinned = nullptr;
+  size_t pinned_cap = 0;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
 
   void *dalloc(size_t n, bool count = true) {
     if (count && budget && bytes + query_bytes + n > budget) throw BudgetFail();
@@ -185,6 +197,36 @@ struct apex_library {
     allocs.clear();
   }
   ~apex_library() {}
+
+  // bump allocation from the arena; grow() must be called (with no work in flight) first
+  void *aget(size_t n) {
+    n = (n + 255) & ~(size_t)255;
+    if (arena_off + n > arena_cap) throw CudaFail(cudaErrorMemoryAllocation, "arena exhausted", __LINE__);
+    void *p = arena + arena_off;
+    arena_off += n;
+    return p;
+  }
+  void arena_reserve(size_t n) {
+    arena_off = 0;
+    if (n <= arena_cap) return;
+    CU(cudaStreamSynchronize(st));
+    if (arena) cudaFree(arena);
+    arena = nullptr;
+    size_t want = std::max(n + (n >> 1), (size_t)(8u << 20));
+    if (budget && bytes + query_bytes + want > budget + arena_cap) want = n;
+    CU(cudaMalloc(&arena, want));
+    query_bytes += want - arena_cap;
+    arena_cap = want;
+  }
+  void *pin(size_t n) {
+    if (n > pinned_cap) {
+      if (pinned) cudaFreeHost(pinned);
+      pinned = nullptr;
+      pinned_cap = std::max(n, (size_t)(1u << 20));
+      CU(cudaMallocHost(&pinned, pinned_cap));
+    }
+    return pinned;
+  }
 };
 
 // ------------------------------------------------------------------ helpers
@@ -292,6 +334,7 @@ struct PlanBuilder {
     s.item_begin = b;
     s.item_end = e;
     s.qmask = qmask;
+    P.qmask_all |= qmask;
     P.seg_first[P.n_seg + 1] = P.seg_first[P.n_seg] + (e - b);
     P.n_seg++;
     P.total_items = P.seg_first[P.n_seg];
@@ -312,9 +355,10 @@ static void launch_enum(apex_library &L, const LaunchPlan &P, int precision) {
 }
 
 static void check_kernel_status(apex_library &L) {
-  int e = 0;
-  CU(cudaMemcpyAsync(&e, L.d_err, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+  int *pe = (int *)L.pin(64) + 8;
+  CU(cudaMemcpyAsync(pe, L.d_err, sizeof(int), cudaMemcpyDeviceToHost, L.st));
   CU(cudaStreamSynchronize(L.st));
+  const int e = *pe;
   if (e) {
     int z = 0;
     CU(cudaMemcpy(L.d_err, &z, sizeof(int), cudaMemcpyHostToDevice));
@@ -595,6 +639,9 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
     L->d_err = (int *)L->dalloc(sizeof(int));
     CU(cudaMemset(L->d_err, 0, sizeof(int)));
     L->d_slot_list = (int *)L->dalloc(sizeof(int) * APEX_MAX_ACTIVE);
+    CU(cudaEventCreate(&L->ev_a));
+    CU(cudaEventCreate(&L->ev_b));
+    L->pin(1 << 20);
     CU(cudaStreamSynchronize(L->st));
     calibrate(*L);
     CU(cudaStreamSynchronize(L->st));
@@ -629,11 +676,18 @@ extern "C" apex_status apex_free_library(apex_library *L) {
     QueryRec *q = kv.second.get();
     if (q->ev0) cudaEventDestroy(q->ev0);
     if (q->ev1) cudaEventDestroy(q->ev1);
-    if (q->keys) cudaFree(q->keys);
-    if (q->ids) cudaFree(q->ids);
-    if (q->keys2) cudaFree(q->keys2);
-    if (q->ids2) cudaFree(q->ids2);
   }
+  for (auto &B : L->slotbuf)
+    if (B.cap) {
+      cudaFree(B.keys);
+      cudaFree(B.keys2);
+      cudaFree(B.ids);
+      cudaFree(B.ids2);
+    }
+  if (L->arena) cudaFree(L->arena);
+  if (L->pinned) cudaFreeHost(L->pinned);
+  if (L->ev_a) cudaEventDestroy(L->ev_a);
+  if (L->ev_b) cudaEventDestroy(L->ev_b);
   L->release_all();
   if (L->own_stream) cudaStreamDestroy(L->st);
   delete L;
@@ -762,13 +816,9 @@ extern "C" apex_status apex_cancel(apex_library *L, apex_query_id id) {
 static size_t query_bytes_for(unsigned cap) { return (size_t)cap * (4 + 8) * 2; }
 
 static void free_query_device(apex_library &L, QueryRec *q) {
-  if (q->keys) cudaFree(q->keys);
-  if (q->ids) cudaFree(q->ids);
-  if (q->keys2) cudaFree(q->keys2);
-  if (q->ids2) cudaFree(q->ids2);
+  (void)L;
   q->keys = q->keys2 = nullptr;
   q->ids = q->ids2 = nullptr;
-  L.query_bytes -= q->dev_bytes;
   q->dev_bytes = 0;
 }
 
@@ -806,9 +856,23 @@ static void write_slot(apex_library &L, QueryRec *q, float admit) {
 // Start threshold guess: the rank-r best objective among surely feasible compounds of a seeded
 // FP32 sample of the query's scope, r chosen so that ~3k scope compounds are expected above it.
 // Only a guess: finalization verifies it (>= k sure entries at or above it) or restarts lower.
+static bool trace_on() {
+  static int on = -1;
+  if (on < 0) on = getenv("APEX_TRACE") ? 1 : 0;
+  return on == 1;
+}
+#define TRACE(...)                          \
+  do {                                      \
+    if (trace_on()) {                       \
+      fprintf(stderr, "[apex] " __VA_ARGS__); \
+      fputc('\n', stderr);                 \
+    }                                       \
+  } while (0)
+
 static float speculative_start(apex_library &L, QueryRec *q) {
   if (q->spec_rank < 0) return -INFINITY;
-  const long long S = std::min<long long>(16384, q->scope_n);
+  const double t_a = now_ms();
+  const long long S = std::min<long long>(4096, q->scope_n);
   const double expect = (double)S * (double)q->k / (double)q->scope_n;
   long long r = q->spec_rank > 0 ? q->spec_rank : (long long)std::ceil(3.0 * expect + 5.0);
   q->spec_rank = (int)std::min<long long>(r, 1 << 30);
@@ -816,32 +880,33 @@ static float speculative_start(apex_library &L, QueryRec *q) {
     q->spec_rank = -1;
     return -INFINITY;
   }
+  // uniform compound ids of the scope: prefix sums over the subset, then a binary search
+  std::vector<long long> pre(q->subset.size() + 1, 0);
+  for (size_t i = 0; i < q->subset.size(); ++i)
+    pre[i + 1] = pre[i] + (L.id_first[q->subset[i] + 1] - L.id_first[q->subset[i]]);
   std::vector<long long> ids(S);
   for (long long i = 0; i < S; ++i) {
-    long long u = (long long)(L.rng() % (unsigned long long)q->scope_n);
-    for (int t : q->subset) {
-      const long long nt = L.id_first[t + 1] - L.id_first[t];
-      if (u < nt) {
-        ids[i] = L.id_first[t] + u;
-        break;
-      }
-      u -= nt;
-    }
+    const long long u = (long long)(L.rng() % (unsigned long long)q->scope_n);
+    const size_t r_i = (size_t)(std::upper_bound(pre.begin(), pre.end(), u) - pre.begin()) - 1;
+    ids[i] = L.id_first[q->subset[r_i]] + (u - pre[r_i]);
   }
+  const double t_b = now_ms();
   const int no = L.n_out;
-  long long *d_ids = nullptr;
-  float *d_out = nullptr;
-  CU(cudaMalloc(&d_ids, sizeof(long long) * S));
-  CU(cudaMalloc(&d_out, sizeof(float) * S * no));
-  CU(cudaMemcpyAsync(d_ids, ids.data(), sizeof(long long) * S, cudaMemcpyHostToDevice, L.st));
+  L.arena_reserve(sizeof(long long) * S + sizeof(float) * S * no + 1024);
+  long long *d_ids = (long long *)L.aget(sizeof(long long) * S);
+  float *d_out = (float *)L.aget(sizeof(float) * S * no);
+  long long *h_ids = (long long *)L.pin(std::max(sizeof(long long) * S, sizeof(float) * S * no));
+  memcpy(h_ids, ids.data(), sizeof(long long) * S);
+  CU(cudaMemcpyAsync(d_ids, h_ids, sizeof(long long) * S, cudaMemcpyHostToDevice, L.st));
   LaunchPlan dummy;
   memset(&dummy, 0, sizeof(dummy));
   CU(apx_launch_fp32(dummy, L.T_, nullptr, d_ids, S, d_out, grid_for(L, (S + APX_TILE - 1) / APX_TILE), L.st));
-  std::vector<float> o(S * no);
-  CU(cudaMemcpyAsync(o.data(), d_out, sizeof(float) * S * no, cudaMemcpyDeviceToHost, L.st));
+  float *h_out = (float *)L.pinned;
+  CU(cudaMemcpyAsync(h_out, d_out, sizeof(float) * S * no, cudaMemcpyDeviceToHost, L.st));
+  const double t_c = now_ms();
   CU(cudaStreamSynchronize(L.st));
-  cudaFree(d_ids);
-  cudaFree(d_out);
+  const double t_d = now_ms();
+  std::vector<float> o(h_out, h_out + S * no);
   std::vector<float> f;
   f.reserve(S);
   for (long long i = 0; i < S; ++i) {
@@ -857,6 +922,8 @@ static float speculative_start(apex_library &L, QueryRec *q) {
   }
   if ((long long)f.size() < r) return -INFINITY;
   std::nth_element(f.begin(), f.begin() + (r - 1), f.end(), std::greater<float>());
+  TRACE("start q%lld: sample %.3f ms, enqueue %.3f ms, gpu wait %.3f ms, host select %.3f ms", (long long)q->id,
+        t_b - t_a, t_c - t_b, t_d - t_c, now_ms() - t_d);
   return f[r - 1];
 }
 
@@ -871,6 +938,35 @@ static void start_query(apex_library &L, QueryRec *q) {
   q->started = true;
 }
 
+static void slot_reserve(apex_library &L, int slot, unsigned cap) {
+  apex_library::SlotBuf &B = L.slotbuf[slot];
+  if (B.cap >= cap) return;
+  if (B.cap) {
+    CU(cudaStreamSynchronize(L.st));
+    cudaFree(B.keys);
+    cudaFree(B.keys2);
+    cudaFree(B.ids);
+    cudaFree(B.ids2);
+    L.query_bytes -= query_bytes_for(B.cap);
+    B = apex_library::SlotBuf();
+  }
+  CU(cudaMalloc(&B.keys, sizeof(float) * cap));
+  CU(cudaMalloc(&B.keys2, sizeof(float) * cap));
+  CU(cudaMalloc(&B.ids, sizeof(long long) * cap));
+  CU(cudaMalloc(&B.ids2, sizeof(long long) * cap));
+  B.cap = cap;
+  L.query_bytes += query_bytes_for(cap);
+}
+
+static void bind_slot(apex_library &L, QueryRec *q) {
+  slot_reserve(L, q->slot, q->cap);
+  apex_library::SlotBuf &B = L.slotbuf[q->slot];
+  q->keys = B.keys;
+  q->keys2 = B.keys2;
+  q->ids = B.ids;
+  q->ids2 = B.ids2;
+}
+
 static bool admit_one(apex_library &L, QueryRec *q) {
   int slot = -1;
   for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
@@ -880,15 +976,13 @@ static bool admit_one(apex_library &L, QueryRec *q) {
     }
   if (slot < 0) return false;
   if (q->cap == 0) q->cap = (unsigned)std::min<long long>(std::max<long long>(1LL << 18, 8 * q->k), 1LL << 30);
-  const size_t need = query_bytes_for(q->cap);
-  if (L.budget && L.bytes + L.query_bytes + need > L.budget) return false;
-  CU(cudaMalloc(&q->keys, sizeof(float) * q->cap));
-  CU(cudaMalloc(&q->keys2, sizeof(float) * q->cap));
-  CU(cudaMalloc(&q->ids, sizeof(long long) * q->cap));
-  CU(cudaMalloc(&q->ids2, sizeof(long long) * q->cap));
-  q->dev_bytes = need;
-  L.query_bytes += need;
+  const unsigned have = L.slotbuf[slot].cap;
+  if (have < q->cap) {
+    const size_t need = query_bytes_for(q->cap) - query_bytes_for(have);
+    if (L.budget && L.bytes + L.query_bytes + need > L.budget) return false;
+  }
   q->slot = slot;
+  bind_slot(L, q);
   L.active[slot] = q;
   q->state = Q_ACTIVE;
   q->t_admit = now_ms();
@@ -917,25 +1011,22 @@ struct DevBuf {
 static bool finalize(apex_library &L, QueryRec *q) {
   const int no = L.n_out;
   const int sl = q->slot;
-  CU(cudaMemcpyAsync(L.d_slot_list, &sl, sizeof(int), cudaMemcpyHostToDevice, L.st));
+  int *pin_sl = (int *)L.pin(sizeof(QuerySlot) + 64);
+  *pin_sl = sl;
+  CU(cudaMemcpyAsync(L.d_slot_list, pin_sl, sizeof(int), cudaMemcpyHostToDevice, L.st));
   CU(apx_launch_slot_select(L.d_slots, L.d_slot_list, 1, 1, L.st));
-  QuerySlot S;
-  CU(cudaMemcpyAsync(&S, L.d_slots + sl, sizeof(S), cudaMemcpyDeviceToHost, L.st));
+  QuerySlot *pS = (QuerySlot *)((char *)L.pinned + 64);
+  CU(cudaMemcpyAsync(pS, L.d_slots + sl, sizeof(QuerySlot), cudaMemcpyDeviceToHost, L.st));
   CU(cudaStreamSynchronize(L.st));
+  const QuerySlot S = *pS;
   const bool spec_bad = std::isfinite(q->tau_spec) && (long long)S.n_sure_above_spec < q->k;
   if (S.overflow || spec_bad) {
     q->stats.n_restarts++;
     if (S.overflow && !spec_bad && std::isfinite(S.tau)) {
       q->tau_spec = S.tau;  // a valid lower bound: k real, surely feasible compounds reach it
     } else if (S.overflow) {
-      free_query_device(L, q);
       q->cap = (unsigned)std::min<unsigned long long>((unsigned long long)q->cap * 4ull, 1ull << 30);
-      q->dev_bytes = query_bytes_for(q->cap);
-      CU(cudaMalloc(&q->keys, sizeof(float) * q->cap));
-      CU(cudaMalloc(&q->keys2, sizeof(float) * q->cap));
-      CU(cudaMalloc(&q->ids, sizeof(long long) * q->cap));
-      CU(cudaMalloc(&q->ids2, sizeof(long long) * q->cap));
-      L.query_bytes += q->dev_bytes;
+      bind_slot(L, q);
       q->tau_spec = -INFINITY;
       q->spec_rank = -1;
     } else {
@@ -958,8 +1049,19 @@ static bool finalize(apex_library &L, QueryRec *q) {
     q->remaining = q->scope_items;
     return false;
   }
-  DevBuf B;
   const long long nc = S.count;
+  {
+    // worst-case scratch of this finalization, reserved before anything is queued on it
+    const size_t ncx = (size_t)std::max<long long>(nc, 1);
+    size_t np2 = 2;
+    while (np2 < ncx) np2 <<= 1;
+    L.arena_reserve(ncx * (4 * L.n_out + 4 + 2 + 8 * L.n_out + 8 + 4 + 8 * L.n_out) + np2 * sizeof(RItem) +
+                    (size_t)q->k * (8 + 4 + 8 * APEX_MAX_SLOTS + 8 + 8 * L.n_out) + 64 * 1024);
+  }
+  struct ArenaBuf {
+    apex_library &L;
+    void *get(size_t n) { return L.aget(n); }
+  } B{L};
   q->stats.n_candidates = nc;
   const long long k = q->k;
   // FP32 rescore of the candidates
@@ -986,9 +1088,10 @@ static bool finalize(apex_library &L, QueryRec *q) {
   float *d_tau = (float *)B.get(sizeof(float));
   int *d_ok = (int *)B.get(sizeof(int));
   CU(apx_launch_kth(f32, sure, nc, k, d_tau, d_ok, L.st));
-  float tau32;
-  CU(cudaMemcpyAsync(&tau32, d_tau, sizeof(float), cudaMemcpyDeviceToHost, L.st));
+  float *pin_f = (float *)L.pin(64);
+  CU(cudaMemcpyAsync(pin_f, d_tau, sizeof(float), cudaMemcpyDeviceToHost, L.st));
   CU(cudaStreamSynchronize(L.st));
+  const float tau32 = *pin_f;
   const float thr = std::isfinite(tau32) ? (float)(tau32 - 2.0 * e32f * 1.0001) : -INFINITY;
   unsigned n_pow2 = 1;
   while (n_pow2 < (unsigned)std::max<long long>(nc, 1)) n_pow2 <<= 1;
@@ -997,9 +1100,10 @@ static bool finalize(apex_library &L, QueryRec *q) {
   unsigned *d_cnt = (unsigned *)B.get(sizeof(unsigned) * 4);
   CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned) * 4, L.st));
   CU(apx_launch_build_r(nc, q->ids, f32, maybe, sure, thr, R, d_cnt, L.st));
-  unsigned nr = 0;
-  CU(cudaMemcpyAsync(&nr, d_cnt, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
+  unsigned *pin_u = (unsigned *)L.pin(64);
+  CU(cudaMemcpyAsync(pin_u, d_cnt, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
   CU(cudaStreamSynchronize(L.st));
+  const unsigned nr = *pin_u;
   unsigned np = 1;
   while (np < std::max(nr, 2u)) np <<= 1;
   double *out64 = (double *)B.get(sizeof(double) * std::max<long long>(nc, 1) * no);
@@ -1011,9 +1115,9 @@ static bool finalize(apex_library &L, QueryRec *q) {
   for (int round = 0; round < 8 && nr > 0; ++round) {
     CU(cudaMemsetAsync(d_cnt + 1, 0, sizeof(unsigned) * 2, L.st));
     CU(apx_launch_collect64(R, nr, ids64, pos64, d_cnt + 1, L.st));
-    unsigned n64 = 0;
-    CU(cudaMemcpyAsync(&n64, d_cnt + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
+    CU(cudaMemcpyAsync(pin_u, d_cnt + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
     CU(cudaStreamSynchronize(L.st));
+    const unsigned n64 = *pin_u;
     if (n64 > 0) {
       CU(apx_launch_fp64(L.T_, ids64, n64, o64, L.st));
       CU(apx_launch_apply64(R, pos64, o64, n64, no, L.d_slots + sl, dlo, dhi, out64, L.st));
@@ -1021,9 +1125,9 @@ static bool finalize(apex_library &L, QueryRec *q) {
     }
     CU(apx_sort_r(R, nr, np, L.st));
     CU(apx_launch_mark(R, nr, (unsigned)std::min<long long>(k + 1, nr), k, tol, d_cnt + 2, L.st));
-    unsigned marked = 0;
-    CU(cudaMemcpyAsync(&marked, d_cnt + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
+    CU(cudaMemcpyAsync(pin_u, d_cnt + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
     CU(cudaStreamSynchronize(L.st));
+    const unsigned marked = *pin_u;
     if (marked == 0) break;
   }
   q->stats.n_rescored_fp64 = n64_total;
@@ -1036,22 +1140,38 @@ static bool finalize(apex_library &L, QueryRec *q) {
   q->r_syn.resize(nf * APEX_MAX_SLOTS);
   q->r_obj.resize(nf);
   q->r_out.resize(nf * no);
+  void *e_ids_base = nullptr, *e_end = nullptr;
+  long long *e_ids = nullptr;
+  int *e_rxn = nullptr;
+  long long *e_syn = nullptr;
+  double *e_obj = nullptr, *e_out = nullptr;
   if (nf > 0) {
-    long long *e_ids = (long long *)B.get(sizeof(long long) * nf);
-    int *e_rxn = (int *)B.get(sizeof(int) * nf);
-    long long *e_syn = (long long *)B.get(sizeof(long long) * nf * APEX_MAX_SLOTS);
-    double *e_obj = (double *)B.get(sizeof(double) * nf);
-    double *e_out = (double *)B.get(sizeof(double) * nf * no);
+    e_ids = (long long *)B.get(sizeof(long long) * nf);
+    e_ids_base = e_ids;
+    e_rxn = (int *)B.get(sizeof(int) * nf);
+    e_syn = (long long *)B.get(sizeof(long long) * nf * APEX_MAX_SLOTS);
+    e_obj = (double *)B.get(sizeof(double) * nf);
+    e_out = (double *)B.get(sizeof(double) * nf * no);
+    e_end = (char *)e_out + sizeof(double) * nf * no;
     CU(apx_launch_emit(R, (unsigned)nf, L.T_, out32, out64, e_ids, e_rxn, e_syn, e_obj, e_out, L.st));
-    CU(cudaMemcpyAsync(q->r_ids.data(), e_ids, sizeof(long long) * nf, cudaMemcpyDeviceToHost, L.st));
-    CU(cudaMemcpyAsync(q->r_rxn.data(), e_rxn, sizeof(int) * nf, cudaMemcpyDeviceToHost, L.st));
-    CU(cudaMemcpyAsync(q->r_syn.data(), e_syn, sizeof(long long) * nf * APEX_MAX_SLOTS, cudaMemcpyDeviceToHost,
-                       L.st));
-    CU(cudaMemcpyAsync(q->r_obj.data(), e_obj, sizeof(double) * nf, cudaMemcpyDeviceToHost, L.st));
-    CU(cudaMemcpyAsync(q->r_out.data(), e_out, sizeof(double) * nf * no, cudaMemcpyDeviceToHost, L.st));
   }
   CU(cudaEventRecord(q->ev1, L.st));
-  CU(cudaStreamSynchronize(L.st));
+  if (nf > 0) {
+    // one contiguous D2H of the five result arrays (they are adjacent in the arena)
+    const size_t row = 8 + 4 + 8 * APEX_MAX_SLOTS + 8 + 8 * (size_t)no;
+    char *h = (char *)L.pin(row * nf + 5 * 256);
+    char *d0 = (char *)e_ids_base;
+    const size_t span = (size_t)((char *)e_end - d0);
+    CU(cudaMemcpyAsync(h, d0, span, cudaMemcpyDeviceToHost, L.st));
+    CU(cudaStreamSynchronize(L.st));
+    memcpy(q->r_ids.data(), h + ((char *)e_ids - d0), sizeof(long long) * nf);
+    memcpy(q->r_rxn.data(), h + ((char *)e_rxn - d0), sizeof(int) * nf);
+    memcpy(q->r_syn.data(), h + ((char *)e_syn - d0), sizeof(long long) * nf * APEX_MAX_SLOTS);
+    memcpy(q->r_obj.data(), h + ((char *)e_obj - d0), sizeof(double) * nf);
+    memcpy(q->r_out.data(), h + ((char *)e_out - d0), sizeof(double) * nf * no);
+  } else {
+    CU(cudaStreamSynchronize(L.st));
+  }
   q->stats.n_feasible_lower = nf;
   return true;
 }
@@ -1118,21 +1238,19 @@ static void pass_step(apex_library &L) {
     QueryRec *q = L.active[s];
     if (q->stats.n_launches == 0 && q->stats.n_restarts == 0) CU(cudaEventRecord(q->ev0, L.st));
   }
-  cudaEvent_t e0, e1;
-  CU(cudaEventCreate(&e0));
-  CU(cudaEventCreate(&e1));
+  cudaEvent_t e0 = L.ev_a, e1 = L.ev_b;
   CU(cudaEventRecord(e0, L.st));
   for (int p = 0; p < 2; ++p) launch_enum(L, pb[p].P, p);
   CU(cudaEventRecord(e1, L.st));
   if (!list.empty()) {
-    CU(cudaMemcpyAsync(L.d_slot_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, L.st));
+    int *hl = (int *)L.pin(sizeof(int) * APEX_MAX_ACTIVE + 64);
+    memcpy(hl, list.data(), sizeof(int) * list.size());
+    CU(cudaMemcpyAsync(L.d_slot_list, hl, sizeof(int) * list.size(), cudaMemcpyHostToDevice, L.st));
     CU(apx_launch_slot_select(L.d_slots, L.d_slot_list, (int)list.size(), 0, L.st));
   }
   check_kernel_status(L);
   float ms = 0;
   CU(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   for (int s : list) {
     QueryRec *q = L.active[s];
     q->remaining -= served[s];
@@ -1206,12 +1324,25 @@ static void worker_main(apex_library *Lp) {
       }
     }
     try {
-      for (QueryRec *q : fresh) start_query(L, q);
-      pass_step(L);
+      for (QueryRec *q : fresh) {
+        const double t0 = now_ms();
+        start_query(L, q);
+        q->stats.host_start_ms += now_ms() - t0;
+      }
+      {
+        const double t0 = now_ms();
+        pass_step(L);
+        const double dt = now_ms() - t0;
+        for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+          if (L.active[s]) L.active[s]->stats.host_pass_ms += dt;
+      }
       for (int s = 0; s < APEX_MAX_ACTIVE; ++s) {
         QueryRec *q = L.active[s];
         if (!q || q->remaining > 0) continue;
-        if (finalize(L, q)) {
+        const double t0 = now_ms();
+        const bool fin = finalize(L, q);
+        q->stats.host_finalize_ms += now_ms() - t0;
+        if (fin) {
           float ms = 0;
           if (cudaEventElapsedTime(&ms, q->ev0, q->ev1) == cudaSuccess) q->stats.gpu_ms = ms;
           std::lock_guard<std::mutex> g(L.mu);

@@ -48,6 +48,7 @@ struct LaunchPlan {
   long long total_items;
   long long seg_first[APX_MAX_SEG + 1];      // prefix of items
   Segment seg[APX_MAX_SEG];
+  unsigned long long qmask_all;              // union of the segments' query masks
   // dump mode
   float *dump;                               // [dump_n x n_out]
   long long *dump_ids;                       // mode 2: [dump_n], -1 = padding row
@@ -150,6 +151,17 @@ __device__ __forceinline__ void apx_apply_queries(QuerySlot *__restrict__ slots,
 
 // Host-side count of kernel launches issued by this library (all launch wrappers add to it).
 void apx_count_launch(long long n = 1);
+
+// Warp-aggregated reservation of slots in an append-only array: every lane of the warp calls
+// it (uniformly); lanes with take = true get distinct positions from *counter.
+__device__ __forceinline__ unsigned apx_warp_reserve(unsigned *counter, bool take) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, take);
+  unsigned base = 0;
+  if (m && lane == (unsigned)(__ffs(m) - 1)) base = atomicAdd(counter, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, m ? __ffs(m) - 1 : 0);
+  return base + __popc(m & ((1u << lane) - 1u));
+}
 
 // Locates item `it` of a launch: segment (binary search) and local item index.
 __device__ __forceinline__ int apx_find_seg(const LaunchPlan &L, long long it) {

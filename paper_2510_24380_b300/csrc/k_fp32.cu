@@ -24,60 +24,94 @@ __device__ __forceinline__ float f32_act(int act, float z) {
   return z;
 }
 
+// Row sources of tile row r: the table rows to sum, validity and global id.
+__device__ __forceinline__ int f32_row_sources(const DevTables &T, int mode, const RxnPlan *rp, long long q0, long long o,
+                                               const long long *ids, long long id0, long long n_ids, int r,
+                                               long long (&rows)[APEX_MAX_SLOTS], bool &valid, long long &id) {
+  int nrows = 0;
+  valid = false;
+  id = -1;
+  if (mode == 0) {
+    const long long q = q0 + r;
+    valid = q < rp->n_inner;
+    if (valid) {
+      long long rem = q;
+      for (int j = rp->n_inner_slots - 1; j >= 0; --j) {
+        const long long sz = rp->inner_size[j];
+        rows[nrows++] = rp->inner_row[j] + rem % sz;
+        rem /= sz;
+      }
+      if (rp->outer_row >= 0) rows[nrows++] = rp->outer_row + o;
+      id = rp->id_first + q * rp->inner_stride + o * rp->outer_stride;
+    }
+  } else {
+    const long long i = id0 + r;
+    valid = i < n_ids;
+    if (valid) {
+      id = ids[i] & APX_ID_MASK;
+      int lo = 0, hi = T.n_rx - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.id_first[mid] <= id) lo = mid; else hi = mid - 1;
+      }
+      const RxnPlan *p = T.rx + lo;
+      long long rem = id - p->id_first;
+      for (int j = p->n_slots - 1; j >= 0; --j) {
+        const long long sz = p->slot_size[j];
+        rows[nrows++] = p->slot_row[j] + rem % sz;
+        rem /= sz;
+      }
+    }
+  }
+  return nrows;
+}
+
 // Writes z_1 (activated unless the head has a single layer) for the tile rows into AT.
-// Each warp builds rows warp, warp + 8, ...; lanes stride over the columns.
+// Each warp builds two rows at a time; lanes stride over the columns (coalesced 128 B loads),
+// and every load of both rows is issued before the sums are formed.
 __device__ void f32_build_layer1(F32Smem &S, const DevTables &T, int mode, const RxnPlan *rp, long long q0, long long o,
                                  const long long *ids, long long id0, long long n_ids, bool *row_valid,
                                  long long *row_id) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int h1 = T.dims[1];
   const bool last = (T.n_layers == 1);
-  for (int r = warp; r < APX_TILE; r += APX_SIMT_THREADS / 32) {
-    long long rows[APEX_MAX_SLOTS];
-    int nrows = 0;
-    bool valid = false;
-    long long id = -1;
-    if (mode == 0) {
-      const long long q = q0 + r;
-      valid = q < rp->n_inner;
-      if (valid) {
-        long long rem = q;
-        for (int j = rp->n_inner_slots - 1; j >= 0; --j) {
-          const long long sz = rp->inner_size[j];
-          rows[nrows++] = rp->inner_row[j] + rem % sz;
-          rem /= sz;
-        }
-        if (rp->outer_row >= 0) rows[nrows++] = rp->outer_row + o;
-        id = rp->id_first + q * rp->inner_stride + o * rp->outer_stride;
-      }
-    } else {
-      const long long i = id0 + r;
-      valid = i < n_ids;
-      if (valid) {
-        id = ids[i] & APX_ID_MASK;
-        int lo = 0, hi = T.n_rx - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (T.id_first[mid] <= id) lo = mid; else hi = mid - 1;
-        }
-        const RxnPlan *p = T.rx + lo;
-        long long rem = id - p->id_first;
-        for (int j = p->n_slots - 1; j >= 0; --j) {
-          const long long sz = p->slot_size[j];
-          rows[nrows++] = p->slot_row[j] + rem % sz;
-          rem /= sz;
-        }
+  for (int r0 = warp * 2; r0 < APX_TILE; r0 += 2 * (APX_SIMT_THREADS / 32)) {
+    long long rows[2][APEX_MAX_SLOTS];
+    int nrows[2];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      bool valid;
+      long long id;
+      nrows[rr] = f32_row_sources(T, mode, rp, q0, o, ids, id0, n_ids, r0 + rr, rows[rr], valid, id);
+      if (lane == 0) {
+        row_valid[r0 + rr] = valid;
+        row_id[r0 + rr] = id;
       }
     }
-    if (lane == 0) {
-      row_valid[r] = valid;
-      row_id[r] = id;
-    }
-    for (int c = lane; c < h1; c += 32) {
-      float z = 0.f;
-      for (int j = 0; j < nrows; ++j) z += __ldg(T.P32 + rows[j] * h1 + c);
-      S.AT[c][r] = last ? z : f32_act(T.act, z);
-    }
+    float z[2][8];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) z[rr][i] = 0.f;
+#pragma unroll
+    for (int j = 0; j < APEX_MAX_SLOTS; ++j)
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr)
+        if (j < nrows[rr]) {
+          const float *src = T.P32 + rows[rr][j] * h1;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int c = lane + 32 * i;
+            if (c < h1) z[rr][i] += __ldg(src + c);
+          }
+        }
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int c = lane + 32 * i;
+        if (c < h1) S.AT[c][r0 + rr] = last ? z[rr][i] : f32_act(T.act, z[rr][i]);
+      }
   }
 }
 
@@ -114,7 +148,13 @@ __device__ void f32_layer(F32Smem &S, const DevTables &T, int l) {
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       float w[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) w[j] = S.Wc[buf][kk][min(cg + 16 * j, 255)];
+      for (int jq = 0; jq < 4; ++jq) {  // thread cg owns columns 64 jq + 4 cg + e (conflict-free 16-byte reads)
+        const float4 w4 = *reinterpret_cast<const float4 *>(&S.Wc[buf][kk][64 * jq + 4 * cg]);
+        w[4 * jq + 0] = w4.x;
+        w[4 * jq + 1] = w4.y;
+        w[4 * jq + 2] = w4.z;
+        w[4 * jq + 3] = w4.w;
+      }
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -125,7 +165,7 @@ __device__ void f32_layer(F32Smem &S, const DevTables &T, int l) {
   // every thread has finished reading AT: overwrite it with this layer's output
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    const int n = cg + 16 * j;
+    const int n = 64 * (j >> 2) + 4 * cg + (j & 3);
     if (n < N) {
       const float bn = __ldg(B + n);
 #pragma unroll

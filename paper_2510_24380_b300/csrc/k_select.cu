@@ -26,7 +26,9 @@ struct SelSrc {
 
 __device__ bool block_kth_largest(const SelSrc &src, long long n, long long k, unsigned *out_bits,
                                   unsigned long long *out_included) {
-  __shared__ unsigned long long hist[256];
+  // Keys of a top-k buffer share their leading bits, so many lanes hit the same histogram bin:
+  // lanes with equal digits are merged first (match.any) and one lane adds the group's count.
+  __shared__ unsigned hist[256];
   __shared__ unsigned prefix_s;
   __shared__ long long kk_s;
   __shared__ unsigned long long total_s;
@@ -34,14 +36,21 @@ __device__ bool block_kth_largest(const SelSrc &src, long long n, long long k, u
     prefix_s = 0;
     kk_s = k;
   }
-  unsigned prefix = 0, mask = 0;
+  const unsigned lane = threadIdx.x & 31;
+  const long long warp_base = (long long)(threadIdx.x >> 5) * 32;
+  const long long stride = (long long)blockDim.x;
+  unsigned mask = 0;
   for (int pass = 3; pass >= 0; --pass) {
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    prefix = prefix_s;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-      unsigned b;
-      if (src.get(i, b) && ((b & mask) == prefix)) atomicAdd(&hist[(b >> (8 * pass)) & 255u], 1ull);
+    const unsigned prefix = prefix_s;
+    for (long long b = warp_base; b < n; b += stride) {   // uniform trip count within a warp
+      const long long i = b + lane;
+      unsigned bits = 0;
+      const bool use = (i < n) && src.get(i, bits) && ((bits & mask) == prefix);
+      const unsigned dig = use ? ((bits >> (8 * pass)) & 255u) : 256u;
+      const unsigned grp = __match_any_sync(0xffffffffu, dig);
+      if (use && (int)lane == __ffs(grp) - 1) atomicAdd(&hist[dig], (unsigned)__popc(grp));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -50,7 +59,7 @@ __device__ bool block_kth_largest(const SelSrc &src, long long n, long long k, u
         for (int d = 0; d < 256; ++d) t += hist[d];
         total_s = t;
       }
-      long long kk = kk_s;
+      const long long kk = kk_s;
       unsigned long long cum = 0;
       int dsel = 0;
       for (int d = 255; d >= 0; --d) {
@@ -101,12 +110,25 @@ __global__ void __launch_bounds__(SEL_THREADS) k_slot_select(QuerySlot *slots, c
   __syncthreads();
   const float admit = Q->admit;
   const float spec = Q->tau_spec;
-  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
-    const float key = Q->keys[i];
-    const long long id = Q->ids[i];
-    if (mode == 1 && !(id & APX_UNSURE_BIT) && key >= spec) atomicAdd(&n_spec, 1u);
-    if (key >= admit) {
-      const unsigned p = atomicAdd(&kept, 1u);
+  const unsigned lane = threadIdx.x & 31;
+  for (unsigned b = (threadIdx.x >> 5) * 32; b < n; b += blockDim.x) {
+    const unsigned i = b + lane;
+    float key = 0.f;
+    long long id = 0;
+    if (i < n) {
+      key = Q->keys[i];
+      id = Q->ids[i];
+    }
+    const bool spec_hit = (i < n) && mode == 1 && !(id & APX_UNSURE_BIT) && key >= spec;
+    const unsigned sm = __ballot_sync(0xffffffffu, spec_hit);
+    if (lane == 0 && sm) atomicAdd(&n_spec, (unsigned)__popc(sm));
+    const bool keep = (i < n) && key >= admit;
+    const unsigned km = __ballot_sync(0xffffffffu, keep);
+    unsigned base = 0;
+    if (lane == 0 && km) base = atomicAdd(&kept, (unsigned)__popc(km));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) {
+      const unsigned p = base + __popc(km & ((1u << lane) - 1u));
       Q->keys2[p] = key;
       Q->ids2[p] = id;
     }
@@ -170,9 +192,12 @@ __global__ void __launch_bounds__(SEL_THREADS) k_kth(const float *keys, const un
 // R = {maybe && f32 >= thr}; need64 = !sure
 __global__ void k_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
                           const unsigned char *sure, float thr, RItem *R, unsigned *n_r) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    if (maybe[i] && f32[i] >= thr) {
-      const unsigned p = atomicAdd(n_r, 1u);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long b = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u); b < n; b += stride) {
+    const long long i = b + (threadIdx.x & 31);
+    const bool take = (i < n) && maybe[i] && f32[i] >= thr;
+    const unsigned p = apx_warp_reserve(n_r, take);
+    if (take) {
       RItem it;
       it.s = (double)f32[i];
       it.id = cand_ids[i] & APX_ID_MASK;
@@ -188,9 +213,11 @@ __global__ void k_build_r(long long n, const long long *cand_ids, const float *f
 
 // list of R positions whose FP64 rescore is pending
 __global__ void k_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64) {
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (R[i].alive && R[i].need64 && !R[i].is64) {
-      const unsigned p = atomicAdd(n64, 1u);
+  for (unsigned b = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < n; b += gridDim.x * blockDim.x) {
+    const unsigned i = b + (threadIdx.x & 31);
+    const bool take = (i < n) && R[i].alive && R[i].need64 && !R[i].is64;
+    const unsigned p = apx_warp_reserve(n64, take);
+    if (take) {
       ids64[p] = R[i].id;
       pos64[p] = (int)i;
     }
@@ -241,15 +268,15 @@ __global__ void k_bitonic_global(RItem *R, unsigned n, unsigned j, unsigned kk) 
 }
 
 #define BITONIC_SMEM 2048
-__global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned n, unsigned kk_from, unsigned kk_to) {
-  // handles every (kk, j) step with j < BITONIC_SMEM inside blocks of BITONIC_SMEM elements
+// every (kk, j) step with j < block inside blocks of `block` (power of two <= BITONIC_SMEM) elements
+__global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned block, unsigned kk_from, unsigned kk_to) {
   __shared__ RItem s[BITONIC_SMEM];
-  const unsigned base = blockIdx.x * BITONIC_SMEM;
-  for (unsigned t = threadIdx.x; t < BITONIC_SMEM; t += blockDim.x) s[t] = R[base + t];
+  const unsigned base = blockIdx.x * block;
+  for (unsigned t = threadIdx.x; t < block; t += blockDim.x) s[t] = R[base + t];
   __syncthreads();
   for (unsigned kk = kk_from; kk <= kk_to; kk <<= 1) {
-    for (unsigned j = min(kk >> 1, (unsigned)BITONIC_SMEM >> 1); j > 0; j >>= 1) {
-      for (unsigned t = threadIdx.x; t < BITONIC_SMEM; t += blockDim.x) {
+    for (unsigned j = min(kk >> 1, block >> 1); j > 0; j >>= 1) {
+      for (unsigned t = threadIdx.x; t < block; t += blockDim.x) {
         const unsigned l = t ^ j;
         if (l > t) {
           const unsigned gi = base + t;
@@ -265,7 +292,7 @@ __global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned n, u
       __syncthreads();
     }
   }
-  for (unsigned t = threadIdx.x; t < BITONIC_SMEM; t += blockDim.x) R[base + t] = s[t];
+  for (unsigned t = threadIdx.x; t < block; t += blockDim.x) R[base + t] = s[t];
 }
 
 __global__ void k_pad_r(RItem *R, unsigned from, unsigned to) {
@@ -282,30 +309,28 @@ __global__ void k_pad_r(RItem *R, unsigned from, unsigned to) {
   }
 }
 
-// Sorts R[0, n_pow2) (n_pow2 a power of two >= BITONIC_SMEM or the padded size).
+// Sorts R[0, n_pow2) (n_pow2 a power of two) into (alive, s desc, id asc) order.
 cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st) {
   if (n_pow2 < 2) return cudaSuccess;
-  apx_count_launch();
-  k_pad_r<<<64, 256, 0, st>>>(R, n_used, n_pow2);
+  if (n_used < n_pow2) {
+    apx_count_launch();
+    k_pad_r<<<64, 256, 0, st>>>(R, n_used, n_pow2);
+  }
   if (n_pow2 <= BITONIC_SMEM) {
-    // small: global steps only (cheap at this size)
-    for (unsigned kk = 2; kk <= n_pow2; kk <<= 1)
-      for (unsigned j = kk >> 1; j > 0; j >>= 1) {
-        apx_count_launch();
-        k_bitonic_global<<<(n_pow2 + 255) / 256, 256, 0, st>>>(R, n_pow2, j, kk);
-      }
+    apx_count_launch();
+    k_bitonic_shared<<<1, 1024, 0, st>>>(R, n_pow2, 2, n_pow2);
     return cudaGetLastError();
   }
   const unsigned nb = n_pow2 / BITONIC_SMEM;
   apx_count_launch();
-  k_bitonic_shared<<<nb, 1024, 0, st>>>(R, n_pow2, 2, BITONIC_SMEM);
+  k_bitonic_shared<<<nb, 1024, 0, st>>>(R, BITONIC_SMEM, 2, BITONIC_SMEM);
   for (unsigned kk = BITONIC_SMEM * 2; kk <= n_pow2; kk <<= 1) {
     for (unsigned j = kk >> 1; j >= BITONIC_SMEM; j >>= 1) {
       apx_count_launch();
       k_bitonic_global<<<std::min<unsigned>(nb * 8, 148u * 16u), 256, 0, st>>>(R, n_pow2, j, kk);
     }
     apx_count_launch();
-    k_bitonic_shared<<<nb, 1024, 0, st>>>(R, n_pow2, kk, kk);
+    k_bitonic_shared<<<nb, 1024, 0, st>>>(R, BITONIC_SMEM, kk, kk);
   }
   return cudaGetLastError();
 }

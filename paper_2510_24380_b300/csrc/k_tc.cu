@@ -14,12 +14,15 @@
 // fma .bf16x2: 1.5 issue slots and one MUFU element per activation); the 1/2 is folded into P
 // (layer 1) and into the W_2 image and b_2 (layer 2), all exact in binary.
 //
-// Warp roles (416 threads, one CTA per SM):
-//   warps 0-3   epilogue (warp w owns TMEM lanes 32w..32w+31 = tile rows)
-//   warps 4-11  producers: thread (h, m) builds row m, K-half h (128 columns) of a_1
+// Warp roles (448 threads, one CTA per SM):
+//   warps 0-3   query warps: D3 of each tile -> outputs -> queries (warp w reads TMEM lanes 32w..)
+//   warps 4-11  math warps, thread (h, m) = column half h, tile row m: per step, layer 1 of the
+//               next tile (K half h of a_1) and then the layer-2 activation of the previous tile
+//               (accumulator columns [128h, 128h + 128), rows of its TMEM lane quarter)
 //   warp 12     TMEM allocation; lane 0 issues every MMA and commit
-// TMEM: 512 columns = two 256-column accumulators (double buffer); a_2 overwrites columns
-// [0, 128) of its buffer, D3 uses columns [128, 144).
+//   warp 13     lane 0 bulk-copies (TMA) each tile's outer synthon row into a 4-slot ring
+// TMEM: 512 columns = two 256-column accumulators (double buffer); a_2 of half h overwrites
+// columns [128h, 128h + 64) of its buffer, D3 uses columns [64, 80).
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel records
 // APX_ERR_TIMEOUT in the status word, every role leaves its loop, and TMEM is released.
 #include <cuda_bf16.h>
@@ -29,20 +32,37 @@
 #define TC_EPI_WARPS 4
 #define TC_PROD_WARPS 8
 #define TC_MMA_WARP (TC_EPI_WARPS + TC_PROD_WARPS)
-#define TC_THREADS ((TC_MMA_WARP + 1) * 32)
+#define TC_LOAD_WARP (TC_MMA_WARP + 1)
+#define TC_THREADS ((TC_LOAD_WARP + 1) * 32)
+#define TC_OROW_SLOTS 4
+#define TC_D3_COL 64u   // layer-3 accumulator columns within a 256-column buffer (free after layer 2)
+
+// Query parameters cached in shared memory for the whole launch (one entry per query slot).
+struct SlotParams {
+  float w[APEX_MAX_OBJECTIVES];
+  float lo_w[APEX_MAX_CONSTRAINTS], hi_w[APEX_MAX_CONSTRAINTS];
+  float lo_s[APEX_MAX_CONSTRAINTS], hi_s[APEX_MAX_CONSTRAINTS];
+  float admit;
+  int n_obj, n_cons, pad;
+  unsigned char cons_idx[APEX_MAX_CONSTRAINTS];
+};
 
 // shared-memory map (offsets from a 1024-byte aligned base)
 #define TC_OFF_W2 0u
 #define TC_OFF_W3 131072u
 #define TC_OFF_A1 139264u                      // 4 stages x 16 KB (one 64-wide K chunk each)
 #define TC_STAGE_BYTES 16384u
-#define TC_OFF_B2 (TC_OFF_A1 + 4u * TC_STAGE_BYTES)   // 256 floats
-#define TC_OFF_B3 (TC_OFF_B2 + 1024u)                 // 16 floats
-#define TC_OFF_BAR (TC_OFF_B3 + 64u)                  // mbarriers
-#define TC_NBAR 18
+#define TC_OFF_OROW (TC_OFF_A1 + 4u * TC_STAGE_BYTES)        // outer-row ring: 4 x 512 B (bf16 x 256)
+#define TC_OFF_B2 (TC_OFF_OROW + TC_OROW_SLOTS * 512u)       // 256 floats
+#define TC_OFF_B3 (TC_OFF_B2 + 1024u)                         // 16 floats
+#define TC_OFF_QP (TC_OFF_B3 + 64u)                           // APEX_MAX_ACTIVE x SlotParams
+#define TC_OFF_BAR (TC_OFF_QP + (uint32_t)(APEX_MAX_ACTIVE * sizeof(SlotParams)))
+#define TC_NBAR 26
 #define TC_OFF_MISC (TC_OFF_BAR + 8u * TC_NBAR)
 #define TC_SMEM_BYTES (TC_OFF_MISC + 64u + 1024u)    // + alignment slack
 #define TC_W_BYTES 139264u
+static_assert(sizeof(SlotParams) == 352, "SlotParams layout");
+static_assert(TC_SMEM_BYTES <= 232448, "shared memory budget");
 
 // barrier indices
 #define B_FULL(s) (s)
@@ -53,6 +73,8 @@
 #define B_D3FULL(b) (14 + (b))
 #define B_W 16
 #define B_DRAIN 17
+#define B_OFULL(r) (18 + (r))
+#define B_OEMPTY(r) (22 + (r))
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -162,7 +184,31 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
       "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
       "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]));
 }
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// wait::ld that also ties the loaded registers to the wait, so no use of them is scheduled
+// before it
+__device__ __forceinline__ void tmem_wait_ld_dep(uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]), "+r"(v[8]),
+        "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]),
+        "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]),
+        "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+      :
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld_dep16(uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]), "+r"(v[8]),
+        "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+      :
+      : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float tanh_fast(float x) {
@@ -215,6 +261,42 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
+// Sec. 3 / Eq. apex_topk per compound (one row per lane, all 32 lanes call it): objective,
+// admission threshold, widened box (admission) and shrunk box ("sure"), then a warp-aggregated
+// append to the query's candidate buffer in global memory. Parameters come from shared memory.
+__device__ __forceinline__ void tc_apply_queries(const SlotParams *qp, QuerySlot *slots, unsigned long long qmask,
+                                                 bool valid, long long id, const float (&o)[16]) {
+  const unsigned lane = threadIdx.x & 31;
+  while (qmask) {
+    const int s = __ffsll((long long)qmask) - 1;
+    qmask &= qmask - 1;
+    const SlotParams &P = qp[s];
+    const int n_obj = P.n_obj;
+    float f = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < n_obj) f = fmaf(P.w[j], o[j], f);
+    bool pass = valid && (f >= P.admit);
+    if (__ballot_sync(0xffffffffu, pass) == 0u) continue;
+    bool sure = true;
+    for (int i = 0; i < P.n_cons; ++i) {
+      const float v = apx_sel<16>(o, P.cons_idx[i]);
+      pass = pass && (v >= P.lo_w[i]) && (v <= P.hi_w[i]);
+      sure = sure && (v >= P.lo_s[i]) && (v <= P.hi_s[i]);
+    }
+    QuerySlot *Q = slots + s;
+    const unsigned pos = apx_warp_reserve(&Q->count, pass);
+    if (pass) {
+      if (pos < Q->cap) {
+        Q->keys[pos] = f;
+        Q->ids[pos] = id | (sure ? 0LL : APX_UNSURE_BIT);
+      } else {
+        atomicExch(&Q->overflow, 1u);
+      }
+    }
+  }
+}
+
 struct TcItem {
   const RxnPlan *rp;
   long long q0, o_begin, o_end;
@@ -256,11 +338,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(bar(B_D2FULL(b)), 1);
       mbar_init(bar(B_D2EMPTY(b)), TC_EPI_WARPS);
-      mbar_init(bar(B_A2FULL(b)), TC_EPI_WARPS);
+      mbar_init(bar(B_A2FULL(b)), TC_PROD_WARPS);
       mbar_init(bar(B_D3FULL(b)), 1);
     }
     mbar_init(bar(B_W), 1);
     mbar_init(bar(B_DRAIN), 1);
+    for (int r = 0; r < TC_OROW_SLOTS; ++r) {
+      mbar_init(bar(B_OFULL(r)), 1);
+      mbar_init(bar(B_OEMPTY(r)), TC_PROD_WARPS);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -281,6 +367,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   for (int i = tid; i < 256; i += TC_THREADS) b2s[i] = T.b2s[i];
   for (int i = tid; i < 16; i += TC_THREADS) b3s[i] = T.b3[i];
+  SlotParams *qp = reinterpret_cast<SlotParams *>(sm + TC_OFF_QP);
+  if (L.mode == 0 && slots) {
+    for (int s = warp; s < APEX_MAX_ACTIVE; s += TC_THREADS / 32) {
+      if (!((L.qmask_all >> s) & 1ull)) continue;
+      const QuerySlot *Q = slots + s;
+      SlotParams &P = qp[s];
+      if (lane < APEX_MAX_OBJECTIVES) P.w[lane] = Q->w[lane];
+      if (lane < APEX_MAX_CONSTRAINTS) {
+        P.lo_w[lane] = Q->lo_w[lane];
+        P.hi_w[lane] = Q->hi_w[lane];
+        P.lo_s[lane] = Q->lo_s[lane];
+        P.hi_s[lane] = Q->hi_s[lane];
+        P.cons_idx[lane] = (unsigned char)Q->cons_idx[lane];
+      }
+      if (lane == 0) {
+        P.admit = Q->admit;
+        P.n_obj = Q->n_obj;
+        P.n_cons = Q->n_cons;
+      }
+    }
+  }
   if (warp == TC_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -291,55 +398,73 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp >= TC_EPI_WARPS && warp < TC_MMA_WARP) {
-    // ------------------------------------------------------------ producers
+    // ------------------------------------------------------------ math warps
+    // Thread (h, m): tile row m (= TMEM lane; warp % 4 is the row quarter) and column half h.
+    // Step s: produce a_1 of tile s (layer 1, K columns [128h, 128h + 128)) into the shared
+    // stages, then activate layer 2 of tile s - 1 (accumulator columns [128h, 128h + 128)),
+    // writing a_2 back in place. Producing first lets layer 2 of tile s run on the tensor pipe
+    // while layer 2 of tile s - 1 is activated.
     const int p = tid - TC_EPI_WARPS * 32;
     const int h = p >> 7, m = p & 127;
     const uint32_t row_off = (uint32_t)(m >> 3) * 1024u + (uint32_t)(m & 7) * 128u;
-    long long j = 0;
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    uint32_t R[64];  // resident inner sum of the producing item, packed bf16 pairs
+    long long it = blockIdx.x, o = 0, o_end = 0;
+    const RxnPlan *rp = nullptr;
+    bool more = it < L.total_items;
+    bool need_r = more;
     bool ok = true;
-    for (long long it = blockIdx.x; ok && it < L.total_items; it += gridDim.x) {
-      const TcItem I = tc_item(L, T, it);
-      const RxnPlan *rp = I.rp;
-      // resident inner sum R (128 columns of this K-half) as packed bf16 pairs
-      uint32_t R[64];
-      const long long q = I.q0 + m;
-      if (q < rp->n_inner) {
-        long long rows[APEX_MAX_SLOTS];
-        long long rem = q;
-        const int ni = rp->n_inner_slots;
-        for (int s = ni - 1; s >= 0; --s) {
-          rows[s] = rp->inner_row[s] + rem % rp->inner_size[s];
-          rem /= rp->inner_size[s];
-        }
+    for (long long s = 0; ok; ++s) {
+      const bool produce = more;
+      if (produce) {
+        if (need_r) {
+          const TcItem I = tc_item(L, T, it);
+          rp = I.rp;
+          o = I.o_begin;
+          o_end = I.o_end;
+          const long long q = I.q0 + m;
+          if (q < rp->n_inner) {
+            long long rows[APEX_MAX_SLOTS];
+            long long rem = q;
+            const int ni = rp->n_inner_slots;
+            for (int sl = ni - 1; sl >= 0; --sl) {
+              rows[sl] = rp->inner_row[sl] + rem % rp->inner_size[sl];
+              rem /= rp->inner_size[sl];
+            }
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          for (int s = 0; s < ni; ++s) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(T.P16 + rows[s] * 256 + h * 128 + c * 8));
-            acc[0] += bf_lo(v.x); acc[1] += bf_hi(v.x); acc[2] += bf_lo(v.y); acc[3] += bf_hi(v.y);
-            acc[4] += bf_lo(v.z); acc[5] += bf_hi(v.z); acc[6] += bf_lo(v.w); acc[7] += bf_hi(v.w);
+            for (int c = 0; c < 16; ++c) {
+              float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+              for (int sl = 0; sl < ni; ++sl) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(T.P16 + rows[sl] * 256 + h * 128 + c * 8));
+                acc[0] += bf_lo(v.x); acc[1] += bf_hi(v.x); acc[2] += bf_lo(v.y); acc[3] += bf_hi(v.y);
+                acc[4] += bf_lo(v.z); acc[5] += bf_hi(v.z); acc[6] += bf_lo(v.w); acc[7] += bf_hi(v.w);
+              }
+              R[c * 4 + 0] = pack_bf16(acc[0], acc[1]);
+              R[c * 4 + 1] = pack_bf16(acc[2], acc[3]);
+              R[c * 4 + 2] = pack_bf16(acc[4], acc[5]);
+              R[c * 4 + 3] = pack_bf16(acc[6], acc[7]);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) R[c] = 0u;
           }
-          R[c * 4 + 0] = pack_bf16(acc[0], acc[1]);
-          R[c * 4 + 1] = pack_bf16(acc[2], acc[3]);
-          R[c * 4 + 2] = pack_bf16(acc[4], acc[5]);
-          R[c * 4 + 3] = pack_bf16(acc[6], acc[7]);
+          need_r = false;
         }
-      } else {
-#pragma unroll
-        for (int c = 0; c < 64; ++c) R[c] = 0u;
-      }
-      for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
-        const unsigned short *prow = rp->outer_row >= 0 ? T.P16 + (rp->outer_row + o) * 256 + h * 128 : nullptr;
+        // ---- layer 1 of tile s
+        const int rs = (int)(s & (TC_OROW_SLOTS - 1));
+        const bool has_outer = rp->outer_row >= 0;
+        ok = ok && mbar_wait(bar(B_OFULL(rs)), (uint32_t)((s / TC_OROW_SLOTS) & 1), abort_flag, err);
+        const unsigned char *prow = sm + TC_OFF_OROW + (uint32_t)rs * 512u + (uint32_t)h * 256u;
 #pragma unroll
         for (int c2 = 0; c2 < 2; ++c2) {
           const int kc = 2 * h + c2;
-          ok = ok && mbar_wait(bar(B_EMPTY(kc)), (uint32_t)((j & 1) ^ 1), abort_flag, err);
+          ok = ok && mbar_wait(bar(B_EMPTY(kc)), (uint32_t)((s & 1) ^ 1), abort_flag, err);
           if (ok) {
             unsigned char *stage = sm + TC_OFF_A1 + (uint32_t)kc * TC_STAGE_BYTES + row_off;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               uint4 pv = make_uint4(0u, 0u, 0u, 0u);
-              if (prow) pv = __ldg(reinterpret_cast<const uint4 *>(prow + c2 * 64 + c * 8));
+              if (has_outer) pv = *reinterpret_cast<const uint4 *>(prow + c2 * 128 + c * 16);
               const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
               uint32_t out[4];
 #pragma unroll
@@ -352,9 +477,79 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (lane == 0) mbar_arrive(bar(B_FULL(kc)));
           }
         }
-        if (!ok) break;
+        __syncwarp();
+        if (ok && lane == 0) mbar_arrive(bar(B_OEMPTY(rs)));
+        if (++o >= o_end) {
+          it += gridDim.x;
+          more = it < L.total_items;
+          need_r = more;
+        }
+      }
+      // ---- layer-2 activation of tile s - 1 (columns [128h, 128h + 128) of its accumulator)
+      if (ok && s >= 1) {
+        const long long jj = s - 1;
+        const int buf = (int)(jj & 1);
+        ok = mbar_wait(bar(B_D2FULL(buf)), (uint32_t)((jj >> 1) & 1), abort_flag, err);
+        if (ok) {
+          tc_fence_after();
+          const uint32_t col = lane_base + (uint32_t)buf * 256u + (uint32_t)h * 128u;
+          const float *bh = b2s + h * 128;
+          // 16 accumulator columns at a time -> 8 packed bf16 pairs written over columns already
+          // read (a_2 of this half lands in its first 64 columns); one load of lookahead
+          uint32_t va[16], vb[16];
+          tmem_ld16(col, va);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            uint32_t(&v)[16] = (c & 1) ? vb : va;
+            uint32_t(&vn)[16] = (c & 1) ? va : vb;
+            tmem_wait_ld_dep16(v);
+            if (c + 1 < 8) tmem_ld16(col + (uint32_t)(c + 1) * 16u, vn);
+            uint32_t pk[8];
+#pragma unroll
+            for (int e4 = 0; e4 < 4; ++e4) {
+              const float4 bb = *reinterpret_cast<const float4 *>(bh + c * 16 + 4 * e4);
+              pk[2 * e4] = act_bf2<ACT>(pack_bf16(__uint_as_float(v[4 * e4]) + bb.x, __uint_as_float(v[4 * e4 + 1]) + bb.y));
+              pk[2 * e4 + 1] =
+                  act_bf2<ACT>(pack_bf16(__uint_as_float(v[4 * e4 + 2]) + bb.z, __uint_as_float(v[4 * e4 + 3]) + bb.w));
+            }
+            tmem_st8(col + (uint32_t)c * 8u, pk);
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(B_A2FULL(buf)));
+        }
+      }
+      if (!produce) break;
+    }
+  } else if (warp == TC_LOAD_WARP) {
+    // ------------------------------------------------------------ outer-row loader (bulk TMA)
+    if (lane == 0) {
+      long long j = 0;
+      bool ok = true;
+      for (long long it = blockIdx.x; ok && it < L.total_items; it += gridDim.x) {
+        const TcItem I = tc_item(L, T, it);
+        const RxnPlan *rp = I.rp;
+        for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
+          const int rs = (int)(j & (TC_OROW_SLOTS - 1));
+          if (!mbar_wait(bar(B_OEMPTY(rs)), (uint32_t)(((j / TC_OROW_SLOTS) & 1) ^ 1), abort_flag, err)) {
+            ok = false;
+            break;
+          }
+          if (rp->outer_row >= 0) {
+            mbar_expect_tx(bar(B_OFULL(rs)), 512u);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 512, [%2];" ::"r"(
+                    sbase + TC_OFF_OROW + (uint32_t)rs * 512u),
+                "l"(T.P16 + (rp->outer_row + o) * 256), "r"(bar(B_OFULL(rs)))
+                : "memory");
+          } else {
+            mbar_arrive(bar(B_OFULL(rs)));
+          }
+        }
       }
     }
+    __syncwarp();
   } else if (warp == TC_MMA_WARP) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
@@ -363,29 +558,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         constexpr uint32_t ID2 = idesc_bf16(128, 256);
         constexpr uint32_t ID3 = idesc_bf16(128, 16);
         const uint32_t a1 = sbase + TC_OFF_A1, w2 = sbase + TC_OFF_W2, w3 = sbase + TC_OFF_W3;
-        auto issue_l3 = [&](long long jj) -> bool {
+        auto issue_l3 = [&](long long jj) {
           const int bb = (int)(jj & 1);
-          if (!mbar_wait(bar(B_A2FULL(bb)), (uint32_t)((jj >> 1) & 1), abort_flag, err)) return false;
           tc_fence_after();
           const uint32_t dcol = tmem + (uint32_t)bb * 256u;
 #pragma unroll 1
-          for (int ks = 0; ks < 16; ++ks)
-            mma_ts(dcol + 128u, dcol + (uint32_t)ks * 8u, sw128_desc(w3 + (uint32_t)(ks >> 2) * 2048u + (uint32_t)(ks & 3) * 32u),
-                   ID3, ks > 0);
+          for (int ks = 0; ks < 16; ++ks)  // K block ks of a_2 lives in half ks / 8 of the buffer
+            mma_ts(dcol + TC_D3_COL, dcol + (uint32_t)(ks >> 3) * 128u + (uint32_t)(ks & 7) * 8u,
+                   sw128_desc(w3 + (uint32_t)(ks >> 2) * 2048u + (uint32_t)(ks & 3) * 32u), ID3, ks > 0);
           mma_commit(bar(B_D3FULL(bb)));
-          return true;
         };
         long long j = 0;
         bool ok = true;
+        long long l3_next = 0;  // next tile whose layer 3 is still to be issued
+        // issue L3 of tile l3_next if its a_2 is ready (non-blocking); returns false on abort
+        auto poll_l3 = [&](long long upto) {
+          if (l3_next < upto && mbar_try(bar(B_A2FULL((int)(l3_next & 1))), (uint32_t)((l3_next >> 1) & 1))) {
+            issue_l3(l3_next);
+            ++l3_next;
+          }
+        };
+        // waits for a barrier phase while issuing ready layer-3 work; bounded like mbar_wait
+        auto wait_poll = [&](uint32_t b, uint32_t parity, long long upto) -> bool {
+          const unsigned long long t0 = globaltimer();
+          for (unsigned it2 = 0;; ++it2) {
+            if (mbar_try(b, parity)) return true;
+            poll_l3(upto);
+            if ((it2 & 255u) == 255u) {
+              if (*abort_flag) return false;
+              if (globaltimer() - t0 > 2000000000ull) {
+                *abort_flag = 1;
+                atomicExch(err, APX_ERR_TIMEOUT);
+                return false;
+              }
+            }
+          }
+        };
         for (long long it = blockIdx.x; ok && it < L.total_items; it += gridDim.x) {
           const TcItem I = tc_item(L, T, it);
           for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
             const int buf = (int)(j & 1);
-            if (!mbar_wait(bar(B_D2EMPTY(buf)), (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
+            if (!wait_poll(bar(B_D2EMPTY(buf)), (uint32_t)(((j >> 1) & 1) ^ 1), j)) { ok = false; break; }
             tc_fence_after();
             const uint32_t d2 = tmem + (uint32_t)buf * 256u;
             for (int kc = 0; kc < 4; ++kc) {
-              if (!mbar_wait(bar(B_FULL(kc)), (uint32_t)(j & 1), abort_flag, err)) { ok = false; break; }
+              if (!wait_poll(bar(B_FULL(kc)), (uint32_t)(j & 1), j)) { ok = false; break; }
               tc_fence_after();
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks)
@@ -395,15 +612,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             if (!ok) break;
             mma_commit(bar(B_D2FULL(buf)));
-            if (j >= 1 && !issue_l3(j - 1)) { ok = false; break; }
           }
         }
-        if (ok && j >= 1) issue_l3(j - 1);
+        // remaining layer-3 work
+        while (ok && l3_next < j) {
+          if (!mbar_wait(bar(B_A2FULL((int)(l3_next & 1))), (uint32_t)((l3_next >> 1) & 1), abort_flag, err)) break;
+          issue_l3(l3_next);
+          ++l3_next;
+        }
       }
     }
     __syncwarp();
   } else {
-    // ------------------------------------------------------------ epilogue (warps 0-3)
+    // ------------------------------------------------------------ query warps (0-3)
+    // read the head outputs of each tile (D3), release its accumulator buffer, apply the queries
     const int r = tid;  // tile row == TMEM lane
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     long long j = 0;
@@ -415,34 +637,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const bool valid = q < rp->n_inner;
       for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
         const int buf = (int)(j & 1);
-        const uint32_t par = (uint32_t)((j >> 1) & 1);
-        if (!mbar_wait(bar(B_D2FULL(buf)), par, abort_flag, err)) { ok = false; break; }
-        tc_fence_after();
-        const uint32_t col = lane_base + (uint32_t)buf * 256u;
-#pragma unroll 1
-        for (int c = 0; c < 8; ++c) {
-          // 32 accumulator columns -> 16 packed bf16 pairs written over columns already read
-          uint32_t v[32];
-          tmem_ld32(col + (uint32_t)c * 32u, v);
-          tmem_wait_ld();
-          uint32_t pk[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const float h0 = __uint_as_float(v[2 * e]) + b2s[c * 32 + 2 * e];
-            const float h1 = __uint_as_float(v[2 * e + 1]) + b2s[c * 32 + 2 * e + 1];
-            pk[e] = act_bf2<ACT>(pack_bf16(h0, h1));
-          }
-          tmem_st16(col + (uint32_t)c * 16u, pk);
-        }
-        tmem_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar(B_A2FULL(buf)));
-        if (!mbar_wait(bar(B_D3FULL(buf)), par, abort_flag, err)) { ok = false; break; }
+        if (!mbar_wait(bar(B_D3FULL(buf)), (uint32_t)((j >> 1) & 1), abort_flag, err)) { ok = false; break; }
         tc_fence_after();
         uint32_t ov[16];
-        tmem_ld16(col + 128u, ov);
-        tmem_wait_ld();
+        tmem_ld16(lane_base + (uint32_t)buf * 256u + TC_D3_COL, ov);
+        tmem_wait_ld_dep16(ov);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_D2EMPTY(buf)));
@@ -451,7 +650,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int n = 0; n < 16; ++n) out[n] = __uint_as_float(ov[n]) + b3s[n];
         const long long id = rp->id_first + q * rp->inner_stride + o * rp->outer_stride;
         if (L.mode == 0) {
-          apx_apply_queries<16>(slots, I.qmask, valid, id, out);
+          tc_apply_queries(qp, slots, I.qmask, valid, id, out);
         } else if (L.mode == 1) {
           if (valid && id >= L.dump_base && id < L.dump_base + L.dump_n) {
 #pragma unroll

@@ -53,10 +53,17 @@ __global__ void k_sel_hist(const float *keys, const long long *ids, long long n,
   __syncthreads();
   const unsigned long long prefix = S->prefix, mask = S->mask;
   const unsigned tau = S->tau;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    bool use;
-    const unsigned long long v = sel_value(stage, keys[i], ids[i], tau, use);
-    if (use && (v & mask) == prefix) atomicAdd(&h[(v >> shift) & 255ull], 1ull);
+  const unsigned lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long b = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u); b < n; b += stride) {
+    const long long i = b + lane;
+    bool use = false;
+    unsigned long long v = 0;
+    if (i < n) v = sel_value(stage, keys[i], ids[i], tau, use);
+    use = use && (v & mask) == prefix;
+    const unsigned dig = use ? (unsigned)((v >> shift) & 255ull) : 256u;
+    const unsigned grp = __match_any_sync(0xffffffffu, dig);   // merge lanes with equal digits
+    if (use && (int)lane == __ffs(grp) - 1) atomicAdd(&h[dig], (unsigned long long)__popc(grp));
   }
   __syncthreads();
   for (int d = threadIdx.x; d < 256; d += blockDim.x)
@@ -93,22 +100,29 @@ __global__ void k_sel_compact(const float *keys, const long long *ids, long long
                               RItem *out) {
   const unsigned tau = S->tau;
   const long long id_max = (long long)S->id_max;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const unsigned kb = apx_key_bits(keys[i]);
-    const bool member = kb > tau || (kb == tau && ids[i] <= id_max);
-    if (member) {
-      const unsigned p = atomicAdd(&S->count, 1u);
-      if (p < (unsigned long long)k) {
-        RItem it;
-        it.s = (double)keys[i];
-        it.id = ids[i];
-        it.src = 0;
-        it.alive = 1;
-        it.is64 = 1;
-        it.need64 = 0;
-        it.pad = 0;
-        out[p] = it;
-      }
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long b = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u); b < n; b += stride) {
+    const long long i = b + (threadIdx.x & 31);
+    bool member = false;
+    float key = 0.f;
+    long long id = 0;
+    if (i < n) {
+      key = keys[i];
+      id = ids[i];
+      const unsigned kb = apx_key_bits(key);
+      member = kb > tau || (kb == tau && id <= id_max);
+    }
+    const unsigned p = apx_warp_reserve(&S->count, member);
+    if (member && p < (unsigned long long)k) {
+      RItem it;
+      it.s = (double)key;
+      it.id = id;
+      it.src = 0;
+      it.alive = 1;
+      it.is64 = 1;
+      it.need64 = 0;
+      it.pad = 0;
+      out[p] = it;
     }
   }
 }

@@ -172,14 +172,26 @@ def test_batch_results_equal_alone(ragged):
 def test_cancel_and_unknown_ids(ragged):
     lib, head, spec, L, rms = ragged
     q = _q([1, 0, 0, 0, 0], k=5)
-    qid = L.query(q)
-    L.cancel(qid)
-    with pytest.raises(apex.ApexError) as e:
-        L.fetch(qid, 5)
-    assert e.value.code in (-6, 0) or True  # cancelled (or already finished before the cancel landed)
+    ids = [L.query(q) for _ in range(6)]
+    for qid in ids:
+        L.cancel(qid)
+    outcomes = []
+    for qid in ids:
+        try:
+            res = L.fetch(qid, 5)          # finished before the cancel landed: a full, valid result
+            assert res["n"] == 5
+            outcomes.append("done")
+        except apex.ApexError as e:
+            assert e.code == -6             # APEX_ECANCELED
+            outcomes.append("cancelled")
+    assert "cancelled" in outcomes          # queued queries cannot all have finished already
     with pytest.raises(apex.ApexError) as e:
         L.fetch(987654321, 5)
     assert e.value.code == -8
+    with pytest.raises(apex.ApexError) as e:
+        L.cancel(987654321)
+    assert e.value.code == -8
+    assert L.run(q)["n"] == 5               # the library keeps working after cancellations
 
 
 def test_query_validation(ragged):
