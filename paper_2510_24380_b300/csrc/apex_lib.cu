@@ -1339,6 +1339,14 @@ static void worker_main(apex_library *Lp) {
       for (int s = 0; s < APEX_MAX_ACTIVE; ++s) {
         QueryRec *q = L.active[s];
         if (!q || q->remaining > 0) continue;
+        {
+          std::lock_guard<std::mutex> g(L.mu);
+          if (q->cancel) {  // cancelled while its pass ran: skip the finalization
+            finish(L, q, Q_CANCELED, APEX_ECANCELED, "cancelled");
+            L.cv_done.notify_all();
+            continue;
+          }
+        }
         const double t0 = now_ms();
         const bool fin = finalize(L, q);
         q->stats.host_finalize_ms += now_ms() - t0;
