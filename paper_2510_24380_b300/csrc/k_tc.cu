@@ -14,15 +14,15 @@
 // fma .bf16x2: 1.5 issue slots and one MUFU element per activation); the 1/2 is folded into P
 // (layer 1) and into the W_2 image and b_2 (layer 2), all exact in binary.
 //
-// Warp roles (448 threads, one CTA per SM):
+// Warp roles (704 threads, one CTA per SM):
 //   warps 0-3   query warps: D3 of each tile -> outputs -> queries (warp w reads TMEM lanes 32w..)
-//   warps 4-11  math warps, thread (h, m) = column half h, tile row m: per step, layer 1 of the
-//               next tile (K half h of a_1) and then the layer-2 activation of the previous tile
-//               (accumulator columns [128h, 128h + 128), rows of its TMEM lane quarter)
-//   warp 12     TMEM allocation; lane 0 issues every MMA and commit
-//   warp 13     lane 0 bulk-copies (TMA) each tile's outer synthon row into a 4-slot ring
-// TMEM: 512 columns = two 256-column accumulators (double buffer); a_2 of half h overwrites
-// columns [128h, 128h + 64) of its buffer, D3 uses columns [64, 80).
+//   warps 4-19  math warps, thread (g, m) = K quarter g, tile row m: per step, layer 1 of the
+//               next tile (stage g of a_1) and then the layer-2 activation of the previous tile
+//               (accumulator columns [64g, 64g + 64), rows of its TMEM lane quarter)
+//   warp 20     TMEM allocation; lane 0 issues every MMA and commit
+//   warp 21     lane 0 bulk-copies (TMA) each tile's outer synthon row into a 4-slot ring
+// TMEM: 512 columns = two 256-column accumulators (double buffer); a_2 of quarter g overwrites
+// columns [64g, 64g + 32) of its buffer, D3 uses columns [32, 48).
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel records
 // APX_ERR_TIMEOUT in the status word, every role leaves its loop, and TMEM is released.
 #include <cuda_bf16.h>
@@ -30,12 +30,12 @@
 #include "common.cuh"
 
 #define TC_EPI_WARPS 4
-#define TC_PROD_WARPS 8
+#define TC_PROD_WARPS 16
 #define TC_MMA_WARP (TC_EPI_WARPS + TC_PROD_WARPS)
 #define TC_LOAD_WARP (TC_MMA_WARP + 1)
 #define TC_THREADS ((TC_LOAD_WARP + 1) * 32)
 #define TC_OROW_SLOTS 4
-#define TC_D3_COL 64u   // layer-3 accumulator columns within a 256-column buffer (free after layer 2)
+#define TC_D3_COL 32u   // layer-3 accumulator columns within a 256-column buffer (free after layer 2)
 
 // Query parameters cached in shared memory for the whole launch (one entry per query slot).
 struct SlotParams {
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mbar_init(bar(B_DRAIN), 1);
     for (int r = 0; r < TC_OROW_SLOTS; ++r) {
       mbar_init(bar(B_OFULL(r)), 1);
-      mbar_init(bar(B_OEMPTY(r)), TC_PROD_WARPS);
+      mbar_init(bar(B_OEMPTY(r)), TC_PROD_WARPS);  // every math warp reads every outer row
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -399,18 +399,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (warp >= TC_EPI_WARPS && warp < TC_MMA_WARP) {
     // ------------------------------------------------------------ math warps
-    // Thread (h, m): tile row m (= TMEM lane; warp % 4 is the row quarter) and column half h.
-    // Step s: produce a_1 of tile s (layer 1, K columns [128h, 128h + 128)) into the shared
-    // stages, then activate layer 2 of tile s - 1 (accumulator columns [128h, 128h + 128)),
-    // writing a_2 back in place. Producing first lets layer 2 of tile s run on the tensor pipe
-    // while layer 2 of tile s - 1 is activated.
+    // Thread (g, m): tile row m (= TMEM lane; warp % 4 is the row quarter) and K quarter g
+    // (64 columns = one a_1 stage). Step s: produce stage g of a_1 for tile s (layer 1), then
+    // activate layer 2 of tile s - 1 on accumulator columns [64g, 64g + 64), writing a_2 back in
+    // place. Producing first lets layer 2 of tile s run on the tensor pipe while layer 2 of tile
+    // s - 1 is activated.
     const int p = tid - TC_EPI_WARPS * 32;
-    const int h = p >> 7, m = p & 127;
+    const int g = p >> 7, m = p & 127;
     const uint32_t row_off = (uint32_t)(m >> 3) * 1024u + (uint32_t)(m & 7) * 128u;
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    uint32_t R[64];  // resident inner sum of the producing item, packed bf16 pairs
+    uint32_t R[32];  // resident inner sum of the producing item (64 columns), packed bf16 pairs
     long long it = blockIdx.x, o = 0, o_end = 0;
-    const RxnPlan *rp = nullptr;
+    bool has_outer = false;  // per-item fields kept in registers (no per-tile global loads)
     bool more = it < L.total_items;
     bool need_r = more;
     bool ok = true;
@@ -419,9 +419,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (produce) {
         if (need_r) {
           const TcItem I = tc_item(L, T, it);
-          rp = I.rp;
+          const RxnPlan *rp = I.rp;
           o = I.o_begin;
           o_end = I.o_end;
+          has_outer = rp->outer_row >= 0;
           const long long q = I.q0 + m;
           if (q < rp->n_inner) {
             long long rows[APEX_MAX_SLOTS];
@@ -432,10 +433,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               rem /= rp->inner_size[sl];
             }
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < 8; ++c) {
               float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
               for (int sl = 0; sl < ni; ++sl) {
-                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(T.P16 + rows[sl] * 256 + h * 128 + c * 8));
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(T.P16 + rows[sl] * 256 + g * 64 + c * 8));
                 acc[0] += bf_lo(v.x); acc[1] += bf_hi(v.x); acc[2] += bf_lo(v.y); acc[3] += bf_hi(v.y);
                 acc[4] += bf_lo(v.z); acc[5] += bf_hi(v.z); acc[6] += bf_lo(v.w); acc[7] += bf_hi(v.w);
               }
@@ -446,64 +447,59 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
           } else {
 #pragma unroll
-            for (int c = 0; c < 64; ++c) R[c] = 0u;
+            for (int c = 0; c < 32; ++c) R[c] = 0u;
           }
           need_r = false;
         }
-        // ---- layer 1 of tile s
+        // ---- layer 1 of tile s: stage g of a_1
         const int rs = (int)(s & (TC_OROW_SLOTS - 1));
-        const bool has_outer = rp->outer_row >= 0;
         ok = ok && mbar_wait(bar(B_OFULL(rs)), (uint32_t)((s / TC_OROW_SLOTS) & 1), abort_flag, err);
-        const unsigned char *prow = sm + TC_OFF_OROW + (uint32_t)rs * 512u + (uint32_t)h * 256u;
+        const unsigned char *prow = sm + TC_OFF_OROW + (uint32_t)rs * 512u + (uint32_t)g * 128u;
+        ok = ok && mbar_wait(bar(B_EMPTY(g)), (uint32_t)((s & 1) ^ 1), abort_flag, err);
+        if (ok) {
+          unsigned char *stage = sm + TC_OFF_A1 + (uint32_t)g * TC_STAGE_BYTES + row_off;
 #pragma unroll
-        for (int c2 = 0; c2 < 2; ++c2) {
-          const int kc = 2 * h + c2;
-          ok = ok && mbar_wait(bar(B_EMPTY(kc)), (uint32_t)((s & 1) ^ 1), abort_flag, err);
-          if (ok) {
-            unsigned char *stage = sm + TC_OFF_A1 + (uint32_t)kc * TC_STAGE_BYTES + row_off;
+          for (int c = 0; c < 8; ++c) {
+            uint4 pv = make_uint4(0u, 0u, 0u, 0u);
+            if (has_outer) pv = *reinterpret_cast<const uint4 *>(prow + c * 16);
+            const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
+            uint32_t out[4];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              uint4 pv = make_uint4(0u, 0u, 0u, 0u);
-              if (has_outer) pv = *reinterpret_cast<const uint4 *>(prow + c2 * 128 + c * 16);
-              const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
-              uint32_t out[4];
-#pragma unroll
-              for (int e = 0; e < 4; ++e) out[e] = act_bf2<ACT>(add_bf2(R[c2 * 32 + c * 4 + e], pw[e]));
-              *reinterpret_cast<uint4 *>(stage + (uint32_t)((c ^ (m & 7)) * 16)) =
-                  make_uint4(out[0], out[1], out[2], out[3]);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar(B_FULL(kc)));
+            for (int e = 0; e < 4; ++e) out[e] = act_bf2<ACT>(add_bf2(R[c * 4 + e], pw[e]));
+            *reinterpret_cast<uint4 *>(stage + (uint32_t)((c ^ (m & 7)) * 16)) = make_uint4(out[0], out[1], out[2], out[3]);
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(bar(B_FULL(g)));
+            mbar_arrive(bar(B_OEMPTY(rs)));
           }
         }
-        __syncwarp();
-        if (ok && lane == 0) mbar_arrive(bar(B_OEMPTY(rs)));
         if (++o >= o_end) {
           it += gridDim.x;
           more = it < L.total_items;
           need_r = more;
         }
       }
-      // ---- layer-2 activation of tile s - 1 (columns [128h, 128h + 128) of its accumulator)
+      // ---- layer-2 activation of tile s - 1 (columns [64g, 64g + 64) of its accumulator)
       if (ok && s >= 1) {
         const long long jj = s - 1;
         const int buf = (int)(jj & 1);
         ok = mbar_wait(bar(B_D2FULL(buf)), (uint32_t)((jj >> 1) & 1), abort_flag, err);
         if (ok) {
           tc_fence_after();
-          const uint32_t col = lane_base + (uint32_t)buf * 256u + (uint32_t)h * 128u;
-          const float *bh = b2s + h * 128;
+          const uint32_t col = lane_base + (uint32_t)buf * 256u + (uint32_t)g * 64u;
+          const float *bh = b2s + g * 64;
           // 16 accumulator columns at a time -> 8 packed bf16 pairs written over columns already
-          // read (a_2 of this half lands in its first 64 columns); one load of lookahead
+          // read (a_2 of this quarter lands in its first 32 columns); one load of lookahead
           uint32_t va[16], vb[16];
           tmem_ld16(col, va);
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
+          for (int c = 0; c < 4; ++c) {
             uint32_t(&v)[16] = (c & 1) ? vb : va;
             uint32_t(&vn)[16] = (c & 1) ? va : vb;
             tmem_wait_ld_dep16(v);
-            if (c + 1 < 8) tmem_ld16(col + (uint32_t)(c + 1) * 16u, vn);
+            if (c + 1 < 4) tmem_ld16(col + (uint32_t)(c + 1) * 16u, vn);
             uint32_t pk[8];
 #pragma unroll
             for (int e4 = 0; e4 < 4; ++e4) {
@@ -529,19 +525,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool ok = true;
       for (long long it = blockIdx.x; ok && it < L.total_items; it += gridDim.x) {
         const TcItem I = tc_item(L, T, it);
-        const RxnPlan *rp = I.rp;
+        const long long orow = I.rp->outer_row;
         for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
           const int rs = (int)(j & (TC_OROW_SLOTS - 1));
           if (!mbar_wait(bar(B_OEMPTY(rs)), (uint32_t)(((j / TC_OROW_SLOTS) & 1) ^ 1), abort_flag, err)) {
             ok = false;
             break;
           }
-          if (rp->outer_row >= 0) {
+          if (orow >= 0) {
             mbar_expect_tx(bar(B_OFULL(rs)), 512u);
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 512, [%2];" ::"r"(
                     sbase + TC_OFF_OROW + (uint32_t)rs * 512u),
-                "l"(T.P16 + (rp->outer_row + o) * 256), "r"(bar(B_OFULL(rs)))
+                "l"(T.P16 + (orow + o) * 256), "r"(bar(B_OFULL(rs)))
                 : "memory");
           } else {
             mbar_arrive(bar(B_OFULL(rs)));
@@ -563,8 +559,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tc_fence_after();
           const uint32_t dcol = tmem + (uint32_t)bb * 256u;
 #pragma unroll 1
-          for (int ks = 0; ks < 16; ++ks)  // K block ks of a_2 lives in half ks / 8 of the buffer
-            mma_ts(dcol + TC_D3_COL, dcol + (uint32_t)(ks >> 3) * 128u + (uint32_t)(ks & 7) * 8u,
+          for (int ks = 0; ks < 16; ++ks)  // K block ks of a_2 lives in quarter ks / 4 of the buffer
+            mma_ts(dcol + TC_D3_COL, dcol + (uint32_t)(ks >> 2) * 64u + (uint32_t)(ks & 3) * 8u,
                    sw128_desc(w3 + (uint32_t)(ks >> 2) * 2048u + (uint32_t)(ks & 3) * 32u), ID3, ks > 0);
           mma_commit(bar(B_D3FULL(bb)));
         };
@@ -635,6 +631,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const RxnPlan *rp = I.rp;
       const long long q = I.q0 + r;
       const bool valid = q < rp->n_inner;
+      const long long id_row = rp->id_first + q * rp->inner_stride;  // id = id_row + o * outer_stride
+      const long long ostride = rp->outer_stride;
       for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
         const int buf = (int)(j & 1);
         if (!mbar_wait(bar(B_D3FULL(buf)), (uint32_t)((j >> 1) & 1), abort_flag, err)) { ok = false; break; }
@@ -648,7 +646,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float out[16];
 #pragma unroll
         for (int n = 0; n < 16; ++n) out[n] = __uint_as_float(ov[n]) + b3s[n];
-        const long long id = rp->id_first + q * rp->inner_stride + o * rp->outer_stride;
+        const long long id = id_row + o * ostride;
         if (L.mode == 0) {
           tc_apply_queries(qp, slots, I.qmask, valid, id, out);
         } else if (L.mode == 1) {
