@@ -10,11 +10,12 @@
 // common.cuh), (b) a list of compound ids (candidate rescoring and calibration).
 #include "common.cuh"
 
-#define F32_AT_STRIDE 132   // floats per row of the transposed activation tile (128 + pad)
 #define F32_KC 16           // K rows of W^T per stage
 
+// TM tile rows: 128 for enumeration work items, 32 for id lists (small batches spread over SMs)
+template <int TM>
 struct F32Smem {
-  float AT[256][F32_AT_STRIDE];      // AT[k][row]
+  float AT[256][TM + 4];             // AT[k][row], transposed activations of the tile
   float Wc[2][F32_KC][256];          // W^T chunk double buffer
 };
 
@@ -69,13 +70,14 @@ __device__ __forceinline__ int f32_row_sources(const DevTables &T, int mode, con
 // Writes z_1 (activated unless the head has a single layer) for the tile rows into AT.
 // Each warp builds two rows at a time; lanes stride over the columns (coalesced 128 B loads),
 // and every load of both rows is issued before the sums are formed.
-__device__ void f32_build_layer1(F32Smem &S, const DevTables &T, int mode, const RxnPlan *rp, long long q0, long long o,
+template <int TM>
+__device__ void f32_build_layer1(F32Smem<TM> &S, const DevTables &T, int mode, const RxnPlan *rp, long long q0, long long o,
                                  const long long *ids, long long id0, long long n_ids, bool *row_valid,
                                  long long *row_id) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int h1 = T.dims[1];
   const bool last = (T.n_layers == 1);
-  for (int r0 = warp * 2; r0 < APX_TILE; r0 += 2 * (APX_SIMT_THREADS / 32)) {
+  for (int r0 = warp * 2; r0 < TM; r0 += 2 * (APX_SIMT_THREADS / 32)) {
     long long rows[2][APEX_MAX_SLOTS];
     int nrows[2];
 #pragma unroll
@@ -116,36 +118,60 @@ __device__ void f32_build_layer1(F32Smem &S, const DevTables &T, int mode, const
 }
 
 // out = act(W^T-chunked GEMM of AT) for layer l (1-based index into dims: K = dims[l], N = dims[l+1]).
-__device__ void f32_layer(F32Smem &S, const DevTables &T, int l) {
+// Thread (rg, cg) owns RPT = TM / 16 rows and the 16 columns 64 jq + 4 cg + e. The next W^T chunk
+// is fetched into registers before the current chunk is consumed and stored to shared memory
+// after it, so its global-load latency overlaps the FMAs.
+template <int TM>
+__device__ void f32_layer(F32Smem<TM> &S, const DevTables &T, int l) {
+  constexpr int RPT = TM / 16;
   const int K = T.dims[l], N = T.dims[l + 1];
   const float *WT = T.WT[l];
   const float *B = T.B[l];
   const bool last = (l == T.n_layers - 1);
   const int t = threadIdx.x;
   const int rg = t >> 4, cg = t & 15;
-  float acc[8][16];
+  float acc[RPT][16];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < RPT; ++i)
 #pragma unroll
     for (int j = 0; j < 16; ++j) acc[i][j] = 0.f;
   const int nk = (K + F32_KC - 1) / F32_KC;
-  auto load_chunk = [&](int kc, int buf) {
-    for (int e = t; e < F32_KC * N; e += APX_SIMT_THREADS) {
-      const int kk = e / N, n = e % N;
+  float pre[F32_KC * 256 / APX_SIMT_THREADS];
+  auto fetch = [&](int kc) {
+#pragma unroll
+    for (int q = 0; q < F32_KC * 256 / APX_SIMT_THREADS; ++q) {
+      const int e = t + q * APX_SIMT_THREADS;
+      const int kk = e >> 8, n = e & 255;
       const int k = kc * F32_KC + kk;
-      S.Wc[buf][kk][n] = (k < K) ? __ldg(WT + (long long)k * N + n) : 0.f;
+      pre[q] = (k < K && n < N) ? __ldg(WT + (long long)k * N + n) : 0.f;
     }
   };
-  load_chunk(0, 0);
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < F32_KC * 256 / APX_SIMT_THREADS; ++q) {
+      const int e = t + q * APX_SIMT_THREADS;
+      S.Wc[buf][e >> 8][e & 255] = pre[q];
+    }
+  };
+  fetch(0);
+  store(0);
   __syncthreads();
   for (int kc = 0; kc < nk; ++kc) {
     const int buf = kc & 1;
-    if (kc + 1 < nk) load_chunk(kc + 1, buf ^ 1);
+    if (kc + 1 < nk) fetch(kc + 1);
     const int kmax = min(F32_KC, K - kc * F32_KC);
     for (int kk = 0; kk < kmax; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4 *>(&S.AT[kc * F32_KC + kk][rg * 8]);
-      const float4 a1 = *reinterpret_cast<const float4 *>(&S.AT[kc * F32_KC + kk][rg * 8 + 4]);
-      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float a[RPT];
+      if (RPT == 8) {
+        const float4 a0 = *reinterpret_cast<const float4 *>(&S.AT[kc * F32_KC + kk][rg * RPT]);
+        const float4 a1 = *reinterpret_cast<const float4 *>(&S.AT[kc * F32_KC + kk][rg * RPT + 4]);
+        a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+        a[4 % RPT] = a1.x; a[5 % RPT] = a1.y; a[6 % RPT] = a1.z; a[7 % RPT] = a1.w;
+      } else {
+        const float2 a0 = *reinterpret_cast<const float2 *>(&S.AT[kc * F32_KC + kk][rg * RPT]);
+        a[0] = a0.x;
+        a[1 % RPT] = a0.y;
+      }
       float w[16];
 #pragma unroll
       for (int jq = 0; jq < 4; ++jq) {  // thread cg owns columns 64 jq + 4 cg + e (conflict-free 16-byte reads)
@@ -156,10 +182,11 @@ __device__ void f32_layer(F32Smem &S, const DevTables &T, int l) {
         w[4 * jq + 3] = w4.w;
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < RPT; ++i)
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
     }
+    if (kc + 1 < nk) store(buf ^ 1);  // the other buffer was last read before the previous barrier
     __syncthreads();
   }
   // every thread has finished reading AT: overwrite it with this layer's output
@@ -169,9 +196,9 @@ __device__ void f32_layer(F32Smem &S, const DevTables &T, int l) {
     if (n < N) {
       const float bn = __ldg(B + n);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < RPT; ++i) {
         const float z = acc[i][j] + bn;
-        S.AT[n][rg * 8 + i] = last ? z : f32_act(T.act, z);
+        S.AT[n][rg * RPT + i] = last ? z : f32_act(T.act, z);
       }
     }
   }
@@ -179,16 +206,17 @@ __device__ void f32_layer(F32Smem &S, const DevTables &T, int l) {
 }
 
 // mode 0: enumeration (LaunchPlan); mode 1: ids[0, n_ids) -> out[n_ids x n_out] (FP32 outputs)
+template <int TM>
 __global__ void __launch_bounds__(APX_SIMT_THREADS, 1)
     k_fp32_head(const __grid_constant__ LaunchPlan L, const __grid_constant__ DevTables T, QuerySlot *slots,
                 const long long *ids, long long n_ids, float *out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  F32Smem &S = *reinterpret_cast<F32Smem *>(smem_raw);
-  __shared__ bool row_valid[APX_TILE];
-  __shared__ long long row_id[APX_TILE];
+  F32Smem<TM> &S = *reinterpret_cast<F32Smem<TM> *>(smem_raw);
+  __shared__ bool row_valid[TM];
+  __shared__ long long row_id[TM];
   const int mode = (ids != nullptr) ? 1 : 0;
   const int n_out = T.n_out;
-  long long n_work = mode == 0 ? L.total_items : (n_ids + APX_TILE - 1) / APX_TILE;
+  long long n_work = mode == 0 ? L.total_items : (n_ids + TM - 1) / TM;
   for (long long it = blockIdx.x; it < n_work; it += gridDim.x) {
     const RxnPlan *rp = nullptr;
     long long q0 = 0, o_begin = 0, o_end = 1;
@@ -205,10 +233,10 @@ __global__ void __launch_bounds__(APX_SIMT_THREADS, 1)
       qmask = seg.qmask;
     }
     for (long long o = o_begin; o < o_end; ++o) {
-      f32_build_layer1(S, T, mode, rp, q0, o, ids, it * APX_TILE, n_ids, row_valid, row_id);
+      f32_build_layer1<TM>(S, T, mode, rp, q0, o, ids, it * TM, n_ids, row_valid, row_id);
       __syncthreads();
-      for (int l = 1; l < T.n_layers; ++l) f32_layer(S, T, l);
-      if (threadIdx.x < APX_TILE) {
+      for (int l = 1; l < T.n_layers; ++l) f32_layer<TM>(S, T, l);
+      if (threadIdx.x < TM) {
         const int r = threadIdx.x;
         float ov[APEX_MAX_OUTPUTS];
 #pragma unroll
@@ -219,7 +247,7 @@ __global__ void __launch_bounds__(APX_SIMT_THREADS, 1)
           if (valid) {
 #pragma unroll
             for (int n = 0; n < APEX_MAX_OUTPUTS; ++n)
-              if (n < n_out) out[(it * APX_TILE + r) * n_out + n] = ov[n];
+              if (n < n_out) out[(it * TM + r) * n_out + n] = ov[n];
           }
         } else if (L.mode == 1) {
           if (valid && id >= L.dump_base && id < L.dump_base + L.dump_n) {
@@ -244,19 +272,31 @@ __global__ void __launch_bounds__(APX_SIMT_THREADS, 1)
   }
 }
 
-size_t apx_fp32_smem_bytes() { return sizeof(F32Smem); }
+size_t apx_fp32_smem_bytes() { return sizeof(F32Smem<128>); }
 
+// Enumeration (ids == nullptr) runs 128-row tiles; id lists run 32-row tiles. grid <= 0: the
+// launcher picks min(tiles, 148 * 2) for id lists.
 cudaError_t apx_launch_fp32(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, const long long *ids,
                             long long n_ids, float *out, int grid, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_fp32_head, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(F32Smem));
+    cudaError_t e = cudaFuncSetAttribute(k_fp32_head<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(F32Smem<128>));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_fp32_head<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(F32Smem<32>));
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (grid <= 0) return cudaSuccess;
-  apx_count_launch();
-  k_fp32_head<<<grid, APX_SIMT_THREADS, sizeof(F32Smem), st>>>(L, T, slots, ids, n_ids, out);
+  if (ids == nullptr) {
+    if (grid <= 0) return cudaSuccess;
+    apx_count_launch();
+    k_fp32_head<128><<<grid, APX_SIMT_THREADS, sizeof(F32Smem<128>), st>>>(L, T, slots, ids, n_ids, out);
+  } else {
+    const long long tiles = (n_ids + 31) / 32;
+    if (tiles <= 0) return cudaSuccess;
+    const int g = (int)(tiles < 148 * 2 ? tiles : 148 * 2);
+    apx_count_launch();
+    k_fp32_head<32><<<g, APX_SIMT_THREADS, sizeof(F32Smem<32>), st>>>(L, T, slots, ids, n_ids, out);
+  }
   return cudaGetLastError();
 }
