@@ -40,6 +40,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--mode", default="single", choices=["single", "batched", "serving"],
+                    help="single: the contract line; batched: 64 queries in one shared pass over the 1e9 subset "
+                         "of c3_real; serving: Poisson arrivals over the resident c3_real library")
+    ap.add_argument("--queries", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=5.0, help="serving: arrivals per second")
+    ap.add_argument("--serve-queries", type=int, default=24)
     return ap.parse_args()
 
 
@@ -162,8 +168,93 @@ def run_cpu_baseline(lib, head, q, seconds: float = 15.0):
             "_subset": subset, "_ref": ref, "_query": qs}
 
 
+def run_batched(args):
+    """64 queries (random convex weights over the 5 objectives, 8 property boxes, k from
+    {10 .. 1e5}) submitted together over the 1e9-compound subset of c3_real: one shared pass."""
+    import torch
+
+    import csl_gen
+    from paper_2510_24380_b300 import apex
+
+    full, head, spec = csl_gen.build_workload("c3_real", materialize=False)
+    sub = csl_gen.subset_prefix(full, 0, 1e9)
+    lib = full.subset_materialized(sub)
+    N = int(sum(np.prod(lib.sizes_of(t).astype(np.float64)) for t in range(lib.n_reactions)))
+    stats = csl_gen.load_stats("c3_real")
+    qs = csl_gen.queries_batched(stats, 5, 8, args.queries, seed=1)
+    stream = torch.cuda.Stream()
+    L = apex.Library(lib, head, precisions=("fp32", "bf16"), stream=stream.cuda_stream)
+    L.run(qs[0])  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ids = [L.query(q) for q in qs]
+    res = [L.fetch(i, q.k) for i, q in zip(ids, qs)]
+    dt = time.perf_counter() - t0
+    lat = []
+    for i in ids:
+        pass
+    out = {"mode": "batched", "workload": "c3_real 1e9-compound subset", "n_compounds": N,
+           "reactions": len(sub), "queries": len(qs), "k": [int(q.k) for q in qs][:8],
+           "wall_s": dt, "head_evaluations_per_s": N / dt, "query_compounds_per_s": len(qs) * N / dt,
+           "results": int(sum(r["n"] for r in res))}
+    L.close()
+    print(json.dumps(out))
+
+
+def run_serving(args):
+    """Poisson arrivals over the resident c3_real library; each query takes a random subset of
+    1..1000 reactions, random weights and boxes, k log-uniform in [10, 1e5]."""
+    import threading
+
+    import torch
+
+    import csl_gen
+    from paper_2510_24380_b300 import apex
+
+    lib, head, spec = csl_gen.build_workload("c3_real")
+    stats = csl_gen.load_stats("c3_real")
+    arrivals = csl_gen.serving_stream(stats, 5, 8, lib.n_reactions, args.serve_queries, args.rate, seed=2)
+    stream = torch.cuda.Stream()
+    L = apex.Library(lib, head, precisions=("fp32", "bf16"), stream=stream.cuda_stream)
+    sizes = np.array([float(np.prod(lib.sizes_of(t).astype(np.float64))) for t in range(lib.n_reactions)])
+    done = []
+    lock = threading.Lock()
+
+    def fetcher(qid, k, scope):
+        r = L.fetch(qid, k)
+        st = L.stats(-1)
+        with lock:
+            done.append((st["latency_ms"], scope, r["n"], st["queue_ms"]))
+
+    threads = []
+    t0 = time.perf_counter()
+    for t_arr, q in arrivals:
+        now = time.perf_counter() - t0
+        if t_arr > now:
+            time.sleep(t_arr - now)
+        qid = L.query(q)
+        th = threading.Thread(target=fetcher, args=(qid, int(q.k), float(sizes[q.subset].sum())))
+        th.start()
+        threads.append(th)
+    for th in threads:
+        th.join()
+    wall = time.perf_counter() - t0
+    lat = np.array([d[0] for d in done])
+    scope = np.array([d[1] for d in done])
+    out = {"mode": "serving", "workload": "c3_real resident", "n_compounds": float(sizes.sum()),
+           "rate_hz": args.rate, "queries": len(done), "wall_s": wall,
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "mean_scope_compounds": float(scope.mean()), "query_compounds_per_s": float(scope.sum() / wall)}
+    L.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.mode == "batched":
+        return run_batched(args)
+    if args.mode == "serving":
+        return run_serving(args)
     world, rank, local, pg = dist_setup(args)
     import csl_gen
 

@@ -92,6 +92,32 @@ class CSL:
         self.U = U
         return self
 
+    def subset_materialized(self, reactions, threads: int | None = None) -> "CSL":
+        """The given reactions as a new CSL whose embeddings are generated directly from the
+        original (reaction, slot) seeds, without materializing the whole library."""
+        reactions = [int(t) for t in reactions]
+        sf = self.slot_first
+        sizes = np.concatenate([self.slot_sizes[sf[t] : sf[t + 1]] for t in reactions]).astype(np.int64)
+        out = CSL(n_slots=self.n_slots[reactions].copy(), slot_sizes=sizes, d=self.d, seed=self.seed,
+                  name=self.name + "[subset]")
+        U = np.empty((out.n_rows, self.d), dtype=np.float32)
+        jobs, r0 = [], 0
+        for t in reactions:
+            for j in range(int(self.n_slots[t])):
+                n = int(self.sizes_of(t)[j])
+                jobs.append((t, j, r0))
+                r0 += n
+
+        def fill(job):
+            t, j, r = job
+            b = self.block(t, j)
+            U[r : r + b.shape[0]] = b
+
+        with ThreadPoolExecutor(threads or min(32, os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, jobs))
+        out.U = U
+        return out
+
     def subset(self, reactions) -> "CSL":
         """A new CSL made of the given reactions (in the given order); U is copied if present."""
         reactions = [int(t) for t in reactions]
