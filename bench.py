@@ -44,6 +44,8 @@ def parse():
                     help="single: the contract line; batched: 64 queries in one shared pass over the 1e9 subset "
                          "of c3_real; serving: Poisson arrivals over the resident c3_real library")
     ap.add_argument("--queries", type=int, default=64)
+    ap.add_argument("--precision", default="fp16", choices=["bf16", "fp16", "fp32"],
+                    help="pass precision of the enumeration (tensor-core bf16/fp16, or fp32 CUDA cores)")
     ap.add_argument("--rate", type=float, default=5.0, help="serving: arrivals per second")
     ap.add_argument("--serve-queries", type=int, default=24)
     return ap.parse_args()
@@ -181,22 +183,25 @@ def run_batched(args):
     lib = full.subset_materialized(sub)
     N = int(sum(np.prod(lib.sizes_of(t).astype(np.float64)) for t in range(lib.n_reactions)))
     stats = csl_gen.load_stats("c3_real")
-    qs = csl_gen.queries_batched(stats, 5, 8, args.queries, seed=1)
+    qs = csl_gen.queries_batched(stats, 5, 8, args.queries, seed=1, precision=args.precision)
     stream = torch.cuda.Stream()
-    L = apex.Library(lib, head, precisions=("fp32", "bf16"), stream=stream.cuda_stream)
+    L = apex.Library(lib, head, precisions=("fp32", args.precision), stream=stream.cuda_stream)
     L.run(qs[0])  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ids = [L.query(q) for q in qs]
-    res = [L.fetch(i, q.k) for i, q in zip(ids, qs)]
+    res, per = [], []
+    for i, q in zip(ids, qs):
+        res.append(L.fetch(i, q.k))
+        st = L.stats(-1)
+        per.append((int(q.k), st["n_restarts"], st["n_candidates"], st["n_rescored_fp64"], round(st["latency_ms"], 1),
+                    round(st["host_finalize_ms"], 1), round(st["host_start_ms"], 1)))
     dt = time.perf_counter() - t0
-    lat = []
-    for i in ids:
-        pass
-    out = {"mode": "batched", "workload": "c3_real 1e9-compound subset", "n_compounds": N,
+    out = {"mode": "batched", "workload": "c3_real 1e9-compound subset", "precision": args.precision, "n_compounds": N,
            "reactions": len(sub), "queries": len(qs), "k": [int(q.k) for q in qs][:8],
            "wall_s": dt, "head_evaluations_per_s": N / dt, "query_compounds_per_s": len(qs) * N / dt,
-           "results": int(sum(r["n"] for r in res))}
+           "results": int(sum(r["n"] for r in res)),
+           "per_query_k_restarts_candidates_fp64_latency_finalize_start": per[:64]}
     L.close()
     print(json.dumps(out))
 
@@ -213,9 +218,10 @@ def run_serving(args):
 
     lib, head, spec = csl_gen.build_workload("c3_real")
     stats = csl_gen.load_stats("c3_real")
-    arrivals = csl_gen.serving_stream(stats, 5, 8, lib.n_reactions, args.serve_queries, args.rate, seed=2)
+    arrivals = csl_gen.serving_stream(stats, 5, 8, lib.n_reactions, args.serve_queries, args.rate, seed=2,
+                                      precision=args.precision)
     stream = torch.cuda.Stream()
-    L = apex.Library(lib, head, precisions=("fp32", "bf16"), stream=stream.cuda_stream)
+    L = apex.Library(lib, head, precisions=("fp32", args.precision), stream=stream.cuda_stream)
     sizes = np.array([float(np.prod(lib.sizes_of(t).astype(np.float64))) for t in range(lib.n_reactions)])
     done = []
     lock = threading.Lock()
@@ -259,10 +265,10 @@ def main():
     import csl_gen
 
     lib, head, spec = csl_gen.build_workload(args.workload)
-    q = csl_gen.query_single(args.workload, spec, precision="bf16")
+    q = csl_gen.query_single(args.workload, spec, precision=args.precision)
     N = int(sum(np.prod(lib.sizes_of(t).astype(np.float64)) for t in range(lib.n_reactions)))
     config = {"workload": args.workload, "n_compounds": N, "k": int(q.k), "n_constraints": int(q.m),
-              "head": "-".join(str(x) for x in head.dims) + f" {head.activation}", "precision": "bf16 pass + fp32/fp64 rescore",
+              "head": "-".join(str(x) for x in head.dims) + f" {head.activation}", "precision": f"{args.precision} pass + fp32/fp64 rescore",
               "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) before every timed step"}
 
     if args.impl == "reference":
@@ -295,7 +301,7 @@ def main():
     dev = local
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
-    L = apex.Library(lib, head, precisions=("fp32", "bf16"), device=dev, stream=stream.cuda_stream, seed=0)
+    L = apex.Library(lib, head, precisions=("fp32", args.precision), device=dev, stream=stream.cuda_stream, seed=0)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
 
     def step(query):
@@ -309,7 +315,7 @@ def main():
     # ------------------------------------------------------------- timed region (device events)
     clocks = Clocks(dev) if rank == 0 else None
     launches0 = apex.apex_kernel_launches()
-    dev_ms, e2e_ms, enum_ms, scored = [], [], [], []
+    dev_ms, e2e_ms, enum_ms, scored, step_stats = [], [], [], [], []
     res = None
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
@@ -327,6 +333,8 @@ def main():
         st = L.stats(-1)
         enum_ms.append(st["enumerate_ms"])
         scored.append(st["n_scored"])
+        step_stats.append({k: round(st[k], 3) if isinstance(st[k], float) else st[k]
+                           for k in ("gpu_ms", "enumerate_ms", "n_restarts", "n_candidates", "n_rescored_fp64")})
     torch.cuda.synchronize()
     launches = apex.apex_kernel_launches() - launches0
     clk = clocks.stop() if clocks else None
@@ -373,7 +381,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16",
+        "dtype": args.precision,
         "data": "synthetic (seeded N(0,1) synthon embeddings, random-init head; paper libraries unavailable)",
         "config": config,
         "e2e": {"value": world * N * args.steps / (t_e2e * 1e-3), "unit": "compounds/s", "h2d_bytes_per_step": h2d,
@@ -383,19 +391,23 @@ def main():
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_tc_head (enumeration, layers 2-3 on tcgen05)",
-                     "flop_per_compound": FLOP_PER_COMPOUND, "peak_kind": f"{kind} bf16 burst",
+                     "flop_per_compound": FLOP_PER_COMPOUND, "peak_kind": f"{kind} bf16 burst (fp16 dense rate equals bf16)",
                      "kernel_ms_per_step": mean_enum},
-        "fp32_plain": {"value": fp32_rate, "unit": "compounds/s", "same_topk_set_as_bf16": bool(same) if fp32_rate else None},
+        "fp32_plain": {"value": fp32_rate, "unit": "compounds/s", "same_topk_set_as_tc_pass": bool(same) if fp32_rate else None},
         "query": {k: last_stats[k] for k in ("n_candidates", "n_rescored_fp64", "n_restarts", "n_launches",
                                              "gpu_ms", "enumerate_ms", "queue_ms", "latency_ms", "host_start_ms",
                                              "host_pass_ms", "host_finalize_ms")},
         "clocks": clk,
+        "steps_detail": step_stats,
+        "margins": {"err_pass": [round(x, 5) for x in list(getattr(L.info(), "err_" + args.precision))[:L.n_outputs]],
+                    "err_fp32": [float("%.3g" % x) for x in list(L.info().err_fp32)[:L.n_outputs]],
+                    "rms": [round(x, 4) for x in list(L.info().rms)[:L.n_outputs]]},
     }
     if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
         cb = run_cpu_baseline(lib, head, q)
         # GPU answer on the same sampled reactions, checked against the oracle's
         qs = cb["_query"]
-        qg = csl_gen.Query(qs.weights, qs.cons_idx, qs.lo, qs.hi, qs.k, qs.subset, "bf16")
+        qg = csl_gen.Query(qs.weights, qs.cons_idx, qs.lo, qs.hi, qs.k, qs.subset, args.precision)
         rg = L.run(qg)
         match = set(rg["ids"].tolist()) == set(cb["_ref"].ids.tolist())
         line["cpu_baseline"] = {k: v for k, v in cb.items() if not k.startswith("_")}

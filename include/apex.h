@@ -49,11 +49,15 @@ typedef int32_t apex_status;
 #define APEX_ACT_SILU 2
 
 /* Query precision of the enumeration pass. FP32: every layer in FP32 on the CUDA cores.
- * BF16: layers 2.. on tcgen05 tensor cores (BF16 operands, FP32 accumulators in TMEM); the
- * candidates are then rescored in FP32 and the top-k boundary band in FP64, so the returned
- * set equals the FP64 top-k when the calibrated error bounds hold. */
+ * BF16 / FP16: layers 2.. on tcgen05 tensor cores (16-bit operands and activations, FP32
+ * accumulators in TMEM); FP16 carries 3 more mantissa bits at the same tensor rate, so its
+ * calibrated margins are tighter. The candidates are then rescored in FP32 and the top-k
+ * boundary band in FP64, so the returned set equals the FP64 top-k when the calibrated error
+ * bounds hold. APEX_FP64 is accepted by apex_score_ids only. */
 #define APEX_FP32 0
 #define APEX_BF16 1
+#define APEX_FP64 2
+#define APEX_FP16 3
 
 #define APEX_MAX_SLOTS 4          /* slots per reaction */
 #define APEX_MAX_OUTPUTS 32       /* head outputs */
@@ -81,7 +85,8 @@ typedef struct {
   int32_t activation;           /* APEX_ACT_*, applied after every layer but the last */
   int32_t n_objectives;         /* outputs [0, n_objectives) may carry objective weight */
   int32_t n_properties;         /* n_objectives + n_properties == dims[n_layers] */
-  uint32_t precisions;          /* bit (1 << APEX_BF16) builds the tensor-core tables; FP32 always */
+  uint32_t precisions;          /* bits (1 << APEX_BF16), (1 << APEX_FP16) build the tensor-core tables;
+                                   FP32 always */
   uint64_t device_mem_budget;   /* bytes the library may hold on the device; 0 = unlimited */
   void *cuda_stream;            /* cudaStream_t to run on; NULL = the library creates one */
   int32_t device;               /* CUDA device ordinal */
@@ -91,7 +96,7 @@ typedef struct {
 /* Query descriptor (Eq. orig_topk: objective weights, constraint boxes, k). Copied by
  * apex_query; the caller may free it when the call returns. */
 typedef struct {
-  int32_t precision;            /* APEX_FP32 or APEX_BF16 */
+  int32_t precision;            /* APEX_FP32, APEX_BF16 or APEX_FP16 */
   const float *objective_weights; /* host [n_objectives]; the objective is maximized */
   int32_t n_constraints;        /* 0..APEX_MAX_CONSTRAINTS */
   const int32_t *output_index;  /* host [n_constraints], any output index */
@@ -111,6 +116,7 @@ typedef struct {
   uint32_t precisions;          /* tables built */
   int32_t n_calibration;        /* compounds in the calibration sample */
   double err_bf16[APEX_MAX_OUTPUTS]; /* per-output admission margin of the BF16 pass */
+  double err_fp16[APEX_MAX_OUTPUTS]; /* per-output admission margin of the FP16 pass */
   double err_fp32[APEX_MAX_OUTPUTS]; /* per-output margin of the FP32 rescore */
   double rms[APEX_MAX_OUTPUTS];      /* output RMS over the calibration sample */
 } apex_library_info_t;
@@ -161,7 +167,9 @@ apex_status apex_query(apex_library *lib, const apex_query_desc *desc, apex_quer
  *   ids [cap], reaction [cap], synthons [cap x APEX_MAX_SLOTS] (-1 padded),
  *   objective [cap], outputs [cap x n_outputs]   -- host buffers; any may be NULL.
  * Objectives and outputs are the FP32 rescore, replaced by FP64 for every compound in the
- * top-k boundary band or tied with a neighbour within the FP32 margin. *n_out = n.
+ * top-k boundary band (within the FP32 margin of the k-th objective) or within the FP32 margin
+ * of a constraint bound; the returned set is the FP64 top-k, and results whose FP32 objectives
+ * are closer than the FP32 margin are ordered by those. *n_out = n.
  * EAGAIN: not done yet (the query stays alive); otherwise the query is released. */
 apex_status apex_topk_fetch(apex_library *lib, apex_query_id id, int64_t capacity, int64_t *ids,
                             int32_t *reaction, int64_t *synthons, double *objective, double *outputs,
@@ -174,7 +182,7 @@ apex_status apex_cancel(apex_library *lib, apex_query_id id);
 apex_status apex_query_stats(apex_library *lib, apex_query_id id, apex_query_stats_t *out);
 
 /* Scores given compounds (host ids [n]) through the gather kernels: precision APEX_FP32
- * (CUDA cores) or 2 (= FP64 plain form g = sum u, then the head). outputs: host [n x n_outputs].
+ * (CUDA cores) or APEX_FP64 (plain form g = sum u, then the head). outputs: host [n x n_outputs].
  * Synchronous. Used for calibration checks and parity tests. */
 apex_status apex_score_ids(apex_library *lib, int32_t precision, int64_t n, const int64_t *ids,
                            double *outputs);

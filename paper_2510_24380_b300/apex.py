@@ -20,7 +20,7 @@ STATUS = {0: "APEX_OK", -1: "APEX_EINVAL", -2: "APEX_ENOMEM", -3: "APEX_EBUSY", 
           -9: "APEX_EUNSUPPORTED"}
 APEX_EAGAIN = -4
 ACT = {"identity": 0, "relu": 1, "silu": 2}
-PREC = {"fp32": 0, "bf16": 1, "fp64": 2}
+PREC = {"fp32": 0, "bf16": 1, "fp64": 2, "fp16": 3}
 MAX_SLOTS = 4
 MAX_OUTPUTS = 32
 
@@ -54,7 +54,8 @@ class LibraryInfo(C.Structure):
     _fields_ = [
         ("n_compounds", C.c_int64), ("n_synthon_rows", C.c_int64), ("max_slots", C.c_int32),
         ("n_outputs", C.c_int32), ("device_bytes", C.c_uint64), ("precisions", C.c_uint32),
-        ("n_calibration", C.c_int32), ("err_bf16", C.c_double * MAX_OUTPUTS), ("err_fp32", C.c_double * MAX_OUTPUTS),
+        ("n_calibration", C.c_int32), ("err_bf16", C.c_double * MAX_OUTPUTS), ("err_fp16", C.c_double * MAX_OUTPUTS),
+        ("err_fp32", C.c_double * MAX_OUTPUTS),
         ("rms", C.c_double * MAX_OUTPUTS),
     ]
 
@@ -135,7 +136,7 @@ def apex_count_compounds(n_slots, slot_sizes) -> int:
 class Library:
     """A loaded library (apex_load_library) built from csl_gen's CSL and Head."""
 
-    def __init__(self, lib, head, precisions=("fp32", "bf16"), device: int = 0, stream=None, budget: int = 0,
+    def __init__(self, lib, head, precisions=("fp32", "bf16", "fp16"), device: int = 0, stream=None, budget: int = 0,
                  seed: int = 0, U_device=None):
         dll = load()
         self._keep = []
@@ -167,7 +168,7 @@ class Library:
         D.activation = ACT[head.activation]
         D.n_objectives = int(head.n_objectives)
         D.n_properties = int(head.n_properties)
-        D.precisions = sum(1 << PREC[p] for p in precisions)
+        D.precisions = sum(1 << PREC[p] for p in set(precisions))
         D.device_mem_budget = int(budget)
         D.cuda_stream = stream
         D.device = int(device)

@@ -35,10 +35,10 @@ cudaError_t apx_launch_fp32(const LaunchPlan &L, const DevTables &T, QuerySlot *
 cudaError_t apx_launch_fp64(const DevTables &T, const long long *ids, long long n, double *out, cudaStream_t st);
 cudaError_t apx_launch_prep(const float *U, const float *W1, const float *b1, const unsigned char *bias_row,
                             long long rows, int K, int N, float *P32, cudaStream_t st);
-cudaError_t apx_launch_p16(const float *P32, long long n, float scale, void *P16, cudaStream_t st);
+cudaError_t apx_launch_p16(const float *P32, long long n, float scale, int fmt, void *P16, cudaStream_t st);
+cudaError_t apx_launch_image(const float *W, int rows_used, int rows, int fmt, void *img, cudaStream_t st);
 cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
-                          cudaStream_t st);
-void apx_make_sw128_image(const float *W, int rows_used, int rows, unsigned char *img);
+                          cudaStream_t st, int fmt);
 cudaError_t apx_launch_slot_select(QuerySlot *slots, const int *slot_list, int n_slots, int mode, cudaStream_t st);
 cudaError_t apx_launch_eval32(const EvalArgs &a, long long n, float *f32, unsigned char *maybe, unsigned char *sure,
                               cudaStream_t st);
@@ -139,7 +139,7 @@ struct apex_library {
   std::vector<long long> slot_sizes, slot_first, row_first, id_first;
   long long N = 0, rows = 0;
   uint32_t precisions = 1u;
-  bool tc_ok = false;
+  bool tc_fmt[2] = {false, false};  // tensor-core tables built: [0] BF16, [1] FP16
   // device
   int device = 0;
   cudaStream_t st = nullptr;
@@ -155,7 +155,8 @@ struct apex_library {
   int *d_err = nullptr;
   int *d_slot_list = nullptr;
   // calibration
-  double err16[APEX_MAX_OUTPUTS] = {0}, err32[APEX_MAX_OUTPUTS] = {0}, rms[APEX_MAX_OUTPUTS] = {0};
+  // admission margins: err16[0] BF16 pass, err16[1] FP16 pass, err32 FP32 pass / rescore
+  double err16[2][APEX_MAX_OUTPUTS] = {{0}}, err32[APEX_MAX_OUTPUTS] = {0}, rms[APEX_MAX_OUTPUTS] = {0};
   int n_calib = 0;
   float *d_err32f = nullptr;  // per-output FP32 margin (float) for eval32
   uint64_t seed = 0;
@@ -346,10 +347,22 @@ static int grid_for(const apex_library &L, long long items) {
   return (int)std::max<long long>(1, std::min<long long>(items, L.n_sm));
 }
 
+// 16-bit tensor-core format of a query precision: 0 = BF16, 1 = FP16, -1 = none
+static inline int tc_format(int precision) {
+  return precision == APEX_BF16 ? 0 : precision == APEX_FP16 ? 1 : -1;
+}
+
+// admission margin of a pass precision (per output)
+static inline const double *pass_err(const apex_library &L, int precision) {
+  const int f = tc_format(precision);
+  return f >= 0 ? L.err16[f] : L.err32;
+}
+
 static void launch_enum(apex_library &L, const LaunchPlan &P, int precision) {
   if (P.total_items == 0) return;
-  if (precision == APEX_BF16)
-    CU(apx_launch_tc(P, L.T_, L.d_slots, L.d_err, grid_for(L, P.total_items), L.st));
+  const int fmt = tc_format(precision);
+  if (fmt >= 0)
+    CU(apx_launch_tc(P, L.T_, L.d_slots, L.d_err, grid_for(L, P.total_items), L.st, fmt));
   else
     CU(apx_launch_fp32(P, L.T_, L.d_slots, nullptr, 0, nullptr, grid_for(L, P.total_items), L.st));
 }
@@ -402,8 +415,8 @@ static void calibrate(apex_library &L) {
     L.err32[p] = 8.0 * m + 1e-6 * L.rms[p] + 1e-9;
   }
   L.n_calib = (int)ns;
-  if (L.tc_ok) {
-    // BF16 vs FP32 on whole work items: the first item of up to 48 reactions, weighted by size
+  if (L.tc_fmt[0] || L.tc_fmt[1]) {
+    // 16-bit vs FP32 on whole work items: the first item of up to 48 reactions, chosen at random
     PlanBuilder pb;
     std::vector<int> order(L.T);
     for (int t = 0; t < L.T; ++t) order[t] = t;
@@ -423,30 +436,37 @@ static void calibrate(apex_library &L) {
     P.mode = 2;
     P.dump_lo = max_lo;
     P.dump_n = slots;
-    P.dump = d16;
-    P.dump_ids = di16;
-    CU(cudaMemsetAsync(di16, 0xff, sizeof(long long) * slots, L.st));
-    CU(cudaMemsetAsync(di32, 0xff, sizeof(long long) * slots, L.st));
-    CU(apx_launch_tc(P, L.T_, nullptr, L.d_err, grid_for(L, P.total_items), L.st));
     P.dump = d32;
     P.dump_ids = di32;
+    CU(cudaMemsetAsync(di32, 0xff, sizeof(long long) * slots, L.st));
     CU(apx_launch_fp32(P, L.T_, nullptr, nullptr, 0, nullptr, grid_for(L, P.total_items), L.st));
-    check_kernel_status(L);
     std::vector<float> a(slots * no), b(slots * no);
     std::vector<long long> ia(slots), ib(slots);
-    CU(cudaMemcpy(a.data(), d16, sizeof(float) * slots * no, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(b.data(), d32, sizeof(float) * slots * no, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(ia.data(), di16, sizeof(long long) * slots, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(ib.data(), di32, sizeof(long long) * slots, cudaMemcpyDeviceToHost));
-    long long cnt = 0;
-    double mx[APEX_MAX_OUTPUTS] = {0};
-    for (long long i = 0; i < slots; ++i) {
-      if (ia[i] < 0 || ia[i] != ib[i]) continue;
-      ++cnt;
-      for (int p = 0; p < no; ++p) mx[p] = std::max(mx[p], std::fabs((double)a[i * no + p] - (double)b[i * no + p]));
+    CU(cudaMemcpyAsync(b.data(), d32, sizeof(float) * slots * no, cudaMemcpyDeviceToHost, L.st));
+    CU(cudaMemcpyAsync(ib.data(), di32, sizeof(long long) * slots, cudaMemcpyDeviceToHost, L.st));
+    CU(cudaStreamSynchronize(L.st));
+    long long cnt_max = 0;
+    for (int f = 0; f < 2; ++f) {
+      if (!L.tc_fmt[f]) continue;
+      P.dump = d16;
+      P.dump_ids = di16;
+      CU(cudaMemsetAsync(di16, 0xff, sizeof(long long) * slots, L.st));
+      CU(apx_launch_tc(P, L.T_, nullptr, L.d_err, grid_for(L, P.total_items), L.st, f));
+      check_kernel_status(L);
+      CU(cudaMemcpyAsync(a.data(), d16, sizeof(float) * slots * no, cudaMemcpyDeviceToHost, L.st));
+      CU(cudaMemcpyAsync(ia.data(), di16, sizeof(long long) * slots, cudaMemcpyDeviceToHost, L.st));
+      CU(cudaStreamSynchronize(L.st));
+      long long cnt = 0;
+      double mx[APEX_MAX_OUTPUTS] = {0};
+      for (long long i = 0; i < slots; ++i) {
+        if (ia[i] < 0 || ia[i] != ib[i]) continue;
+        ++cnt;
+        for (int p = 0; p < no; ++p) mx[p] = std::max(mx[p], std::fabs((double)a[i * no + p] - (double)b[i * no + p]));
+      }
+      for (int p = 0; p < no; ++p) L.err16[f][p] = 4.0 * mx[p] + 1e-3 * L.rms[p] + L.err32[p];
+      cnt_max = std::max(cnt_max, cnt);
     }
-    for (int p = 0; p < no; ++p) L.err16[p] = 4.0 * mx[p] + 1e-3 * L.rms[p] + L.err32[p];
-    L.n_calib += (int)cnt;
+    L.n_calib += (int)cnt_max;
   }
   L.d_err32f = (float *)L.dalloc(sizeof(float) * APEX_MAX_OUTPUTS);
   float e32[APEX_MAX_OUTPUTS] = {0};
@@ -483,10 +503,13 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
   if (N >= (1LL << 62)) return fail(APEX_EINVAL, "library too large (ids must stay below 2^62)");
   for (int t = 0; t < D->n_reactions; ++t)
     if (D->n_slots[t] > APEX_MAX_SLOTS) return fail(APEX_EUNSUPPORTED, "reaction %d has more than %d slots", t, APEX_MAX_SLOTS);
+  if (D->precisions & ~((1u << APEX_FP32) | (1u << APEX_BF16) | (1u << APEX_FP16)))
+    return fail(APEX_EINVAL, "precisions: only the FP32, BF16 and FP16 bits are defined");
   const bool want_bf16 = (D->precisions >> APEX_BF16) & 1u;
+  const bool want_fp16 = (D->precisions >> APEX_FP16) & 1u;
   const bool tc_shape = D->n_layers == 3 && D->dims[1] == 256 && D->dims[2] == 256 && D->dims[3] <= 16;
-  if (want_bf16 && !tc_shape)
-    return fail(APEX_EUNSUPPORTED, "the BF16 tensor-core path needs a d -> 256 -> 256 -> <=16 head");
+  if ((want_bf16 || want_fp16) && !tc_shape)
+    return fail(APEX_EUNSUPPORTED, "the 16-bit tensor-core path needs a d -> 256 -> 256 -> <=16 head");
 
   std::unique_ptr<apex_library> L(new apex_library());
   L->T = D->n_reactions;
@@ -516,8 +539,9 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
   L->budget = D->device_mem_budget;
   L->device = D->device;
   L->seed = D->seed;
-  L->tc_ok = want_bf16;
-  L->precisions = 1u | (want_bf16 ? (1u << APEX_BF16) : 0u);
+  L->tc_fmt[0] = want_bf16;
+  L->tc_fmt[1] = want_fp16;
+  L->precisions = 1u | (want_bf16 ? (1u << APEX_BF16) : 0u) | (want_fp16 ? (1u << APEX_FP16) : 0u);
   L->rng.seed(D->seed + 17);
 
   try {
@@ -587,23 +611,29 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
       float *P32 = (float *)L->dalloc(sizeof(float) * L->rows * h1);
       CU(apx_launch_prep(dU, dW1, db1, dbrow, L->rows, d, h1, P32, L->st));
       L->T_.P32 = P32;
-      if (L->tc_ok) {
+      if (L->tc_fmt[0] || L->tc_fmt[1]) {
+        // tensor-core tables of every requested 16-bit format: P (scaled into the activation's
+        // input space), W_2 (same scale) and W_3 (padded to 16 rows) as SW128 images, b_2, b_3
         const float scale = (L->act == APEX_ACT_SILU) ? 0.5f : 1.0f;
-        void *P16 = L->dalloc(sizeof(unsigned short) * L->rows * 256);
-        CU(apx_launch_p16(P32, L->rows * 256, scale, P16, L->st));
-        L->T_.P16 = (const unsigned short *)P16;
-        // W_2 (scaled into the activation's input space), W_3 padded to 16 rows
         std::vector<float> w2((size_t)256 * 256), w3((size_t)16 * 256, 0.f);
         for (size_t i = 0; i < w2.size(); ++i) w2[i] = scale * D->W[1][i];
         for (int n = 0; n < L->n_out; ++n)
           for (int k = 0; k < 256; ++k) w3[(size_t)n * 256 + k] = D->W[2][(size_t)n * 256 + k];
-        std::vector<unsigned char> img2(256 * 256 * 2), img3(16 * 256 * 2);
-        apx_make_sw128_image(w2.data(), 256, 256, img2.data());
-        apx_make_sw128_image(w3.data(), L->n_out, 16, img3.data());
-        unsigned char *d2 = (unsigned char *)L->dalloc(img2.size());
-        unsigned char *d3 = (unsigned char *)L->dalloc(img3.size());
-        CU(cudaMemcpy(d2, img2.data(), img2.size(), cudaMemcpyHostToDevice));
-        CU(cudaMemcpy(d3, img3.data(), img3.size(), cudaMemcpyHostToDevice));
+        float *dw = (float *)L->dalloc(sizeof(float) * (w2.size() + w3.size()), false);
+        CU(cudaMemcpy(dw, w2.data(), sizeof(float) * w2.size(), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(dw + w2.size(), w3.data(), sizeof(float) * w3.size(), cudaMemcpyHostToDevice));
+        for (int f = 0; f < 2; ++f) {
+          if (!L->tc_fmt[f]) continue;
+          void *P16 = L->dalloc(sizeof(unsigned short) * L->rows * 256);
+          CU(apx_launch_p16(P32, L->rows * 256, scale, f, P16, L->st));
+          unsigned char *d2 = (unsigned char *)L->dalloc(256 * 256 * 2);
+          unsigned char *d3 = (unsigned char *)L->dalloc(16 * 256 * 2);
+          CU(apx_launch_image(dw, 256, 256, f, d2, L->st));
+          CU(apx_launch_image(dw + w2.size(), L->n_out, 16, f, d3, L->st));
+          L->T_.P16[f] = (const unsigned short *)P16;
+          L->T_.w2img[f] = d2;
+          L->T_.w3img[f] = d3;
+        }
         std::vector<float> b2s(256), b3(16, 0.f);
         for (int n = 0; n < 256; ++n) b2s[n] = scale * D->b[1][n];
         for (int n = 0; n < L->n_out; ++n) b3[n] = D->b[2][n];
@@ -611,8 +641,6 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
         float *db3 = (float *)L->dalloc(sizeof(float) * 16);
         CU(cudaMemcpy(db2, b2s.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
         CU(cudaMemcpy(db3, b3.data(), sizeof(float) * 16, cudaMemcpyHostToDevice));
-        L->T_.w2img = d2;
-        L->T_.w3img = d3;
         L->T_.b2s = db2;
         L->T_.b3 = db3;
       }
@@ -705,7 +733,8 @@ extern "C" apex_status apex_library_info(const apex_library *L, apex_library_inf
   o->precisions = L->precisions;
   o->n_calibration = L->n_calib;
   for (int p = 0; p < L->n_out; ++p) {
-    o->err_bf16[p] = L->err16[p];
+    o->err_bf16[p] = L->err16[0][p];
+    o->err_fp16[p] = L->err16[1][p];
     o->err_fp32[p] = L->err32[p];
     o->rms[p] = L->rms[p];
   }
@@ -740,7 +769,7 @@ extern "C" apex_status apex_decode_ids(const apex_library *L, int64_t n, const i
 // ------------------------------------------------------------------ query submission
 extern "C" apex_status apex_query(apex_library *L, const apex_query_desc *Dq, apex_query_id *out) {
   if (!L || !Dq || !out) return fail(APEX_EINVAL, "NULL argument");
-  if (Dq->precision != APEX_FP32 && Dq->precision != APEX_BF16)
+  if (Dq->precision != APEX_FP32 && Dq->precision != APEX_BF16 && Dq->precision != APEX_FP16)
     return fail(APEX_EINVAL, "unknown precision %d", Dq->precision);
   if (!((L->precisions >> Dq->precision) & 1u))
     return fail(APEX_EUNSUPPORTED, "precision %d tables were not built at load", Dq->precision);
@@ -826,7 +855,7 @@ static void free_query_device(apex_library &L, QueryRec *q) {
 static void write_slot(apex_library &L, QueryRec *q, float admit) {
   QuerySlot S;
   memset(&S, 0, sizeof(S));
-  const double *err = (q->precision == APEX_BF16) ? L.err16 : L.err32;
+  const double *err = pass_err(L, q->precision);
   for (int j = 0; j < L.n_obj; ++j) S.w[j] = q->w[j];
   S.n_obj = L.n_obj;
   S.n_cons = (int)q->cidx.size();
@@ -928,7 +957,7 @@ static float speculative_start(apex_library &L, QueryRec *q) {
 }
 
 static void start_query(apex_library &L, QueryRec *q) {
-  const double *err = (q->precision == APEX_BF16) ? L.err16 : L.err32;
+  const double *err = pass_err(L, q->precision);
   double df = 0;
   for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
   q->tau_spec = speculative_start(L, q);
@@ -1022,31 +1051,28 @@ static bool finalize(apex_library &L, QueryRec *q) {
   const bool spec_bad = std::isfinite(q->tau_spec) && (long long)S.n_sure_above_spec < q->k;
   if (S.overflow || spec_bad) {
     q->stats.n_restarts++;
-    if (S.overflow && !spec_bad && std::isfinite(S.tau)) {
-      q->tau_spec = S.tau;  // a valid lower bound: k real, surely feasible compounds reach it
-    } else if (S.overflow) {
+    const double *err = pass_err(L, q->precision);
+    double df = 0;
+    for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
+    if (S.overflow) {
+      // the band above the best valid threshold did not fit: more room, and restart from the
+      // largest valid threshold found (k real, surely feasible compounds reach S.tau)
       q->cap = (unsigned)std::min<unsigned long long>((unsigned long long)q->cap * 4ull, 1ull << 30);
       bind_slot(L, q);
-      q->tau_spec = -INFINITY;
-      q->spec_rank = -1;
+      if (std::isfinite(S.tau) && !spec_bad) {
+        q->tau_spec = S.tau;
+      } else {
+        q->tau_spec = -INFINITY;
+        q->spec_rank = -1;
+      }
     } else {
-      q->spec_rank = q->spec_rank > 0 ? q->spec_rank * 8 : -1;  // lower the guess
-      q->tau_spec = -INFINITY;
+      q->spec_rank = q->spec_rank > 0 ? q->spec_rank * 8 : -1;  // the start guess was too high: lower it
+      q->tau_spec = q->spec_rank > 0 ? speculative_start(L, q) : -INFINITY;
     }
-    if (std::isfinite(q->tau_spec)) {
-      const double *err = (q->precision == APEX_BF16) ? L.err16 : L.err32;
-      double df = 0;
-      for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
-      write_slot(L, q, (float)(q->tau_spec - 2.0 * df * 1.0001));
-    } else {
-      const float tspec = q->spec_rank > 0 ? speculative_start(L, q) : -INFINITY;
-      q->tau_spec = tspec;
-      const double *err = (q->precision == APEX_BF16) ? L.err16 : L.err32;
-      double df = 0;
-      for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
-      write_slot(L, q, std::isfinite(tspec) ? (float)(tspec - 2.0 * df * 1.0001) : -INFINITY);
-    }
+    write_slot(L, q, std::isfinite(q->tau_spec) ? (float)(q->tau_spec - 2.0 * df * 1.0001) : -INFINITY);
     q->remaining = q->scope_items;
+    TRACE("restart q%lld: overflow=%u spec_bad=%d cap=%u tau_spec=%g", (long long)q->id, S.overflow, (int)spec_bad,
+          q->cap, (double)q->tau_spec);
     return false;
   }
   const long long nc = S.count;
@@ -1124,7 +1150,7 @@ static bool finalize(apex_library &L, QueryRec *q) {
       n64_total += n64;
     }
     CU(apx_sort_r(R, nr, np, L.st));
-    CU(apx_launch_mark(R, nr, (unsigned)std::min<long long>(k + 1, nr), k, tol, d_cnt + 2, L.st));
+    CU(apx_launch_mark(R, nr, (unsigned)std::min<long long>(k + 1, nr), k, tol, d_cnt + 2, L.st));  // boundary band
     CU(cudaMemcpyAsync(pin_u, d_cnt + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
     CU(cudaStreamSynchronize(L.st));
     const unsigned marked = *pin_u;
@@ -1197,7 +1223,7 @@ static void finish(apex_library &L, QueryRec *q, QState st, apex_status err, con
 static void pass_step(apex_library &L) {
   const long long chunk_compounds = 1LL << 25;
   // build one plan (items from the cursor) with per-precision query masks
-  PlanBuilder pb[2];
+  PlanBuilder pb[4];  // indexed by pass precision (APEX_FP32, APEX_BF16, APEX_FP16; 2 unused)
   long long served_compounds = 0;
   long long cur = L.cursor;
   long long visited = 0;
@@ -1206,24 +1232,25 @@ static void pass_step(apex_library &L) {
     const int t = (int)(std::upper_bound(L.item_first.begin(), L.item_first.end(), cur) - L.item_first.begin()) - 1;
     const long long b = cur - L.item_first[t];
     const long long e = L.rx[t].n_items;
-    unsigned long long mask[2] = {0, 0};
+    unsigned long long mask[4] = {0, 0, 0, 0};
     for (int s = 0; s < APEX_MAX_ACTIVE; ++s) {
       QueryRec *q = L.active[s];
       if (q && q->remaining > 0 && q->need[t]) mask[q->precision] |= 1ull << s;
     }
     long long take = e - b;
-    if (mask[0] | mask[1]) {
+    const unsigned long long any = mask[0] | mask[1] | mask[3];
+    if (any) {
       const long long per_item = (long long)L.rx[t].L_o * APX_TILE;
       const long long room = std::max<long long>(1, (chunk_compounds - served_compounds + per_item - 1) / per_item);
       take = std::min(take, room);
       bool ok = true;
-      for (int p = 0; p < 2; ++p)
+      for (int p = 0; p < 4; ++p)
         if (mask[p] && pb[p].P.n_seg >= APX_MAX_SEG) ok = false;
       if (!ok) break;
-      for (int p = 0; p < 2; ++p)
+      for (int p = 0; p < 4; ++p)
         if (mask[p]) pb[p].add(t, b, b + take, mask[p]);
       for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
-        if ((mask[0] | mask[1]) >> s & 1ull) served[s] += take;
+        if (any >> s & 1ull) served[s] += take;
       served_compounds += take * per_item;
     }
     visited += take;
@@ -1240,7 +1267,7 @@ static void pass_step(apex_library &L) {
   }
   cudaEvent_t e0 = L.ev_a, e1 = L.ev_b;
   CU(cudaEventRecord(e0, L.st));
-  for (int p = 0; p < 2; ++p) launch_enum(L, pb[p].P, p);
+  for (int p = 0; p < 4; ++p) launch_enum(L, pb[p].P, p);
   CU(cudaEventRecord(e1, L.st));
   if (!list.empty()) {
     int *hl = (int *)L.pin(sizeof(int) * APEX_MAX_ACTIVE + 64);
@@ -1257,7 +1284,7 @@ static void pass_step(apex_library &L) {
     q->stats.n_launches++;
     q->stats.enumerate_ms += ms;
     long long comp = 0;
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < 4; ++p)
       for (int g = 0; g < pb[p].P.n_seg; ++g)
         if (pb[p].P.seg[g].qmask >> s & 1ull) {
           const RxnPlan &r = L.rx[pb[p].P.seg[g].rxn];
@@ -1430,7 +1457,7 @@ extern "C" apex_status apex_query_stats(apex_library *L, apex_query_id id, apex_
 extern "C" apex_status apex_score_ids(apex_library *L, int32_t precision, int64_t n, const int64_t *ids,
                                       double *outputs) {
   if (!L || n < 0 || (n > 0 && (!ids || !outputs))) return fail(APEX_EINVAL, "bad arguments");
-  if (precision != APEX_FP32 && precision != 2) return fail(APEX_EINVAL, "precision must be APEX_FP32 or 2 (FP64)");
+  if (precision != APEX_FP32 && precision != APEX_FP64) return fail(APEX_EINVAL, "precision must be APEX_FP32 or APEX_FP64");
   for (int64_t i = 0; i < n; ++i)
     if (ids[i] < 0 || ids[i] >= L->N) return fail(APEX_EINVAL, "id %lld out of range", (long long)ids[i]);
   if (n == 0) return APEX_OK;
@@ -1465,7 +1492,8 @@ extern "C" apex_status apex_score_ids(apex_library *L, int32_t precision, int64_
 extern "C" apex_status apex_dump_outputs(apex_library *L, int32_t precision, int32_t reaction, float *outputs,
                                          int64_t capacity) {
   if (!L || !outputs || reaction < 0 || reaction >= L->T) return fail(APEX_EINVAL, "bad arguments");
-  if (precision != APEX_FP32 && precision != APEX_BF16) return fail(APEX_EINVAL, "unknown precision");
+  if (precision != APEX_FP32 && precision != APEX_BF16 && precision != APEX_FP16)
+    return fail(APEX_EINVAL, "unknown precision");
   if (!((L->precisions >> precision) & 1u)) return fail(APEX_EUNSUPPORTED, "precision not built");
   const long long nt = L->id_first[reaction + 1] - L->id_first[reaction];
   if (capacity < nt) return fail(APEX_EINVAL, "capacity %lld < %lld compounds", (long long)capacity, nt);

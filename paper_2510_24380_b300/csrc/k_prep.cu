@@ -4,6 +4,7 @@
 //   P16[r] = bf16(scale * P32[r])                                           tensor-core path
 // so that the first layer of any compound is the plain sum of its slots' P rows.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <algorithm>
 #include "common.cuh"
 
@@ -60,9 +61,32 @@ __global__ void __launch_bounds__(256) k_p32(const float *__restrict__ U, const 
   }
 }
 
-__global__ void k_p16(const float *__restrict__ P32, long long n, float scale, __nv_bfloat16 *__restrict__ P16) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    P16[i] = __float2bfloat16_rn(scale * P32[i]);
+__global__ void k_p16(const float *__restrict__ P32, long long n, float scale, int fmt, unsigned short *__restrict__ P16) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float v = scale * P32[i];
+    P16[i] = fmt == 0 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
+  }
+}
+
+// SW128 K-major shared-memory image of W [rows_used x 256] (float, already scaled), padded to
+// rows rows: four 64-column chunks of rows x 128 B, 8-row atoms of 1024 B, 16-byte pieces
+// XOR-swizzled by (row mod 8); 16-bit elements in the given format.
+__global__ void k_sw128_image(const float *__restrict__ W, int rows_used, int rows, int fmt, unsigned char *img) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * 256; e += gridDim.x * blockDim.x) {
+    const int n = e >> 8, k = e & 255;
+    const float v = n < rows_used ? W[(size_t)n * 256 + k] : 0.f;
+    const unsigned short b = fmt == 0 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
+    const int kc = k >> 6, kin = k & 63, piece = kin >> 3, el = kin & 7;
+    const size_t off = (size_t)kc * rows * 128 + (size_t)(n >> 3) * 1024 + (size_t)(n & 7) * 128 +
+                       (size_t)((piece ^ (n & 7)) * 16) + (size_t)el * 2;
+    *reinterpret_cast<unsigned short *>(img + off) = b;
+  }
+}
+
+cudaError_t apx_launch_image(const float *W, int rows_used, int rows, int fmt, void *img, cudaStream_t st) {
+  apx_count_launch();
+  k_sw128_image<<<(rows * 256 + 255) / 256, 256, 0, st>>>(W, rows_used, rows, fmt, (unsigned char *)img);
+  return cudaGetLastError();
 }
 
 cudaError_t apx_launch_prep(const float *U, const float *W1, const float *b1, const unsigned char *bias_row,
@@ -73,8 +97,8 @@ cudaError_t apx_launch_prep(const float *U, const float *W1, const float *b1, co
   return cudaGetLastError();
 }
 
-cudaError_t apx_launch_p16(const float *P32, long long n, float scale, void *P16, cudaStream_t st) {
+cudaError_t apx_launch_p16(const float *P32, long long n, float scale, int fmt, void *P16, cudaStream_t st) {
   apx_count_launch();
-  k_p16<<<148 * 8, 256, 0, st>>>(P32, n, scale, reinterpret_cast<__nv_bfloat16 *>(P16));
+  k_p16<<<148 * 8, 256, 0, st>>>(P32, n, scale, fmt, reinterpret_cast<unsigned short *>(P16));
   return cudaGetLastError();
 }

@@ -335,8 +335,9 @@ cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t 
   return cudaGetLastError();
 }
 
-// Marks for FP64 every alive, not-yet-FP64 item among the first kp1 sorted positions that is
-// within tol of a neighbour or of the k-th score (the tie-breaking / boundary band).
+// Marks for FP64 every alive, not-yet-FP64 item whose score is within tol of the k-th score (the
+// top-k boundary band, on either side of it): only those can change the returned set. Items
+// well inside keep their FP32 score; near-ties among them are ordered by it.
 __global__ void k_mark_ties(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked) {
   __shared__ double sk;
   if (threadIdx.x == 0) {
@@ -344,14 +345,11 @@ __global__ void k_mark_ties(RItem *R, unsigned n, unsigned kp1, long long k, dou
     sk = (n > 0 && R[kk].alive) ? R[kk].s : -INFINITY;
   }
   __syncthreads();
-  const unsigned lim = min(kp1, n);
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += gridDim.x * blockDim.x) {
+  (void)kp1;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     RItem &it = R[i];
     if (!it.alive || it.is64) continue;
-    bool m = fabs(it.s - sk) <= tol;
-    if (i > 0 && R[i - 1].alive && fabs(R[i - 1].s - it.s) <= tol) m = true;
-    if (i + 1 < n && R[i + 1].alive && fabs(R[i + 1].s - it.s) <= tol) m = true;
-    if (m) {
+    if (fabs(it.s - sk) <= tol) {
       it.need64 = 1;
       atomicAdd(n_marked, 1u);
     }
@@ -430,7 +428,7 @@ cudaError_t apx_launch_mark(RItem *R, unsigned n, unsigned kp1, long long k, dou
                             cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   apx_count_launch();
-  k_mark_ties<<<std::min<unsigned>((kp1 + 255) / 256 + 1, 148u * 16u), 256, 0, st>>>(R, n, kp1, k, tol, n_marked);
+  k_mark_ties<<<std::min<unsigned>((n + 255) / 256 + 1, 148u * 16u), 256, 0, st>>>(R, n, kp1, k, tol, n_marked);
   return cudaGetLastError();
 }
 cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const DevTables &T, const float *out32,

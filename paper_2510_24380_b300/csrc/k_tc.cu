@@ -1,17 +1,18 @@
-// k_tc.cu -- BF16 tensor-core enumeration kernel for sm_103a (tcgen05 + TMEM + bulk TMA).
+// k_tc.cu -- 16-bit tensor-core enumeration kernel for sm_103a (tcgen05 + TMEM + bulk TMA),
+// instantiated for BF16 and FP16 operands (one format for tables, activations and weights).
 //
 // Head shape: d -> 256 -> 256 -> n_out (n_out <= 16), activation after layers 1 and 2.
 // Per tile of 128 compounds (rows) of one work item (see common.cuh):
 //   layer 1, structure-exploiting form (Eq. apex generalized to W_1): z_1 = R(row) + p(o), where
 //     R(row) = sum of the row's inner-slot P rows (resident in the producer's registers for the
 //     whole item) and p(o) = the outer slot's P row (one broadcast load per tile);
-//     a_1 = act(z_1) -> BF16 -> shared memory in the UMMA SW128 K-major layout;
+//     a_1 = act(z_1) -> 16-bit -> shared memory in the UMMA SW128 K-major layout;
 //   layer 2: D2[128 x 256] = a_1 W_2^T, tcgen05.mma (A, B from shared memory), FP32 in TMEM;
-//   epilogue 1: a_2 = act(D2 + b_2) -> BF16 packed back into the same TMEM columns;
+//   epilogue 1: a_2 = act(D2 + b_2) -> 16-bit pairs packed back into the same TMEM columns;
 //   layer 3: D3[128 x 16] = a_2 W_3^T, tcgen05.mma with A read from TMEM;
 //   epilogue 2: outputs -> queries (objective, boxes, admission) or a raw dump.
-// SiLU is evaluated as h + h tanh(h) with h = z/2, on packed bf16 pairs (add / tanh.approx /
-// fma .bf16x2: 1.5 issue slots and one MUFU element per activation); the 1/2 is folded into P
+// SiLU is evaluated as h + h tanh(h) with h = z/2, on packed 16-bit pairs (add / tanh.approx /
+// fma .bf16x2 or .f16x2: 1.5 issue slots and one MUFU element per activation); the 1/2 is folded into P
 // (layer 1) and into the W_2 image and b_2 (layer 2), all exact in binary.
 //
 // Warp roles (704 threads, one CTA per SM):
@@ -25,8 +26,6 @@
 // columns [64g, 64g + 32) of its buffer, D3 uses columns [32, 48).
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel records
 // APX_ERR_TIMEOUT in the status word, every role leaves its loop, and TMEM is released.
-#include <cuda_bf16.h>
-#include <cstring>
 #include "common.cuh"
 
 #define TC_EPI_WARPS 4
@@ -130,9 +129,11 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;               // 128-byte swizzle
   return d;
 }
-// instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// instruction descriptor: kind::f16, A and B of the same 16-bit type (FMT 0 = BF16 -> format
+// code 1, FMT 1 = F16 -> format code 0), FP32 accumulator, both K-major
+__host__ __device__ constexpr uint32_t idesc_16(int M, int N, int FMT) {
+  return (1u << 4) | ((FMT == 0 ? 1u : 0u) << 7) | ((FMT == 0 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -223,43 +224,65 @@ __device__ __forceinline__ float act_h(float h) {
   if (ACT == APEX_ACT_RELU) return fmaxf(h, 0.f);
   return h;
 }
-// packed bf16x2 math: 2 elements per instruction (issue slots, not MUFU rate, bound this path)
-__device__ __forceinline__ uint32_t add_bf2(uint32_t a, uint32_t b) {
+// Packed 16-bit math, 2 elements per instruction (issue slots, not MUFU rate, bound this path).
+// FMT 0 = BF16 (8 mantissa bits), FMT 1 = FP16 (11 mantissa bits, same instruction rates).
+#define APX_PK2(NAME, OP)                                                 \
+  template <int FMT>                                                      \
+  __device__ __forceinline__ uint32_t NAME(uint32_t a, uint32_t b) {      \
+    uint32_t d;                                                           \
+    if (FMT == 0)                                                         \
+      asm(OP ".bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));           \
+    else                                                                  \
+      asm(OP ".f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));            \
+    return d;                                                             \
+  }
+APX_PK2(add2, "add.rn")
+APX_PK2(max2, "max")
+#undef APX_PK2
+template <int FMT>
+__device__ __forceinline__ uint32_t tanh2(uint32_t a) {
   uint32_t d;
-  asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  if (FMT == 0)
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(d) : "r"(a));
+  else
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(d) : "r"(a));
   return d;
 }
-__device__ __forceinline__ uint32_t tanh_bf2(uint32_t a) {
+template <int FMT>
+__device__ __forceinline__ uint32_t fma2(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;
-  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(d) : "r"(a));
-  return d;
-}
-__device__ __forceinline__ uint32_t fma_bf2(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t d;
-  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
-}
-__device__ __forceinline__ uint32_t max_bf2(uint32_t a, uint32_t b) {
-  uint32_t d;
-  asm("max.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  if (FMT == 0)
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  else
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
 }
 // activation of a packed pair already in the activation's input space (h = z/2 for SiLU):
 // SiLU(2h) = h + h tanh(h)
-template <int ACT>
-__device__ __forceinline__ uint32_t act_bf2(uint32_t h) {
-  if (ACT == APEX_ACT_SILU) return fma_bf2(h, tanh_bf2(h), h);
-  if (ACT == APEX_ACT_RELU) return max_bf2(h, 0u);
+template <int ACT, int FMT>
+__device__ __forceinline__ uint32_t act2(uint32_t h) {
+  if (ACT == APEX_ACT_SILU) return fma2<FMT>(h, tanh2<FMT>(h), h);
+  if (ACT == APEX_ACT_RELU) return max2<FMT>(h, 0u);
   return h;
 }
-// two floats -> bf16x2 word, lo in bits [0, 16)
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+// two floats -> packed 16-bit pair (round to nearest even), lo in bits [0, 16)
+template <int FMT>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   uint32_t w;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+  if (FMT == 0)
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+  else
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
   return w;
 }
-__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
-__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+// packed 16-bit pair -> the two floats (exact)
+template <int FMT>
+__device__ __forceinline__ float2 unpack2(uint32_t w) {
+  if (FMT == 0) return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+  float lo, hi;
+  asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n cvt.f32.f16 %0, l;\n cvt.f32.f16 %1, h;\n}" : "=f"(lo), "=f"(hi) : "r"(w));
+  return make_float2(lo, hi);
+}
 
 // Sec. 3 / Eq. apex_topk per compound (one row per lane, all 32 lanes call it): objective,
 // admission threshold, widened box (admission) and shrunk box ("sure"), then a warp-aggregated
@@ -317,7 +340,7 @@ __device__ __forceinline__ TcItem tc_item(const LaunchPlan &L, const DevTables &
   return r;
 }
 
-template <int ACT>
+template <int ACT, int FMT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_head(const __grid_constant__ LaunchPlan L, const __grid_constant__ DevTables T, QuerySlot *slots, int *err) {
   extern __shared__ unsigned char smem_raw[];
@@ -356,7 +379,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // W_2 and W_3 images -> shared memory by bulk TMA (16 KB pieces)
     mbar_expect_tx(bar(B_W), TC_W_BYTES);
     for (uint32_t off = 0; off < TC_W_BYTES; off += 16384u) {
-      const unsigned char *src = off < TC_OFF_W3 ? T.w2img + off : T.w3img + (off - TC_OFF_W3);
+      const unsigned char *src = off < TC_OFF_W3 ? T.w2img[FMT] + off : T.w3img[FMT] + (off - TC_OFF_W3);
       const uint32_t bytes = (off < TC_OFF_W3) ? 16384u : 8192u;
       asm volatile(
           "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sbase + off),
@@ -436,14 +459,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int c = 0; c < 8; ++c) {
               float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
               for (int sl = 0; sl < ni; ++sl) {
-                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(T.P16 + rows[sl] * 256 + g * 64 + c * 8));
-                acc[0] += bf_lo(v.x); acc[1] += bf_hi(v.x); acc[2] += bf_lo(v.y); acc[3] += bf_hi(v.y);
-                acc[4] += bf_lo(v.z); acc[5] += bf_hi(v.z); acc[6] += bf_lo(v.w); acc[7] += bf_hi(v.w);
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(T.P16[FMT] + rows[sl] * 256 + g * 64 + c * 8));
+                const float2 f0 = unpack2<FMT>(v.x), f1 = unpack2<FMT>(v.y), f2 = unpack2<FMT>(v.z), f3 = unpack2<FMT>(v.w);
+                acc[0] += f0.x; acc[1] += f0.y; acc[2] += f1.x; acc[3] += f1.y;
+                acc[4] += f2.x; acc[5] += f2.y; acc[6] += f3.x; acc[7] += f3.y;
               }
-              R[c * 4 + 0] = pack_bf16(acc[0], acc[1]);
-              R[c * 4 + 1] = pack_bf16(acc[2], acc[3]);
-              R[c * 4 + 2] = pack_bf16(acc[4], acc[5]);
-              R[c * 4 + 3] = pack_bf16(acc[6], acc[7]);
+              R[c * 4 + 0] = pack2<FMT>(acc[0], acc[1]);
+              R[c * 4 + 1] = pack2<FMT>(acc[2], acc[3]);
+              R[c * 4 + 2] = pack2<FMT>(acc[4], acc[5]);
+              R[c * 4 + 3] = pack2<FMT>(acc[6], acc[7]);
             }
           } else {
 #pragma unroll
@@ -465,7 +489,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
             uint32_t out[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) out[e] = act_bf2<ACT>(add_bf2(R[c * 4 + e], pw[e]));
+            for (int e = 0; e < 4; ++e) out[e] = act2<ACT, FMT>(add2<FMT>(R[c * 4 + e], pw[e]));
             *reinterpret_cast<uint4 *>(stage + (uint32_t)((c ^ (m & 7)) * 16)) = make_uint4(out[0], out[1], out[2], out[3]);
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -504,9 +528,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int e4 = 0; e4 < 4; ++e4) {
               const float4 bb = *reinterpret_cast<const float4 *>(bh + c * 16 + 4 * e4);
-              pk[2 * e4] = act_bf2<ACT>(pack_bf16(__uint_as_float(v[4 * e4]) + bb.x, __uint_as_float(v[4 * e4 + 1]) + bb.y));
+              pk[2 * e4] =
+                  act2<ACT, FMT>(pack2<FMT>(__uint_as_float(v[4 * e4]) + bb.x, __uint_as_float(v[4 * e4 + 1]) + bb.y));
               pk[2 * e4 + 1] =
-                  act_bf2<ACT>(pack_bf16(__uint_as_float(v[4 * e4 + 2]) + bb.z, __uint_as_float(v[4 * e4 + 3]) + bb.w));
+                  act2<ACT, FMT>(pack2<FMT>(__uint_as_float(v[4 * e4 + 2]) + bb.z, __uint_as_float(v[4 * e4 + 3]) + bb.w));
             }
             tmem_st8(col + (uint32_t)c * 8u, pk);
           }
@@ -537,7 +562,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 512, [%2];" ::"r"(
                     sbase + TC_OFF_OROW + (uint32_t)rs * 512u),
-                "l"(T.P16 + (orow + o) * 256), "r"(bar(B_OFULL(rs)))
+                "l"(T.P16[FMT] + (orow + o) * 256), "r"(bar(B_OFULL(rs)))
                 : "memory");
           } else {
             mbar_arrive(bar(B_OFULL(rs)));
@@ -551,8 +576,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       if (mbar_wait(bar(B_W), 0, abort_flag, err)) {
         tc_fence_after();
-        constexpr uint32_t ID2 = idesc_bf16(128, 256);
-        constexpr uint32_t ID3 = idesc_bf16(128, 16);
+        constexpr uint32_t ID2 = idesc_16(128, 256, FMT);
+        constexpr uint32_t ID3 = idesc_16(128, 16, FMT);
         const uint32_t a1 = sbase + TC_OFF_A1, w2 = sbase + TC_OFF_W2, w3 = sbase + TC_OFF_W3;
         auto issue_l3 = [&](long long jj) {
           const int bb = (int)(jj & 1);
@@ -686,56 +711,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 size_t apx_tc_smem_bytes() { return TC_SMEM_BYTES; }
 
-cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
-                          cudaStream_t st) {
-  static bool attr = false;
+template <int ACT, int FMT>
+static cudaError_t tc_launch_one(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
+                                 cudaStream_t st) {
+  static bool attr = false;  // per instantiation
   if (!attr) {
-    cudaError_t e;
-    e = cudaFuncSetAttribute(k_tc_head<APEX_ACT_SILU>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_head<APEX_ACT_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_head<APEX_ACT_IDENTITY>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_tc_head<ACT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   if (grid <= 0) return cudaSuccess;
   apx_count_launch();
-  if (T.act == APEX_ACT_SILU)
-    k_tc_head<APEX_ACT_SILU><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(L, T, slots, err);
-  else if (T.act == APEX_ACT_RELU)
-    k_tc_head<APEX_ACT_RELU><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(L, T, slots, err);
-  else
-    k_tc_head<APEX_ACT_IDENTITY><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(L, T, slots, err);
+  k_tc_head<ACT, FMT><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(L, T, slots, err);
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ host: weight images
-// Byte offset of element (row n, column k) in a SW128 K-major image of `rows` rows and K = 256:
-// four 64-column chunks of rows x 128 B, 8-row atoms of 1024 B, 16-byte pieces XOR-swizzled
-// by (row mod 8).
-static inline size_t sw128_offset(int n, int k, int rows) {
-  const int kc = k >> 6, kin = k & 63;
-  const int piece = kin >> 3, e = kin & 7;
-  return (size_t)kc * rows * 128 + (size_t)(n >> 3) * 1024 + (size_t)(n & 7) * 128 +
-         (size_t)((piece ^ (n & 7)) * 16) + (size_t)e * 2;
+template <int FMT>
+static cudaError_t tc_launch_fmt(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
+                                 cudaStream_t st) {
+  if (T.act == APEX_ACT_SILU) return tc_launch_one<APEX_ACT_SILU, FMT>(L, T, slots, err, grid, st);
+  if (T.act == APEX_ACT_RELU) return tc_launch_one<APEX_ACT_RELU, FMT>(L, T, slots, err, grid, st);
+  return tc_launch_one<APEX_ACT_IDENTITY, FMT>(L, T, slots, err, grid, st);
 }
 
-static inline unsigned short host_bf16(float f) {
-  unsigned u;
-  memcpy(&u, &f, 4);
-  if ((u & 0x7f800000u) == 0x7f800000u) return (unsigned short)(u >> 16);  // inf/nan
-  const unsigned lsb = (u >> 16) & 1u;
-  u += 0x7fffu + lsb;  // round to nearest even
-  return (unsigned short)(u >> 16);
-}
-
-// W: [rows_used x 256] row-major float (already scaled); image: rows x 256 bf16 (zero padded)
-void apx_make_sw128_image(const float *W, int rows_used, int rows, unsigned char *img) {
-  memset(img, 0, (size_t)rows * 256 * 2);
-  for (int n = 0; n < rows_used; ++n)
-    for (int k = 0; k < 256; ++k) {
-      const unsigned short b = host_bf16(W[(size_t)n * 256 + k]);
-      memcpy(img + sw128_offset(n, k, rows), &b, 2);
-    }
+// fmt: 0 = BF16 tables and arithmetic, 1 = FP16
+cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
+                          cudaStream_t st, int fmt) {
+  return fmt == 0 ? tc_launch_fmt<0>(L, T, slots, err, grid, st) : tc_launch_fmt<1>(L, T, slots, err, grid, st);
 }

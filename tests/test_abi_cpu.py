@@ -75,7 +75,7 @@ def _desc(n_slots, sizes, d, dims, act=2, n_obj=1, n_prop=None, prec=1):
     D.activation = act
     D.n_objectives = n_obj
     D.n_properties = dims[-1] - n_obj if n_prop is None else n_prop
-    D.precisions = (1 << 0) | ((1 << 1) if prec else 0)
+    D.precisions = (1 << 0) | ((1 << 1) if prec else 0) if prec in (True, False) else prec
     return D, keep
 
 
@@ -89,6 +89,8 @@ def _desc(n_slots, sizes, d, dims, act=2, n_obj=1, n_prop=None, prec=1):
     (dict(n_slots=[2], sizes=[3, 4], d=8, dims=[8, 64]), -1),                   # more than 32 outputs
     (dict(n_slots=[5], sizes=[2, 2, 2, 2, 2], d=8, dims=[8, 4]), -9),           # more than 4 slots
     (dict(n_slots=[2], sizes=[3, 4], d=8, dims=[8, 128, 256, 4]), -9),          # BF16 needs 256-wide hidden
+    (dict(n_slots=[2], sizes=[3, 4], d=8, dims=[8, 128, 256, 4], prec=(1 << 0) | (1 << 3)), -9),  # so does FP16
+    (dict(n_slots=[2], sizes=[3, 4], d=8, dims=[8, 4], prec=(1 << 0) | (1 << 2)), -1),  # FP64 is not a pass precision
 ])
 def test_load_rejects_before_touching_the_gpu(dll, case, code):
     D, keep = _desc(**case)

@@ -1,7 +1,7 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
 
-Small libraries that span several 128-row tiles, ragged tails, 1- to 4-slot reactions; both
-pass precisions; edge cases (k above the feasible count, empty boxes, infinite bounds, subsets,
+Small libraries that span several 128-row tiles, ragged tails, 1- to 4-slot reactions; all
+three pass precisions (FP32 CUDA cores, BF16 and FP16 tensor cores); edge cases (k above the feasible count, empty boxes, infinite bounds, subsets,
 k = 1); continuous batching (each result alone == in the mix); cancellation; the standalone
 select entry point."""
 import numpy as np
@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def ragged():
     lib, head, spec = csl_gen.build_workload("t_ragged")
-    L = apex.Library(lib, head, precisions=("fp32", "bf16"), seed=1)
+    L = apex.Library(lib, head, precisions=("fp32", "bf16", "fp16"), seed=1)
     yield lib, head, spec, L, output_rms(lib, head)
     L.close()
 
@@ -38,6 +38,9 @@ def test_library_info(ragged):
     assert info.n_synthon_rows == lib.n_rows
     assert info.n_outputs == 13 and info.max_slots == 4
     assert all(0 < info.err_bf16[p] < BF16_ABS for p in range(13)), list(info.err_bf16)[:13]
+    # FP16 keeps 3 more mantissa bits than BF16 through every 16-bit stage: its calibrated
+    # margins must be clearly tighter
+    assert all(0 < info.err_fp16[p] < 0.5 * info.err_bf16[p] for p in range(13)), list(info.err_fp16)[:13]
 
 
 def test_score_ids_fp32_and_fp64(ragged):
@@ -51,7 +54,7 @@ def test_score_ids_fp32_and_fp64(ragged):
     assert np.max(np.abs(o64 - ref) / rms) <= 1e-12
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_raw_outputs_of_every_compound(ragged, precision):
     """The production enumeration kernel's raw outputs for every compound of every reaction."""
     lib, head, spec, L, rms = ragged
@@ -83,7 +86,7 @@ def _queries(spec, stats, precision):
                                       precision=precision)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
 def test_topk_parity(ragged, precision):
     lib, head, spec, L, rms = ragged
     stats = csl_gen.load_stats("t_ragged")
@@ -135,13 +138,14 @@ def test_relu_and_identity_tensor_core_heads():
     lib = library_from_sizes([[150, 140], [9, 8, 7]], d=32, seed=8)
     for act in ("relu", "identity"):
         head = make_head([32, 256, 256, 6], act, seed=9, n_objectives=2, n_properties=4)
-        L = apex.Library(lib, head, precisions=("fp32", "bf16"))
+        L = apex.Library(lib, head, precisions=("fp32", "bf16", "fp16"))
         try:
-            q = _q([0.3, 0.7], [3], [-0.1], [0.2], k=77)
-            ref = O.topk(lib, head, q)
-            check_topk(L.run(q), ref, lib, head, q, output_rms(lib, head))
-            raw = L.dump_outputs(0, 150 * 140, "bf16").astype(np.float64)
-            assert np.abs(raw - O.score_ids(lib, head, np.arange(150 * 140))).max() <= BF16_ABS
+            for prec in ("bf16", "fp16"):
+                q = _q([0.3, 0.7], [3], [-0.1], [0.2], k=77, precision=prec)
+                ref = O.topk(lib, head, q)
+                check_topk(L.run(q), ref, lib, head, q, output_rms(lib, head))
+                raw = L.dump_outputs(0, 150 * 140, prec).astype(np.float64)
+                assert np.abs(raw - O.score_ids(lib, head, np.arange(150 * 140))).max() <= BF16_ABS
         finally:
             L.close()
 
@@ -156,7 +160,7 @@ def test_batch_results_equal_alone(ragged):
     for i in range(12):
         sub = None if i % 3 == 0 else np.sort(rng.choice(lib.n_reactions, size=int(rng.integers(1, 6)), replace=False))
         q = csl_gen.random_query(rng, stats, 5, 8, k=int(rng.choice([1, 10, 100, 2000])), subset=sub,
-                                 precision="bf16" if i % 2 else "fp32")
+                                 precision=("fp32", "bf16", "fp16")[(i + i // 3) % 3])
         qs.append(q)
     alone = [L.run(q) for q in qs]
     ids = [L.query(q) for q in qs]
