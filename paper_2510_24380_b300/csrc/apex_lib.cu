@@ -32,7 +32,8 @@
 // ------------------------------------------------------------------ kernels (other files)
 cudaError_t apx_launch_fp32(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, const long long *ids,
                             long long n_ids, float *out, int grid, cudaStream_t st);
-cudaError_t apx_launch_fp64(const DevTables &T, const long long *ids, long long n, double *out, cudaStream_t st);
+cudaError_t apx_launch_fp64(const DevTables &T, const long long *ids, long long n, double *out, cudaStream_t st,
+                            const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_prep(const float *U, const float *W1, const float *b1, const unsigned char *bias_row,
                             long long rows, int K, int N, float *P32, cudaStream_t st);
 cudaError_t apx_launch_p16(const float *P32, long long n, float scale, int fmt, void *P16, cudaStream_t st);
@@ -45,18 +46,23 @@ cudaError_t apx_launch_eval32(const EvalArgs &a, long long n, float *f32, unsign
 cudaError_t apx_launch_kth(const float *keys, const unsigned char *flag, long long n, long long k, float *out_tau,
                            int *out_ok, cudaStream_t st);
 cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
-                               const unsigned char *sure, float thr, RItem *R, unsigned *n_r, cudaStream_t st);
+                               const unsigned char *sure, const float *tau32, float margin2, RItem *R, unsigned *n_r,
+                               cudaStream_t st);
 cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64, cudaStream_t st);
-cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, int n_out,
-                               const QuerySlot *Q, const double *lo, const double *hi, double *out_rows,
+cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, const unsigned *n64_dev,
+                               int n_out, const QuerySlot *Q, const double *lo, const double *hi, double *out_rows,
                                cudaStream_t st);
 cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st);
 cudaError_t apx_launch_mark(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked,
                             cudaStream_t st);
-cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const DevTables &T, const float *out32,
-                            const double *out64_rows, long long *ids, int *rxn, long long *syn, double *obj,
-                            double *outs, cudaStream_t st);
-int apx_count_alive(const RItem *R, unsigned n, cudaStream_t st, unsigned *d_tmp, cudaError_t *e);
+cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const unsigned *n_alive, const DevTables &T,
+                            const float *out32, const double *out64_rows, long long *ids, int *rxn, long long *syn,
+                            double *obj, double *outs, cudaStream_t st);
+cudaError_t apx_launch_count_alive(const RItem *R, unsigned n, unsigned *d_out, cudaStream_t st);
+cudaError_t apx_launch_spec_ids(const int *rxn, const long long *pre, int n_sub, const long long *id_first,
+                                long long scope_n, unsigned long long seed, long long S, long long *ids, cudaStream_t st);
+cudaError_t apx_launch_spec_select(const float *out, long long S, const SpecArgs &a, float *keys, unsigned char *flag,
+                                   QuerySlot *slot, cudaStream_t st);
 
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_err;
@@ -882,9 +888,6 @@ static void write_slot(apex_library &L, QueryRec *q, float admit) {
   CU(cudaMemcpyAsync(L.d_slots + q->slot, &S, sizeof(S), cudaMemcpyHostToDevice, L.st));
 }
 
-// Start threshold guess: the rank-r best objective among surely feasible compounds of a seeded
-// FP32 sample of the query's scope, r chosen so that ~3k scope compounds are expected above it.
-// Only a guess: finalization verifies it (>= k sure entries at or above it) or restarts lower.
 static bool trace_on() {
   static int on = -1;
   if (on < 0) on = getenv("APEX_TRACE") ? 1 : 0;
@@ -898,8 +901,15 @@ static bool trace_on() {
     }                                       \
   } while (0)
 
-static float speculative_start(apex_library &L, QueryRec *q) {
-  if (q->spec_rank < 0) return -INFINITY;
+// Start threshold guess, computed on the device without a host round trip: the rank-r best
+// objective among the feasible compounds (exact boxes, FP32 outputs) of a uniform sample of the
+// query's scope, r chosen so that ~3k scope compounds are expected above it. The kernel writes
+// the slot's start threshold and admission threshold (start - 2 delta_f) in stream order before
+// the enumeration launch. Only a guess: finalization verifies it (>= k sure entries at or above
+// it) or restarts lower. Returns false (and leaves the slot's -inf thresholds) when the sample
+// cannot hold rank r.
+static bool speculative_start(apex_library &L, QueryRec *q, double margin2) {
+  if (q->spec_rank < 0) return false;
   const double t_a = now_ms();
   const long long S = std::min<long long>(4096, q->scope_n);
   const double expect = (double)S * (double)q->k / (double)q->scope_n;
@@ -907,62 +917,57 @@ static float speculative_start(apex_library &L, QueryRec *q) {
   q->spec_rank = (int)std::min<long long>(r, 1 << 30);
   if (r >= S) {
     q->spec_rank = -1;
-    return -INFINITY;
+    return false;
   }
-  // uniform compound ids of the scope: prefix sums over the subset, then a binary search
-  std::vector<long long> pre(q->subset.size() + 1, 0);
-  for (size_t i = 0; i < q->subset.size(); ++i)
-    pre[i + 1] = pre[i] + (L.id_first[q->subset[i] + 1] - L.id_first[q->subset[i]]);
-  std::vector<long long> ids(S);
-  for (long long i = 0; i < S; ++i) {
-    const long long u = (long long)(L.rng() % (unsigned long long)q->scope_n);
-    const size_t r_i = (size_t)(std::upper_bound(pre.begin(), pre.end(), u) - pre.begin()) - 1;
-    ids[i] = L.id_first[q->subset[r_i]] + (u - pre[r_i]);
-  }
-  const double t_b = now_ms();
+  const int n_sub = (int)q->subset.size();
+  std::vector<long long> pre(n_sub + 1, 0);
+  for (int i = 0; i < n_sub; ++i) pre[i + 1] = pre[i] + (L.id_first[q->subset[i] + 1] - L.id_first[q->subset[i]]);
   const int no = L.n_out;
-  L.arena_reserve(sizeof(long long) * S + sizeof(float) * S * no + 1024);
+  L.arena_reserve(sizeof(int) * n_sub + sizeof(long long) * (n_sub + 1) + sizeof(long long) * S +
+                  sizeof(float) * S * (no + 1) + S + 8 * 256);
+  int *d_rxn = (int *)L.aget(sizeof(int) * n_sub);
+  long long *d_pre = (long long *)L.aget(sizeof(long long) * (n_sub + 1));
   long long *d_ids = (long long *)L.aget(sizeof(long long) * S);
   float *d_out = (float *)L.aget(sizeof(float) * S * no);
-  long long *h_ids = (long long *)L.pin(std::max(sizeof(long long) * S, sizeof(float) * S * no));
-  memcpy(h_ids, ids.data(), sizeof(long long) * S);
-  CU(cudaMemcpyAsync(d_ids, h_ids, sizeof(long long) * S, cudaMemcpyHostToDevice, L.st));
+  float *d_keys = (float *)L.aget(sizeof(float) * S);
+  unsigned char *d_flag = (unsigned char *)L.aget(S);
+  // pageable sources: the copies are staged before the calls return
+  CU(cudaMemcpyAsync(d_rxn, q->subset.data(), sizeof(int) * n_sub, cudaMemcpyHostToDevice, L.st));
+  CU(cudaMemcpyAsync(d_pre, pre.data(), sizeof(long long) * (n_sub + 1), cudaMemcpyHostToDevice, L.st));
+  CU(apx_launch_spec_ids(d_rxn, d_pre, n_sub, L.T_.id_first, q->scope_n, L.rng(), S, d_ids, L.st));
   LaunchPlan dummy;
   memset(&dummy, 0, sizeof(dummy));
   CU(apx_launch_fp32(dummy, L.T_, nullptr, d_ids, S, d_out, grid_for(L, (S + APX_TILE - 1) / APX_TILE), L.st));
-  float *h_out = (float *)L.pinned;
-  CU(cudaMemcpyAsync(h_out, d_out, sizeof(float) * S * no, cudaMemcpyDeviceToHost, L.st));
-  const double t_c = now_ms();
-  CU(cudaStreamSynchronize(L.st));
-  const double t_d = now_ms();
-  std::vector<float> o(h_out, h_out + S * no);
-  std::vector<float> f;
-  f.reserve(S);
-  for (long long i = 0; i < S; ++i) {
-    bool ok = true;
-    for (size_t c = 0; c < q->cidx.size(); ++c) {
-      const double v = o[i * no + q->cidx[c]];
-      if (!(v >= q->lo[c] && v <= q->hi[c])) ok = false;
-    }
-    if (!ok) continue;
-    double s = 0;
-    for (int j = 0; j < L.n_obj; ++j) s += (double)q->w[j] * o[i * no + j];
-    f.push_back((float)s);
+  SpecArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int j = 0; j < L.n_obj; ++j) a.w[j] = q->w[j];
+  a.n_obj = L.n_obj;
+  a.n_cons = (int)q->cidx.size();
+  a.n_out = no;
+  for (int c = 0; c < a.n_cons; ++c) {
+    a.cons_idx[c] = q->cidx[c];
+    a.lo[c] = q->lo[c];
+    a.hi[c] = q->hi[c];
   }
-  if ((long long)f.size() < r) return -INFINITY;
-  std::nth_element(f.begin(), f.begin() + (r - 1), f.end(), std::greater<float>());
-  TRACE("start q%lld: sample %.3f ms, enqueue %.3f ms, gpu wait %.3f ms, host select %.3f ms", (long long)q->id,
-        t_b - t_a, t_c - t_b, t_d - t_c, now_ms() - t_d);
-  return f[r - 1];
+  a.rank = r;
+  a.margin2 = (float)margin2;
+  CU(apx_launch_spec_select(d_out, S, a, d_keys, d_flag, L.d_slots + q->slot, L.st));
+  TRACE("start q%lld: host %.3f ms (sample of %lld, rank %lld)", (long long)q->id, now_ms() - t_a, S, r);
+  return true;
 }
 
-static void start_query(apex_library &L, QueryRec *q) {
+static double pass_delta_f(const apex_library &L, const QueryRec *q) {
   const double *err = pass_err(L, q->precision);
   double df = 0;
   for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
-  q->tau_spec = speculative_start(L, q);
-  const float admit = std::isfinite(q->tau_spec) ? (float)(q->tau_spec - 2.0 * df * 1.0001) : -INFINITY;
-  write_slot(L, q, admit);
+  return df;
+}
+
+static void start_query(apex_library &L, QueryRec *q) {
+  const double df = pass_delta_f(L, q);
+  q->tau_spec = -INFINITY;  // the device-side guess lands in the slot; finalization reads it back
+  write_slot(L, q, -INFINITY);
+  speculative_start(L, q, 2.0 * df * 1.0001);
   q->remaining = q->scope_items;
   q->started = true;
 }
@@ -1038,6 +1043,7 @@ struct DevBuf {
 
 // returns false when the query must restart (start guess too high or candidate overflow)
 static bool finalize(apex_library &L, QueryRec *q) {
+  const double t_f0 = now_ms();
   const int no = L.n_out;
   const int sl = q->slot;
   int *pin_sl = (int *)L.pin(sizeof(QuerySlot) + 64);
@@ -1048,12 +1054,12 @@ static bool finalize(apex_library &L, QueryRec *q) {
   CU(cudaMemcpyAsync(pS, L.d_slots + sl, sizeof(QuerySlot), cudaMemcpyDeviceToHost, L.st));
   CU(cudaStreamSynchronize(L.st));
   const QuerySlot S = *pS;
-  const bool spec_bad = std::isfinite(q->tau_spec) && (long long)S.n_sure_above_spec < q->k;
+  const double t_f1 = now_ms();
+  const bool spec_bad = std::isfinite(S.tau_spec) && (long long)S.n_sure_above_spec < q->k;
   if (S.overflow || spec_bad) {
     q->stats.n_restarts++;
-    const double *err = pass_err(L, q->precision);
-    double df = 0;
-    for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
+    const double df = pass_delta_f(L, q);
+    bool device_guess = false;
     if (S.overflow) {
       // the band above the best valid threshold did not fit: more room, and restart from the
       // largest valid threshold found (k real, surely feasible compounds reach S.tau)
@@ -1067,12 +1073,14 @@ static bool finalize(apex_library &L, QueryRec *q) {
       }
     } else {
       q->spec_rank = q->spec_rank > 0 ? q->spec_rank * 8 : -1;  // the start guess was too high: lower it
-      q->tau_spec = q->spec_rank > 0 ? speculative_start(L, q) : -INFINITY;
+      q->tau_spec = -INFINITY;
+      device_guess = q->spec_rank > 0;
     }
     write_slot(L, q, std::isfinite(q->tau_spec) ? (float)(q->tau_spec - 2.0 * df * 1.0001) : -INFINITY);
+    if (device_guess) speculative_start(L, q, 2.0 * df * 1.0001);
     q->remaining = q->scope_items;
-    TRACE("restart q%lld: overflow=%u spec_bad=%d cap=%u tau_spec=%g", (long long)q->id, S.overflow, (int)spec_bad,
-          q->cap, (double)q->tau_spec);
+    TRACE("restart q%lld: overflow=%u spec_bad=%d cap=%u tau_spec=%g rank=%d", (long long)q->id, S.overflow,
+          (int)spec_bad, q->cap, (double)S.tau_spec, q->spec_rank);
     return false;
   }
   const long long nc = S.count;
@@ -1081,8 +1089,9 @@ static bool finalize(apex_library &L, QueryRec *q) {
     const size_t ncx = (size_t)std::max<long long>(nc, 1);
     size_t np2 = 2;
     while (np2 < ncx) np2 <<= 1;
+    const size_t kx = (size_t)std::min<long long>(q->k, (long long)ncx);
     L.arena_reserve(ncx * (4 * L.n_out + 4 + 2 + 8 * L.n_out + 8 + 4 + 8 * L.n_out) + np2 * sizeof(RItem) +
-                    (size_t)q->k * (8 + 4 + 8 * APEX_MAX_SLOTS + 8 + 8 * L.n_out) + 64 * 1024);
+                    kx * (8 + 4 + 8 * APEX_MAX_SLOTS + 8 + 8 * L.n_out) + 64 * 1024);
   }
   struct ArenaBuf {
     apex_library &L;
@@ -1114,22 +1123,21 @@ static bool finalize(apex_library &L, QueryRec *q) {
   float *d_tau = (float *)B.get(sizeof(float));
   int *d_ok = (int *)B.get(sizeof(int));
   CU(apx_launch_kth(f32, sure, nc, k, d_tau, d_ok, L.st));
-  float *pin_f = (float *)L.pin(64);
-  CU(cudaMemcpyAsync(pin_f, d_tau, sizeof(float), cudaMemcpyDeviceToHost, L.st));
-  CU(cudaStreamSynchronize(L.st));
-  const float tau32 = *pin_f;
-  const float thr = std::isfinite(tau32) ? (float)(tau32 - 2.0 * e32f * 1.0001) : -INFINITY;
+  // R = the candidates that may reach the FP32 top-k band (threshold taken on the device)
   unsigned n_pow2 = 1;
   while (n_pow2 < (unsigned)std::max<long long>(nc, 1)) n_pow2 <<= 1;
   n_pow2 = std::max(n_pow2, 2u);
   RItem *R = (RItem *)B.get(sizeof(RItem) * n_pow2);
-  unsigned *d_cnt = (unsigned *)B.get(sizeof(unsigned) * 4);
-  CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned) * 4, L.st));
-  CU(apx_launch_build_r(nc, q->ids, f32, maybe, sure, thr, R, d_cnt, L.st));
+  // device counters: [0] |R|, [1] FP64 batch, [2] newly marked, [3] alive, [4] FP64-rescored
+  unsigned *d_cnt = (unsigned *)B.get(sizeof(unsigned) * 8);
+  CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned) * 8, L.st));
+  CU(apx_launch_build_r(nc, q->ids, f32, maybe, sure, d_tau, (float)(2.0 * e32f * 1.0001), R, d_cnt, L.st));
   unsigned *pin_u = (unsigned *)L.pin(64);
   CU(cudaMemcpyAsync(pin_u, d_cnt, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
   CU(cudaStreamSynchronize(L.st));
   const unsigned nr = *pin_u;
+  const double t_f3 = now_ms();
+  const double t_f2 = t_f3;
   unsigned np = 1;
   while (np < std::max(nr, 2u)) np <<= 1;
   double *out64 = (double *)B.get(sizeof(double) * std::max<long long>(nc, 1) * no);
@@ -1137,68 +1145,79 @@ static bool finalize(apex_library &L, QueryRec *q) {
   int *pos64 = (int *)B.get(sizeof(int) * std::max(nr, 1u));
   double *o64 = (double *)B.get(sizeof(double) * std::max(nr, 1u) * no);
   const double tol = 2.0 * e32f * 1.0001 + 1e-300;
-  long long n64_total = 0;
-  for (int round = 0; round < 8 && nr > 0; ++round) {
+  // FP64 rounds: rescore what is pending (near a box bound, or in the boundary band of the k-th
+  // score), re-sort, re-mark the band. The band is marked once before the first round, so one
+  // round usually settles it; that round is queued without host synchronization (the FP64
+  // launch reads its batch size on the device), and further rounds run only when the last one
+  // still marked new entries.
+  auto fp64_round = [&]() {
     CU(cudaMemsetAsync(d_cnt + 1, 0, sizeof(unsigned) * 2, L.st));
     CU(apx_launch_collect64(R, nr, ids64, pos64, d_cnt + 1, L.st));
-    CU(cudaMemcpyAsync(pin_u, d_cnt + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
-    CU(cudaStreamSynchronize(L.st));
-    const unsigned n64 = *pin_u;
-    if (n64 > 0) {
-      CU(apx_launch_fp64(L.T_, ids64, n64, o64, L.st));
-      CU(apx_launch_apply64(R, pos64, o64, n64, no, L.d_slots + sl, dlo, dhi, out64, L.st));
-      n64_total += n64;
-    }
+    CU(apx_launch_fp64(L.T_, ids64, nr, o64, L.st, d_cnt + 1));
+    CU(apx_launch_apply64(R, pos64, o64, nr, d_cnt + 1, no, L.d_slots + sl, dlo, dhi, out64, L.st));
     CU(apx_sort_r(R, nr, np, L.st));
     CU(apx_launch_mark(R, nr, (unsigned)std::min<long long>(k + 1, nr), k, tol, d_cnt + 2, L.st));  // boundary band
-    CU(cudaMemcpyAsync(pin_u, d_cnt + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
-    CU(cudaStreamSynchronize(L.st));
-    const unsigned marked = *pin_u;
-    if (marked == 0) break;
+  };
+  // final rows: min(k, alive) of them, emitted on the device from the device count
+  const unsigned n_rows = (unsigned)std::min<long long>(k, nr);
+  long long *e_ids = nullptr;
+  int *e_rxn = nullptr;
+  long long *e_syn = nullptr;
+  double *e_obj = nullptr, *e_out = nullptr;
+  char *e_base = nullptr, *e_end = nullptr;
+  if (n_rows > 0) {
+    e_ids = (long long *)B.get(sizeof(long long) * n_rows);
+    e_rxn = (int *)B.get(sizeof(int) * n_rows);
+    e_syn = (long long *)B.get(sizeof(long long) * n_rows * APEX_MAX_SLOTS);
+    e_obj = (double *)B.get(sizeof(double) * n_rows);
+    e_out = (double *)B.get(sizeof(double) * n_rows * no);
+    e_base = (char *)e_ids;
+    e_end = (char *)e_out + sizeof(double) * n_rows * no;
   }
-  q->stats.n_rescored_fp64 = n64_total;
-  cudaError_t ce = cudaSuccess;
-  const int alive = nr > 0 ? apx_count_alive(R, nr, L.st, d_cnt + 3, &ce) : 0;
-  CU(ce);
+  const size_t span = (size_t)(e_end - e_base);
+  char *h = (char *)L.pin(span + 128);
+  unsigned *h_cnt = (unsigned *)(h + ((span + 63) & ~(size_t)63));  // counters land after the rows
+  auto emit_and_read = [&]() {
+    CU(cudaMemsetAsync(d_cnt + 3, 0, sizeof(unsigned) * 2, L.st));
+    CU(apx_launch_count_alive(R, nr, d_cnt + 3, L.st));
+    CU(apx_launch_emit(R, n_rows, d_cnt + 3, L.T_, out32, out64, e_ids, e_rxn, e_syn, e_obj, e_out, L.st));
+    CU(cudaEventRecord(q->ev1, L.st));
+    if (span) CU(cudaMemcpyAsync(h, e_base, span, cudaMemcpyDeviceToHost, L.st));
+    CU(cudaMemcpyAsync(h_cnt, d_cnt, sizeof(unsigned) * 8, cudaMemcpyDeviceToHost, L.st));
+    CU(cudaStreamSynchronize(L.st));
+  };
+  int rounds = 0;
+  if (nr > 0) {
+    CU(apx_sort_r(R, nr, np, L.st));
+    CU(apx_launch_mark(R, nr, (unsigned)std::min<long long>(k + 1, nr), k, tol, d_cnt + 2, L.st));
+    fp64_round();
+    rounds = 1;
+  }
+  emit_and_read();
+  while (nr > 0 && h_cnt[2] > 0 && rounds < 8) {  // rare: the band moved in the last round
+    fp64_round();
+    ++rounds;
+    emit_and_read();
+  }
+  const double t_f4 = now_ms();
+  q->stats.n_rescored_fp64 = nr > 0 ? (long long)h_cnt[4] : 0;
+  const long long alive = nr > 0 ? (long long)h_cnt[3] : 0;
   const long long nf = std::min<long long>(k, alive);
   q->r_ids.resize(nf);
   q->r_rxn.resize(nf);
   q->r_syn.resize(nf * APEX_MAX_SLOTS);
   q->r_obj.resize(nf);
   q->r_out.resize(nf * no);
-  void *e_ids_base = nullptr, *e_end = nullptr;
-  long long *e_ids = nullptr;
-  int *e_rxn = nullptr;
-  long long *e_syn = nullptr;
-  double *e_obj = nullptr, *e_out = nullptr;
   if (nf > 0) {
-    e_ids = (long long *)B.get(sizeof(long long) * nf);
-    e_ids_base = e_ids;
-    e_rxn = (int *)B.get(sizeof(int) * nf);
-    e_syn = (long long *)B.get(sizeof(long long) * nf * APEX_MAX_SLOTS);
-    e_obj = (double *)B.get(sizeof(double) * nf);
-    e_out = (double *)B.get(sizeof(double) * nf * no);
-    e_end = (char *)e_out + sizeof(double) * nf * no;
-    CU(apx_launch_emit(R, (unsigned)nf, L.T_, out32, out64, e_ids, e_rxn, e_syn, e_obj, e_out, L.st));
-  }
-  CU(cudaEventRecord(q->ev1, L.st));
-  if (nf > 0) {
-    // one contiguous D2H of the five result arrays (they are adjacent in the arena)
-    const size_t row = 8 + 4 + 8 * APEX_MAX_SLOTS + 8 + 8 * (size_t)no;
-    char *h = (char *)L.pin(row * nf + 5 * 256);
-    char *d0 = (char *)e_ids_base;
-    const size_t span = (size_t)((char *)e_end - d0);
-    CU(cudaMemcpyAsync(h, d0, span, cudaMemcpyDeviceToHost, L.st));
-    CU(cudaStreamSynchronize(L.st));
-    memcpy(q->r_ids.data(), h + ((char *)e_ids - d0), sizeof(long long) * nf);
-    memcpy(q->r_rxn.data(), h + ((char *)e_rxn - d0), sizeof(int) * nf);
-    memcpy(q->r_syn.data(), h + ((char *)e_syn - d0), sizeof(long long) * nf * APEX_MAX_SLOTS);
-    memcpy(q->r_obj.data(), h + ((char *)e_obj - d0), sizeof(double) * nf);
-    memcpy(q->r_out.data(), h + ((char *)e_out - d0), sizeof(double) * nf * no);
-  } else {
-    CU(cudaStreamSynchronize(L.st));
+    memcpy(q->r_ids.data(), h + ((char *)e_ids - e_base), sizeof(long long) * nf);
+    memcpy(q->r_rxn.data(), h + ((char *)e_rxn - e_base), sizeof(int) * nf);
+    memcpy(q->r_syn.data(), h + ((char *)e_syn - e_base), sizeof(long long) * nf * APEX_MAX_SLOTS);
+    memcpy(q->r_obj.data(), h + ((char *)e_obj - e_base), sizeof(double) * nf);
+    memcpy(q->r_out.data(), h + ((char *)e_out - e_base), sizeof(double) * nf * no);
   }
   q->stats.n_feasible_lower = nf;
+  TRACE("finalize q%lld: nc %lld nr %u rounds %d | select+read %.3f, rescore32+build_r %.3f, fp64 rounds+emit %.3f ms",
+        (long long)q->id, nc, nr, rounds, t_f1 - t_f0, t_f3 - t_f1, t_f4 - t_f2);
   return true;
 }
 

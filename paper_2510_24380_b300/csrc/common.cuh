@@ -78,6 +78,17 @@ struct QuerySlot {
   long long *ids2;
 };
 
+// Speculative start threshold of one query, evaluated on the device: the rank-th best objective
+// (exact boxes, FP32 outputs) of a uniform sample of the query's scope.
+struct SpecArgs {
+  float w[APEX_MAX_OBJECTIVES];
+  int n_obj, n_cons, n_out, pad;
+  int cons_idx[APEX_MAX_CONSTRAINTS];
+  double lo[APEX_MAX_CONSTRAINTS], hi[APEX_MAX_CONSTRAINTS];
+  long long rank;
+  float margin2;  // admission threshold = start threshold - margin2 (twice the pass objective margin)
+};
+
 #define APX_UNSURE_BIT (1LL << 62)
 #define APX_ID_MASK ((1LL << 62) - 1)
 

@@ -189,9 +189,12 @@ __global__ void __launch_bounds__(SEL_THREADS) k_kth(const float *keys, const un
 
 // ------------------------------------------------------------------ result set R
 
-// R = {maybe && f32 >= thr}; need64 = !sure
+// R = {maybe && f32 >= thr}, thr = tau32 - margin2 (-inf when fewer than k sure entries exist);
+// need64 = !sure
 __global__ void k_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
-                          const unsigned char *sure, float thr, RItem *R, unsigned *n_r) {
+                          const unsigned char *sure, const float *tau32, float margin2, RItem *R, unsigned *n_r) {
+  const float tau = *tau32;
+  const float thr = isfinite(tau) ? tau - margin2 : -INFINITY;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long b = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31u); b < n; b += stride) {
     const long long i = b + (threadIdx.x & 31);
@@ -225,8 +228,10 @@ __global__ void k_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, 
 }
 
 // apply FP64 outputs: exact objective and box; drop infeasible
-__global__ void k_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, int n_out, const QuerySlot *Q,
-                          const double *lo, const double *hi, double *out_rows /* [n_candidates x n_out], by src */) {
+__global__ void k_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64_max, const unsigned *n64_dev,
+                          int n_out, const QuerySlot *Q, const double *lo, const double *hi,
+                          double *out_rows /* [n_candidates x n_out], by src */) {
+  const unsigned n64 = n64_dev ? min(n64_max, *n64_dev) : n64_max;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n64; i += gridDim.x * blockDim.x) {
     const double *o = out64 + (size_t)i * n_out;
     double f = 0.0;
@@ -357,8 +362,10 @@ __global__ void k_mark_ties(RItem *R, unsigned n, unsigned kp1, long long k, dou
 }
 
 // Final rows: ids, reaction, synthons, objective, outputs (FP64 where rescored, else FP32)
-__global__ void k_emit(const RItem *R, unsigned n_final, const __grid_constant__ DevTables T, const float *out32,
-                       const double *out64_rows, long long *ids, int *rxn, long long *syn, double *obj, double *outs) {
+__global__ void k_emit(const RItem *R, unsigned n_max, const unsigned *n_alive, const __grid_constant__ DevTables T,
+                       const float *out32, const double *out64_rows, long long *ids, int *rxn, long long *syn,
+                       double *obj, double *outs) {
+  const unsigned n_final = n_alive ? min(n_max, *n_alive) : n_max;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_final; i += gridDim.x * blockDim.x) {
     const RItem it = R[i];
     const long long id = it.id;
@@ -403,11 +410,12 @@ cudaError_t apx_launch_kth(const float *keys, const unsigned char *flag, long lo
   return cudaGetLastError();
 }
 cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
-                               const unsigned char *sure, float thr, RItem *R, unsigned *n_r, cudaStream_t st) {
+                               const unsigned char *sure, const float *tau32, float margin2, RItem *R, unsigned *n_r,
+                               cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   apx_count_launch();
-  k_build_r<<<(unsigned)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0, st>>>(n, cand_ids, f32, maybe, sure, thr, R,
-                                                                                 n_r);
+  k_build_r<<<(unsigned)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0, st>>>(n, cand_ids, f32, maybe, sure, tau32,
+                                                                                 margin2, R, n_r);
   return cudaGetLastError();
 }
 cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64, cudaStream_t st) {
@@ -416,12 +424,14 @@ cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *po
   k_collect64<<<std::min<unsigned>((n + 255) / 256, 148u * 16u), 256, 0, st>>>(R, n, ids64, pos64, n64);
   return cudaGetLastError();
 }
-cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, int n_out,
-                               const QuerySlot *Q, const double *lo, const double *hi, double *out_rows,
+// n64_dev (optional): device count, at most n64
+cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, const unsigned *n64_dev,
+                               int n_out, const QuerySlot *Q, const double *lo, const double *hi, double *out_rows,
                                cudaStream_t st) {
   if (n64 == 0) return cudaSuccess;
   apx_count_launch();
-  k_apply64<<<std::min<unsigned>((n64 + 255) / 256, 148u * 16u), 256, 0, st>>>(R, pos64, out64, n64, n_out, Q, lo, hi, out_rows);
+  k_apply64<<<std::min<unsigned>((n64 + 255) / 256, 148u * 16u), 256, 0, st>>>(R, pos64, out64, n64, n64_dev, n_out, Q,
+                                                                                lo, hi, out_rows);
   return cudaGetLastError();
 }
 cudaError_t apx_launch_mark(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked,
@@ -431,21 +441,42 @@ cudaError_t apx_launch_mark(RItem *R, unsigned n, unsigned kp1, long long k, dou
   k_mark_ties<<<std::min<unsigned>((n + 255) / 256 + 1, 148u * 16u), 256, 0, st>>>(R, n, kp1, k, tol, n_marked);
   return cudaGetLastError();
 }
-cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const DevTables &T, const float *out32,
-                            const double *out64_rows, long long *ids, int *rxn, long long *syn, double *obj,
-                            double *outs, cudaStream_t st) {
+// rows emitted: min(n_final, *n_alive) (n_alive optional, a device count)
+cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const unsigned *n_alive, const DevTables &T,
+                            const float *out32, const double *out64_rows, long long *ids, int *rxn, long long *syn,
+                            double *obj, double *outs, cudaStream_t st) {
   if (n_final == 0) return cudaSuccess;
   apx_count_launch();
-  k_emit<<<std::min<unsigned>((n_final + 127) / 128, 148u * 4u), 128, 0, st>>>(R, n_final, T, out32, out64_rows, ids, rxn, syn, obj,
-                                                               outs);
+  k_emit<<<std::min<unsigned>((n_final + 127) / 128, 148u * 4u), 128, 0, st>>>(R, n_final, n_alive, T, out32, out64_rows,
+                                                                               ids, rxn, syn, obj, outs);
   return cudaGetLastError();
 }
 
-__global__ void k_count_alive(const RItem *R, unsigned n, unsigned *out) {
-  unsigned c = 0;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) c += R[i].alive;
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+// out[0] += alive entries of R[0, n); out[1] (optional) += entries rescored in FP64
+__global__ void k_count_alive(const RItem *R, unsigned n, unsigned *out, unsigned *out64) {
+  unsigned c = 0, c64 = 0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const RItem it = R[i];
+    c += it.alive;
+    c64 += (it.is64 && it.src >= 0) ? 1u : 0u;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_down_sync(0xffffffffu, c, o);
+    c64 += __shfl_down_sync(0xffffffffu, c64, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (c) atomicAdd(out, c);
+    if (out64 && c64) atomicAdd(out64, c64);
+  }
+}
+
+// alive entries of R[0, n) added to d_out[0] and FP64-rescored ones to d_out[1] (both zeroed by
+// the caller), no host synchronization
+cudaError_t apx_launch_count_alive(const RItem *R, unsigned n, unsigned *d_out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  apx_count_launch();
+  k_count_alive<<<std::min<unsigned>((n + 255) / 256, 148u * 4u), 256, 0, st>>>(R, n, d_out, d_out + 1);
+  return cudaGetLastError();
 }
 
 int apx_count_alive(const RItem *R, unsigned n, cudaStream_t st, unsigned *d_tmp, cudaError_t *e) {
@@ -453,11 +484,80 @@ int apx_count_alive(const RItem *R, unsigned n, cudaStream_t st, unsigned *d_tmp
   *e = cudaMemsetAsync(d_tmp, 0, sizeof(unsigned), st);
   if (*e != cudaSuccess) return 0;
   apx_count_launch();
-  k_count_alive<<<std::min<unsigned>((n + 255) / 256, 148u * 4u), 256, 0, st>>>(R, n, d_tmp);
+  k_count_alive<<<std::min<unsigned>((n + 255) / 256, 148u * 4u), 256, 0, st>>>(R, n, d_tmp, nullptr);
   *e = cudaGetLastError();
   if (*e != cudaSuccess) return 0;
   *e = cudaMemcpyAsync(&h, d_tmp, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
   if (*e != cudaSuccess) return 0;
   *e = cudaStreamSynchronize(st);
   return (int)h;
+}
+
+// ------------------------------------------------------------------ speculative start threshold
+// SplitMix64 output function (Steele, Lea and Flood, 2014): a counter-based 64-bit generator.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// S compound ids drawn uniformly from the scope: pre[] = prefix counts of the scope's reactions
+// rxn[] (n_sub + 1 entries, pre[n_sub] = scope size), id_first[] = first id of every reaction.
+__global__ void k_spec_ids(const int *rxn, const long long *pre, int n_sub, const long long *id_first, long long scope_n,
+                           unsigned long long seed, long long S, long long *ids) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S; i += (long long)gridDim.x * blockDim.x) {
+    const long long u = (long long)(splitmix64(seed + (unsigned long long)i * 0x2545f4914f6cdd1dull) %
+                                    (unsigned long long)scope_n);
+    int lo = 0, hi = n_sub - 1;  // last r with pre[r] <= u
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pre[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    ids[i] = id_first[rxn[lo]] + (u - pre[lo]);
+  }
+}
+
+// Objective of the feasible sample entries (exact boxes on FP32 outputs), its rank-th largest
+// value, and the query slot's start and admission thresholds (-inf when fewer than rank sample
+// entries are feasible). One CTA.
+__global__ void __launch_bounds__(SEL_THREADS) k_spec_select(const float *out, long long S, const __grid_constant__ SpecArgs a,
+                                                             float *keys, unsigned char *flag, QuerySlot *slot) {
+  for (long long i = threadIdx.x; i < S; i += blockDim.x) {
+    const float *o = out + i * a.n_out;
+    bool ok = true;
+    for (int c = 0; c < a.n_cons; ++c) {
+      const double v = (double)o[a.cons_idx[c]];
+      ok = ok && v >= a.lo[c] && v <= a.hi[c];
+    }
+    float f = 0.f;
+    for (int j = 0; j < a.n_obj; ++j) f = fmaf(a.w[j], o[j], f);
+    keys[i] = f;
+    flag[i] = ok;
+  }
+  __syncthreads();
+  SelSrc src{keys, nullptr, flag};
+  unsigned bits;
+  const bool ok = block_kth_largest(src, S, a.rank, &bits, nullptr);
+  if (threadIdx.x == 0) {
+    const float t = ok ? apx_bits_key(bits) : -INFINITY;
+    slot->tau_spec = t;
+    slot->admit = ok ? t - a.margin2 : -INFINITY;
+  }
+}
+
+cudaError_t apx_launch_spec_ids(const int *rxn, const long long *pre, int n_sub, const long long *id_first,
+                                long long scope_n, unsigned long long seed, long long S, long long *ids, cudaStream_t st) {
+  if (S <= 0 || n_sub <= 0) return cudaSuccess;
+  apx_count_launch();
+  k_spec_ids<<<(unsigned)std::min<long long>((S + 255) / 256, 148 * 4), 256, 0, st>>>(rxn, pre, n_sub, id_first, scope_n,
+                                                                                    seed, S, ids);
+  return cudaGetLastError();
+}
+
+cudaError_t apx_launch_spec_select(const float *out, long long S, const SpecArgs &a, float *keys, unsigned char *flag,
+                                   QuerySlot *slot, cudaStream_t st) {
+  apx_count_launch();
+  k_spec_select<<<1, SEL_THREADS, 0, st>>>(out, S, a, keys, flag, slot);
+  return cudaGetLastError();
 }
