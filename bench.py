@@ -61,22 +61,73 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """SM clock and clock-event reasons sampled every few ms through NVML (read-only queries)
+    during the timed region; nvidia-smi at 200 ms when NVML is unavailable."""
 
-    def __init__(self, index: int):
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
+               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
+               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
+               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"))
+
+    def __init__(self, index: int, period_s: float = 0.005):
+        import threading
+
+        self.samples, self.reasons, self.max_mhz, self.p = [], set(), None, None
+        self.stop_ev = threading.Event()
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            import pynvml as N
+            import torch
+
+            N.nvmlInit()
+            self.N = N
+            pr = torch.cuda.get_device_properties(index)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+            try:
+                self.h = N.nvmlDeviceGetHandleByPciBusId(bus.encode())
+            except Exception:
+                self.h = N.nvmlDeviceGetHandleByIndex(index)
+            self.max_mhz = float(N.nvmlDeviceGetMaxClockInfo(self.h, N.NVML_CLOCK_SM))
+            self.period = period_s
+            self.sample()
+            self.t = threading.Thread(target=self.loop, daemon=True)
+            self.t.start()
         except Exception:
-            self.p = None
+            self.N = None
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            try:
+                self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          stderr=subprocess.DEVNULL)
+            except Exception:
+                self.p = None
+
+    def sample(self):
+        N = self.N
+        self.samples.append(float(N.nvmlDeviceGetClockInfo(self.h, N.NVML_CLOCK_SM)))
+        r = N.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+        for name, const in self.REASONS:
+            if r & getattr(N, const):
+                self.reasons.add(name)
+
+    def loop(self):
+        while not self.stop_ev.wait(self.period):
+            try:
+                self.sample()
+            except Exception:
+                return
 
     def stop(self):
+        if self.N is not None:
+            self.stop_ev.set()
+            self.t.join(timeout=2)
+            self.sample()
+            return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
+                    "reasons": sorted(self.reasons), "samples": len(self.samples), "source": "nvml"}
         if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -89,14 +140,14 @@ class Clocks:
         sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].strip().replace(".", "").isdigit()]
         reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        names = [n for n, _ in self.REASONS]
         for r in rows:
             if len(r) > 8:
                 for n, v in zip(names, r[5:9]):
                     if v.strip() == "Active":
                         reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(rows), "source": "nvidia-smi"}
 
 
 def dist_setup(args):

@@ -331,9 +331,8 @@ static DevTables upload_plans(apex_library &L) {
 // Builds a launch over [first item, ...) of the given reactions' items (a "chunk").
 struct PlanBuilder {
   LaunchPlan P;
-  PlanBuilder() {
-    memset(&P, 0, sizeof(P));
-  }
+  const std::vector<RxnPlan> *rx;
+  explicit PlanBuilder(const std::vector<RxnPlan> &r) : rx(&r) { memset(&P, 0, sizeof(P)); }
   bool add(int rxn, long long b, long long e, unsigned long long qmask) {
     if (P.n_seg >= APX_MAX_SEG || e <= b) return false;
     Segment &s = P.seg[P.n_seg];
@@ -343,8 +342,11 @@ struct PlanBuilder {
     s.qmask = qmask;
     P.qmask_all |= qmask;
     P.seg_first[P.n_seg + 1] = P.seg_first[P.n_seg] + (e - b);
+    const RxnPlan &p = (*rx)[rxn];
+    P.seg_tile_first[P.n_seg + 1] = P.seg_tile_first[P.n_seg] + apx_tiles_before(p, e) - apx_tiles_before(p, b);
     P.n_seg++;
     P.total_items = P.seg_first[P.n_seg];
+    P.total_tiles = P.seg_tile_first[P.n_seg];
     return true;
   }
 };
@@ -367,8 +369,8 @@ static inline const double *pass_err(const apex_library &L, int precision) {
 static void launch_enum(apex_library &L, const LaunchPlan &P, int precision) {
   if (P.total_items == 0) return;
   const int fmt = tc_format(precision);
-  if (fmt >= 0)
-    CU(apx_launch_tc(P, L.T_, L.d_slots, L.d_err, grid_for(L, P.total_items), L.st, fmt));
+  if (fmt >= 0)  // every CTA takes an equal share of the launch's tiles
+    CU(apx_launch_tc(P, L.T_, L.d_slots, L.d_err, grid_for(L, P.total_tiles), L.st, fmt));
   else
     CU(apx_launch_fp32(P, L.T_, L.d_slots, nullptr, 0, nullptr, grid_for(L, P.total_items), L.st));
 }
@@ -423,24 +425,21 @@ static void calibrate(apex_library &L) {
   L.n_calib = (int)ns;
   if (L.tc_fmt[0] || L.tc_fmt[1]) {
     // 16-bit vs FP32 on whole work items: the first item of up to 48 reactions, chosen at random
-    PlanBuilder pb;
+    PlanBuilder pb(L.rx);
     std::vector<int> order(L.T);
     for (int t = 0; t < L.T; ++t) order[t] = t;
     std::shuffle(order.begin(), order.end(), g);
-    int max_lo = 1;
     for (int t : order) {
       if (pb.P.n_seg >= 48) break;
       pb.add(t, 0, 1, 0);
-      max_lo = std::max(max_lo, L.rx[t].L_o);
     }
-    const long long slots = pb.P.total_items * max_lo * APX_TILE;
+    const long long slots = pb.P.total_tiles * APX_TILE;
     float *d16 = (float *)L.dalloc(sizeof(float) * slots * no, false);
     float *d32 = (float *)L.dalloc(sizeof(float) * slots * no, false);
     long long *di16 = (long long *)L.dalloc(sizeof(long long) * slots, false);
     long long *di32 = (long long *)L.dalloc(sizeof(long long) * slots, false);
     LaunchPlan P = pb.P;
     P.mode = 2;
-    P.dump_lo = max_lo;
     P.dump_n = slots;
     P.dump = d32;
     P.dump_ids = di32;
@@ -457,7 +456,7 @@ static void calibrate(apex_library &L) {
       P.dump = d16;
       P.dump_ids = di16;
       CU(cudaMemsetAsync(di16, 0xff, sizeof(long long) * slots, L.st));
-      CU(apx_launch_tc(P, L.T_, nullptr, L.d_err, grid_for(L, P.total_items), L.st, f));
+      CU(apx_launch_tc(P, L.T_, nullptr, L.d_err, grid_for(L, P.total_tiles), L.st, f));
       check_kernel_status(L);
       CU(cudaMemcpyAsync(a.data(), d16, sizeof(float) * slots * no, cudaMemcpyDeviceToHost, L.st));
       CU(cudaMemcpyAsync(ia.data(), di16, sizeof(long long) * slots, cudaMemcpyDeviceToHost, L.st));
@@ -1242,7 +1241,8 @@ static void finish(apex_library &L, QueryRec *q, QState st, apex_status err, con
 static void pass_step(apex_library &L) {
   const long long chunk_compounds = 1LL << 25;
   // build one plan (items from the cursor) with per-precision query masks
-  PlanBuilder pb[4];  // indexed by pass precision (APEX_FP32, APEX_BF16, APEX_FP16; 2 unused)
+  // indexed by pass precision (APEX_FP32, APEX_BF16, APEX_FP16; 2 unused)
+  PlanBuilder pb[4] = {PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx)};
   long long served_compounds = 0;
   long long cur = L.cursor;
   long long visited = 0;
@@ -1522,7 +1522,7 @@ extern "C" apex_status apex_dump_outputs(apex_library *L, int32_t precision, int
     CU(cudaSetDevice(L->device));
     DevBuf B;
     float *d = (float *)B.get(sizeof(float) * nt * no);
-    PlanBuilder pb;
+    PlanBuilder pb(L->rx);
     const long long items = L->rx[reaction].n_items;
     for (long long b = 0; b < items; b += 1LL << 30) pb.add(reaction, b, std::min(items, b + (1LL << 30)), 0);
     LaunchPlan P = pb.P;

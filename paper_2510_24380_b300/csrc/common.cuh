@@ -43,15 +43,18 @@ struct Segment {
 // One enumeration launch: a list of item ranges, passed by value as a kernel parameter.
 struct LaunchPlan {
   int n_seg;
-  int mode;                                  // 0 = queries, 1 = dump by id, 2 = dump by tile slot
-  int dump_lo;                               // mode 2: slots per item = dump_lo * APX_TILE
+  int mode;                                  // 0 = queries, 1 = dump by id, 2 = dump by launch tile
+  int pad;
   long long total_items;
   long long seg_first[APX_MAX_SEG + 1];      // prefix of items
+  long long total_tiles;
+  long long seg_tile_first[APX_MAX_SEG + 1]; // prefix of tiles (128 inner rows x one outer index)
   Segment seg[APX_MAX_SEG];
   unsigned long long qmask_all;              // union of the segments' query masks
   // dump mode
   float *dump;                               // [dump_n x n_out]
-  long long *dump_ids;                       // mode 2: [dump_n], -1 = padding row
+  long long *dump_ids;                       // mode 2: [dump_n], row r of launch tile t at t * 128 + r,
+                                             // -1 = padding row
   long long dump_base, dump_n;
 };
 
@@ -175,6 +178,48 @@ __device__ __forceinline__ unsigned apx_warp_reserve(unsigned *counter, bool tak
 }
 
 // Locates item `it` of a launch: segment (binary search) and local item index.
+// Tiles of a reaction before its item i, in (inner block b, outer index o) order: item
+// b * n_oc + oc covers the tiles b * n_outer + [oc * L_o, min((oc + 1) * L_o, n_outer)).
+__host__ __device__ __forceinline__ long long apx_tiles_before(const RxnPlan &p, long long i) {
+  const long long r = (i % p.n_oc) * p.L_o;
+  return (i / p.n_oc) * p.n_outer + (r < p.n_outer ? r : p.n_outer);
+}
+
+// A run of consecutive tiles of one segment that share their inner block: rows q0 + [0, 128),
+// outer indices [o_begin, o_end).
+struct TileRun {
+  const RxnPlan *rp;
+  int sg;
+  long long b, q0, o_begin, o_end;
+  unsigned long long qmask;
+};
+
+// The run that starts at launch tile `tile` and ends at the segment's end, the inner block's
+// end or t_end, whichever comes first.
+__device__ __forceinline__ TileRun apx_tile_run(const LaunchPlan &L, const RxnPlan *rx, long long tile,
+                                                long long t_end) {
+  int lo = 0, hi = L.n_seg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L.seg_tile_first[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  const Segment &seg = L.seg[lo];
+  TileRun r;
+  r.sg = lo;
+  r.rp = rx + seg.rxn;
+  const long long x = apx_tiles_before(*r.rp, seg.item_begin) + (tile - L.seg_tile_first[lo]);
+  const long long x_end = apx_tiles_before(*r.rp, seg.item_end);
+  r.b = x / r.rp->n_outer;
+  r.o_begin = x - r.b * r.rp->n_outer;
+  long long n = r.rp->n_outer - r.o_begin;
+  if (x_end - x < n) n = x_end - x;
+  if (t_end - tile < n) n = t_end - tile;
+  r.o_end = r.o_begin + n;
+  r.q0 = r.b * APX_TILE;
+  r.qmask = seg.qmask;
+  return r;
+}
+
 __device__ __forceinline__ int apx_find_seg(const LaunchPlan &L, long long it) {
   int lo = 0, hi = L.n_seg - 1;
   while (lo < hi) {

@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(APX_SIMT_THREADS, 1)
   long long n_work = mode == 0 ? L.total_items : (n_ids + TM - 1) / TM;
   for (long long it = blockIdx.x; it < n_work; it += gridDim.x) {
     const RxnPlan *rp = nullptr;
-    long long q0 = 0, o_begin = 0, o_end = 1;
+    long long q0 = 0, o_begin = 0, o_end = 1, tile0 = 0;
     unsigned long long qmask = 0;
     if (mode == 0) {
       const int sg = apx_find_seg(L, it);
@@ -231,6 +231,8 @@ __global__ void __launch_bounds__(APX_SIMT_THREADS, 1)
       o_begin = oc * rp->L_o;
       o_end = min(o_begin + rp->L_o, rp->n_outer);
       qmask = seg.qmask;
+      // launch tile of outer index o_begin (mode-2 dump layout shared with the tensor-core kernel)
+      tile0 = L.seg_tile_first[sg] + apx_tiles_before(*rp, local) - apx_tiles_before(*rp, seg.item_begin);
     }
     for (long long o = o_begin; o < o_end; ++o) {
       f32_build_layer1<TM>(S, T, mode, rp, q0, o, ids, it * TM, n_ids, row_valid, row_id);
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(APX_SIMT_THREADS, 1)
               if (n < n_out) L.dump[(id - L.dump_base) * n_out + n] = ov[n];
           }
         } else if (L.mode == 2) {
-          const long long slot = (it * (long long)L.dump_lo + (o - o_begin)) * APX_TILE + r;
+          const long long slot = (tile0 + (o - o_begin)) * APX_TILE + r;
           if (slot < L.dump_n) {
             L.dump_ids[slot] = valid ? id : -1;
 #pragma unroll

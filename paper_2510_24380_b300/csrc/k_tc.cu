@@ -2,7 +2,8 @@
 // instantiated for BF16 and FP16 operands (one format for tables, activations and weights).
 //
 // Head shape: d -> 256 -> 256 -> n_out (n_out <= 16), activation after layers 1 and 2.
-// Per tile of 128 compounds (rows) of one work item (see common.cuh):
+// Per tile of 128 compounds (rows): inner block b (rows q0 + [0, 128) of the reaction's inner
+// slots) x one outer index o; each CTA walks an equal contiguous share of the launch's tiles:
 //   layer 1, structure-exploiting form (Eq. apex generalized to W_1): z_1 = R(row) + p(o), where
 //     R(row) = sum of the row's inner-slot P rows (resident in the producer's registers for the
 //     whole item) and p(o) = the outer slot's P row (one broadcast load per tile);
@@ -16,14 +17,15 @@
 // (layer 1) and into the W_2 image and b_2 (layer 2), all exact in binary.
 //
 // Warp roles (704 threads, one CTA per SM):
-//   warps 0-3   query warps: D3 of each tile -> outputs -> queries (warp w reads TMEM lanes 32w..)
+//   warps 0-3   query warps: D3 of each tile -> outputs -> queries (warp w reads TMEM lanes 32w..);
+//               lane 0 of warp 0 issues each tile's layer-3 MMAs once its a_2 is complete
 //   warps 4-19  math warps, thread (g, m) = K quarter g, tile row m: per step, layer 1 of the
 //               next tile (stage g of a_1) and then the layer-2 activation of the previous tile
 //               (accumulator columns [64g, 64g + 64), rows of its TMEM lane quarter)
-//   warp 20     TMEM allocation; lane 0 issues every MMA and commit
+//   warp 20     TMEM allocation; lane 0 issues the layer-2 MMAs and their commits
 //   warp 21     lane 0 bulk-copies (TMA) each tile's outer synthon row into a 4-slot ring
 // TMEM: 512 columns = two 256-column accumulators (double buffer); a_2 of quarter g overwrites
-// columns [64g, 64g + 32) of its buffer, D3 uses columns [32, 48).
+// columns [64g, 64g + 32) of its buffer, the four layer-3 partial sums use [32, 64) and [96, 128).
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel records
 // APX_ERR_TIMEOUT in the status word, every role leaves its loop, and TMEM is released.
 #include "common.cuh"
@@ -34,7 +36,11 @@
 #define TC_LOAD_WARP (TC_MMA_WARP + 1)
 #define TC_THREADS ((TC_LOAD_WARP + 1) * 32)
 #define TC_OROW_SLOTS 4
-#define TC_D3_COL 32u   // layer-3 accumulator columns within a 256-column buffer (free after layer 2)
+// Layer 3 accumulates in four independent chains (K blocks c, c + 4, c + 8, c + 12 go to chain c),
+// so that consecutive MMAs do not wait on each other; chain c uses 16 of the columns that layer
+// 2's activation has freed, the upper half of quarter c / 2 of the 256-column buffer.
+#define TC_L3_CHAINS 4
+__host__ __device__ constexpr uint32_t tc_d3_col(int c) { return 64u * (uint32_t)(c >> 1) + 32u + 16u * (uint32_t)(c & 1); }
 
 // Query parameters cached in shared memory for the whole launch (one entry per query slot).
 struct SlotParams {
@@ -56,7 +62,7 @@ struct SlotParams {
 #define TC_OFF_B3 (TC_OFF_B2 + 1024u)                         // 16 floats
 #define TC_OFF_QP (TC_OFF_B3 + 64u)                           // APEX_MAX_ACTIVE x SlotParams
 #define TC_OFF_BAR (TC_OFF_QP + (uint32_t)(APEX_MAX_ACTIVE * sizeof(SlotParams)))
-#define TC_NBAR 26
+#define TC_NBAR 27
 #define TC_OFF_MISC (TC_OFF_BAR + 8u * TC_NBAR)
 #define TC_SMEM_BYTES (TC_OFF_MISC + 64u + 1024u)    // + alignment slack
 #define TC_W_BYTES 139264u
@@ -72,6 +78,7 @@ static_assert(TC_SMEM_BYTES <= 232448, "shared memory budget");
 #define B_D3FULL(b) (14 + (b))
 #define B_W 16
 #define B_DRAIN 17
+#define B_DRAIN3 26  // layer-3 issuer's drain
 #define B_OFULL(r) (18 + (r))
 #define B_OEMPTY(r) (22 + (r))
 
@@ -88,12 +95,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+// Potentially blocking probe: the thread may be suspended (up to the hint, in ns) until the
+// phase completes, so waiting warps do not take issue slots from the working ones.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(20000u)
       : "memory");
   return ok != 0;
 }
@@ -320,26 +329,6 @@ __device__ __forceinline__ void tc_apply_queries(const SlotParams *qp, QuerySlot
   }
 }
 
-struct TcItem {
-  const RxnPlan *rp;
-  long long q0, o_begin, o_end;
-  unsigned long long qmask;
-};
-
-__device__ __forceinline__ TcItem tc_item(const LaunchPlan &L, const DevTables &T, long long it) {
-  const int sg = apx_find_seg(L, it);
-  const Segment &seg = L.seg[sg];
-  TcItem r;
-  r.rp = T.rx + seg.rxn;
-  const long long local = seg.item_begin + (it - L.seg_first[sg]);
-  const long long b = local / r.rp->n_oc, oc = local % r.rp->n_oc;
-  r.q0 = b * APX_TILE;
-  r.o_begin = oc * r.rp->L_o;
-  r.o_end = min(r.o_begin + (long long)r.rp->L_o, r.rp->n_outer);
-  r.qmask = seg.qmask;
-  return r;
-}
-
 template <int ACT, int FMT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_head(const __grid_constant__ LaunchPlan L, const __grid_constant__ DevTables T, QuerySlot *slots, int *err) {
@@ -353,6 +342,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   auto bar = [&](int i) { return sbase + TC_OFF_BAR + 8u * (uint32_t)i; };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // this CTA's share of the launch: tiles [t_begin, t_end), equal counts across CTAs (every tile
+  // costs the same), walked by every role in the same order of runs
+  const long long t_begin = (long long)blockIdx.x * L.total_tiles / gridDim.x;
+  const long long t_end = (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x;
   if (tid == 0) {
     for (int s = 0; s < 4; ++s) {
       mbar_init(bar(B_FULL(s)), 4);
@@ -366,6 +359,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     mbar_init(bar(B_W), 1);
     mbar_init(bar(B_DRAIN), 1);
+    mbar_init(bar(B_DRAIN3), 1);
     for (int r = 0; r < TC_OROW_SLOTS; ++r) {
       mbar_init(bar(B_OFULL(r)), 1);
       mbar_init(bar(B_OEMPTY(r)), TC_PROD_WARPS);  // every math warp reads every outer row
@@ -388,7 +382,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (bytes == 8192u) break;
     }
   }
-  for (int i = tid; i < 256; i += TC_THREADS) b2s[i] = T.b2s[i];
+  // b_2 as packed 16-bit pairs: added to the packed accumulator pair in the activation
+  for (int i = tid; i < 128; i += TC_THREADS)
+    reinterpret_cast<uint32_t *>(b2s)[i] = pack2<FMT>(T.b2s[2 * i], T.b2s[2 * i + 1]);
   for (int i = tid; i < 16; i += TC_THREADS) b3s[i] = T.b3[i];
   SlotParams *qp = reinterpret_cast<SlotParams *>(sm + TC_OFF_QP);
   if (L.mode == 0 && slots) {
@@ -432,34 +428,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t row_off = (uint32_t)(m >> 3) * 1024u + (uint32_t)(m & 7) * 128u;
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     uint32_t R[32];  // resident inner sum of the producing item (64 columns), packed bf16 pairs
-    long long it = blockIdx.x, o = 0, o_end = 0;
-    bool has_outer = false;  // per-item fields kept in registers (no per-tile global loads)
-    bool more = it < L.total_items;
+    long long tile = t_begin;
+    int left = 0;            // tiles left in the current run
+    bool has_outer = false;  // per-run fields kept in registers (no per-tile global loads)
+    bool more = tile < (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x;
     bool need_r = more;
     bool ok = true;
-    for (long long s = 0; ok; ++s) {
+    for (unsigned s = 0; ok; ++s) {
       const bool produce = more;
       if (produce) {
         if (need_r) {
-          const TcItem I = tc_item(L, T, it);
+          const TileRun I = apx_tile_run(L, T.rx, tile, (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x);
           const RxnPlan *rp = I.rp;
-          o = I.o_begin;
-          o_end = I.o_end;
+          left = (int)(I.o_end - I.o_begin);
           has_outer = rp->outer_row >= 0;
           const long long q = I.q0 + m;
           if (q < rp->n_inner) {
-            long long rows[APEX_MAX_SLOTS];
+            // the row's synthon of every inner slot (mixed radix, last slot fastest); unrolled
+            // over the slot count so that the row pointers stay in registers
+            const unsigned short *src[APEX_MAX_SLOTS];
             long long rem = q;
             const int ni = rp->n_inner_slots;
-            for (int sl = ni - 1; sl >= 0; --sl) {
-              rows[sl] = rp->inner_row[sl] + rem % rp->inner_size[sl];
-              rem /= rp->inner_size[sl];
+#pragma unroll
+            for (int sl = APEX_MAX_SLOTS - 1; sl >= 0; --sl) {
+              src[sl] = T.P16[FMT] + g * 64;
+              if (sl < ni) {
+                const long long sz = rp->inner_size[sl];
+                src[sl] += (rp->inner_row[sl] + rem % sz) * 256;
+                rem /= sz;
+              }
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-              for (int sl = 0; sl < ni; ++sl) {
-                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(T.P16[FMT] + rows[sl] * 256 + g * 64 + c * 8));
+#pragma unroll
+              for (int sl = 0; sl < APEX_MAX_SLOTS; ++sl) {
+                if (sl >= ni) break;
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(src[sl] + c * 8));
                 const float2 f0 = unpack2<FMT>(v.x), f1 = unpack2<FMT>(v.y), f2 = unpack2<FMT>(v.z), f3 = unpack2<FMT>(v.w);
                 acc[0] += f0.x; acc[1] += f0.y; acc[2] += f1.x; acc[3] += f1.y;
                 acc[4] += f2.x; acc[5] += f2.y; acc[6] += f3.x; acc[7] += f3.y;
@@ -499,21 +504,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_arrive(bar(B_OEMPTY(rs)));
           }
         }
-        if (++o >= o_end) {
-          it += gridDim.x;
-          more = it < L.total_items;
+        ++tile;
+        if (--left == 0) {
+          more = tile < (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x;
           need_r = more;
         }
       }
       // ---- layer-2 activation of tile s - 1 (columns [64g, 64g + 64) of its accumulator)
       if (ok && s >= 1) {
-        const long long jj = s - 1;
+        const unsigned jj = s - 1;
         const int buf = (int)(jj & 1);
         ok = mbar_wait(bar(B_D2FULL(buf)), (uint32_t)((jj >> 1) & 1), abort_flag, err);
         if (ok) {
           tc_fence_after();
           const uint32_t col = lane_base + (uint32_t)buf * 256u + (uint32_t)g * 64u;
-          const float *bh = b2s + g * 64;
+          const uint32_t *bh = reinterpret_cast<const uint32_t *>(b2s) + g * 32;
           // 16 accumulator columns at a time -> 8 packed bf16 pairs written over columns already
           // read (a_2 of this quarter lands in its first 32 columns); one load of lookahead
           uint32_t va[16], vb[16];
@@ -526,12 +531,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (c + 1 < 4) tmem_ld16(col + (uint32_t)(c + 1) * 16u, vn);
             uint32_t pk[8];
 #pragma unroll
-            for (int e4 = 0; e4 < 4; ++e4) {
-              const float4 bb = *reinterpret_cast<const float4 *>(bh + c * 16 + 4 * e4);
-              pk[2 * e4] =
-                  act2<ACT, FMT>(pack2<FMT>(__uint_as_float(v[4 * e4]) + bb.x, __uint_as_float(v[4 * e4 + 1]) + bb.y));
-              pk[2 * e4 + 1] =
-                  act2<ACT, FMT>(pack2<FMT>(__uint_as_float(v[4 * e4 + 2]) + bb.z, __uint_as_float(v[4 * e4 + 3]) + bb.w));
+            for (int e4 = 0; e4 < 2; ++e4) {
+              const uint4 bb = *reinterpret_cast<const uint4 *>(bh + c * 8 + 4 * e4);
+              const uint32_t bw[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                pk[4 * e4 + e] = act2<ACT, FMT>(add2<FMT>(
+                    pack2<FMT>(__uint_as_float(v[8 * e4 + 2 * e]), __uint_as_float(v[8 * e4 + 2 * e + 1])), bw[e]));
             }
             tmem_st8(col + (uint32_t)c * 8u, pk);
           }
@@ -548,8 +554,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       long long j = 0;
       bool ok = true;
-      for (long long it = blockIdx.x; ok && it < L.total_items; it += gridDim.x) {
-        const TcItem I = tc_item(L, T, it);
+      for (long long tile = t_begin; ok && tile < t_end;) {
+        const TileRun I = apx_tile_run(L, T.rx, tile, t_end);
+        tile += I.o_end - I.o_begin;
         const long long orow = I.rp->outer_row;
         for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
           const int rs = (int)(j & (TC_OROW_SLOTS - 1));
@@ -577,53 +584,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (mbar_wait(bar(B_W), 0, abort_flag, err)) {
         tc_fence_after();
         constexpr uint32_t ID2 = idesc_16(128, 256, FMT);
-        constexpr uint32_t ID3 = idesc_16(128, 16, FMT);
-        const uint32_t a1 = sbase + TC_OFF_A1, w2 = sbase + TC_OFF_W2, w3 = sbase + TC_OFF_W3;
-        auto issue_l3 = [&](long long jj) {
-          const int bb = (int)(jj & 1);
-          tc_fence_after();
-          const uint32_t dcol = tmem + (uint32_t)bb * 256u;
-#pragma unroll 1
-          for (int ks = 0; ks < 16; ++ks)  // K block ks of a_2 lives in quarter ks / 4 of the buffer
-            mma_ts(dcol + TC_D3_COL, dcol + (uint32_t)(ks >> 2) * 64u + (uint32_t)(ks & 3) * 8u,
-                   sw128_desc(w3 + (uint32_t)(ks >> 2) * 2048u + (uint32_t)(ks & 3) * 32u), ID3, ks > 0);
-          mma_commit(bar(B_D3FULL(bb)));
-        };
+        const uint32_t a1 = sbase + TC_OFF_A1, w2 = sbase + TC_OFF_W2;
         long long j = 0;
         bool ok = true;
-        long long l3_next = 0;  // next tile whose layer 3 is still to be issued
-        // issue L3 of tile l3_next if its a_2 is ready (non-blocking); returns false on abort
-        auto poll_l3 = [&](long long upto) {
-          if (l3_next < upto && mbar_try(bar(B_A2FULL((int)(l3_next & 1))), (uint32_t)((l3_next >> 1) & 1))) {
-            issue_l3(l3_next);
-            ++l3_next;
-          }
-        };
-        // waits for a barrier phase while issuing ready layer-3 work; bounded like mbar_wait
-        auto wait_poll = [&](uint32_t b, uint32_t parity, long long upto) -> bool {
-          const unsigned long long t0 = globaltimer();
-          for (unsigned it2 = 0;; ++it2) {
-            if (mbar_try(b, parity)) return true;
-            poll_l3(upto);
-            if ((it2 & 255u) == 255u) {
-              if (*abort_flag) return false;
-              if (globaltimer() - t0 > 2000000000ull) {
-                *abort_flag = 1;
-                atomicExch(err, APX_ERR_TIMEOUT);
-                return false;
-              }
-            }
-          }
-        };
-        for (long long it = blockIdx.x; ok && it < L.total_items; it += gridDim.x) {
-          const TcItem I = tc_item(L, T, it);
+        for (long long tile = t_begin; ok && tile < t_end;) {
+          const TileRun I = apx_tile_run(L, T.rx, tile, t_end);
+          tile += I.o_end - I.o_begin;
           for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
             const int buf = (int)(j & 1);
-            if (!wait_poll(bar(B_D2EMPTY(buf)), (uint32_t)(((j >> 1) & 1) ^ 1), j)) { ok = false; break; }
+            if (!mbar_wait(bar(B_D2EMPTY(buf)), (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
             tc_fence_after();
             const uint32_t d2 = tmem + (uint32_t)buf * 256u;
             for (int kc = 0; kc < 4; ++kc) {
-              if (!wait_poll(bar(B_FULL(kc)), (uint32_t)(j & 1), j)) { ok = false; break; }
+              if (!mbar_wait(bar(B_FULL(kc)), (uint32_t)(j & 1), abort_flag, err)) { ok = false; break; }
               tc_fence_after();
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks)
@@ -635,12 +608,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mma_commit(bar(B_D2FULL(buf)));
           }
         }
-        // remaining layer-3 work
-        while (ok && l3_next < j) {
-          if (!mbar_wait(bar(B_A2FULL((int)(l3_next & 1))), (uint32_t)((l3_next >> 1) & 1), abort_flag, err)) break;
-          issue_l3(l3_next);
-          ++l3_next;
-        }
       }
     }
     __syncwarp();
@@ -651,8 +618,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     long long j = 0;
     bool ok = true;
-    for (long long it = blockIdx.x; ok && it < L.total_items; it += gridDim.x) {
-      const TcItem I = tc_item(L, T, it);
+    for (long long tile = t_begin; ok && tile < t_end;) {
+      const TileRun I = apx_tile_run(L, T.rx, tile, t_end);
+      const long long run_tile0 = tile - I.o_begin;  // launch tile of outer index o: run_tile0 + o
+      tile += I.o_end - I.o_begin;
       const RxnPlan *rp = I.rp;
       const long long q = I.q0 + r;
       const bool valid = q < rp->n_inner;
@@ -660,17 +629,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const long long ostride = rp->outer_stride;
       for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
         const int buf = (int)(j & 1);
+        if (warp == 0) {
+          // layer 3 of this tile, issued here as soon as its a_2 is complete, so that it does
+          // not queue behind the MMA warp's layer-2 work of the next tile
+          int good = 1;
+          if (lane == 0) {
+            good = (j > 0 || mbar_wait(bar(B_W), 0, abort_flag, err)) &&
+                   mbar_wait(bar(B_A2FULL(buf)), (uint32_t)((j >> 1) & 1), abort_flag, err);
+            if (good) {
+              tc_fence_after();
+              constexpr uint32_t ID3 = idesc_16(128, 16, FMT);
+              const uint32_t w3 = sbase + TC_OFF_W3;
+              const uint32_t dcol = tmem + (uint32_t)buf * 256u;
+#pragma unroll
+              for (int ks = 0; ks < 16; ++ks)  // K block ks of a_2 lives in quarter ks / 4 of the buffer
+                mma_ts(dcol + tc_d3_col(ks % TC_L3_CHAINS), dcol + (uint32_t)(ks >> 2) * 64u + (uint32_t)(ks & 3) * 8u,
+                       sw128_desc(w3 + (uint32_t)(ks >> 2) * 2048u + (uint32_t)(ks & 3) * 32u), ID3,
+                       ks >= TC_L3_CHAINS);
+              mma_commit(bar(B_D3FULL(buf)));
+            }
+          }
+          good = __shfl_sync(0xffffffffu, good, 0);
+          if (!good) { ok = false; break; }
+        }
         if (!mbar_wait(bar(B_D3FULL(buf)), (uint32_t)((j >> 1) & 1), abort_flag, err)) { ok = false; break; }
         tc_fence_after();
-        uint32_t ov[16];
-        tmem_ld16(lane_base + (uint32_t)buf * 256u + TC_D3_COL, ov);
-        tmem_wait_ld_dep16(ov);
+        // the four layer-3 partial sums, two chains (32 adjacent columns) per load
+        float out[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) out[n] = b3s[n];
+#pragma unroll
+        for (int c = 0; c < TC_L3_CHAINS; c += 2) {
+          uint32_t pa[32];
+          tmem_ld32(lane_base + (uint32_t)buf * 256u + tc_d3_col(c), pa);
+          tmem_wait_ld_dep(pa);
+#pragma unroll
+          for (int n = 0; n < 16; ++n) out[n] += __uint_as_float(pa[n]) + __uint_as_float(pa[16 + n]);
+        }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_D2EMPTY(buf)));
-        float out[16];
-#pragma unroll
-        for (int n = 0; n < 16; ++n) out[n] = __uint_as_float(ov[n]) + b3s[n];
         const long long id = id_row + o * ostride;
         if (L.mode == 0) {
           tc_apply_queries(qp, slots, I.qmask, valid, id, out);
@@ -681,7 +679,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               if (n < T.n_out) L.dump[(id - L.dump_base) * T.n_out + n] = out[n];
           }
         } else {
-          const long long slot = (it * (long long)L.dump_lo + (o - I.o_begin)) * APX_TILE + r;
+          const long long slot = (run_tile0 + o) * APX_TILE + r;
           if (slot < L.dump_n) {
             L.dump_ids[slot] = valid ? id : -1;
 #pragma unroll
@@ -695,6 +693,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   tc_fence_before();
   __syncthreads();
+  if (warp == 0 && lane == 0 && *abort_flag) {
+    // after an abort, layer-3 MMAs of this issuer may still be in flight: wait (bounded)
+    tc_fence_after();
+    mma_commit(bar(B_DRAIN3));
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try(bar(B_DRAIN3), 0) && globaltimer() - t0 < 2000000000ull) {
+    }
+  }
   if (warp == TC_MMA_WARP) {
     tc_fence_after();
     if (*abort_flag && lane == 0) {
