@@ -60,39 +60,88 @@ def peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
-class Clocks:
-    """SM clock and clock-event reasons sampled every few ms through NVML (read-only queries)
-    during the timed region; nvidia-smi at 200 ms when NVML is unavailable."""
+def recorded_traffic(profile: str = "k_tc_head_c2_10m.md"):
+    """DRAM bytes per launch of the enumeration kernel from the committed ncu summary, when the
+    kernel source is still the one the counters were taken on (sha256 of k_tc.cu + common.cuh +
+    tc_sync.cuh);
+    None otherwise."""
+    import hashlib
+    import re
 
-    REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
-               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
-               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
-               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"))
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+        csrc = os.path.join(ROOT, "paper_2510_24380_b300", "csrc")
+        h = hashlib.sha256()
+        for f in ("k_tc.cu", "common.cuh", "tc_sync.cuh"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+        want = re.search(r"sha256\[:16\][^:]*:\s*([0-9a-f]{16})", text).group(1)
+        traffic = int(re.search(r"traffic_bytes_per_launch:\s*(\d+)", text).group(1))
+        return traffic if h.hexdigest()[:16] == want else None
+    except Exception:
+        return None
+
+
+class _Nvml:
+    """Read-only NVML queries through ctypes (the driver's libnvidia-ml): SM clock, max SM clock,
+    clock-event reasons. Reason bits are the NVML API constants."""
+
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, cuda_index: int):
+        import ctypes as C
+
+        self.C = C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.lib = lib
+        self.h = C.c_void_p()
+        import torch
+
+        pr = torch.cuda.get_device_properties(cuda_index)
+        bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+        if lib.nvmlDeviceGetHandleByPciBusId_v2(C.c_char_p(bus), C.byref(self.h)) != 0:
+            if lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(cuda_index), C.byref(self.h)) != 0:
+                raise RuntimeError("no NVML handle")
+        self.get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def clock(self, kind: str = "cur") -> float:
+        C = self.C
+        v = C.c_uint()
+        fn = self.lib.nvmlDeviceGetClockInfo if kind == "cur" else self.lib.nvmlDeviceGetMaxClockInfo
+        if fn(self.h, C.c_int(1), C.byref(v)) != 0:  # NVML_CLOCK_SM = 1
+            raise RuntimeError("clock query failed")
+        return float(v.value)
+
+    def reasons(self) -> set:
+        C = self.C
+        v = C.c_ulonglong()
+        if self.get_reasons(self.h, C.byref(v)) != 0:
+            raise RuntimeError("reason query failed")
+        return {n for n, bit in self.REASONS.items() if v.value & bit}
+
+
+class Clocks:
+    """SM clock and clock-event reasons sampled every few ms through NVML during the timed region;
+    nvidia-smi at 200 ms when NVML cannot be opened."""
+
+    REASON_NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index: int, period_s: float = 0.005):
         import threading
 
-        self.samples, self.reasons, self.max_mhz, self.p = [], set(), None, None
+        self.samples, self.reasons, self.p, self.nv = [], set(), None, None
         self.stop_ev = threading.Event()
         try:
-            import pynvml as N
-            import torch
-
-            N.nvmlInit()
-            self.N = N
-            pr = torch.cuda.get_device_properties(index)
-            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
-            try:
-                self.h = N.nvmlDeviceGetHandleByPciBusId(bus.encode())
-            except Exception:
-                self.h = N.nvmlDeviceGetHandleByIndex(index)
-            self.max_mhz = float(N.nvmlDeviceGetMaxClockInfo(self.h, N.NVML_CLOCK_SM))
+            self.nv = _Nvml(index)
+            self.max_mhz = self.nv.clock("max")
             self.period = period_s
             self.sample()
             self.t = threading.Thread(target=self.loop, daemon=True)
             self.t.start()
         except Exception:
-            self.N = None
+            self.nv = None
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -105,12 +154,8 @@ class Clocks:
                 self.p = None
 
     def sample(self):
-        N = self.N
-        self.samples.append(float(N.nvmlDeviceGetClockInfo(self.h, N.NVML_CLOCK_SM)))
-        r = N.nvmlDeviceGetCurrentClocksEventReasons(self.h)
-        for name, const in self.REASONS:
-            if r & getattr(N, const):
-                self.reasons.add(name)
+        self.samples.append(self.nv.clock("cur"))
+        self.reasons |= self.nv.reasons()
 
     def loop(self):
         while not self.stop_ev.wait(self.period):
@@ -120,7 +165,7 @@ class Clocks:
                 return
 
     def stop(self):
-        if self.N is not None:
+        if self.nv is not None:
             self.stop_ev.set()
             self.t.join(timeout=2)
             self.sample()
@@ -140,10 +185,9 @@ class Clocks:
         sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].strip().replace(".", "").isdigit()]
         reasons = set()
-        names = [n for n, _ in self.REASONS]
         for r in rows:
             if len(r) > 8:
-                for n, v in zip(names, r[5:9]):
+                for n, v in zip(self.REASON_NAMES, r[5:9]):
                     if v.strip() == "Active":
                         reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
@@ -440,7 +484,8 @@ def main():
                 "p99_ms": float(np.percentile(e2e_ms, 99))},
         "gpu_launches": int(launches),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": recorded_traffic() if args.workload == "c2_10m" and args.precision == "fp16" else None,
                      "kernel": "k_tc_head (enumeration, layers 2-3 on tcgen05)",
                      "flop_per_compound": FLOP_PER_COMPOUND, "peak_kind": f"{kind} bf16 burst (fp16 dense rate equals bf16)",
                      "kernel_ms_per_step": mean_enum},

@@ -223,6 +223,16 @@ apex_status apex_topk_select_noalloc(const float *keys, const int64_t *ids, int6
  * libraries, all entry points). Pure host counter. */
 apex_status apex_kernel_launches(int64_t *out);
 
+/* Failure-detection self-test of the bounded device waits. Every wait inside this library's
+ * kernels (mbarrier phases between warp roles) gives up after a time limit (2 s in production
+ * kernels), records a timeout in the launch's status word and returns; the host then fails the
+ * affected queries with APEX_ETIMEDOUT and the CUDA context stays usable. This call launches one
+ * thread that waits, with the same routine and a limit of limit_ms (1..2000), on a barrier phase
+ * that nothing completes, on the library's stream, with a status word of its own (running
+ * queries are not affected, but their next synchronization waits for it).
+ * Returns APEX_ETIMEDOUT when the wait gave up as designed, APEX_ECUDA if it did not. */
+apex_status apex_selftest_wait_timeout(apex_library *lib, int32_t limit_ms);
+
 /* Thread-local message describing the last error returned on this thread ("" if none). */
 const char *apex_last_error(void);
 

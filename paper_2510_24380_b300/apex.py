@@ -93,6 +93,7 @@ SYMBOLS = {
     "apex_topk_select_noalloc": [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                  C.POINTER(C.c_int64), C.c_void_p],
     "apex_kernel_launches": [C.POINTER(C.c_int64)],
+    "apex_selftest_wait_timeout": [C.c_void_p, C.c_int32],
     "apex_last_error": [],
 }
 
@@ -111,6 +112,11 @@ def load(path: str = LIB_PATH):
         dll.apex_last_error.restype = C.c_char_p
         _dll = dll
     return _dll
+
+
+def last_error() -> str:
+    """The calling thread's last error message from the library."""
+    return load().apex_last_error().decode(errors="replace")
 
 
 def _check(code, what=""):
@@ -260,6 +266,10 @@ class Library:
         _check(load().apex_dump_outputs(self.h, PREC[precision], int(reaction), _p(out, C.c_float),
                                         int(n_compounds)), "apex_dump_outputs")
         return out
+
+    def selftest_wait_timeout(self, limit_ms: int = 50) -> int:
+        """Runs the device-wait self-test; returns the status code (APEX_ETIMEDOUT = -5 expected)."""
+        return int(load().apex_selftest_wait_timeout(self.h, int(limit_ms)))
 
     def decode(self, ids):
         ids = np.ascontiguousarray(ids, np.int64)

@@ -59,6 +59,7 @@ cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const unsigned *n_
                             const float *out32, const double *out64_rows, long long *ids, int *rxn, long long *syn,
                             double *obj, double *outs, cudaStream_t st);
 cudaError_t apx_launch_count_alive(const RItem *R, unsigned n, unsigned *d_out, cudaStream_t st);
+cudaError_t apx_launch_wait_selftest(int *err, unsigned long long limit_ns, cudaStream_t st);
 cudaError_t apx_launch_spec_ids(const int *rxn, const long long *pre, int n_sub, const long long *id_first,
                                 long long scope_n, unsigned long long seed, long long S, long long *ids, cudaStream_t st);
 cudaError_t apx_launch_spec_select(const float *out, long long S, const SpecArgs &a, float *keys, unsigned char *flag,
@@ -1538,6 +1539,26 @@ extern "C" apex_status apex_dump_outputs(apex_library *L, int32_t precision, int
                 cudaGetErrorString(f.e));
   }
   return APEX_OK;
+}
+
+extern "C" apex_status apex_selftest_wait_timeout(apex_library *L, int32_t limit_ms) {
+  if (!L) return fail(APEX_EINVAL, "NULL library");
+  if (limit_ms < 1 || limit_ms > 2000) return fail(APEX_EINVAL, "limit_ms = %d outside 1..2000", limit_ms);
+  std::lock_guard<std::mutex> g(L->mu);
+  int code = 0;
+  try {
+    CU(cudaSetDevice(L->device));
+    DevBuf B;
+    int *d_err = (int *)B.get(sizeof(int));  // a status word of its own: queries never see this one
+    CU(cudaMemsetAsync(d_err, 0, sizeof(int), L->st));
+    CU(apx_launch_wait_selftest(d_err, (unsigned long long)limit_ms * 1000000ull, L->st));
+    CU(cudaMemcpyAsync(&code, d_err, sizeof(int), cudaMemcpyDeviceToHost, L->st));  // pageable: complete after the sync
+    CU(cudaStreamSynchronize(L->st));
+  } catch (const CudaFail &f) {
+    return fail(APEX_ECUDA, "wait self-test: %s failed: %s", f.what, cudaGetErrorString(f.e));
+  }
+  if (code == APX_ERR_TIMEOUT) return fail(APEX_ETIMEDOUT, "device wait gave up after %d ms (expected)", limit_ms);
+  return fail(APEX_ECUDA, "wait self-test: the wait returned without timing out (status %d)", code);
 }
 
 extern "C" apex_status apex_kernel_launches(int64_t *out) {

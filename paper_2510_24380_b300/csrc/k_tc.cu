@@ -29,6 +29,7 @@
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel records
 // APX_ERR_TIMEOUT in the status word, every role leaves its loop, and TMEM is released.
 #include "common.cuh"
+#include "tc_sync.cuh"
 
 #define TC_EPI_WARPS 4
 #define TC_PROD_WARPS 16
@@ -81,52 +82,6 @@ static_assert(TC_SMEM_BYTES <= 232448, "shared memory budget");
 #define B_DRAIN3 26  // layer-3 issuer's drain
 #define B_OFULL(r) (18 + (r))
 #define B_OEMPTY(r) (22 + (r))
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-// Potentially blocking probe: the thread may be suspended (up to the hint, in ns) until the
-// phase completes, so waiting warps do not take issue slots from the working ones.
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(20000u)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-// bounded wait: false when the CTA aborted (another role timed out) or this wait timed out
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  for (unsigned it = 0;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 255u) == 255u) {
-      if (*abort_flag) return false;
-      if (globaltimer() - t0 > 2000000000ull) {
-        *abort_flag = 1;
-        atomicExch(err, APX_ERR_TIMEOUT);
-        return false;
-      }
-    }
-  }
-}
 
 // UMMA shared-memory descriptor: SW128 K-major, 8-row atoms 1024 B apart (SBO)
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {

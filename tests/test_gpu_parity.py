@@ -231,3 +231,18 @@ def test_topk_select_entry_point():
         assert m == min(k, n)
         assert np.array_equal(oi.cpu().numpy(), ids[order])
         assert np.array_equal(ok.cpu().numpy(), keys[order])
+
+
+def test_bounded_wait_gives_up_and_library_keeps_working(ragged):
+    """Failure detection without a GPU fault: a device wait on a barrier phase that nothing
+    completes must give up after its limit, report APEX_ETIMEDOUT, and leave the context usable."""
+    import time
+
+    lib, head, spec, L, rms = ragged
+    t0 = time.perf_counter()
+    assert L.selftest_wait_timeout(50) == -5
+    dt = time.perf_counter() - t0
+    assert 0.045 < dt < 1.5, dt
+    assert "expected" in apex.last_error()
+    q = _q([1, 0, 0, 0, 0], [5], [-0.1], [0.1], k=25, precision="fp16")
+    check_topk(L.run(q), O.topk(lib, head, q), lib, head, q, rms)
