@@ -84,7 +84,9 @@ __device__ bool block_kth_largest(const SelSrc &src, long long n, long long k, u
 }
 
 // ------------------------------------------------------------------ per-slot select / compaction
-// mode 0: only when the buffer is more than half full; mode 1: always (end of the pass).
+// mode 0 (between the launches of a pass): whenever the buffer holds more than k entries, so the
+// admission threshold tightens after the first launch instead of waiting for the buffer to
+// fill; mode 1: always (end of the pass).
 // Raises tau (k-th largest sure key) and the admission threshold tau - 2 delta_f, then keeps
 // only entries at or above the admission threshold.
 __global__ void __launch_bounds__(SEL_THREADS) k_slot_select(QuerySlot *slots, const int *slot_list, int mode) {
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_slot_select(QuerySlot *slots, c
   __shared__ unsigned kept;
   __shared__ unsigned n_spec;
   const unsigned n = min(*((volatile unsigned *)&Q->count), Q->cap);
-  if (mode == 0 && n <= Q->cap / 2) return;
+  if (mode == 0 && (long long)n <= Q->k) return;
   SelSrc src{Q->keys, Q->ids, nullptr};
   unsigned bits;
   if (block_kth_largest(src, n, Q->k, &bits, nullptr)) {

@@ -16,14 +16,14 @@
 // fma .bf16x2 or .f16x2: 1.5 issue slots and one MUFU element per activation); the 1/2 is folded into P
 // (layer 1) and into the W_2 image and b_2 (layer 2), all exact in binary.
 //
-// Warp roles (704 threads, one CTA per SM):
-//   warps 0-3   query warps: D3 of each tile -> outputs -> queries (warp w reads TMEM lanes 32w..);
-//               lane 0 of warp 0 issues each tile's layer-3 MMAs once its a_2 is complete
+// Warp roles (736 threads, one CTA per SM):
+//   warps 0-3   query warps: D3 of each tile -> outputs -> queries (warp w reads TMEM lanes 32w..)
 //   warps 4-19  math warps, thread (g, m) = K quarter g, tile row m: per step, layer 1 of the
 //               next tile (stage g of a_1) and then the layer-2 activation of the previous tile
 //               (accumulator columns [64g, 64g + 64), rows of its TMEM lane quarter)
 //   warp 20     TMEM allocation; lane 0 issues the layer-2 MMAs and their commits
 //   warp 21     lane 0 bulk-copies (TMA) each tile's outer synthon row into a 4-slot ring
+//   warp 22     lane 0 issues each tile's layer-3 MMAs once its a_2 is complete
 // TMEM: 512 columns = two 256-column accumulators (double buffer); a_2 of quarter g overwrites
 // columns [64g, 64g + 32) of its buffer, the four layer-3 partial sums use [32, 64) and [96, 128).
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel records
@@ -35,7 +35,8 @@
 #define TC_PROD_WARPS 16
 #define TC_MMA_WARP (TC_EPI_WARPS + TC_PROD_WARPS)
 #define TC_LOAD_WARP (TC_MMA_WARP + 1)
-#define TC_THREADS ((TC_LOAD_WARP + 1) * 32)
+#define TC_L3_WARP (TC_LOAD_WARP + 1)
+#define TC_THREADS ((TC_L3_WARP + 1) * 32)
 #define TC_OROW_SLOTS 4
 // Layer 3 accumulates in four independent chains (K blocks c, c + 4, c + 8, c + 12 go to chain c),
 // so that consecutive MMAs do not wait on each other; chain c uses 16 of the columns that layer
@@ -43,14 +44,16 @@
 #define TC_L3_CHAINS 4
 __host__ __device__ constexpr uint32_t tc_d3_col(int c) { return 64u * (uint32_t)(c >> 1) + 32u + 16u * (uint32_t)(c & 1); }
 
-// Query parameters cached in shared memory for the whole launch (one entry per query slot).
+// Query parameters cached in shared memory for the whole launch (one entry per query slot). The
+// boxes are stored per output (several constraints on one output intersect), so the epilogue
+// tests outputs at compile-time register indices: cmask bit j = output j is constrained.
 struct SlotParams {
-  float w[APEX_MAX_OBJECTIVES];
-  float lo_w[APEX_MAX_CONSTRAINTS], hi_w[APEX_MAX_CONSTRAINTS];
-  float lo_s[APEX_MAX_CONSTRAINTS], hi_s[APEX_MAX_CONSTRAINTS];
+  float w[APEX_MAX_OBJECTIVES];  // zero beyond n_obj
+  float lo_w[16], hi_w[16];      // admission box (widened by the pass margin), per output
+  float lo_s[16], hi_s[16];      // "sure" box (shrunk by the margin), per output
   float admit;
-  int n_obj, n_cons, pad;
-  unsigned char cons_idx[APEX_MAX_CONSTRAINTS];
+  unsigned cmask;
+  int n_obj, pad;
 };
 
 // shared-memory map (offsets from a 1024-byte aligned base)
@@ -65,9 +68,10 @@ struct SlotParams {
 #define TC_OFF_BAR (TC_OFF_QP + (uint32_t)(APEX_MAX_ACTIVE * sizeof(SlotParams)))
 #define TC_NBAR 27
 #define TC_OFF_MISC (TC_OFF_BAR + 8u * TC_NBAR)
-#define TC_SMEM_BYTES (TC_OFF_MISC + 64u + 1024u)    // + alignment slack
+#define TC_OFF_QLIST (TC_OFF_MISC + 64u)               // per query warp: its run's query slots (64 B)
+#define TC_SMEM_BYTES (TC_OFF_QLIST + 4u * APEX_MAX_ACTIVE + 1024u)    // + alignment slack
 #define TC_W_BYTES 139264u
-static_assert(sizeof(SlotParams) == 352, "SlotParams layout");
+static_assert(sizeof(SlotParams) == 336, "SlotParams layout");
 static_assert(TC_SMEM_BYTES <= 232448, "shared memory budget");
 
 // barrier indices
@@ -251,37 +255,76 @@ __device__ __forceinline__ float2 unpack2(uint32_t w) {
 // Sec. 3 / Eq. apex_topk per compound (one row per lane, all 32 lanes call it): objective,
 // admission threshold, widened box (admission) and shrunk box ("sure"), then a warp-aggregated
 // append to the query's candidate buffer in global memory. Parameters come from shared memory.
-__device__ __forceinline__ void tc_apply_queries(const SlotParams *qp, QuerySlot *slots, unsigned long long qmask,
-                                                 bool valid, long long id, const float (&o)[16]) {
-  const unsigned lane = threadIdx.x & 31;
-  while (qmask) {
-    const int s = __ffsll((long long)qmask) - 1;
-    qmask &= qmask - 1;
-    const SlotParams &P = qp[s];
-    const int n_obj = P.n_obj;
-    float f = 0.f;
+__device__ __forceinline__ void tc_apply_query_slow(const SlotParams &P, QuerySlot *Q, bool pass, float f, long long id,
+                                                    const float (&o)[16]) {
+  bool sure = true;
+  const unsigned cm = P.cmask;
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if (j < n_obj) f = fmaf(P.w[j], o[j], f);
-    bool pass = valid && (f >= P.admit);
-    if (__ballot_sync(0xffffffffu, pass) == 0u) continue;
-    bool sure = true;
-    for (int i = 0; i < P.n_cons; ++i) {
-      const float v = apx_sel<16>(o, P.cons_idx[i]);
-      pass = pass && (v >= P.lo_w[i]) && (v <= P.hi_w[i]);
-      sure = sure && (v >= P.lo_s[i]) && (v <= P.hi_s[i]);
+  for (int j = 0; j < 16; ++j)
+    if (cm & (1u << j)) {  // warp-uniform
+      pass = pass && (o[j] >= P.lo_w[j]) && (o[j] <= P.hi_w[j]);
+      sure = sure && (o[j] >= P.lo_s[j]) && (o[j] <= P.hi_s[j]);
     }
-    QuerySlot *Q = slots + s;
-    const unsigned pos = apx_warp_reserve(&Q->count, pass);
-    if (pass) {
-      if (pos < Q->cap) {
-        Q->keys[pos] = f;
-        Q->ids[pos] = id | (sure ? 0LL : APX_UNSURE_BIT);
-      } else {
-        atomicExch(&Q->overflow, 1u);
-      }
+  const unsigned pos = apx_warp_reserve(&Q->count, pass);
+  if (pass) {
+    if (pos < Q->cap) {
+      Q->keys[pos] = f;
+      Q->ids[pos] = id | (sure ? 0LL : APX_UNSURE_BIT);
+    } else {
+      atomicExch(&Q->overflow, 1u);
     }
   }
+}
+
+// objective of one query: its weights are zero beyond n_obj, so a fixed-length dot product serves
+template <int NW>
+__device__ __forceinline__ float tc_objective(const SlotParams &P, const float (&o)[16]) {
+  float f0 = 0.f, f1 = 0.f;  // two independent partial sums
+#pragma unroll
+  for (int j = 0; j < NW; j += 4) {
+    const float4 w = *reinterpret_cast<const float4 *>(&P.w[j]);
+    f0 = fmaf(w.x, o[j], f0);
+    f1 = fmaf(w.y, o[j + 1], f1);
+    f0 = fmaf(w.z, o[j + 2], f0);
+    f1 = fmaf(w.w, o[j + 3], f1);
+  }
+  return f0 + f1;
+}
+
+// Sec. 3 / Eq. apex_topk per compound (one row per lane, all 32 lanes call it): objective,
+// admission threshold, widened box (admission) and shrunk box ("sure"), then a warp-aggregated
+// append to the query's candidate buffer in global memory. Parameters come from shared memory.
+// Objectives are formed for four queries at a time (independent dot products); the constraint
+// boxes are read only for the queries that some lane of the warp admits on the objective. The
+// query slots of the run come as a list in shared memory (built once per run), so the per-tile
+// loop uses no bit scans (those would queue on the MUFU pipe behind the activations).
+template <int NW>
+__device__ __forceinline__ void tc_apply_queries_n(const SlotParams *qp, QuerySlot *slots, const unsigned char *qlist,
+                                                   int nq, bool valid, long long id, const float (&o)[16]) {
+  for (int i = 0; i < nq; i += 4) {
+    int sq[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sq[u] = i + u < nq ? (int)qlist[i + u] : -1;
+    float f[4];
+    bool pass[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const SlotParams &P = qp[sq[u] < 0 ? 0 : sq[u]];
+      f[u] = tc_objective<NW>(P, o);
+      pass[u] = valid && sq[u] >= 0 && f[u] >= P.admit;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (__ballot_sync(0xffffffffu, pass[u]) != 0u) tc_apply_query_slow(qp[sq[u]], slots + sq[u], pass[u], f[u], id, o);
+  }
+}
+
+__device__ __forceinline__ void tc_apply_queries(const SlotParams *qp, QuerySlot *slots, const unsigned char *qlist,
+                                                 int nq, bool valid, long long id, const float (&o)[16], int n_obj) {
+  if (n_obj <= 8)
+    tc_apply_queries_n<8>(qp, slots, qlist, nq, valid, id, o);
+  else
+    tc_apply_queries_n<16>(qp, slots, qlist, nq, valid, id, o);
 }
 
 template <int ACT, int FMT>
@@ -348,17 +391,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const QuerySlot *Q = slots + s;
       SlotParams &P = qp[s];
       if (lane < APEX_MAX_OBJECTIVES) P.w[lane] = Q->w[lane];
-      if (lane < APEX_MAX_CONSTRAINTS) {
-        P.lo_w[lane] = Q->lo_w[lane];
-        P.hi_w[lane] = Q->hi_w[lane];
-        P.lo_s[lane] = Q->lo_s[lane];
-        P.hi_s[lane] = Q->hi_s[lane];
-        P.cons_idx[lane] = (unsigned char)Q->cons_idx[lane];
+      if (lane < 16) {  // output `lane`: the intersection of the boxes of every constraint on it
+        float lw = -INFINITY, hw = INFINITY, ls = -INFINITY, hs = INFINITY;
+        bool any = false;
+        for (int c = 0; c < Q->n_cons; ++c)
+          if (Q->cons_idx[c] == lane) {
+            any = true;
+            lw = fmaxf(lw, Q->lo_w[c]);
+            hw = fminf(hw, Q->hi_w[c]);
+            ls = fmaxf(ls, Q->lo_s[c]);
+            hs = fminf(hs, Q->hi_s[c]);
+          }
+        P.lo_w[lane] = lw;
+        P.hi_w[lane] = hw;
+        P.lo_s[lane] = ls;
+        P.hi_s[lane] = hs;
+        const unsigned cm = __ballot_sync(0x0000ffffu, any);
+        if (lane == 0) P.cmask = cm;
       }
       if (lane == 0) {
         P.admit = Q->admit;
         P.n_obj = Q->n_obj;
-        P.n_cons = Q->n_cons;
       }
     }
   }
@@ -566,16 +619,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
     __syncwarp();
+  } else if (warp == TC_L3_WARP) {
+    // ------------------------------------------------------------ layer-3 issuer
+    // Issues each tile's layer-3 MMAs as soon as its a_2 is complete, so that they neither queue
+    // behind the MMA warp's layer-2 work of the next tile nor wait for the query epilogue.
+    if (lane == 0 && mbar_wait(bar(B_W), 0, abort_flag, err)) {
+      constexpr uint32_t ID3 = idesc_16(128, 16, FMT);
+      const uint32_t w3 = sbase + TC_OFF_W3;
+      for (long long j = 0; j < t_end - t_begin; ++j) {
+        const int buf = (int)(j & 1);
+        if (!mbar_wait(bar(B_A2FULL(buf)), (uint32_t)((j >> 1) & 1), abort_flag, err)) break;
+        tc_fence_after();
+        const uint32_t dcol = tmem + (uint32_t)buf * 256u;
+#pragma unroll
+        for (int ks = 0; ks < 16; ++ks)  // K block ks of a_2 lives in quarter ks / 4 of the buffer
+          mma_ts(dcol + tc_d3_col(ks % TC_L3_CHAINS), dcol + (uint32_t)(ks >> 2) * 64u + (uint32_t)(ks & 3) * 8u,
+                 sw128_desc(w3 + (uint32_t)(ks >> 2) * 2048u + (uint32_t)(ks & 3) * 32u), ID3, ks >= TC_L3_CHAINS);
+        mma_commit(bar(B_D3FULL(buf)));
+      }
+    }
+    __syncwarp();
   } else {
     // ------------------------------------------------------------ query warps (0-3)
     // read the head outputs of each tile (D3), release its accumulator buffer, apply the queries
     const int r = tid;  // tile row == TMEM lane
+    // every query of a library has the library's objective count
+    const int qp_n_obj = L.qmask_all ? qp[__ffsll((long long)L.qmask_all) - 1].n_obj : APEX_MAX_OBJECTIVES;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     long long j = 0;
     bool ok = true;
     for (long long tile = t_begin; ok && tile < t_end;) {
       const TileRun I = apx_tile_run(L, T.rx, tile, t_end);
       const long long run_tile0 = tile - I.o_begin;  // launch tile of outer index o: run_tile0 + o
+      // this run's query slots, as a list
+      unsigned char *qlist = sm + TC_OFF_QLIST + (uint32_t)warp * APEX_MAX_ACTIVE;
+      int nq = 0;
+      if (lane == 0) {
+        for (unsigned long long m = I.qmask; m; m &= m - 1) qlist[nq++] = (unsigned char)(__ffsll((long long)m) - 1);
+      }
+      nq = __shfl_sync(0xffffffffu, nq, 0);
+      __syncwarp();
       tile += I.o_end - I.o_begin;
       const RxnPlan *rp = I.rp;
       const long long q = I.q0 + r;
@@ -584,29 +667,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const long long ostride = rp->outer_stride;
       for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
         const int buf = (int)(j & 1);
-        if (warp == 0) {
-          // layer 3 of this tile, issued here as soon as its a_2 is complete, so that it does
-          // not queue behind the MMA warp's layer-2 work of the next tile
-          int good = 1;
-          if (lane == 0) {
-            good = (j > 0 || mbar_wait(bar(B_W), 0, abort_flag, err)) &&
-                   mbar_wait(bar(B_A2FULL(buf)), (uint32_t)((j >> 1) & 1), abort_flag, err);
-            if (good) {
-              tc_fence_after();
-              constexpr uint32_t ID3 = idesc_16(128, 16, FMT);
-              const uint32_t w3 = sbase + TC_OFF_W3;
-              const uint32_t dcol = tmem + (uint32_t)buf * 256u;
-#pragma unroll
-              for (int ks = 0; ks < 16; ++ks)  // K block ks of a_2 lives in quarter ks / 4 of the buffer
-                mma_ts(dcol + tc_d3_col(ks % TC_L3_CHAINS), dcol + (uint32_t)(ks >> 2) * 64u + (uint32_t)(ks & 3) * 8u,
-                       sw128_desc(w3 + (uint32_t)(ks >> 2) * 2048u + (uint32_t)(ks & 3) * 32u), ID3,
-                       ks >= TC_L3_CHAINS);
-              mma_commit(bar(B_D3FULL(buf)));
-            }
-          }
-          good = __shfl_sync(0xffffffffu, good, 0);
-          if (!good) { ok = false; break; }
-        }
         if (!mbar_wait(bar(B_D3FULL(buf)), (uint32_t)((j >> 1) & 1), abort_flag, err)) { ok = false; break; }
         tc_fence_after();
         // the four layer-3 partial sums, two chains (32 adjacent columns) per load
@@ -626,7 +686,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) mbar_arrive(bar(B_D2EMPTY(buf)));
         const long long id = id_row + o * ostride;
         if (L.mode == 0) {
-          tc_apply_queries(qp, slots, I.qmask, valid, id, out);
+          tc_apply_queries(qp, slots, qlist, nq, valid, id, out, qp_n_obj);
         } else if (L.mode == 1) {
           if (valid && id >= L.dump_base && id < L.dump_base + L.dump_n) {
 #pragma unroll
@@ -648,7 +708,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   tc_fence_before();
   __syncthreads();
-  if (warp == 0 && lane == 0 && *abort_flag) {
+  if (warp == TC_L3_WARP && lane == 0 && *abort_flag) {
     // after an abort, layer-3 MMAs of this issuer may still be in flight: wait (bounded)
     tc_fence_after();
     mma_commit(bar(B_DRAIN3));

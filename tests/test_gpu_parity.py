@@ -84,6 +84,9 @@ def _queries(spec, stats, precision):
     yield "one_slot_only", _q([0, 1, 0, 0, 0], k=20, subset=[3], precision=precision)
     yield "objective_constrained", _q([0.5, 0.5, 0, 0, 0], [0, 12], [-0.05, -np.inf], [np.inf, 0.02], k=300,
                                       precision=precision)
+    # several boxes on one output intersect
+    yield "boxes_on_one_output", _q([0.1, 0.9, 0, 0, 0], [5, 5, 6, 5], [-0.2, -0.1, -np.inf, -0.15],
+                                    [0.3, 0.2, 0.1, 0.25], k=50, precision=precision)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
