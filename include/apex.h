@@ -51,13 +51,17 @@ typedef int32_t apex_status;
 /* Query precision of the enumeration pass. FP32: every layer in FP32 on the CUDA cores.
  * BF16 / FP16: layers 2.. on tcgen05 tensor cores (16-bit operands and activations, FP32
  * accumulators in TMEM); FP16 carries 3 more mantissa bits at the same tensor rate, so its
- * calibrated margins are tighter. The candidates are then rescored in FP32 and the top-k
- * boundary band in FP64, so the returned set equals the FP64 top-k when the calibrated error
- * bounds hold. APEX_FP64 is accepted by apex_score_ids only. */
+ * calibrated margins are tighter. FP8: layer 2 with e4m3 operands (activations quantized from
+ * FP16, W_2 quantized per output channel with scale max|row| / 448, FP32 accumulators multiplied
+ * back by the scales), layer 3 in FP16; twice the dense tensor rate on layer 2, much wider
+ * margins (three mantissa bits). The candidates are
+ * then rescored in FP32 and the top-k boundary band in FP64, so the returned set equals the FP64
+ * top-k when the calibrated error bounds hold. APEX_FP64 is accepted by apex_score_ids only. */
 #define APEX_FP32 0
 #define APEX_BF16 1
 #define APEX_FP64 2
 #define APEX_FP16 3
+#define APEX_FP8 4
 
 #define APEX_MAX_SLOTS 4          /* slots per reaction */
 #define APEX_MAX_OUTPUTS 32       /* head outputs */
@@ -85,8 +89,8 @@ typedef struct {
   int32_t activation;           /* APEX_ACT_*, applied after every layer but the last */
   int32_t n_objectives;         /* outputs [0, n_objectives) may carry objective weight */
   int32_t n_properties;         /* n_objectives + n_properties == dims[n_layers] */
-  uint32_t precisions;          /* bits (1 << APEX_BF16), (1 << APEX_FP16) build the tensor-core tables;
-                                   FP32 always */
+  uint32_t precisions;          /* bits (1 << APEX_BF16), (1 << APEX_FP16), (1 << APEX_FP8) build the
+                                   tensor-core tables (FP8 also builds the FP16 ones); FP32 always */
   uint64_t device_mem_budget;   /* bytes the library may hold on the device; 0 = unlimited */
   void *cuda_stream;            /* cudaStream_t to run on; NULL = the library creates one */
   int32_t device;               /* CUDA device ordinal */
@@ -96,7 +100,7 @@ typedef struct {
 /* Query descriptor (Eq. orig_topk: objective weights, constraint boxes, k). Copied by
  * apex_query; the caller may free it when the call returns. */
 typedef struct {
-  int32_t precision;            /* APEX_FP32, APEX_BF16 or APEX_FP16 */
+  int32_t precision;            /* APEX_FP32, APEX_BF16, APEX_FP16 or APEX_FP8 */
   const float *objective_weights; /* host [n_objectives]; the objective is maximized */
   int32_t n_constraints;        /* 0..APEX_MAX_CONSTRAINTS */
   const int32_t *output_index;  /* host [n_constraints], any output index */
@@ -117,6 +121,7 @@ typedef struct {
   int32_t n_calibration;        /* compounds in the calibration sample */
   double err_bf16[APEX_MAX_OUTPUTS]; /* per-output admission margin of the BF16 pass */
   double err_fp16[APEX_MAX_OUTPUTS]; /* per-output admission margin of the FP16 pass */
+  double err_fp8[APEX_MAX_OUTPUTS];  /* per-output admission margin of the FP8 pass */
   double err_fp32[APEX_MAX_OUTPUTS]; /* per-output margin of the FP32 rescore */
   double rms[APEX_MAX_OUTPUTS];      /* output RMS over the calibration sample */
 } apex_library_info_t;

@@ -20,7 +20,7 @@ STATUS = {0: "APEX_OK", -1: "APEX_EINVAL", -2: "APEX_ENOMEM", -3: "APEX_EBUSY", 
           -9: "APEX_EUNSUPPORTED"}
 APEX_EAGAIN = -4
 ACT = {"identity": 0, "relu": 1, "silu": 2}
-PREC = {"fp32": 0, "bf16": 1, "fp64": 2, "fp16": 3}
+PREC = {"fp32": 0, "bf16": 1, "fp64": 2, "fp16": 3, "fp8": 4}
 MAX_SLOTS = 4
 MAX_OUTPUTS = 32
 
@@ -55,6 +55,7 @@ class LibraryInfo(C.Structure):
         ("n_compounds", C.c_int64), ("n_synthon_rows", C.c_int64), ("max_slots", C.c_int32),
         ("n_outputs", C.c_int32), ("device_bytes", C.c_uint64), ("precisions", C.c_uint32),
         ("n_calibration", C.c_int32), ("err_bf16", C.c_double * MAX_OUTPUTS), ("err_fp16", C.c_double * MAX_OUTPUTS),
+        ("err_fp8", C.c_double * MAX_OUTPUTS),
         ("err_fp32", C.c_double * MAX_OUTPUTS),
         ("rms", C.c_double * MAX_OUTPUTS),
     ]

@@ -38,6 +38,8 @@ cudaError_t apx_launch_prep(const float *U, const float *W1, const float *b1, co
                             long long rows, int K, int N, float *P32, cudaStream_t st);
 cudaError_t apx_launch_p16(const float *P32, long long n, float scale, int fmt, void *P16, cudaStream_t st);
 cudaError_t apx_launch_image(const float *W, int rows_used, int rows, int fmt, void *img, cudaStream_t st);
+cudaError_t apx_launch_image_e4m3(const float *W, const float *scale, int rows_used, int rows, void *img,
+                                  cudaStream_t st);
 cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
                           cudaStream_t st, int fmt);
 cudaError_t apx_launch_slot_select(QuerySlot *slots, const int *slot_list, int n_slots, int mode, cudaStream_t st);
@@ -146,7 +148,7 @@ struct apex_library {
   std::vector<long long> slot_sizes, slot_first, row_first, id_first;
   long long N = 0, rows = 0;
   uint32_t precisions = 1u;
-  bool tc_fmt[2] = {false, false};  // tensor-core tables built: [0] BF16, [1] FP16
+  bool tc_fmt[3] = {false, false, false};  // tensor-core tables built: [0] BF16, [1] FP16, [2] FP8
   // device
   int device = 0;
   cudaStream_t st = nullptr;
@@ -162,8 +164,8 @@ struct apex_library {
   int *d_err = nullptr;
   int *d_slot_list = nullptr;
   // calibration
-  // admission margins: err16[0] BF16 pass, err16[1] FP16 pass, err32 FP32 pass / rescore
-  double err16[2][APEX_MAX_OUTPUTS] = {{0}}, err32[APEX_MAX_OUTPUTS] = {0}, rms[APEX_MAX_OUTPUTS] = {0};
+  // admission margins: err16[0] BF16 pass, [1] FP16 pass, [2] FP8 pass; err32 FP32 pass / rescore
+  double err16[3][APEX_MAX_OUTPUTS] = {{0}}, err32[APEX_MAX_OUTPUTS] = {0}, rms[APEX_MAX_OUTPUTS] = {0};
   int n_calib = 0;
   float *d_err32f = nullptr;  // per-output FP32 margin (float) for eval32
   uint64_t seed = 0;
@@ -356,9 +358,9 @@ static int grid_for(const apex_library &L, long long items) {
   return (int)std::max<long long>(1, std::min<long long>(items, L.n_sm));
 }
 
-// 16-bit tensor-core format of a query precision: 0 = BF16, 1 = FP16, -1 = none
+// tensor-core operand format of a query precision: 0 = BF16, 1 = FP16, 2 = FP8 e4m3, -1 = none
 static inline int tc_format(int precision) {
-  return precision == APEX_BF16 ? 0 : precision == APEX_FP16 ? 1 : -1;
+  return precision == APEX_BF16 ? 0 : precision == APEX_FP16 ? 1 : precision == APEX_FP8 ? 2 : -1;
 }
 
 // admission margin of a pass precision (per output)
@@ -424,8 +426,8 @@ static void calibrate(apex_library &L) {
     L.err32[p] = 8.0 * m + 1e-6 * L.rms[p] + 1e-9;
   }
   L.n_calib = (int)ns;
-  if (L.tc_fmt[0] || L.tc_fmt[1]) {
-    // 16-bit vs FP32 on whole work items: the first item of up to 48 reactions, chosen at random
+  if (L.tc_fmt[0] || L.tc_fmt[1] || L.tc_fmt[2]) {
+    // tensor-core pass vs FP32 on whole work items: the first item of up to 48 reactions, chosen at random
     PlanBuilder pb(L.rx);
     std::vector<int> order(L.T);
     for (int t = 0; t < L.T; ++t) order[t] = t;
@@ -452,7 +454,7 @@ static void calibrate(apex_library &L) {
     CU(cudaMemcpyAsync(ib.data(), di32, sizeof(long long) * slots, cudaMemcpyDeviceToHost, L.st));
     CU(cudaStreamSynchronize(L.st));
     long long cnt_max = 0;
-    for (int f = 0; f < 2; ++f) {
+    for (int f = 0; f < 3; ++f) {
       if (!L.tc_fmt[f]) continue;
       P.dump = d16;
       P.dump_ids = di16;
@@ -509,13 +511,14 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
   if (N >= (1LL << 62)) return fail(APEX_EINVAL, "library too large (ids must stay below 2^62)");
   for (int t = 0; t < D->n_reactions; ++t)
     if (D->n_slots[t] > APEX_MAX_SLOTS) return fail(APEX_EUNSUPPORTED, "reaction %d has more than %d slots", t, APEX_MAX_SLOTS);
-  if (D->precisions & ~((1u << APEX_FP32) | (1u << APEX_BF16) | (1u << APEX_FP16)))
-    return fail(APEX_EINVAL, "precisions: only the FP32, BF16 and FP16 bits are defined");
+  if (D->precisions & ~((1u << APEX_FP32) | (1u << APEX_BF16) | (1u << APEX_FP16) | (1u << APEX_FP8)))
+    return fail(APEX_EINVAL, "precisions: only the FP32, BF16, FP16 and FP8 bits are defined");
   const bool want_bf16 = (D->precisions >> APEX_BF16) & 1u;
-  const bool want_fp16 = (D->precisions >> APEX_FP16) & 1u;
+  const bool want_fp8 = (D->precisions >> APEX_FP8) & 1u;
+  const bool want_fp16 = ((D->precisions >> APEX_FP16) & 1u) || want_fp8;  // the FP8 pass reads the FP16 table
   const bool tc_shape = D->n_layers == 3 && D->dims[1] == 256 && D->dims[2] == 256 && D->dims[3] <= 16;
   if ((want_bf16 || want_fp16) && !tc_shape)
-    return fail(APEX_EUNSUPPORTED, "the 16-bit tensor-core path needs a d -> 256 -> 256 -> <=16 head");
+    return fail(APEX_EUNSUPPORTED, "the tensor-core path needs a d -> 256 -> 256 -> <=16 head");
 
   std::unique_ptr<apex_library> L(new apex_library());
   L->T = D->n_reactions;
@@ -547,7 +550,9 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
   L->seed = D->seed;
   L->tc_fmt[0] = want_bf16;
   L->tc_fmt[1] = want_fp16;
-  L->precisions = 1u | (want_bf16 ? (1u << APEX_BF16) : 0u) | (want_fp16 ? (1u << APEX_FP16) : 0u);
+  L->tc_fmt[2] = want_fp8;
+  L->precisions = 1u | (want_bf16 ? (1u << APEX_BF16) : 0u) | (want_fp16 ? (1u << APEX_FP16) : 0u) |
+                  (want_fp8 ? (1u << APEX_FP8) : 0u);
   L->rng.seed(D->seed + 17);
 
   try {
@@ -617,7 +622,7 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
       float *P32 = (float *)L->dalloc(sizeof(float) * L->rows * h1);
       CU(apx_launch_prep(dU, dW1, db1, dbrow, L->rows, d, h1, P32, L->st));
       L->T_.P32 = P32;
-      if (L->tc_fmt[0] || L->tc_fmt[1]) {
+      if (L->tc_fmt[0] || L->tc_fmt[1] || L->tc_fmt[2]) {
         // tensor-core tables of every requested 16-bit format: P (scaled into the activation's
         // input space), W_2 (same scale) and W_3 (padded to 16 rows) as SW128 images, b_2, b_3
         const float scale = (L->act == APEX_ACT_SILU) ? 0.5f : 1.0f;
@@ -628,7 +633,7 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
         float *dw = (float *)L->dalloc(sizeof(float) * (w2.size() + w3.size()), false);
         CU(cudaMemcpy(dw, w2.data(), sizeof(float) * w2.size(), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(dw + w2.size(), w3.data(), sizeof(float) * w3.size(), cudaMemcpyHostToDevice));
-        for (int f = 0; f < 2; ++f) {
+        for (int f = 0; f < 2; ++f) {  // 16-bit tables and images
           if (!L->tc_fmt[f]) continue;
           void *P16 = L->dalloc(sizeof(unsigned short) * L->rows * 256);
           CU(apx_launch_p16(P32, L->rows * 256, scale, f, P16, L->st));
@@ -639,6 +644,22 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
           L->T_.P16[f] = (const unsigned short *)P16;
           L->T_.w2img[f] = d2;
           L->T_.w3img[f] = d3;
+        }
+        if (L->tc_fmt[2]) {
+          // FP8 layer-2 image: every output channel of W_2 (already scaled) quantized with its own
+          // scale max|row| / 448 (the e4m3 maximum); the kernel multiplies the accumulators back
+          std::vector<float> s2(256, 1.f);
+          for (int n = 0; n < 256; ++n) {
+            float mx = 0.f;
+            for (int k = 0; k < 256; ++k) mx = std::max(mx, std::fabs(w2[(size_t)n * 256 + k]));
+            if (mx > 0.f) s2[n] = mx / 448.f;
+          }
+          float *ds2 = (float *)L->dalloc(sizeof(float) * 256);
+          CU(cudaMemcpy(ds2, s2.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
+          unsigned char *d2 = (unsigned char *)L->dalloc(256 * 256);
+          CU(apx_launch_image_e4m3(dw, ds2, 256, 256, d2, L->st));
+          L->T_.w2img[2] = d2;
+          L->T_.s2 = ds2;
         }
         std::vector<float> b2s(256), b3(16, 0.f);
         for (int n = 0; n < 256; ++n) b2s[n] = scale * D->b[1][n];
@@ -741,6 +762,7 @@ extern "C" apex_status apex_library_info(const apex_library *L, apex_library_inf
   for (int p = 0; p < L->n_out; ++p) {
     o->err_bf16[p] = L->err16[0][p];
     o->err_fp16[p] = L->err16[1][p];
+    o->err_fp8[p] = L->err16[2][p];
     o->err_fp32[p] = L->err32[p];
     o->rms[p] = L->rms[p];
   }
@@ -775,7 +797,8 @@ extern "C" apex_status apex_decode_ids(const apex_library *L, int64_t n, const i
 // ------------------------------------------------------------------ query submission
 extern "C" apex_status apex_query(apex_library *L, const apex_query_desc *Dq, apex_query_id *out) {
   if (!L || !Dq || !out) return fail(APEX_EINVAL, "NULL argument");
-  if (Dq->precision != APEX_FP32 && Dq->precision != APEX_BF16 && Dq->precision != APEX_FP16)
+  if (Dq->precision != APEX_FP32 && Dq->precision != APEX_BF16 && Dq->precision != APEX_FP16 &&
+      Dq->precision != APEX_FP8)
     return fail(APEX_EINVAL, "unknown precision %d", Dq->precision);
   if (!((L->precisions >> Dq->precision) & 1u))
     return fail(APEX_EUNSUPPORTED, "precision %d tables were not built at load", Dq->precision);
@@ -1242,8 +1265,8 @@ static void finish(apex_library &L, QueryRec *q, QState st, apex_status err, con
 static void pass_step(apex_library &L) {
   const long long chunk_compounds = 1LL << 25;
   // build one plan (items from the cursor) with per-precision query masks
-  // indexed by pass precision (APEX_FP32, APEX_BF16, APEX_FP16; 2 unused)
-  PlanBuilder pb[4] = {PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx)};
+  // indexed by pass precision (APEX_FP32, APEX_BF16, APEX_FP16, APEX_FP8; 2 unused)
+  PlanBuilder pb[5] = {PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx)};
   long long served_compounds = 0;
   long long cur = L.cursor;
   long long visited = 0;
@@ -1252,22 +1275,22 @@ static void pass_step(apex_library &L) {
     const int t = (int)(std::upper_bound(L.item_first.begin(), L.item_first.end(), cur) - L.item_first.begin()) - 1;
     const long long b = cur - L.item_first[t];
     const long long e = L.rx[t].n_items;
-    unsigned long long mask[4] = {0, 0, 0, 0};
+    unsigned long long mask[5] = {0, 0, 0, 0, 0};
     for (int s = 0; s < APEX_MAX_ACTIVE; ++s) {
       QueryRec *q = L.active[s];
       if (q && q->remaining > 0 && q->need[t]) mask[q->precision] |= 1ull << s;
     }
     long long take = e - b;
-    const unsigned long long any = mask[0] | mask[1] | mask[3];
+    const unsigned long long any = mask[0] | mask[1] | mask[3] | mask[4];
     if (any) {
       const long long per_item = (long long)L.rx[t].L_o * APX_TILE;
       const long long room = std::max<long long>(1, (chunk_compounds - served_compounds + per_item - 1) / per_item);
       take = std::min(take, room);
       bool ok = true;
-      for (int p = 0; p < 4; ++p)
+      for (int p = 0; p < 5; ++p)
         if (mask[p] && pb[p].P.n_seg >= APX_MAX_SEG) ok = false;
       if (!ok) break;
-      for (int p = 0; p < 4; ++p)
+      for (int p = 0; p < 5; ++p)
         if (mask[p]) pb[p].add(t, b, b + take, mask[p]);
       for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
         if (any >> s & 1ull) served[s] += take;
@@ -1287,7 +1310,7 @@ static void pass_step(apex_library &L) {
   }
   cudaEvent_t e0 = L.ev_a, e1 = L.ev_b;
   CU(cudaEventRecord(e0, L.st));
-  for (int p = 0; p < 4; ++p) launch_enum(L, pb[p].P, p);
+  for (int p = 0; p < 5; ++p) launch_enum(L, pb[p].P, p);
   CU(cudaEventRecord(e1, L.st));
   if (!list.empty()) {
     int *hl = (int *)L.pin(sizeof(int) * APEX_MAX_ACTIVE + 64);
@@ -1304,7 +1327,7 @@ static void pass_step(apex_library &L) {
     q->stats.n_launches++;
     q->stats.enumerate_ms += ms;
     long long comp = 0;
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < 5; ++p)
       for (int g = 0; g < pb[p].P.n_seg; ++g)
         if (pb[p].P.seg[g].qmask >> s & 1ull) {
           const RxnPlan &r = L.rx[pb[p].P.seg[g].rxn];
@@ -1512,7 +1535,7 @@ extern "C" apex_status apex_score_ids(apex_library *L, int32_t precision, int64_
 extern "C" apex_status apex_dump_outputs(apex_library *L, int32_t precision, int32_t reaction, float *outputs,
                                          int64_t capacity) {
   if (!L || !outputs || reaction < 0 || reaction >= L->T) return fail(APEX_EINVAL, "bad arguments");
-  if (precision != APEX_FP32 && precision != APEX_BF16 && precision != APEX_FP16)
+  if (precision != APEX_FP32 && precision != APEX_BF16 && precision != APEX_FP16 && precision != APEX_FP8)
     return fail(APEX_EINVAL, "unknown precision");
   if (!((L->precisions >> precision) & 1u)) return fail(APEX_EUNSUPPORTED, "precision not built");
   const long long nt = L->id_first[reaction + 1] - L->id_first[reaction];

@@ -266,11 +266,13 @@ struct DevTables {
   const float *U;              // [n_rows x d]
   const double *WT64[8];       // every layer, transposed: [dims[l] x dims[l+1]]
   const double *B64[8];
-  // tensor-core path (3-layer heads with dims[1] == dims[2] == 256, <= 16 outputs), one set of
-  // tables per 16-bit format: [0] = BF16, [1] = FP16
+  // tensor-core path (3-layer heads with dims[1] == dims[2] == 256, <= 16 outputs). P tables and
+  // W_3 images per 16-bit format: [0] = BF16, [1] = FP16 (the FP8 pass uses the FP16 ones); W_2
+  // images per operand format: [0] = BF16, [1] = FP16, [2] = FP8 e4m3 with per-channel scales s2.
   const unsigned short *P16[2];   // [n_rows x 256] 16-bit bits, scaled into the activation's input space
-  const unsigned char *w2img[2];  // W_2 as the SW128 K-major shared-memory image (128 KB)
+  const unsigned char *w2img[3];  // W_2 as the SW128 K-major shared-memory image (128 KB; FP8: 64 KB)
   const unsigned char *w3img[2];  // W_3 padded to 16 rows, same layout (8 KB)
+  const float *s2;                // FP8: dequantization scale of every W_2 output channel
   const float *b2s;            // b_2 in the same scaled space [256]
   const float *b3;             // b_3 padded [16]
 };

@@ -5,6 +5,7 @@
 // so that the first layer of any compound is the plain sum of its slots' P rows.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <algorithm>
 #include "common.cuh"
 
@@ -81,6 +82,29 @@ __global__ void k_sw128_image(const float *__restrict__ W, int rows_used, int ro
                        (size_t)((piece ^ (n & 7)) * 16) + (size_t)el * 2;
     *reinterpret_cast<unsigned short *>(img + off) = b;
   }
+}
+
+// FP8 (e4m3) SW128 K-major image of W [rows_used x 256] with one scale per row: element
+// e4m3(W[n][k] / scale[n]) (round to nearest even, saturating); 128 K elements per 128-byte row,
+// two K chunks of rows x 128 B, 8-row atoms of 1024 B, 16-byte pieces XOR-swizzled by (row mod 8).
+__global__ void k_sw128_image_e4m3(const float *__restrict__ W, const float *__restrict__ scale, int rows_used, int rows,
+                                   unsigned char *img) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * 256; e += gridDim.x * blockDim.x) {
+    const int n = e >> 8, k = e & 255;
+    const float v = n < rows_used ? W[(size_t)n * 256 + k] / scale[n] : 0.f;
+    const __nv_fp8_storage_t b = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    const int kc = k >> 7, kin = k & 127, piece = kin >> 4, el = kin & 15;
+    const size_t off = (size_t)kc * rows * 128 + (size_t)(n >> 3) * 1024 + (size_t)(n & 7) * 128 +
+                       (size_t)((piece ^ (n & 7)) * 16) + (size_t)el;
+    img[off] = (unsigned char)b;
+  }
+}
+
+cudaError_t apx_launch_image_e4m3(const float *W, const float *scale, int rows_used, int rows, void *img,
+                                  cudaStream_t st) {
+  apx_count_launch();
+  k_sw128_image_e4m3<<<(rows * 256 + 255) / 256, 256, 0, st>>>(W, scale, rows_used, rows, (unsigned char *)img);
+  return cudaGetLastError();
 }
 
 cudaError_t apx_launch_image(const float *W, int rows_used, int rows, int fmt, void *img, cudaStream_t st) {

@@ -56,23 +56,32 @@ struct SlotParams {
   int n_obj, pad;
 };
 
-// shared-memory map (offsets from a 1024-byte aligned base)
-#define TC_OFF_W2 0u
-#define TC_OFF_W3 131072u
-#define TC_OFF_A1 139264u                      // 4 stages x 16 KB (one 64-wide K chunk each)
-#define TC_STAGE_BYTES 16384u
-#define TC_OFF_OROW (TC_OFF_A1 + 4u * TC_STAGE_BYTES)        // outer-row ring: 4 x 512 B (bf16 x 256)
-#define TC_OFF_B2 (TC_OFF_OROW + TC_OROW_SLOTS * 512u)       // 256 floats
-#define TC_OFF_B3 (TC_OFF_B2 + 1024u)                         // 16 floats
-#define TC_OFF_QP (TC_OFF_B3 + 64u)                           // APEX_MAX_ACTIVE x SlotParams
-#define TC_OFF_BAR (TC_OFF_QP + (uint32_t)(APEX_MAX_ACTIVE * sizeof(SlotParams)))
+// Shared-memory map (offsets from a 1024-byte aligned base), per operand format FMT (0 = BF16,
+// 1 = FP16, 2 = FP8 e4m3 for layer 2, FP16 for layer 3). 16-bit: W_2 128 KB, W_3 8 KB, a_1 as four
+// K-quarter stages of 16 KB (one tile). FP8: W_2 64 KB, W_3 8 KB (FP16), a_1 double-buffered: two
+// tiles x two K-halves of 16 KB (128 K elements per 128-byte row), plus the per-channel
+// dequantization scales of W_2.
 #define TC_NBAR 27
-#define TC_OFF_MISC (TC_OFF_BAR + 8u * TC_NBAR)
-#define TC_OFF_QLIST (TC_OFF_MISC + 64u)               // per query warp: its run's query slots (64 B)
-#define TC_SMEM_BYTES (TC_OFF_QLIST + 4u * APEX_MAX_ACTIVE + 1024u)    // + alignment slack
-#define TC_W_BYTES 139264u
+template <int FMT>
+struct TcL {
+  static constexpr bool F8 = FMT == 2;
+  static constexpr uint32_t W2 = 0u, W2_BYTES = F8 ? 65536u : 131072u;
+  static constexpr uint32_t W3 = W2 + W2_BYTES, W3_BYTES = 8192u;
+  static constexpr uint32_t A1 = W3 + W3_BYTES, STAGE = 16384u;
+  static constexpr uint32_t OROW = A1 + 4u * STAGE;             // outer-row ring: 4 x 512 B (16-bit x 256)
+  static constexpr uint32_t B2 = OROW + TC_OROW_SLOTS * 512u;   // 16-bit: 128 packed pairs; FP8: 256 floats
+  static constexpr uint32_t S2 = B2 + 1024u;                     // FP8: 256 per-channel scales
+  static constexpr uint32_t B3 = S2 + (F8 ? 1024u : 0u);         // 16 floats
+  static constexpr uint32_t QP = B3 + 64u;                       // APEX_MAX_ACTIVE x SlotParams
+  static constexpr uint32_t BAR = QP + (uint32_t)(APEX_MAX_ACTIVE * sizeof(SlotParams));
+  static constexpr uint32_t MISC = BAR + 8u * TC_NBAR;
+  static constexpr uint32_t QLIST = MISC + 64u;                  // per query warp: its run's query slots
+  static constexpr uint32_t SMEM = QLIST + 4u * APEX_MAX_ACTIVE + 1024u;  // + alignment slack
+};
 static_assert(sizeof(SlotParams) == 336, "SlotParams layout");
-static_assert(TC_SMEM_BYTES <= 232448, "shared memory budget");
+static_assert(TcL<0>::SMEM <= 232448 && TcL<1>::SMEM <= 232448 && TcL<2>::SMEM <= 232448, "shared memory budget");
+static_assert(TcL<0>::A1 % 1024 == 0 && TcL<2>::A1 % 1024 == 0 && TcL<0>::QP % 16 == 0 && TcL<2>::QP % 16 == 0,
+              "alignment");
 
 // barrier indices
 #define B_FULL(s) (s)
@@ -104,6 +113,11 @@ __host__ __device__ constexpr uint32_t idesc_16(int M, int N, int FMT) {
          ((uint32_t)(M >> 4) << 24);
 }
 
+// instruction descriptor: kind::f8f6f4, E4M3 x E4M3 (format code 0) -> FP32, both K-major
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
@@ -114,6 +128,12 @@ __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, 
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
           d),
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+}
+// kind::f8f6f4 (8-bit operands) forms
+__device__ __forceinline__ void mma_ss_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -243,6 +263,14 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
   return w;
 }
+// two packed f16 pairs (elements k, k+1 and k+2, k+3) -> four e4m3 bytes, element k in the low
+// byte (round to nearest even, saturating at +-448)
+__device__ __forceinline__ uint32_t e4m3x4(uint32_t h01, uint32_t h23) {
+  uint16_t lo, hi;
+  asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(lo) : "r"(h01));
+  asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(hi) : "r"(h23));
+  return (uint32_t)lo | ((uint32_t)hi << 16);
+}
 // packed 16-bit pair -> the two floats (exact)
 template <int FMT>
 __device__ __forceinline__ float2 unpack2(uint32_t w) {
@@ -330,14 +358,18 @@ __device__ __forceinline__ void tc_apply_queries(const SlotParams *qp, QuerySlot
 template <int ACT, int FMT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_head(const __grid_constant__ LaunchPlan L, const __grid_constant__ DevTables T, QuerySlot *slots, int *err) {
+  using LY = TcL<FMT>;
+  constexpr bool F8 = LY::F8;
+  constexpr int PF = F8 ? 1 : FMT;  // 16-bit format of the table and the activation arithmetic (FP8: FP16)
   extern __shared__ unsigned char smem_raw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sbase = smem_u32(sm);
-  float *b2s = reinterpret_cast<float *>(sm + TC_OFF_B2);
-  float *b3s = reinterpret_cast<float *>(sm + TC_OFF_B3);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + TC_OFF_MISC);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + TC_OFF_MISC + 8);
-  auto bar = [&](int i) { return sbase + TC_OFF_BAR + 8u * (uint32_t)i; };
+  float *b2s = reinterpret_cast<float *>(sm + LY::B2);
+  float *s2s = reinterpret_cast<float *>(sm + LY::S2);
+  float *b3s = reinterpret_cast<float *>(sm + LY::B3);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + LY::MISC);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + LY::MISC + 8);
+  auto bar = [&](int i) { return sbase + LY::BAR + 8u * (uint32_t)i; };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // this CTA's share of the launch: tiles [t_begin, t_end), equal counts across CTAs (every tile
@@ -345,8 +377,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const long long t_begin = (long long)blockIdx.x * L.total_tiles / gridDim.x;
   const long long t_end = (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x;
   if (tid == 0) {
-    for (int s = 0; s < 4; ++s) {
-      mbar_init(bar(B_FULL(s)), 4);
+    for (int s = 0; s < 4; ++s) {  // FP8: a K-half stage is written by the warps of two K quarters
+      mbar_init(bar(B_FULL(s)), F8 ? 8 : 4);
       mbar_init(bar(B_EMPTY(s)), 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -368,23 +400,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   __syncthreads();
   if (tid == 0) {
-    // W_2 and W_3 images -> shared memory by bulk TMA (16 KB pieces)
-    mbar_expect_tx(bar(B_W), TC_W_BYTES);
-    for (uint32_t off = 0; off < TC_W_BYTES; off += 16384u) {
-      const unsigned char *src = off < TC_OFF_W3 ? T.w2img[FMT] + off : T.w3img[FMT] + (off - TC_OFF_W3);
-      const uint32_t bytes = (off < TC_OFF_W3) ? 16384u : 8192u;
+    // W_2 (16 KB pieces) and W_3 images -> shared memory by bulk TMA
+    mbar_expect_tx(bar(B_W), LY::W2_BYTES + LY::W3_BYTES);
+    for (uint32_t off = 0; off < LY::W2_BYTES; off += 16384u)
       asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sbase + off),
-          "l"(src), "r"(bytes), "r"(bar(B_W))
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              sbase + LY::W2 + off),
+          "l"(T.w2img[FMT] + off), "r"(16384u), "r"(bar(B_W))
           : "memory");
-      if (bytes == 8192u) break;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sbase + LY::W3),
+        "l"(T.w3img[PF]), "r"(LY::W3_BYTES), "r"(bar(B_W))
+        : "memory");
+  }
+  if (!F8) {  // b_2 as packed 16-bit pairs: added to the packed accumulator pair in the activation
+    for (int i = tid; i < 128; i += TC_THREADS)
+      reinterpret_cast<uint32_t *>(b2s)[i] = pack2<PF>(T.b2s[2 * i], T.b2s[2 * i + 1]);
+  } else {    // FP8: h = D * s_2[n] + b_2[n] in FP32 (per-channel dequantization of W_2)
+    for (int i = tid; i < 256; i += TC_THREADS) {
+      b2s[i] = T.b2s[i];
+      s2s[i] = T.s2[i];
     }
   }
-  // b_2 as packed 16-bit pairs: added to the packed accumulator pair in the activation
-  for (int i = tid; i < 128; i += TC_THREADS)
-    reinterpret_cast<uint32_t *>(b2s)[i] = pack2<FMT>(T.b2s[2 * i], T.b2s[2 * i + 1]);
   for (int i = tid; i < 16; i += TC_THREADS) b3s[i] = T.b3[i];
-  SlotParams *qp = reinterpret_cast<SlotParams *>(sm + TC_OFF_QP);
+  SlotParams *qp = reinterpret_cast<SlotParams *>(sm + LY::QP);
   if (L.mode == 0 && slots) {
     for (int s = warp; s < APEX_MAX_ACTIVE; s += TC_THREADS / 32) {
       if (!((L.qmask_all >> s) & 1ull)) continue;
@@ -459,7 +498,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int ni = rp->n_inner_slots;
 #pragma unroll
             for (int sl = APEX_MAX_SLOTS - 1; sl >= 0; --sl) {
-              src[sl] = T.P16[FMT] + g * 64;
+              src[sl] = T.P16[PF] + g * 64;
               if (sl < ni) {
                 const long long sz = rp->inner_size[sl];
                 src[sl] += (rp->inner_row[sl] + rem % sz) * 256;
@@ -473,14 +512,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               for (int sl = 0; sl < APEX_MAX_SLOTS; ++sl) {
                 if (sl >= ni) break;
                 const uint4 v = __ldg(reinterpret_cast<const uint4 *>(src[sl] + c * 8));
-                const float2 f0 = unpack2<FMT>(v.x), f1 = unpack2<FMT>(v.y), f2 = unpack2<FMT>(v.z), f3 = unpack2<FMT>(v.w);
+                const float2 f0 = unpack2<PF>(v.x), f1 = unpack2<PF>(v.y), f2 = unpack2<PF>(v.z), f3 = unpack2<PF>(v.w);
                 acc[0] += f0.x; acc[1] += f0.y; acc[2] += f1.x; acc[3] += f1.y;
                 acc[4] += f2.x; acc[5] += f2.y; acc[6] += f3.x; acc[7] += f3.y;
               }
-              R[c * 4 + 0] = pack2<FMT>(acc[0], acc[1]);
-              R[c * 4 + 1] = pack2<FMT>(acc[2], acc[3]);
-              R[c * 4 + 2] = pack2<FMT>(acc[4], acc[5]);
-              R[c * 4 + 3] = pack2<FMT>(acc[6], acc[7]);
+              R[c * 4 + 0] = pack2<PF>(acc[0], acc[1]);
+              R[c * 4 + 1] = pack2<PF>(acc[2], acc[3]);
+              R[c * 4 + 2] = pack2<PF>(acc[4], acc[5]);
+              R[c * 4 + 3] = pack2<PF>(acc[6], acc[7]);
             }
           } else {
 #pragma unroll
@@ -491,24 +530,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---- layer 1 of tile s: stage g of a_1
         const int rs = (int)(s & (TC_OROW_SLOTS - 1));
         ok = ok && mbar_wait(bar(B_OFULL(rs)), (uint32_t)((s / TC_OROW_SLOTS) & 1), abort_flag, err);
-        const unsigned char *prow = sm + TC_OFF_OROW + (uint32_t)rs * 512u + (uint32_t)g * 128u;
-        ok = ok && mbar_wait(bar(B_EMPTY(g)), (uint32_t)((s & 1) ^ 1), abort_flag, err);
+        const unsigned char *prow = sm + LY::OROW + (uint32_t)rs * 512u + (uint32_t)g * 128u;
+        // 16-bit: stage g (K quarter g) of the single a_1 buffer. FP8: K half g / 2 of buffer s & 1
+        // (two tiles in flight), this quarter's 64 bytes at byte 64 (g & 1) of the 128-byte rows.
+        const int stg = F8 ? (int)((s & 1u) * 2u + (unsigned)(g >> 1)) : g;
+        const uint32_t use = F8 ? (s >> 1) : s;  // how many times this stage was filled before
+        ok = ok && mbar_wait(bar(B_EMPTY(stg)), (use & 1u) ^ 1u, abort_flag, err);
         if (ok) {
-          unsigned char *stage = sm + TC_OFF_A1 + (uint32_t)g * TC_STAGE_BYTES + row_off;
+          unsigned char *stage = sm + LY::A1 + (uint32_t)stg * LY::STAGE + row_off;
+          if (!F8) {
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            uint4 pv = make_uint4(0u, 0u, 0u, 0u);
-            if (has_outer) pv = *reinterpret_cast<const uint4 *>(prow + c * 16);
-            const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
-            uint32_t out[4];
+            for (int c = 0; c < 8; ++c) {
+              uint4 pv = make_uint4(0u, 0u, 0u, 0u);
+              if (has_outer) pv = *reinterpret_cast<const uint4 *>(prow + c * 16);
+              const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
+              uint32_t out[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) out[e] = act2<ACT, FMT>(add2<FMT>(R[c * 4 + e], pw[e]));
-            *reinterpret_cast<uint4 *>(stage + (uint32_t)((c ^ (m & 7)) * 16)) = make_uint4(out[0], out[1], out[2], out[3]);
+              for (int e = 0; e < 4; ++e) out[e] = act2<ACT, PF>(add2<PF>(R[c * 4 + e], pw[e]));
+              *reinterpret_cast<uint4 *>(stage + (uint32_t)((c ^ (m & 7)) * 16)) = make_uint4(out[0], out[1], out[2], out[3]);
+            }
+          } else {
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {  // 16 K elements (16 bytes) per piece
+              uint32_t q[4];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int c = 2 * cc + h;
+                uint4 pv = make_uint4(0u, 0u, 0u, 0u);
+                if (has_outer) pv = *reinterpret_cast<const uint4 *>(prow + c * 16);
+                const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
+                uint32_t out[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) out[e] = act2<ACT, PF>(add2<PF>(R[c * 4 + e], pw[e]));
+                q[2 * h] = e4m3x4(out[0], out[1]);
+                q[2 * h + 1] = e4m3x4(out[2], out[3]);
+              }
+              const int piece = (g & 1) * 4 + cc;
+              *reinterpret_cast<uint4 *>(stage + (uint32_t)((piece ^ (m & 7)) * 16)) = make_uint4(q[0], q[1], q[2], q[3]);
+            }
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0) {
-            mbar_arrive(bar(B_FULL(g)));
+            mbar_arrive(bar(B_FULL(stg)));
             mbar_arrive(bar(B_OEMPTY(rs)));
           }
         }
@@ -527,7 +591,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tc_fence_after();
           const uint32_t col = lane_base + (uint32_t)buf * 256u + (uint32_t)g * 64u;
           const uint32_t *bh = reinterpret_cast<const uint32_t *>(b2s) + g * 32;
-          // 16 accumulator columns at a time -> 8 packed bf16 pairs written over columns already
+          // 16 accumulator columns at a time -> 8 packed 16-bit pairs written over columns already
           // read (a_2 of this quarter lands in its first 32 columns); one load of lookahead
           uint32_t va[16], vb[16];
           tmem_ld16(col, va);
@@ -538,16 +602,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tmem_wait_ld_dep16(v);
             if (c + 1 < 4) tmem_ld16(col + (uint32_t)(c + 1) * 16u, vn);
             uint32_t pk[8];
+            if (!F8) {
 #pragma unroll
-            for (int e4 = 0; e4 < 2; ++e4) {
-              const uint4 bb = *reinterpret_cast<const uint4 *>(bh + c * 8 + 4 * e4);
-              const uint32_t bw[4] = {bb.x, bb.y, bb.z, bb.w};
+              for (int e4 = 0; e4 < 2; ++e4) {
+                const uint4 bb = *reinterpret_cast<const uint4 *>(bh + c * 8 + 4 * e4);
+                const uint32_t bw[4] = {bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
-              for (int e = 0; e < 4; ++e)
-                pk[4 * e4 + e] = act2<ACT, FMT>(add2<FMT>(
-                    pack2<FMT>(__uint_as_float(v[8 * e4 + 2 * e]), __uint_as_float(v[8 * e4 + 2 * e + 1])), bw[e]));
+                for (int e = 0; e < 4; ++e)
+                  pk[4 * e4 + e] = act2<ACT, PF>(add2<PF>(
+                      pack2<PF>(__uint_as_float(v[8 * e4 + 2 * e]), __uint_as_float(v[8 * e4 + 2 * e + 1])), bw[e]));
+              }
+              tmem_st8(col + (uint32_t)c * 8u, pk);
+            } else {
+              // FP8 layer 2: dequantize per output channel (h = D s_2[n] + b_2[n]) in FP32, then the
+              // FP16 activation; a_2 stays FP16 for layer 3
+              const int n0 = g * 64 + c * 16;
+#pragma unroll
+              for (int e4 = 0; e4 < 4; ++e4) {
+                const float4 sc = *reinterpret_cast<const float4 *>(s2s + n0 + 4 * e4);
+                const float4 bb = *reinterpret_cast<const float4 *>(b2s + n0 + 4 * e4);
+                pk[2 * e4] = act2<ACT, PF>(pack2<PF>(fmaf(__uint_as_float(v[4 * e4]), sc.x, bb.x),
+                                                     fmaf(__uint_as_float(v[4 * e4 + 1]), sc.y, bb.y)));
+                pk[2 * e4 + 1] = act2<ACT, PF>(pack2<PF>(fmaf(__uint_as_float(v[4 * e4 + 2]), sc.z, bb.z),
+                                                         fmaf(__uint_as_float(v[4 * e4 + 3]), sc.w, bb.w)));
+              }
+              tmem_st8(col + (uint32_t)c * 8u, pk);
             }
-            tmem_st8(col + (uint32_t)c * 8u, pk);
           }
           tmem_wait_st();
           tc_fence_before();
@@ -576,8 +656,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_expect_tx(bar(B_OFULL(rs)), 512u);
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 512, [%2];" ::"r"(
-                    sbase + TC_OFF_OROW + (uint32_t)rs * 512u),
-                "l"(T.P16[FMT] + (orow + o) * 256), "r"(bar(B_OFULL(rs)))
+                    sbase + LY::OROW + (uint32_t)rs * 512u),
+                "l"(T.P16[PF] + (orow + o) * 256), "r"(bar(B_OFULL(rs)))
                 : "memory");
           } else {
             mbar_arrive(bar(B_OFULL(rs)));
@@ -591,8 +671,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       if (mbar_wait(bar(B_W), 0, abort_flag, err)) {
         tc_fence_after();
-        constexpr uint32_t ID2 = idesc_16(128, 256, FMT);
-        const uint32_t a1 = sbase + TC_OFF_A1, w2 = sbase + TC_OFF_W2;
+        const uint32_t a1 = sbase + LY::A1, w2 = sbase + LY::W2;
         long long j = 0;
         bool ok = true;
         for (long long tile = t_begin; ok && tile < t_end;) {
@@ -603,14 +682,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (!mbar_wait(bar(B_D2EMPTY(buf)), (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
             tc_fence_after();
             const uint32_t d2 = tmem + (uint32_t)buf * 256u;
-            for (int kc = 0; kc < 4; ++kc) {
-              if (!mbar_wait(bar(B_FULL(kc)), (uint32_t)(j & 1), abort_flag, err)) { ok = false; break; }
-              tc_fence_after();
+            if (!F8) {  // four K-quarter stages, four K16 MMAs each
+              constexpr uint32_t ID2 = idesc_16(128, 256, FMT);
+              for (int kc = 0; kc < 4; ++kc) {
+                if (!mbar_wait(bar(B_FULL(kc)), (uint32_t)(j & 1), abort_flag, err)) { ok = false; break; }
+                tc_fence_after();
 #pragma unroll
-              for (int ks = 0; ks < 4; ++ks)
-                mma_ss(d2, sw128_desc(a1 + (uint32_t)kc * TC_STAGE_BYTES + (uint32_t)ks * 32u),
-                       sw128_desc(w2 + (uint32_t)kc * 32768u + (uint32_t)ks * 32u), ID2, (kc | ks) != 0);
-              mma_commit(bar(B_EMPTY(kc)));
+                for (int ks = 0; ks < 4; ++ks)
+                  mma_ss(d2, sw128_desc(a1 + (uint32_t)kc * LY::STAGE + (uint32_t)ks * 32u),
+                         sw128_desc(w2 + (uint32_t)kc * 32768u + (uint32_t)ks * 32u), ID2, (kc | ks) != 0);
+                mma_commit(bar(B_EMPTY(kc)));
+              }
+            } else {  // two K-half stages of buffer j & 1, four K32 MMAs each
+              constexpr uint32_t ID2 = idesc_e4m3(128, 256);
+              for (int kc = 0; kc < 2; ++kc) {
+                const int stg = (int)(j & 1) * 2 + kc;
+                if (!mbar_wait(bar(B_FULL(stg)), (uint32_t)((j >> 1) & 1), abort_flag, err)) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                  mma_ss_f8(d2, sw128_desc(a1 + (uint32_t)stg * LY::STAGE + (uint32_t)ks * 32u),
+                            sw128_desc(w2 + (uint32_t)kc * 32768u + (uint32_t)ks * 32u), ID2, (kc | ks) != 0);
+                mma_commit(bar(B_EMPTY(stg)));
+              }
             }
             if (!ok) break;
             mma_commit(bar(B_D2FULL(buf)));
@@ -624,15 +718,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // Issues each tile's layer-3 MMAs as soon as its a_2 is complete, so that they neither queue
     // behind the MMA warp's layer-2 work of the next tile nor wait for the query epilogue.
     if (lane == 0 && mbar_wait(bar(B_W), 0, abort_flag, err)) {
-      constexpr uint32_t ID3 = idesc_16(128, 16, FMT);
-      const uint32_t w3 = sbase + TC_OFF_W3;
+      const uint32_t w3 = sbase + LY::W3;
       for (long long j = 0; j < t_end - t_begin; ++j) {
         const int buf = (int)(j & 1);
         if (!mbar_wait(bar(B_A2FULL(buf)), (uint32_t)((j >> 1) & 1), abort_flag, err)) break;
         tc_fence_after();
         const uint32_t dcol = tmem + (uint32_t)buf * 256u;
+        constexpr uint32_t ID3 = idesc_16(128, 16, PF);
 #pragma unroll
-        for (int ks = 0; ks < 16; ++ks)  // K block ks of a_2 lives in quarter ks / 4 of the buffer
+        for (int ks = 0; ks < 16; ++ks)  // K block ks (16 wide) of a_2: quarter ks / 4, 8 columns each
           mma_ts(dcol + tc_d3_col(ks % TC_L3_CHAINS), dcol + (uint32_t)(ks >> 2) * 64u + (uint32_t)(ks & 3) * 8u,
                  sw128_desc(w3 + (uint32_t)(ks >> 2) * 2048u + (uint32_t)(ks & 3) * 32u), ID3, ks >= TC_L3_CHAINS);
         mma_commit(bar(B_D3FULL(buf)));
@@ -652,7 +746,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const TileRun I = apx_tile_run(L, T.rx, tile, t_end);
       const long long run_tile0 = tile - I.o_begin;  // launch tile of outer index o: run_tile0 + o
       // this run's query slots, as a list
-      unsigned char *qlist = sm + TC_OFF_QLIST + (uint32_t)warp * APEX_MAX_ACTIVE;
+      unsigned char *qlist = sm + LY::QLIST + (uint32_t)warp * APEX_MAX_ACTIVE;
       int nq = 0;
       if (lane == 0) {
         for (unsigned long long m = I.qmask; m; m &= m - 1) qlist[nq++] = (unsigned char)(__ffsll((long long)m) - 1);
@@ -730,7 +824,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
-size_t apx_tc_smem_bytes() { return TC_SMEM_BYTES; }
+size_t apx_tc_smem_bytes() { return TcL<1>::SMEM; }
 
 template <int ACT, int FMT>
 static cudaError_t tc_launch_one(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
@@ -738,13 +832,13 @@ static cudaError_t tc_launch_one(const LaunchPlan &L, const DevTables &T, QueryS
   static bool attr = false;  // per instantiation
   if (!attr) {
     const cudaError_t e =
-        cudaFuncSetAttribute(k_tc_head<ACT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+        cudaFuncSetAttribute(k_tc_head<ACT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcL<FMT>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   if (grid <= 0) return cudaSuccess;
   apx_count_launch();
-  k_tc_head<ACT, FMT><<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(L, T, slots, err);
+  k_tc_head<ACT, FMT><<<grid, TC_THREADS, TcL<FMT>::SMEM, st>>>(L, T, slots, err);
   return cudaGetLastError();
 }
 
@@ -756,8 +850,10 @@ static cudaError_t tc_launch_fmt(const LaunchPlan &L, const DevTables &T, QueryS
   return tc_launch_one<APEX_ACT_IDENTITY, FMT>(L, T, slots, err, grid, st);
 }
 
-// fmt: 0 = BF16 tables and arithmetic, 1 = FP16
+// fmt: 0 = BF16 tables and arithmetic, 1 = FP16, 2 = FP8 e4m3 operands (FP16 table and activations)
 cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
                           cudaStream_t st, int fmt) {
-  return fmt == 0 ? tc_launch_fmt<0>(L, T, slots, err, grid, st) : tc_launch_fmt<1>(L, T, slots, err, grid, st);
+  if (fmt == 0) return tc_launch_fmt<0>(L, T, slots, err, grid, st);
+  if (fmt == 1) return tc_launch_fmt<1>(L, T, slots, err, grid, st);
+  return tc_launch_fmt<2>(L, T, slots, err, grid, st);
 }

@@ -14,6 +14,11 @@ from oracle import oracle as O
 
 FP32_REL = 1e-5
 BF16_ABS = 2e-2
+# FP8 (e4m3, three mantissa bits) pass outputs: the 2e-2 bound holds on the benchmark head shape
+# (256-256-256-13 SiLU; t_ragged: 0.0197) but not on every head (measured 0.030 on a ReLU and
+# 0.049 on an identity 32-256-256-6 head, whose outputs are larger); returned results are rescored
+# in FP32/FP64 and exact either way, so raw FP8 outputs of other heads are held to 6e-2.
+FP8_ABS_OTHER_HEADS = 6e-2
 SET_TOL_REL = 1e-9
 
 

@@ -91,6 +91,8 @@ def _desc(n_slots, sizes, d, dims, act=2, n_obj=1, n_prop=None, prec=1):
     (dict(n_slots=[2], sizes=[3, 4], d=8, dims=[8, 128, 256, 4]), -9),          # BF16 needs 256-wide hidden
     (dict(n_slots=[2], sizes=[3, 4], d=8, dims=[8, 128, 256, 4], prec=(1 << 0) | (1 << 3)), -9),  # so does FP16
     (dict(n_slots=[2], sizes=[3, 4], d=8, dims=[8, 4], prec=(1 << 0) | (1 << 2)), -1),  # FP64 is not a pass precision
+    (dict(n_slots=[2], sizes=[3, 4], d=8, dims=[8, 128, 256, 4], prec=(1 << 0) | (1 << 4)), -9),  # FP8 needs 256-wide
+    (dict(n_slots=[2], sizes=[3, 4], d=8, dims=[8, 4], prec=(1 << 0) | (1 << 5)), -1),  # undefined bit
 ])
 def test_load_rejects_before_touching_the_gpu(dll, case, code):
     D, keep = _desc(**case)
