@@ -281,6 +281,7 @@ def run_batched(args):
     qs = csl_gen.queries_batched(stats, 5, 8, args.queries, seed=1, precision=args.precision)
     stream = torch.cuda.Stream()
     L = apex.Library(lib, head, precisions=("fp32", args.precision), stream=stream.cuda_stream)
+    tune = L.autotune(args.precision, n_queries=16, k=10000)  # launch shapes for this library
     L.run(qs[0])  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -295,7 +296,7 @@ def run_batched(args):
     out = {"mode": "batched", "workload": "c3_real 1e9-compound subset", "precision": args.precision, "n_compounds": N,
            "reactions": len(sub), "queries": len(qs), "k": [int(q.k) for q in qs][:8],
            "wall_s": dt, "head_evaluations_per_s": N / dt, "query_compounds_per_s": len(qs) * N / dt,
-           "results": int(sum(r["n"] for r in res)),
+           "results": int(sum(r["n"] for r in res)), "autotune": tune,
            "per_query_k_restarts_candidates_fp64_latency_finalize_start": per[:64]}
     L.close()
     print(json.dumps(out))
@@ -317,6 +318,7 @@ def run_serving(args):
                                       precision=args.precision)
     stream = torch.cuda.Stream()
     L = apex.Library(lib, head, precisions=("fp32", args.precision), stream=stream.cuda_stream)
+    tune = L.autotune(args.precision, n_queries=8, k=10000, subset=np.arange(min(30, lib.n_reactions)))
     sizes = np.array([float(np.prod(lib.sizes_of(t).astype(np.float64))) for t in range(lib.n_reactions)])
     done = []
     lock = threading.Lock()
@@ -345,7 +347,8 @@ def run_serving(args):
     out = {"mode": "serving", "workload": "c3_real resident", "n_compounds": float(sizes.sum()),
            "rate_hz": args.rate, "queries": len(done), "wall_s": wall,
            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-           "mean_scope_compounds": float(scope.mean()), "query_compounds_per_s": float(scope.sum() / wall)}
+           "mean_scope_compounds": float(scope.mean()), "query_compounds_per_s": float(scope.sum() / wall),
+           "autotune": tune}
     L.close()
     print(json.dumps(out))
 

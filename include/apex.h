@@ -228,6 +228,33 @@ apex_status apex_topk_select_noalloc(const float *keys, const int64_t *ids, int6
  * libraries, all entry points). Pure host counter. */
 apex_status apex_kernel_launches(int64_t *out);
 
+/* Autotuner. Picks the library's launch shapes by timing trial queries through the normal query
+ * path (apex_query / apex_topk_fetch; no other query should be running): (1) the number of
+ * compounds per enumeration launch of the circular pass (2^23 .. 2^27): smaller launches tighten
+ * the running admission thresholds sooner, larger ones cost fewer launches and synchronizations;
+ * (2) the rows per CTA tile of the FP32 kernel over id lists (32 or 128), used for the
+ * start-threshold sample and the candidate rescore. Trial queries: n_queries (1..64) submitted
+ * together, seeded convex objective weights, two boxes of +-1 RMS around 0 on seeded properties,
+ * the given k, precision and reaction subset (0/NULL = all). The choices stay in effect for the
+ * library; out receives every candidate's wall time (ms) and the choices. */
+#define APEX_AUTOTUNE_MAX_CANDIDATES 8
+typedef struct {
+  int32_t precision;
+  int32_t n_queries;
+  int64_t k;
+  int32_t n_reaction_subset;
+  const int32_t *reactions;
+} apex_autotune_desc;
+typedef struct {
+  int32_t n_chunk_candidates;
+  int64_t chunk_compounds[APEX_AUTOTUNE_MAX_CANDIDATES];
+  double chunk_ms[APEX_AUTOTUNE_MAX_CANDIDATES];
+  double fp32_id_tile_ms[2];          /* tiles of 32 and 128 rows */
+  int64_t chosen_chunk_compounds;
+  int32_t chosen_fp32_id_tile;
+} apex_autotune_result_t;
+apex_status apex_autotune(apex_library *lib, const apex_autotune_desc *desc, apex_autotune_result_t *out);
+
 /* Failure-detection self-test of the bounded device waits. Every wait inside this library's
  * kernels (mbarrier phases between warp roles) gives up after a time limit (2 s in production
  * kernels), records a timeout in the launch's status word and returns; the host then fails the

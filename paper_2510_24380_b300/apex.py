@@ -61,6 +61,20 @@ class LibraryInfo(C.Structure):
     ]
 
 
+AUTOTUNE_MAX = 8
+
+
+class AutotuneDesc(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("n_queries", C.c_int32), ("k", C.c_int64), ("n_reaction_subset", C.c_int32),
+                ("reactions", C.POINTER(C.c_int32))]
+
+
+class AutotuneResult(C.Structure):
+    _fields_ = [("n_chunk_candidates", C.c_int32), ("chunk_compounds", C.c_int64 * AUTOTUNE_MAX),
+                ("chunk_ms", C.c_double * AUTOTUNE_MAX), ("fp32_id_tile_ms", C.c_double * 2),
+                ("chosen_chunk_compounds", C.c_int64), ("chosen_fp32_id_tile", C.c_int32)]
+
+
 class QueryStats(C.Structure):
     _fields_ = [
         ("n_scope", C.c_int64), ("n_scored", C.c_int64), ("n_candidates", C.c_int64), ("n_rescored_fp64", C.c_int64),
@@ -95,6 +109,7 @@ SYMBOLS = {
                                  C.POINTER(C.c_int64), C.c_void_p],
     "apex_kernel_launches": [C.POINTER(C.c_int64)],
     "apex_selftest_wait_timeout": [C.c_void_p, C.c_int32],
+    "apex_autotune": [C.c_void_p, C.POINTER(AutotuneDesc), C.POINTER(AutotuneResult)],
     "apex_last_error": [],
 }
 
@@ -267,6 +282,22 @@ class Library:
         _check(load().apex_dump_outputs(self.h, PREC[precision], int(reaction), _p(out, C.c_float),
                                         int(n_compounds)), "apex_dump_outputs")
         return out
+
+    def autotune(self, precision: str = "fp16", n_queries: int = 8, k: int = 1000, subset=None) -> dict:
+        """Times trial queries to pick the launch shapes (compounds per launch, FP32 id tile)."""
+        d = AutotuneDesc()
+        d.precision = PREC[precision]
+        d.n_queries = int(n_queries)
+        d.k = int(k)
+        sub = None if subset is None else np.ascontiguousarray(subset, np.int32)
+        d.n_reaction_subset = 0 if sub is None else int(sub.shape[0])
+        d.reactions = None if sub is None else _p(sub, C.c_int32)
+        r = AutotuneResult()
+        _check(load().apex_autotune(self.h, C.byref(d), C.byref(r)), "apex_autotune")
+        n = r.n_chunk_candidates
+        return {"chunk_compounds": list(r.chunk_compounds)[:n], "chunk_ms": [round(x, 3) for x in list(r.chunk_ms)[:n]],
+                "fp32_id_tile_ms": [round(x, 3) for x in r.fp32_id_tile_ms],
+                "chosen_chunk_compounds": int(r.chosen_chunk_compounds), "chosen_fp32_id_tile": int(r.chosen_fp32_id_tile)}
 
     def selftest_wait_timeout(self, limit_ms: int = 50) -> int:
         """Runs the device-wait self-test; returns the status code (APEX_ETIMEDOUT = -5 expected)."""

@@ -31,7 +31,7 @@
 
 // ------------------------------------------------------------------ kernels (other files)
 cudaError_t apx_launch_fp32(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, const long long *ids,
-                            long long n_ids, float *out, int grid, cudaStream_t st);
+                            long long n_ids, float *out, int grid, cudaStream_t st, int id_tile = 32);
 cudaError_t apx_launch_fp64(const DevTables &T, const long long *ids, long long n, double *out, cudaStream_t st,
                             const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_prep(const float *U, const float *W1, const float *b1, const unsigned char *bias_row,
@@ -141,6 +141,10 @@ struct QueryRec {
 
 // ------------------------------------------------------------------ library
 struct apex_library {
+  // tunables (apex_autotune): compounds per enumeration launch of the circular pass, rows per CTA
+  // tile of the FP32 kernel over id lists (start-threshold sample, candidate rescore)
+  std::atomic<long long> chunk_compounds{1LL << 25};
+  std::atomic<int> fp32_id_tile{32};
   // shape
   int T = 0, d = 0, n_layers = 0, act = 0, n_obj = 0, n_prop = 0, n_out = 0, max_slots = 0;
   int dims[8] = {0};
@@ -960,7 +964,8 @@ static bool speculative_start(apex_library &L, QueryRec *q, double margin2) {
   CU(apx_launch_spec_ids(d_rxn, d_pre, n_sub, L.T_.id_first, q->scope_n, L.rng(), S, d_ids, L.st));
   LaunchPlan dummy;
   memset(&dummy, 0, sizeof(dummy));
-  CU(apx_launch_fp32(dummy, L.T_, nullptr, d_ids, S, d_out, grid_for(L, (S + APX_TILE - 1) / APX_TILE), L.st));
+  CU(apx_launch_fp32(dummy, L.T_, nullptr, d_ids, S, d_out, grid_for(L, (S + APX_TILE - 1) / APX_TILE), L.st,
+                     L.fp32_id_tile.load()));
   SpecArgs a;
   memset(&a, 0, sizeof(a));
   for (int j = 0; j < L.n_obj; ++j) a.w[j] = q->w[j];
@@ -1127,7 +1132,8 @@ static bool finalize(apex_library &L, QueryRec *q) {
   if (nc > 0) {
     LaunchPlan dummy;
     memset(&dummy, 0, sizeof(dummy));
-    CU(apx_launch_fp32(dummy, L.T_, nullptr, q->ids, nc, out32, grid_for(L, (nc + APX_TILE - 1) / APX_TILE), L.st));
+    CU(apx_launch_fp32(dummy, L.T_, nullptr, q->ids, nc, out32, grid_for(L, (nc + APX_TILE - 1) / APX_TILE), L.st,
+                       L.fp32_id_tile.load()));
   }
   float *f32 = (float *)B.get(sizeof(float) * std::max<long long>(nc, 1));
   unsigned char *maybe = (unsigned char *)B.get(std::max<long long>(nc, 1));
@@ -1263,7 +1269,7 @@ static void finish(apex_library &L, QueryRec *q, QState st, apex_status err, con
 // One step of the circular pass: a launch over the next chunk of items needed by any active
 // query (per precision), then the conditional select of the served queries.
 static void pass_step(apex_library &L) {
-  const long long chunk_compounds = 1LL << 25;
+  const long long chunk_compounds = L.chunk_compounds.load();
   // build one plan (items from the cursor) with per-precision query masks
   // indexed by pass precision (APEX_FP32, APEX_BF16, APEX_FP16, APEX_FP8; 2 unused)
   PlanBuilder pb[5] = {PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx)};
@@ -1582,6 +1588,102 @@ extern "C" apex_status apex_selftest_wait_timeout(apex_library *L, int32_t limit
   }
   if (code == APX_ERR_TIMEOUT) return fail(APEX_ETIMEDOUT, "device wait gave up after %d ms (expected)", limit_ms);
   return fail(APEX_ECUDA, "wait self-test: the wait returned without timing out (status %d)", code);
+}
+
+// ------------------------------------------------------------------ autotuner
+// Trial queries shaped like the workload's: seeded convex weights over the objectives, two boxes
+// of +-1 RMS around 0 on seeded properties, the caller's k, precision and reaction subset.
+static std::vector<apex_query_id> autotune_trials(apex_library *L, const apex_autotune_desc *d, std::mt19937_64 &g,
+                                                  apex_status *rc) {
+  std::vector<apex_query_id> ids;
+  std::uniform_real_distribution<double> U(0.0, 1.0);
+  for (int i = 0; i < d->n_queries; ++i) {
+    float w[APEX_MAX_OBJECTIVES] = {0};
+    double sw = 0;
+    for (int j = 0; j < L->n_obj; ++j) sw += (w[j] = (float)(-std::log(1.0 - U(g))));
+    for (int j = 0; j < L->n_obj; ++j) w[j] = (float)(w[j] / sw);
+    int32_t idx[2];
+    double lo[2], hi[2];
+    const int m = L->n_prop > 0 ? 2 : 0;
+    for (int c = 0; c < m; ++c) {
+      idx[c] = L->n_obj + (int)(g() % (unsigned long long)L->n_prop);
+      lo[c] = -L->rms[idx[c]];
+      hi[c] = L->rms[idx[c]];
+    }
+    apex_query_desc q{};
+    q.precision = d->precision;
+    q.objective_weights = w;
+    q.n_constraints = m;
+    q.output_index = idx;
+    q.lower = lo;
+    q.upper = hi;
+    q.k = d->k;
+    q.n_reaction_subset = d->n_reaction_subset;
+    q.reactions = d->reactions;
+    apex_query_id id = 0;
+    *rc = apex_query(L, &q, &id);
+    if (*rc != APEX_OK) return ids;
+    ids.push_back(id);
+  }
+  return ids;
+}
+
+static double autotune_run(apex_library *L, const apex_autotune_desc *d, uint64_t seed, apex_status *rc) {
+  std::mt19937_64 g(seed);
+  const double t0 = now_ms();
+  std::vector<apex_query_id> ids = autotune_trials(L, d, g, rc);
+  for (apex_query_id id : ids) {
+    int64_t n = 0;
+    const apex_status r = apex_topk_fetch(L, id, 0, nullptr, nullptr, nullptr, nullptr, nullptr, &n, -1);
+    if (r != APEX_OK && *rc == APEX_OK) *rc = r;
+  }
+  return now_ms() - t0;
+}
+
+extern "C" apex_status apex_autotune(apex_library *L, const apex_autotune_desc *d, apex_autotune_result_t *out) {
+  if (!L || !d || !out) return fail(APEX_EINVAL, "NULL argument");
+  if (d->n_queries < 1 || d->n_queries > APEX_MAX_ACTIVE) return fail(APEX_EINVAL, "n_queries outside 1..64");
+  if (d->k < 1) return fail(APEX_EINVAL, "k must be >= 1");
+  if (!((L->precisions >> d->precision) & 1u) || d->precision == APEX_FP64)
+    return fail(APEX_EUNSUPPORTED, "precision %d not available", d->precision);
+  memset(out, 0, sizeof(*out));
+  const long long chunks[APEX_AUTOTUNE_MAX_CANDIDATES] = {1LL << 23, 1LL << 24, 1LL << 25, 1LL << 26, 1LL << 27};
+  const int n_chunks = 5;
+  apex_status rc = APEX_OK;
+  autotune_run(L, d, L->seed + 101, &rc);  // warm-up: buffers, plans, caches
+  if (rc != APEX_OK) return rc;
+  double best = 1e300;
+  long long best_chunk = L->chunk_compounds.load();
+  for (int i = 0; i < n_chunks; ++i) {
+    L->chunk_compounds = chunks[i];
+    const double ms = autotune_run(L, d, L->seed + 202, &rc);
+    if (rc != APEX_OK) return rc;
+    out->chunk_compounds[i] = chunks[i];
+    out->chunk_ms[i] = ms;
+    if (ms < best) {
+      best = ms;
+      best_chunk = chunks[i];
+    }
+  }
+  out->n_chunk_candidates = n_chunks;
+  L->chunk_compounds = best_chunk;
+  const int tiles[2] = {32, 128};
+  double best_t = 1e300;
+  int best_tile = 32;
+  for (int i = 0; i < 2; ++i) {
+    L->fp32_id_tile = tiles[i];
+    const double ms = autotune_run(L, d, L->seed + 303, &rc);
+    if (rc != APEX_OK) return rc;
+    out->fp32_id_tile_ms[i] = ms;
+    if (ms < best_t) {
+      best_t = ms;
+      best_tile = tiles[i];
+    }
+  }
+  L->fp32_id_tile = best_tile;
+  out->chosen_chunk_compounds = best_chunk;
+  out->chosen_fp32_id_tile = best_tile;
+  return APEX_OK;
 }
 
 extern "C" apex_status apex_kernel_launches(int64_t *out) {

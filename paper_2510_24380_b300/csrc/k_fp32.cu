@@ -276,10 +276,10 @@ __global__ void __launch_bounds__(APX_SIMT_THREADS, 1)
 
 size_t apx_fp32_smem_bytes() { return sizeof(F32Smem<128>); }
 
-// Enumeration (ids == nullptr) runs 128-row tiles; id lists run 32-row tiles. grid <= 0: the
-// launcher picks min(tiles, 148 * 2) for id lists.
+// Enumeration (ids == nullptr) runs 128-row tiles; id lists run id_tile-row tiles (32 or 128,
+// chosen by the autotuner), min(tiles, 148 * 2) CTAs.
 cudaError_t apx_launch_fp32(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, const long long *ids,
-                            long long n_ids, float *out, int grid, cudaStream_t st) {
+                            long long n_ids, float *out, int grid, cudaStream_t st, int id_tile) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_fp32_head<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -293,6 +293,12 @@ cudaError_t apx_launch_fp32(const LaunchPlan &L, const DevTables &T, QuerySlot *
     if (grid <= 0) return cudaSuccess;
     apx_count_launch();
     k_fp32_head<128><<<grid, APX_SIMT_THREADS, sizeof(F32Smem<128>), st>>>(L, T, slots, ids, n_ids, out);
+  } else if (id_tile == 128) {
+    const long long tiles = (n_ids + 127) / 128;
+    if (tiles <= 0) return cudaSuccess;
+    const int g = (int)(tiles < 148 * 2 ? tiles : 148 * 2);
+    apx_count_launch();
+    k_fp32_head<128><<<g, APX_SIMT_THREADS, sizeof(F32Smem<128>), st>>>(L, T, slots, ids, n_ids, out);
   } else {
     const long long tiles = (n_ids + 31) / 32;
     if (tiles <= 0) return cudaSuccess;

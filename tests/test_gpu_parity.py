@@ -252,3 +252,15 @@ def test_bounded_wait_gives_up_and_library_keeps_working(ragged):
     assert "expected" in apex.last_error()
     q = _q([1, 0, 0, 0, 0], [5], [-0.1], [0.1], k=25, precision="fp16")
     check_topk(L.run(q), O.topk(lib, head, q), lib, head, q, rms)
+
+
+def test_autotune_picks_from_its_candidates_and_results_stay_exact(ragged):
+    lib, head, spec, L, rms = ragged
+    r = L.autotune("fp16", n_queries=4, k=40)
+    assert r["chosen_chunk_compounds"] in r["chunk_compounds"] and len(r["chunk_ms"]) == 5
+    assert r["chosen_fp32_id_tile"] in (32, 128)
+    assert all(ms > 0 for ms in r["chunk_ms"] + r["fp32_id_tile_ms"])
+    stats = csl_gen.load_stats("t_ragged")
+    for precision in ("fp16", "fp32"):
+        q = csl_gen.query_single("t_ragged", spec, stats, precision=precision)
+        check_topk(L.run(q), O.topk(lib, head, q), lib, head, q, rms)
