@@ -60,6 +60,24 @@ def peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
+def linear_roofline(N, q, lib, enum_ms, clk):
+    """Linear head (Eq. apex): the work per compound is the scalar sums and compares, ALU-bound:
+    (1 + m)(n - 1) additions + 2m comparisons (m constraints, n slots), against the FP32/INT
+    lane rate 148 SMs x 128 lanes x the SM clock sampled during the run."""
+    m = int(q.m)
+    ops = 0.0
+    for t in range(lib.n_reactions):
+        n = len(lib.sizes_of(t))
+        ops += float(np.prod(lib.sizes_of(t).astype(np.float64))) * ((1 + m) * (n - 1) + 2 * m)
+    mhz = (clk or {}).get("sm_mhz") or 2032.0
+    peak = 148 * 128 * mhz * 1e6 / 1e12  # Tops/s
+    achieved = ops / (enum_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_linear (per-synthon scalar sums, Eq. apex)",
+            "ops_per_compound": ops / N, "peak_kind": "148 SMs x 128 lanes x sampled SM clock",
+            "kernel_ms_per_step": enum_ms}
+
+
 def recorded_traffic(profile: str = "k_tc_head_c2_10m.md"):
     """DRAM bytes per launch of the enumeration kernel from the committed ncu summary, when the
     kernel source is still the one the counters were taken on (sha256 of k_tc.cu + common.cuh +
@@ -465,6 +483,7 @@ def main():
     mean_enum = float(np.mean(enum_ms))
     achieved = FLOP_PER_COMPOUND * N / (mean_enum * 1e-3) / 1e12
     peak = P.get("bf16_tflops", 1800.0)
+    linear = len(head.dims) == 2
     d2h = int(res["n"]) * (8 + 4 + 8 * 4 + 8 + 8 * L.n_outputs)
     h2d = 4 * len(q.weights) + (4 + 8 + 8) * q.m + 752  # query weights/boxes + the device query slot
     value = world * N * args.steps / (t_dev * 1e-3)
@@ -486,7 +505,7 @@ def main():
                 "d2h_bytes_per_step": d2h, "p50_ms": float(np.percentile(e2e_ms, 50)),
                 "p99_ms": float(np.percentile(e2e_ms, 99))},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "roofline": linear_roofline(N, q, lib, mean_enum, clk) if linear else {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": recorded_traffic() if args.workload == "c2_10m" and args.precision == "fp16" else None,
                      "kernel": "k_tc_head (enumeration, layers 2-3 on tcgen05)",

@@ -30,6 +30,13 @@ WORKLOADS = {
     # test-sized library for the linear (paper-exact, Eq. apex) head
     "t_linear": dict(sizes=[[40, 60], [25, 30, 9], [200]], d=64, dims=[64, 3], act="identity", n_obj=1, n_prop=2,
                      seed=11, k=40, precision="fp32"),
+    # 3-slot linear library the oracle enumerates in full (8e6 compounds, d = 1024)
+    "t_linear_3x200": dict(sizes=[[200, 200, 200]], d=1024, dims=[1024, 3], act="identity", n_obj=1, n_prop=2,
+                           seed=13, k=1000, precision="fp32"),
+    # the paper's worked example (Sec. 3.3): 1 reaction x 3 slots x 10^4 synthons = 10^12 compounds,
+    # d = 1024, with a linear head (1 objective + 2 properties)
+    "linear_1e12": dict(sizes=[[10000, 10000, 10000]], d=1024, dims=[1024, 3], act="identity", n_obj=1, n_prop=2,
+                        seed=17, k=1000, precision="fp32"),
 }
 
 

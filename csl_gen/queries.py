@@ -79,6 +79,11 @@ def query_single(name: str, spec: dict, stats: dict | None = None, precision: st
     if name == "t_linear":
         idx = np.array([1], dtype=np.int32)
         return Query(w, idx, np.array([quantile(stats, 1, 0.2)]), np.array([np.inf]), k, sub, prec)
+    if name in ("t_linear_3x200", "linear_1e12"):
+        # property 1 above its 0.2 quantile, property 2 below its 0.9 quantile
+        idx = np.array([1, 2], dtype=np.int32)
+        return Query(w, idx, np.array([quantile(stats, 1, 0.2), -np.inf]), np.array([np.inf, quantile(stats, 2, 0.9)]),
+                     k, sub, prec)
     raise KeyError(name)
 
 

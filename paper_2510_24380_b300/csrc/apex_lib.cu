@@ -62,6 +62,7 @@ cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const unsigned *n_
                             double *obj, double *outs, cudaStream_t st);
 cudaError_t apx_launch_count_alive(const RItem *R, unsigned n, unsigned *d_out, cudaStream_t st);
 cudaError_t apx_launch_wait_selftest(int *err, unsigned long long limit_ns, cudaStream_t st);
+cudaError_t apx_launch_linear(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int n_sm, cudaStream_t st);
 cudaError_t apx_launch_spec_ids(const int *rxn, const long long *pre, int n_sub, const long long *id_first,
                                 long long scope_n, unsigned long long seed, long long S, long long *ids, cudaStream_t st);
 cudaError_t apx_launch_spec_select(const float *out, long long S, const SpecArgs &a, float *keys, unsigned char *flag,
@@ -378,6 +379,8 @@ static void launch_enum(apex_library &L, const LaunchPlan &P, int precision) {
   const int fmt = tc_format(precision);
   if (fmt >= 0)  // every CTA takes an equal share of the launch's tiles
     CU(apx_launch_tc(P, L.T_, L.d_slots, L.d_err, grid_for(L, P.total_tiles), L.st, fmt));
+  else if (L.n_layers == 1 && P.mode == 0)  // linear head: per-synthon scalar sums (Eq. apex)
+    CU(apx_launch_linear(P, L.T_, L.d_slots, L.n_sm, L.st));
   else
     CU(apx_launch_fp32(P, L.T_, L.d_slots, nullptr, 0, nullptr, grid_for(L, P.total_items), L.st));
 }
@@ -1084,11 +1087,24 @@ static bool finalize(apex_library &L, QueryRec *q) {
   const QuerySlot S = *pS;
   const double t_f1 = now_ms();
   const bool spec_bad = std::isfinite(S.tau_spec) && (long long)S.n_sure_above_spec < q->k;
-  if (S.overflow || spec_bad) {
+  // An overflow is harmless when every dropped candidate's pass key lies below tau - 2 delta_f:
+  // every member of the exact top-k has a pass key at or above that (k surely feasible compounds
+  // reach tau), so none of them was dropped.
+  bool overflow = S.overflow != 0;
+  if (overflow && std::isfinite(S.tau)) {
+    const unsigned u = S.dropped_bits;
+    uint32_t fb = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    float dropped_max;
+    memcpy(&dropped_max, &fb, 4);
+    if (u != 0 && (double)dropped_max < (double)S.tau - 2.0 * pass_delta_f(L, q) * 1.0001) overflow = false;
+    TRACE("overflow q%lld: dropped max %g, tau %g -> %s", (long long)q->id, (double)dropped_max, (double)S.tau,
+          overflow ? "rerun" : "harmless");
+  }
+  if (overflow || spec_bad) {
     q->stats.n_restarts++;
     const double df = pass_delta_f(L, q);
     bool device_guess = false;
-    if (S.overflow) {
+    if (overflow) {
       // the band above the best valid threshold did not fit: more room, and restart from the
       // largest valid threshold found (k real, surely feasible compounds reach S.tau)
       q->cap = (unsigned)std::min<unsigned long long>((unsigned long long)q->cap * 4ull, 1ull << 30);
@@ -1269,7 +1285,15 @@ static void finish(apex_library &L, QueryRec *q, QState st, apex_status err, con
 // One step of the circular pass: a launch over the next chunk of items needed by any active
 // query (per precision), then the conditional select of the served queries.
 static void pass_step(apex_library &L) {
-  const long long chunk_compounds = L.chunk_compounds.load();
+  // a linear head costs ~100x less per compound than the MLP: larger launches. A query's first
+  // launches are small and grow 4x per launch (2^24, 2^26, ...): its admission threshold is only
+  // a sampled guess until the select after a launch raises it, and a large first launch at a loose
+  // threshold would overflow its candidate buffer.
+  int fresh = 1 << 20;
+  for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+    if (L.active[s] && L.active[s]->remaining > 0) fresh = std::min(fresh, L.active[s]->stats.n_launches);
+  const long long base_chunk = L.chunk_compounds.load() << (L.n_layers == 1 ? 8 : 0);
+  const long long chunk_compounds = fresh < 10 ? std::min(base_chunk, 1LL << (24 + 2 * fresh)) : base_chunk;
   // build one plan (items from the cursor) with per-precision query masks
   // indexed by pass precision (APEX_FP32, APEX_BF16, APEX_FP16, APEX_FP8; 2 unused)
   PlanBuilder pb[5] = {PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx)};

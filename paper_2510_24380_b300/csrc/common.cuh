@@ -74,6 +74,7 @@ struct QuerySlot {
   unsigned cap;
   unsigned count;     // appended entries (atomic)
   unsigned overflow;
+  unsigned dropped_bits;  // order-preserving bits of the largest key that did not fit (0 = none)
   unsigned n_sure_above_spec;
   float *keys;
   long long *ids;     // bit 62 set = not surely feasible
@@ -107,6 +108,14 @@ __device__ __forceinline__ unsigned apx_key_bits(float f) {
 }
 __device__ __forceinline__ float apx_bits_key(unsigned u) {
   return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// A candidate that did not fit its query's buffer: the buffer has overflowed, and the largest
+// dropped key is kept, so finalization can tell whether any dropped compound could still reach
+// the top-k (only then is the query rerun).
+__device__ __forceinline__ void apx_note_dropped(QuerySlot *Q, float key) {
+  atomicExch(&Q->overflow, 1u);
+  atomicMax(&Q->dropped_bits, apx_key_bits(key));
 }
 
 template <int N>
@@ -157,7 +166,7 @@ __device__ __forceinline__ void apx_apply_queries(QuerySlot *__restrict__ slots,
         Q->keys[pos] = f;
         Q->ids[pos] = id | (sure ? 0LL : APX_UNSURE_BIT);
       } else {
-        atomicExch(&Q->overflow, 1u);
+        apx_note_dropped(Q, f);
       }
     }
   }

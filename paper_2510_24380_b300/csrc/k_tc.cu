@@ -299,7 +299,7 @@ __device__ __forceinline__ void tc_apply_query_slow(const SlotParams &P, QuerySl
       Q->keys[pos] = f;
       Q->ids[pos] = id | (sure ? 0LL : APX_UNSURE_BIT);
     } else {
-      atomicExch(&Q->overflow, 1u);
+      apx_note_dropped(Q, f);
     }
   }
 }

@@ -264,3 +264,29 @@ def test_autotune_picks_from_its_candidates_and_results_stay_exact(ragged):
     for precision in ("fp16", "fp32"):
         q = csl_gen.query_single("t_ragged", spec, stats, precision=precision)
         check_topk(L.run(q), O.topk(lib, head, q), lib, head, q, rms)
+
+
+def test_linear_fast_path_three_slots_full_oracle():
+    """The paper's linear probe (Eq. apex): per-synthon scalar sums, 8e6 compounds enumerated in
+    full by the oracle; exact top-k under the boundary rule, single and batched queries."""
+    lib, head, spec = csl_gen.build_workload("t_linear_3x200")
+    L = apex.Library(lib, head, precisions=("fp32",))
+    try:
+        stats = csl_gen.load_stats("t_linear_3x200")
+        rms = output_rms(lib, head)
+        q = csl_gen.query_single("t_linear_3x200", spec, stats)
+        ref = O.topk(lib, head, q)
+        res = L.run(q)
+        check_topk(res, ref, lib, head, q, rms)
+        # same set; members closer than the FP32 margin may keep their FP32 order
+        assert set(res["ids"].tolist()) == set(ref.ids.tolist())
+        rng = np.random.default_rng(5)
+        qs = [csl_gen.random_query(rng, stats, 1, 2, k=int(k), precision="fp32", n_boxes=2) for k in (1, 100, 5000)]
+        alone = [L.run(x) for x in qs]
+        ids = [L.query(x) for x in qs]
+        for x, a, i in zip(qs, alone, ids):
+            m = L.fetch(i, x.k)
+            assert np.array_equal(a["ids"], m["ids"])
+            check_topk(m, O.topk(lib, head, x), lib, head, x, rms)
+    finally:
+        L.close()
