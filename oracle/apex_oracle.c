@@ -25,7 +25,8 @@
  * activation collapsing the head to one affine map; activation values at closed-form points;
  * a linear head reducing to Eq. apex (top-k of the X+Y sums, full sort); brute force on tiny
  * libraries; 1-slot reactions as a plain sort; permutation invariance; monotonicity in k;
- * the lexicographic-queue equivalence; id decode round trips.
+ * the lexicographic-queue equivalence; id decode round trips; the associative embeddings
+ * u = K_r v_s (Eq. assoc_embeds) against identity keys, basis values and linearity.
  */
 #include <math.h>
 #include <pthread.h>
@@ -234,6 +235,28 @@ int orc_linear_cost(int32_t n_reactions, const int32_t *n_slots, const int64_t *
   *total_flops = flops;
   *n_compounds = P.id_first[n_reactions];
   prep_free(&P);
+  return 0;
+}
+
+/* Associative embeddings of Eq. assoc_embeds: u_{r,s} = K_r v_s for every synthon row of every
+ * R-group slot r (slots in library order, rows slot-major). K: [n_slots_total x d x d_u], each
+ * K_r row-major (d rows of d_u); V: [rows x d_u]; U: [rows x d]. Every product is formed in
+ * double precision, K and V widened from float32, summed over the d_u terms in order. */
+int orc_assoc(int64_t n_slots_total, const int64_t *slot_sizes, int32_t d, int32_t d_u, const float *K,
+              const float *V, double *U) {
+  if (n_slots_total < 0 || d < 1 || d_u < 1) return -1;
+  int64_t row = 0;
+  for (int64_t r = 0; r < n_slots_total; ++r) {
+    const float *Kr = K + (size_t)r * d * d_u;
+    for (int64_t s = 0; s < slot_sizes[r]; ++s, ++row) {
+      const float *v = V + (size_t)row * d_u;
+      for (int32_t i = 0; i < d; ++i) {
+        double acc = 0.0;
+        for (int32_t j = 0; j < d_u; ++j) acc += (double)Kr[(size_t)i * d_u + j] * (double)v[j];
+        U[(size_t)row * d + i] = acc;
+      }
+    }
+  }
   return 0;
 }
 

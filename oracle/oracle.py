@@ -68,7 +68,7 @@ def _load():
         _dll = C.CDLL(build())
         _dll.orc_count.restype = C.c_int64
         _dll.orc_count.argtypes = [C.POINTER(_Lib)]
-        for name in ("orc_decode", "orc_head", "orc_score_ids", "orc_topk", "orc_linear_cost"):
+        for name in ("orc_decode", "orc_head", "orc_score_ids", "orc_topk", "orc_linear_cost", "orc_assoc"):
             getattr(_dll, name).restype = C.c_int
     return _dll
 
@@ -200,3 +200,20 @@ def topk(lib, head, query, threads: int = 0) -> TopK:
         raise ValueError(f"orc_topk failed ({rc})")
     n = n_out.value
     return TopK(ids[:n].copy(), scores[:n].copy(), outs[:n].copy(), n_feas.value, n_en.value)
+
+
+def assoc_embeddings(slot_sizes, K, V):
+    """Eq. assoc_embeds: u_{r,s} = K_r v_s for every synthon row of every slot (FP64).
+    slot_sizes: [n_slots_total]; K: float32 [n_slots_total, d, d_u]; V: float32 [rows, d_u] (rows
+    slot-major). Returns float64 [rows, d]."""
+    sizes = np.ascontiguousarray(slot_sizes, dtype=np.int64)
+    K = np.ascontiguousarray(K, dtype=np.float32)
+    V = np.ascontiguousarray(V, dtype=np.float32)
+    n_slots, d, d_u = K.shape
+    assert sizes.shape[0] == n_slots and V.shape == (int(sizes.sum()), d_u)
+    U = np.empty((V.shape[0], d), dtype=np.float64)
+    rc = _load().orc_assoc(C.c_int64(n_slots), _p(sizes, C.c_int64), C.c_int32(d), C.c_int32(d_u), _p(K, C.c_float),
+                           _p(V, C.c_float), _p(U, C.c_double))
+    if rc != 0:
+        raise ValueError("orc_assoc failed")
+    return U

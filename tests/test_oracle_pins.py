@@ -293,3 +293,29 @@ def test_decode_roundtrip_beyond_32_bits():
         assert off[tt] + v == i
     with pytest.raises(ValueError):
         O.decode(lib, np.array([N]))
+
+
+def test_assoc_embeddings_pins():
+    """Eq. assoc_embeds, u_{r,s} = K_r v_s, pinned by closed forms: identity keys return the
+    values; a basis value picks a column of the key; scaling and adding values act linearly;
+    each slot uses its own key."""
+    rng = np.random.default_rng(3)
+    sizes = np.array([3, 1, 4], np.int64)
+    d = d_u = 5
+    K = np.stack([np.eye(d, dtype=np.float32)] * 3)
+    V = rng.standard_normal((8, d_u)).astype(np.float32)
+    assert np.array_equal(O.assoc_embeddings(sizes, K, V), V.astype(np.float64))
+    d, d_u = 6, 4
+    K = rng.standard_normal((3, d, d_u)).astype(np.float32)
+    E = np.zeros((8, d_u), np.float32)
+    rows_slot = np.repeat(np.arange(3), sizes)
+    for row in range(8):
+        E[row, row % d_u] = 1.0
+    U = O.assoc_embeddings(sizes, K, E)
+    for row in range(8):  # u = column (row mod d_u) of the key of the row's own slot
+        assert np.array_equal(U[row], K[rows_slot[row]][:, row % d_u].astype(np.float64))
+    A = rng.integers(-3, 4, (8, d_u)).astype(np.float32)
+    B = rng.integers(-3, 4, (8, d_u)).astype(np.float32)
+    Ki = rng.integers(-3, 4, (3, d, d_u)).astype(np.float32)  # small integers: exact in FP64
+    ua, ub, uab = (O.assoc_embeddings(sizes, Ki, X) for X in (A, B, 2 * A + B))
+    assert np.array_equal(uab, 2 * ua + ub)
