@@ -228,6 +228,19 @@ apex_status apex_topk_select_noalloc(const float *keys, const int64_t *ids, int6
  * libraries, all entry points). Pure host counter. */
 apex_status apex_kernel_launches(int64_t *out);
 
+/* Associative embeddings, Eq. assoc_embeds: u_{r,s} = K_r v_s for every synthon row of every
+ * R-group slot r (Sec. 3.2: an R-group key matrix times a synthon value vector), the table U that
+ * apex_library_desc.U takes. Slots are in library order (reaction -> slot) and rows slot-major,
+ * as in apex_library_desc. K: [n_slots_total x d x d_u] float, each K_r row-major (d rows of d_u);
+ * V: [sum slot_sizes x d_u]; U (out): [sum slot_sizes x d]. FP32 on the CUDA cores, one pass.
+ * device_pointers = 1: K, V, U are device pointers (U may be handed to apex_load_library with
+ * U_on_device = 1); 0: host pointers, copied in and out. cuda_stream: cudaStream_t or NULL.
+ * Synchronizes the stream before returning. Errors: APEX_EINVAL (empty slot, d or d_u outside
+ * 1..4096, NULL pointer), APEX_ECUDA. */
+apex_status apex_associative_embeddings(int64_t n_slots_total, const int64_t *slot_sizes, int32_t d, int32_t d_u,
+                                        const float *K, const float *V, float *U, int32_t device_pointers,
+                                        void *cuda_stream);
+
 /* Autotuner. Picks the library's launch shapes by timing trial queries through the normal query
  * path (apex_query / apex_topk_fetch; no other query should be running): (1) the number of
  * compounds per enumeration launch of the circular pass (2^23 .. 2^27): smaller launches tighten

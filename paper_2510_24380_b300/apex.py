@@ -110,6 +110,8 @@ SYMBOLS = {
     "apex_kernel_launches": [C.POINTER(C.c_int64)],
     "apex_selftest_wait_timeout": [C.c_void_p, C.c_int32],
     "apex_autotune": [C.c_void_p, C.POINTER(AutotuneDesc), C.POINTER(AutotuneResult)],
+    "apex_associative_embeddings": [C.c_int64, C.POINTER(C.c_int64), C.c_int32, C.c_int32, C.POINTER(C.c_float),
+                                    C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32, C.c_void_p],
     "apex_last_error": [],
 }
 
@@ -128,6 +130,19 @@ def load(path: str = LIB_PATH):
         dll.apex_last_error.restype = C.c_char_p
         _dll = dll
     return _dll
+
+
+def associative_embeddings(slot_sizes, K, V, stream=None):
+    """Eq. assoc_embeds on the GPU: U[row] = K[slot(row)] @ V[row] (host numpy in and out)."""
+    sizes = np.ascontiguousarray(slot_sizes, np.int64)
+    K = np.ascontiguousarray(K, np.float32)
+    V = np.ascontiguousarray(V, np.float32)
+    n, d, d_u = K.shape
+    U = np.empty((V.shape[0], d), np.float32)
+    _check(load().apex_associative_embeddings(int(n), _p(sizes, C.c_int64), int(d), int(d_u), _p(K, C.c_float),
+                                              _p(V, C.c_float), _p(U, C.c_float), 0, C.c_void_p(stream or 0)),
+           "apex_associative_embeddings")
+    return U
 
 
 def last_error() -> str:

@@ -63,6 +63,10 @@ cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const unsigned *n_
 cudaError_t apx_launch_count_alive(const RItem *R, unsigned n, unsigned *d_out, cudaStream_t st);
 cudaError_t apx_launch_wait_selftest(int *err, unsigned long long limit_ns, cudaStream_t st);
 cudaError_t apx_launch_linear(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int n_sm, cudaStream_t st);
+cudaError_t apx_launch_assoc(const void *blocks, int n_blocks, int d, int d_u, const float *K, const float *V, float *U,
+                             cudaStream_t st);
+int apx_assoc_blocks(long long n_slots_total, const int64_t *slot_sizes, void *out, int capacity);
+size_t apx_assoc_block_bytes();
 cudaError_t apx_launch_spec_ids(const int *rxn, const long long *pre, int n_sub, const long long *id_first,
                                 long long scope_n, unsigned long long seed, long long S, long long *ids, cudaStream_t st);
 cudaError_t apx_launch_spec_select(const float *out, long long S, const SpecArgs &a, float *keys, unsigned char *flag,
@@ -1707,6 +1711,46 @@ extern "C" apex_status apex_autotune(apex_library *L, const apex_autotune_desc *
   L->fp32_id_tile = best_tile;
   out->chosen_chunk_compounds = best_chunk;
   out->chosen_fp32_id_tile = best_tile;
+  return APEX_OK;
+}
+
+extern "C" apex_status apex_associative_embeddings(int64_t n_slots_total, const int64_t *slot_sizes, int32_t d,
+                                                   int32_t d_u, const float *K, const float *V, float *U,
+                                                   int32_t device_pointers, void *cuda_stream) {
+  if (n_slots_total < 1 || !slot_sizes || !K || !V || !U) return fail(APEX_EINVAL, "bad arguments");
+  if (d < 1 || d > 4096 || d_u < 1 || d_u > 4096) return fail(APEX_EINVAL, "d / d_u outside 1..4096");
+  long long rows = 0;
+  for (int64_t s = 0; s < n_slots_total; ++s) {
+    if (slot_sizes[s] < 1) return fail(APEX_EINVAL, "slot %lld has no synthon", (long long)s);
+    rows += slot_sizes[s];
+  }
+  const int nb = apx_assoc_blocks(n_slots_total, slot_sizes, nullptr, 0);
+  if (nb <= 0 || (long long)nb * 64 < rows - 64 * n_slots_total) return fail(APEX_EINVAL, "too many rows");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  DevBuf B;
+  try {
+    std::vector<unsigned char> hb(apx_assoc_block_bytes() * nb);
+    apx_assoc_blocks(n_slots_total, slot_sizes, hb.data(), nb);
+    void *db = B.get(hb.size());
+    CU(cudaMemcpyAsync(db, hb.data(), hb.size(), cudaMemcpyHostToDevice, st));
+    const size_t kb = sizeof(float) * (size_t)n_slots_total * d * d_u, vb = sizeof(float) * (size_t)rows * d_u,
+                 ub = sizeof(float) * (size_t)rows * d;
+    const float *dK = K, *dV = V;
+    float *dU = U;
+    if (!device_pointers) {
+      float *k2 = (float *)B.get(kb), *v2 = (float *)B.get(vb);
+      CU(cudaMemcpyAsync(k2, K, kb, cudaMemcpyHostToDevice, st));
+      CU(cudaMemcpyAsync(v2, V, vb, cudaMemcpyHostToDevice, st));
+      dK = k2;
+      dV = v2;
+      dU = (float *)B.get(ub);
+    }
+    CU(apx_launch_assoc(db, nb, d, d_u, dK, dV, dU, st));
+    if (!device_pointers) CU(cudaMemcpyAsync(U, dU, ub, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+  } catch (const CudaFail &f) {
+    return fail(APEX_ECUDA, "associative embeddings: %s failed: %s", f.what, cudaGetErrorString(f.e));
+  }
   return APEX_OK;
 }
 

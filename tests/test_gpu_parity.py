@@ -290,3 +290,17 @@ def test_linear_fast_path_three_slots_full_oracle():
             check_topk(m, O.topk(lib, head, x), lib, head, x, rms)
     finally:
         L.close()
+
+
+def test_associative_embeddings_match_oracle():
+    """Eq. assoc_embeds on the GPU vs the FP64 oracle: slots of 1..200 rows (several 64-row
+    blocks, ragged tails), d = 130 (three column blocks), d_u = 70 (three K chunks)."""
+    rng = np.random.default_rng(21)
+    sizes = np.array([1, 200, 64, 65, 7], np.int64)
+    d, d_u = 130, 70
+    K = rng.standard_normal((sizes.shape[0], d, d_u)).astype(np.float32) / np.sqrt(d_u)
+    V = rng.standard_normal((int(sizes.sum()), d_u)).astype(np.float32)
+    got = apex.associative_embeddings(sizes, K, V).astype(np.float64)
+    ref = O.assoc_embeddings(sizes, K, V)
+    scale = np.sqrt((ref ** 2).mean())
+    assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), scale)) <= FP32_REL
