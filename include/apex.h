@@ -228,6 +228,17 @@ apex_status apex_topk_select_noalloc(const float *keys, const int64_t *ids, int6
  * libraries, all entry points). Pure host counter. */
 apex_status apex_kernel_launches(int64_t *out);
 
+/* Library files. apex_save_library writes everything a library was loaded from (reaction
+ * shapes, U read back from the device, the head, activation, objective/property split, the
+ * requested precisions, the seed) plus its calibrated margins to one binary file (little
+ * endian, "APEXLIB1" magic at both ends, host-native layout). apex_load_library_file rebuilds
+ * the library from such a file on `device`, with the given stream (NULL: own stream) and memory
+ * budget (0: none), restoring the margins instead of recalibrating. Errors: APEX_EINVAL (cannot
+ * open, wrong magic or version, truncated or invalid contents), plus apex_load_library's. */
+apex_status apex_save_library(const apex_library *lib, const char *path);
+apex_status apex_load_library_file(const char *path, int32_t device, void *cuda_stream, uint64_t device_mem_budget,
+                                   apex_library **out);
+
 /* Associative embeddings, Eq. assoc_embeds: u_{r,s} = K_r v_s for every synthon row of every
  * R-group slot r (Sec. 3.2: an R-group key matrix times a synthon value vector), the table U that
  * apex_library_desc.U takes. Slots are in library order (reaction -> slot) and rows slot-major,

@@ -110,6 +110,8 @@ SYMBOLS = {
     "apex_kernel_launches": [C.POINTER(C.c_int64)],
     "apex_selftest_wait_timeout": [C.c_void_p, C.c_int32],
     "apex_autotune": [C.c_void_p, C.POINTER(AutotuneDesc), C.POINTER(AutotuneResult)],
+    "apex_save_library": [C.c_void_p, C.c_char_p],
+    "apex_load_library_file": [C.c_char_p, C.c_int32, C.c_void_p, C.c_uint64, C.POINTER(C.c_void_p)],
     "apex_associative_embeddings": [C.c_int64, C.POINTER(C.c_int64), C.c_int32, C.c_int32, C.POINTER(C.c_float),
                                     C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32, C.c_void_p],
     "apex_last_error": [],
@@ -216,6 +218,23 @@ class Library:
         self.h = h
         self.n_outputs = int(head.dims[-1])
         self.n_objectives = int(head.n_objectives)
+
+    @classmethod
+    def from_file(cls, path: str, n_objectives: int, device: int = 0, stream=None, budget: int = 0) -> "Library":
+        """A library rebuilt from a file written by save() (apex_load_library_file)."""
+        self = cls.__new__(cls)
+        self._keep = []
+        h = C.c_void_p()
+        _check(load().apex_load_library_file(str(path).encode(), int(device), C.c_void_p(stream or 0), int(budget),
+                                             C.byref(h)), "apex_load_library_file")
+        self.h = h
+        self.n_outputs = int(self.info().n_outputs)
+        self.n_objectives = int(n_objectives)
+        return self
+
+    def save(self, path: str):
+        """Writes the library (shapes, U, head, margins) to a file (apex_save_library)."""
+        _check(load().apex_save_library(self.h, str(path).encode()), "apex_save_library")
 
     def close(self):
         if self.h:

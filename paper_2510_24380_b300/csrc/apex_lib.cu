@@ -172,6 +172,8 @@ struct apex_library {
   QuerySlot *d_slots = nullptr;
   int *d_err = nullptr;
   int *d_slot_list = nullptr;
+  std::vector<std::vector<float>> hW, hb;  // host copies of the head (for apex_save_library)
+  uint32_t precisions_requested = 1u;
   // calibration
   // admission margins: err16[0] BF16 pass, [1] FP16 pass, [2] FP8 pass; err32 FP32 pass / rescore
   double err16[3][APEX_MAX_OUTPUTS] = {{0}}, err32[APEX_MAX_OUTPUTS] = {0}, rms[APEX_MAX_OUTPUTS] = {0};
@@ -407,6 +409,19 @@ static void check_kernel_status(apex_library &L) {
 // FP32 gather kernel and the FP64 kernel score the same sampled ids. margin = factor * max
 // |difference| + a floor relative to the output RMS. The sample bounds the error empirically;
 // there is no closed-form bound through bf16 rounding and tanh.approx.
+static void upload_err32(apex_library &L) {
+  L.d_err32f = (float *)L.dalloc(sizeof(float) * APEX_MAX_OUTPUTS);
+  float e32[APEX_MAX_OUTPUTS] = {0};
+  for (int p = 0; p < L.n_out; ++p) e32[p] = (float)L.err32[p];
+  CU(cudaMemcpy(L.d_err32f, e32, sizeof(e32), cudaMemcpyHostToDevice));
+}
+
+// Margins saved with a library file (apex_save_library), restored instead of recalibrating.
+struct SavedCal {
+  int32_t n_calib;
+  double err32[APEX_MAX_OUTPUTS], err16[3][APEX_MAX_OUTPUTS], rms[APEX_MAX_OUTPUTS];
+};
+
 static void calibrate(apex_library &L) {
   const int no = L.n_out;
   std::mt19937_64 g(L.seed ^ 0x9e3779b97f4a7c15ull);
@@ -487,16 +502,19 @@ static void calibrate(apex_library &L) {
     }
     L.n_calib += (int)cnt_max;
   }
-  L.d_err32f = (float *)L.dalloc(sizeof(float) * APEX_MAX_OUTPUTS);
-  float e32[APEX_MAX_OUTPUTS] = {0};
-  for (int p = 0; p < no; ++p) e32[p] = (float)L.err32[p];
-  CU(cudaMemcpy(L.d_err32f, e32, sizeof(e32), cudaMemcpyHostToDevice));
+  upload_err32(L);
 }
 
 // ------------------------------------------------------------------ load
 static void worker_main(apex_library *L);
 
+static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, apex_library **out);
+
 extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_library **out) {
+  return load_impl(D, nullptr, out);
+}
+
+static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, apex_library **out) {
   if (!out) return fail(APEX_EINVAL, "out is NULL");
   *out = nullptr;
   if (!D) return fail(APEX_EINVAL, "desc is NULL");
@@ -565,6 +583,11 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
   L->precisions = 1u | (want_bf16 ? (1u << APEX_BF16) : 0u) | (want_fp16 ? (1u << APEX_FP16) : 0u) |
                   (want_fp8 ? (1u << APEX_FP8) : 0u);
   L->rng.seed(D->seed + 17);
+  L->precisions_requested = D->precisions;
+  for (int l = 0; l < D->n_layers; ++l) {
+    L->hW.emplace_back(D->W[l], D->W[l] + (size_t)D->dims[l + 1] * D->dims[l]);
+    L->hb.emplace_back(D->b[l], D->b[l] + D->dims[l + 1]);
+  }
 
   try {
     CU(cudaSetDevice(L->device));
@@ -709,7 +732,15 @@ extern "C" apex_status apex_load_library(const apex_library_desc *D, apex_librar
     CU(cudaEventCreate(&L->ev_b));
     L->pin(1 << 20);
     CU(cudaStreamSynchronize(L->st));
-    calibrate(*L);
+    if (cal) {
+      L->n_calib = cal->n_calib;
+      memcpy(L->err32, cal->err32, sizeof(L->err32));
+      memcpy(L->err16, cal->err16, sizeof(L->err16));
+      memcpy(L->rms, cal->rms, sizeof(L->rms));
+      upload_err32(*L);
+    } else {
+      calibrate(*L);
+    }
     CU(cudaStreamSynchronize(L->st));
   } catch (const CudaFail &f) {
     apex_status code = (f.e == cudaErrorMemoryAllocation) ? APEX_ENOMEM : APEX_ECUDA;
@@ -1752,6 +1783,125 @@ extern "C" apex_status apex_associative_embeddings(int64_t n_slots_total, const 
     return fail(APEX_ECUDA, "associative embeddings: %s failed: %s", f.what, cudaGetErrorString(f.e));
   }
   return APEX_OK;
+}
+
+// ------------------------------------------------------------------ library files
+static const char kMagic[8] = {'A', 'P', 'E', 'X', 'L', 'I', 'B', '1'};
+
+extern "C" apex_status apex_save_library(const apex_library *L, const char *path) {
+  if (!L || !path) return fail(APEX_EINVAL, "NULL argument");
+  std::vector<float> U((size_t)L->rows * L->d);
+  if (cudaMemcpy(U.data(), L->T_.U, sizeof(float) * U.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(APEX_ECUDA, "save: reading U back failed");
+  FILE *f = fopen(path, "wb");
+  if (!f) return fail(APEX_EINVAL, "save: cannot open %s", path);
+  bool ok = true;
+  auto put = [&](const void *p, size_t n) { ok = ok && fwrite(p, 1, n, f) == n; };
+  const int32_t hdr[8] = {1, L->T, L->d, L->n_layers, L->act, L->n_obj, L->n_prop, (int32_t)L->precisions_requested};
+  put(kMagic, 8);
+  put(hdr, sizeof(hdr));
+  put(&L->seed, sizeof(L->seed));
+  put(L->n_slots.data(), sizeof(int32_t) * L->T);
+  put(L->slot_sizes.data(), sizeof(int64_t) * L->slot_sizes.size());
+  put(L->dims, sizeof(int32_t) * (L->n_layers + 1));
+  for (int l = 0; l < L->n_layers; ++l) {
+    put(L->hW[l].data(), sizeof(float) * L->hW[l].size());
+    put(L->hb[l].data(), sizeof(float) * L->hb[l].size());
+  }
+  put(U.data(), sizeof(float) * U.size());
+  SavedCal c;
+  memset(&c, 0, sizeof(c));
+  c.n_calib = L->n_calib;
+  memcpy(c.err32, L->err32, sizeof(c.err32));
+  memcpy(c.err16, L->err16, sizeof(c.err16));
+  memcpy(c.rms, L->rms, sizeof(c.rms));
+  put(&c, sizeof(c));
+  put(kMagic, 8);  // trailer: a truncated file is rejected at load
+  ok = (fclose(f) == 0) && ok;
+  return ok ? APEX_OK : fail(APEX_EINVAL, "save: write to %s failed", path);
+}
+
+extern "C" apex_status apex_load_library_file(const char *path, int32_t device, void *cuda_stream,
+                                              uint64_t device_mem_budget, apex_library **out) {
+  if (!path || !out) return fail(APEX_EINVAL, "NULL argument");
+  *out = nullptr;
+  FILE *f = fopen(path, "rb");
+  if (!f) return fail(APEX_EINVAL, "load: cannot open %s", path);
+  bool ok = true;
+  auto get = [&](void *p, size_t n) { ok = ok && fread(p, 1, n, f) == n; };
+  char magic[8];
+  int32_t hdr[8];
+  uint64_t seed = 0;
+  get(magic, 8);
+  get(hdr, sizeof(hdr));
+  get(&seed, sizeof(seed));
+  if (!ok || memcmp(magic, kMagic, 8) != 0 || hdr[0] != 1) {
+    fclose(f);
+    return fail(APEX_EINVAL, "load: %s is not a library file of this version", path);
+  }
+  const int T = hdr[1], d = hdr[2], n_layers = hdr[3];
+  if (T < 1 || T > (1 << 24) || d < 1 || d > 1024 || n_layers < 1 || n_layers > 7) {
+    fclose(f);
+    return fail(APEX_EINVAL, "load: %s has an invalid header", path);
+  }
+  std::vector<int32_t> n_slots(T);
+  get(n_slots.data(), sizeof(int32_t) * T);
+  long long S = 0;
+  for (int t = 0; ok && t < T; ++t) {
+    if (n_slots[t] < 1 || n_slots[t] > APEX_MAX_SLOTS) ok = false;
+    S += n_slots[t];
+  }
+  std::vector<int64_t> sizes(ok ? S : 0);
+  get(sizes.data(), sizeof(int64_t) * sizes.size());
+  long long rows = 0;
+  for (long long j = 0; ok && j < S; ++j) {
+    if (sizes[j] < 1 || sizes[j] > (1LL << 40)) ok = false;
+    rows += sizes[j];
+  }
+  std::vector<int32_t> dims(n_layers + 1);
+  get(dims.data(), sizeof(int32_t) * dims.size());
+  for (int l = 0; ok && l <= n_layers; ++l)
+    if (dims[l] < 1 || dims[l] > 1024) ok = false;
+  std::vector<std::vector<float>> W, b;
+  for (int l = 0; ok && l < n_layers; ++l) {
+    W.emplace_back((size_t)dims[l + 1] * dims[l]);
+    b.emplace_back((size_t)dims[l + 1]);
+    get(W.back().data(), sizeof(float) * W.back().size());
+    get(b.back().data(), sizeof(float) * b.back().size());
+  }
+  std::vector<float> U(ok ? (size_t)rows * d : 0);
+  get(U.data(), sizeof(float) * U.size());
+  SavedCal cal;
+  get(&cal, sizeof(cal));
+  get(magic, 8);
+  fclose(f);
+  if (!ok || memcmp(magic, kMagic, 8) != 0) return fail(APEX_EINVAL, "load: %s is truncated or corrupt", path);
+  std::vector<const float *> Wp(n_layers), bp(n_layers);
+  for (int l = 0; l < n_layers; ++l) {
+    Wp[l] = W[l].data();
+    bp[l] = b[l].data();
+  }
+  apex_library_desc D;
+  memset(&D, 0, sizeof(D));
+  D.n_reactions = T;
+  D.n_slots = n_slots.data();
+  D.slot_sizes = sizes.data();
+  D.d = d;
+  D.U = U.data();
+  D.U_on_device = 0;
+  D.n_layers = n_layers;
+  D.dims = dims.data();
+  D.W = Wp.data();
+  D.b = bp.data();
+  D.activation = hdr[4];
+  D.n_objectives = hdr[5];
+  D.n_properties = hdr[6];
+  D.precisions = (uint32_t)hdr[7];
+  D.device_mem_budget = device_mem_budget;
+  D.cuda_stream = cuda_stream;
+  D.device = device;
+  D.seed = seed;
+  return load_impl(&D, &cal, out);
 }
 
 extern "C" apex_status apex_kernel_launches(int64_t *out) {

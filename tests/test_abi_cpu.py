@@ -109,3 +109,18 @@ def test_null_arguments(dll):
     assert dll.apex_free_library(None) == 0
     n = C.c_int64()
     assert dll.apex_topk_select(None, None, 10, 0, None, None, C.byref(n), None) == -1
+
+
+def test_library_file_rejected_before_the_gpu(dll, tmp_path):
+    """Files that are missing, not library files, or truncated are refused with APEX_EINVAL
+    before any device call."""
+    h = C.c_void_p()
+    assert dll.apex_load_library_file(str(tmp_path / "missing.apx").encode(), 0, None, 0, C.byref(h)) == -1
+    bad = tmp_path / "bad.apx"
+    bad.write_bytes(b"NOTAPEX!" + bytes(64))
+    assert dll.apex_load_library_file(str(bad).encode(), 0, None, 0, C.byref(h)) == -1
+    trunc = tmp_path / "trunc.apx"
+    trunc.write_bytes(b"APEXLIB1" + np.array([1, 1, 8, 1, 0, 1, 0, 1], np.int32).tobytes() + bytes(8)
+                      + np.array([2], np.int32).tobytes())  # stops inside the slot sizes
+    assert dll.apex_load_library_file(str(trunc).encode(), 0, None, 0, C.byref(h)) == -1
+    assert not h.value

@@ -304,3 +304,22 @@ def test_associative_embeddings_match_oracle():
     ref = O.assoc_embeddings(sizes, K, V)
     scale = np.sqrt((ref ** 2).mean())
     assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), scale)) <= FP32_REL
+
+
+def test_library_file_round_trip(ragged, tmp_path):
+    """save -> load from file: same margins (restored, not recalibrated) and identical results."""
+    lib, head, spec, L, rms = ragged
+    path = tmp_path / "t_ragged.apx"
+    L.save(path)
+    L2 = apex.Library.from_file(path, n_objectives=head.n_objectives)
+    try:
+        a, b = L.info(), L2.info()
+        assert a.n_compounds == b.n_compounds and a.n_calibration == b.n_calibration
+        assert list(a.err_fp16) == list(b.err_fp16) and list(a.err_fp32) == list(b.err_fp32)
+        stats = csl_gen.load_stats("t_ragged")
+        for precision in ("fp16", "fp32"):
+            q = csl_gen.query_single("t_ragged", spec, stats, precision=precision)
+            r1, r2 = L.run(q), L2.run(q)
+            assert np.array_equal(r1["ids"], r2["ids"]) and np.array_equal(r1["objective"], r2["objective"])
+    finally:
+        L2.close()
