@@ -61,6 +61,8 @@ cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const unsigned *n_
                             const float *out32, const double *out64_rows, long long *ids, int *rxn, long long *syn,
                             double *obj, double *outs, cudaStream_t st);
 cudaError_t apx_launch_count_alive(const RItem *R, unsigned n, unsigned *d_out, cudaStream_t st);
+cudaError_t apx_launch_mark_near(RItem *R, unsigned n, const float *ref, double tol, unsigned *n_marked,
+                                 cudaStream_t st);
 cudaError_t apx_launch_wait_selftest(int *err, unsigned long long limit_ns, cudaStream_t st);
 cudaError_t apx_launch_linear(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int n_sm, cudaStream_t st);
 cudaError_t apx_launch_assoc(const void *blocks, int n_blocks, int d, int d_u, const float *K, const float *V, float *U,
@@ -1268,8 +1270,7 @@ static bool finalize(apex_library &L, QueryRec *q) {
   };
   int rounds = 0;
   if (nr > 0) {
-    CU(apx_sort_r(R, nr, np, L.st));
-    CU(apx_launch_mark(R, nr, (unsigned)std::min<long long>(k + 1, nr), k, tol, d_cnt + 2, L.st));
+    CU(apx_launch_mark_near(R, nr, d_tau, tol, d_cnt + 2, L.st));  // band around the FP32 k-th score
     fp64_round();
     rounds = 1;
   }
@@ -1377,11 +1378,16 @@ static void pass_step(apex_library &L) {
   CU(cudaEventRecord(e0, L.st));
   for (int p = 0; p < 5; ++p) launch_enum(L, pb[p].P, p);
   CU(cudaEventRecord(e1, L.st));
-  if (!list.empty()) {
+  // select between launches only for queries with work left (a finished pass is selected by
+  // its finalization right after)
+  std::vector<int> cont;
+  for (int s : list)
+    if (L.active[s]->remaining > served[s]) cont.push_back(s);
+  if (!cont.empty()) {
     int *hl = (int *)L.pin(sizeof(int) * APEX_MAX_ACTIVE + 64);
-    memcpy(hl, list.data(), sizeof(int) * list.size());
-    CU(cudaMemcpyAsync(L.d_slot_list, hl, sizeof(int) * list.size(), cudaMemcpyHostToDevice, L.st));
-    CU(apx_launch_slot_select(L.d_slots, L.d_slot_list, (int)list.size(), 0, L.st));
+    memcpy(hl, cont.data(), sizeof(int) * cont.size());
+    CU(cudaMemcpyAsync(L.d_slot_list, hl, sizeof(int) * cont.size(), cudaMemcpyHostToDevice, L.st));
+    CU(apx_launch_slot_select(L.d_slots, L.d_slot_list, (int)cont.size(), 0, L.st));
   }
   check_kernel_status(L);
   float ms = 0;

@@ -24,7 +24,17 @@ struct SelSrc {
   }
 };
 
-__device__ bool block_kth_largest(const SelSrc &src, long long n, long long k, unsigned *out_bits,
+// Keys staged in shared memory as order-preserving bits, 0 = excluded (no finite key maps to 0).
+struct SelSmem {
+  const unsigned *bits;
+  __device__ __forceinline__ bool get(long long i, unsigned &b) const {
+    b = bits[i];
+    return b != 0u;
+  }
+};
+
+template <class Src>
+__device__ bool block_kth_largest(const Src &src, long long n, long long k, unsigned *out_bits,
                                   unsigned long long *out_included) {
   // Keys of a top-k buffer share their leading bits, so many lanes hit the same histogram bin:
   // lanes with equal digits are merged first (match.any) and one lane adds the group's count.
@@ -89,15 +99,26 @@ __device__ bool block_kth_largest(const SelSrc &src, long long n, long long k, u
 // fill; mode 1: always (end of the pass).
 // Raises tau (k-th largest sure key) and the admission threshold tau - 2 delta_f, then keeps
 // only entries at or above the admission threshold.
+#define SEL_SMEM_KEYS 49152  // buffers up to this size are selected from shared memory (192 KB)
 __global__ void __launch_bounds__(SEL_THREADS) k_slot_select(QuerySlot *slots, const int *slot_list, int mode) {
   QuerySlot *Q = slots + slot_list[blockIdx.x];
+  extern __shared__ unsigned sel_bits[];  // SEL_SMEM_KEYS entries
   __shared__ unsigned kept;
   __shared__ unsigned n_spec;
   const unsigned n = min(*((volatile unsigned *)&Q->count), Q->cap);
   if (mode == 0 && (long long)n <= Q->k) return;
-  SelSrc src{Q->keys, Q->ids, nullptr};
   unsigned bits;
-  if (block_kth_largest(src, n, Q->k, &bits, nullptr)) {
+  bool found;
+  if (n <= SEL_SMEM_KEYS) {
+    // one coalesced pass stages the keys (unsure entries excluded), the radix passes read shared memory
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x)
+      sel_bits[i] = (Q->ids[i] & APX_UNSURE_BIT) ? 0u : apx_key_bits(Q->keys[i]);
+    __syncthreads();
+    found = block_kth_largest(SelSmem{sel_bits}, n, Q->k, &bits, nullptr);
+  } else {
+    found = block_kth_largest(SelSrc{Q->keys, Q->ids, nullptr}, n, Q->k, &bits, nullptr);
+  }
+  if (found) {
     if (threadIdx.x == 0) {
       const float tau = apx_bits_key(bits);
       if (!(tau <= Q->tau)) Q->tau = tau;
@@ -150,7 +171,14 @@ __global__ void __launch_bounds__(SEL_THREADS) k_slot_select(QuerySlot *slots, c
 cudaError_t apx_launch_slot_select(QuerySlot *slots, const int *slot_list, int n_slots, int mode, cudaStream_t st) {
   if (n_slots <= 0) return cudaSuccess;
   apx_count_launch();
-  k_slot_select<<<n_slots, SEL_THREADS, 0, st>>>(slots, slot_list, mode);
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_slot_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(SEL_SMEM_KEYS * sizeof(unsigned)));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_slot_select<<<n_slots, SEL_THREADS, SEL_SMEM_KEYS * sizeof(unsigned), st>>>(slots, slot_list, mode);
   return cudaGetLastError();
 }
 
@@ -180,9 +208,16 @@ __global__ void k_eval32(EvalArgs a, long long n, float *f32, unsigned char *may
 // tau32 = k-th largest f32 among sure entries (one CTA)
 __global__ void __launch_bounds__(SEL_THREADS) k_kth(const float *keys, const unsigned char *flag, long long n, long long k,
                                                      float *out_tau, int *out_ok) {
-  SelSrc src{keys, nullptr, flag};
+  extern __shared__ unsigned sel_bits[];
   unsigned bits;
-  const bool ok = block_kth_largest(src, n, k, &bits, nullptr);
+  bool ok;
+  if (n <= SEL_SMEM_KEYS) {  // stage once, select from shared memory
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) sel_bits[i] = flag[i] ? apx_key_bits(keys[i]) : 0u;
+    __syncthreads();
+    ok = block_kth_largest(SelSmem{sel_bits}, n, k, &bits, nullptr);
+  } else {
+    ok = block_kth_largest(SelSrc{keys, nullptr, flag}, n, k, &bits, nullptr);
+  }
   if (threadIdx.x == 0) {
     *out_tau = ok ? apx_bits_key(bits) : -INFINITY;
     *out_ok = ok;
@@ -363,6 +398,30 @@ __global__ void k_mark_ties(RItem *R, unsigned n, unsigned kp1, long long k, dou
   }
 }
 
+// The same band marked around a reference score already on the device (the FP32 k-th score),
+// without sorting first: used before the first FP64 round; the band is re-marked around the
+// sorted k-th score after every round, so a differing reference only costs another round.
+__global__ void k_mark_near(RItem *R, unsigned n, const float *ref, double tol, unsigned *n_marked) {
+  const double sk = (double)*ref;
+  if (!(sk > -INFINITY)) return;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    RItem &it = R[i];
+    if (!it.alive || it.is64) continue;
+    if (fabs(it.s - sk) <= tol) {
+      it.need64 = 1;
+      atomicAdd(n_marked, 1u);
+    }
+  }
+}
+
+cudaError_t apx_launch_mark_near(RItem *R, unsigned n, const float *ref, double tol, unsigned *n_marked,
+                                 cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  apx_count_launch();
+  k_mark_near<<<std::min<unsigned>((n + 255) / 256, 148u * 16u), 256, 0, st>>>(R, n, ref, tol, n_marked);
+  return cudaGetLastError();
+}
+
 // Final rows: ids, reaction, synthons, objective, outputs (FP64 where rescored, else FP32)
 __global__ void k_emit(const RItem *R, unsigned n_max, const unsigned *n_alive, const __grid_constant__ DevTables T,
                        const float *out32, const double *out64_rows, long long *ids, int *rxn, long long *syn,
@@ -407,8 +466,15 @@ cudaError_t apx_launch_eval32(const EvalArgs &a, long long n, float *f32, unsign
 }
 cudaError_t apx_launch_kth(const float *keys, const unsigned char *flag, long long n, long long k, float *out_tau,
                            int *out_ok, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_kth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SEL_SMEM_KEYS * sizeof(unsigned)));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   apx_count_launch();
-  k_kth<<<1, SEL_THREADS, 0, st>>>(keys, flag, n, k, out_tau, out_ok);
+  k_kth<<<1, SEL_THREADS, SEL_SMEM_KEYS * sizeof(unsigned), st>>>(keys, flag, n, k, out_tau, out_ok);
   return cudaGetLastError();
 }
 cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
@@ -525,6 +591,8 @@ __global__ void k_spec_ids(const int *rxn, const long long *pre, int n_sub, cons
 // entries are feasible). One CTA.
 __global__ void __launch_bounds__(SEL_THREADS) k_spec_select(const float *out, long long S, const __grid_constant__ SpecArgs a,
                                                              float *keys, unsigned char *flag, QuerySlot *slot) {
+  __shared__ unsigned spec_bits[4096];  // the sample's objective bits, 0 = infeasible
+  const bool in_smem = S <= 4096;
   for (long long i = threadIdx.x; i < S; i += blockDim.x) {
     const float *o = out + i * a.n_out;
     bool ok = true;
@@ -534,13 +602,17 @@ __global__ void __launch_bounds__(SEL_THREADS) k_spec_select(const float *out, l
     }
     float f = 0.f;
     for (int j = 0; j < a.n_obj; ++j) f = fmaf(a.w[j], o[j], f);
-    keys[i] = f;
-    flag[i] = ok;
+    if (in_smem) {
+      spec_bits[i] = ok ? apx_key_bits(f) : 0u;
+    } else {
+      keys[i] = f;
+      flag[i] = ok;
+    }
   }
   __syncthreads();
-  SelSrc src{keys, nullptr, flag};
   unsigned bits;
-  const bool ok = block_kth_largest(src, S, a.rank, &bits, nullptr);
+  const bool ok = in_smem ? block_kth_largest(SelSmem{spec_bits}, S, a.rank, &bits, nullptr)
+                          : block_kth_largest(SelSrc{keys, nullptr, flag}, S, a.rank, &bits, nullptr);
   if (threadIdx.x == 0) {
     const float t = ok ? apx_bits_key(bits) : -INFINITY;
     slot->tau_spec = t;

@@ -322,27 +322,28 @@ __device__ __forceinline__ float tc_objective(const SlotParams &P, const float (
 // Sec. 3 / Eq. apex_topk per compound (one row per lane, all 32 lanes call it): objective,
 // admission threshold, widened box (admission) and shrunk box ("sure"), then a warp-aggregated
 // append to the query's candidate buffer in global memory. Parameters come from shared memory.
-// Objectives are formed for four queries at a time (independent dot products); the constraint
+// Objectives are formed for TC_QGROUP queries at a time (independent dot products); the constraint
 // boxes are read only for the queries that some lane of the warp admits on the objective. The
 // query slots of the run come as a list in shared memory (built once per run), so the per-tile
 // loop uses no bit scans (those would queue on the MUFU pipe behind the activations).
+#define TC_QGROUP 2  // queries per step of the epilogue loop (wider groups spill registers)
 template <int NW>
 __device__ __forceinline__ void tc_apply_queries_n(const SlotParams *qp, QuerySlot *slots, const unsigned char *qlist,
                                                    int nq, bool valid, long long id, const float (&o)[16]) {
-  for (int i = 0; i < nq; i += 4) {
-    int sq[4];
+  for (int i = 0; i < nq; i += TC_QGROUP) {
+    int sq[TC_QGROUP];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) sq[u] = i + u < nq ? (int)qlist[i + u] : -1;
-    float f[4];
-    bool pass[4];
+    for (int u = 0; u < TC_QGROUP; ++u) sq[u] = i + u < nq ? (int)qlist[i + u] : -1;
+    float f[TC_QGROUP];
+    bool pass[TC_QGROUP];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < TC_QGROUP; ++u) {
       const SlotParams &P = qp[sq[u] < 0 ? 0 : sq[u]];
       f[u] = tc_objective<NW>(P, o);
       pass[u] = valid && sq[u] >= 0 && f[u] >= P.admit;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < TC_QGROUP; ++u)
       if (__ballot_sync(0xffffffffu, pass[u]) != 0u) tc_apply_query_slow(qp[sq[u]], slots + sq[u], pass[u], f[u], id, o);
   }
 }
@@ -763,17 +764,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int buf = (int)(j & 1);
         if (!mbar_wait(bar(B_D3FULL(buf)), (uint32_t)((j >> 1) & 1), abort_flag, err)) { ok = false; break; }
         tc_fence_after();
-        // the four layer-3 partial sums, two chains (32 adjacent columns) per load
+        // the four layer-3 partial sums, one chain (16 columns) per load
         float out[16];
 #pragma unroll
         for (int n = 0; n < 16; ++n) out[n] = b3s[n];
 #pragma unroll
-        for (int c = 0; c < TC_L3_CHAINS; c += 2) {
-          uint32_t pa[32];
-          tmem_ld32(lane_base + (uint32_t)buf * 256u + tc_d3_col(c), pa);
-          tmem_wait_ld_dep(pa);
+        for (int c = 0; c < TC_L3_CHAINS; ++c) {
+          uint32_t pa[16];
+          tmem_ld16(lane_base + (uint32_t)buf * 256u + tc_d3_col(c), pa);
+          tmem_wait_ld_dep16(pa);
 #pragma unroll
-          for (int n = 0; n < 16; ++n) out[n] += __uint_as_float(pa[n]) + __uint_as_float(pa[16 + n]);
+          for (int n = 0; n < 16; ++n) out[n] += __uint_as_float(pa[n]);
         }
         tc_fence_before();
         __syncwarp();
