@@ -60,6 +60,27 @@ def peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
+# tanh.approx.f16x2 (one per SiLU pair) issues 7.3 times per clock per SM: CUDA-event timed over a
+# full-occupancy kernel of independent chains on a B300
+MUFU_SILU_PER_CLK_SM = 14.6
+
+
+def mufu_bound(N, head, enum_ms, clk):
+    """Second bound of the tensor-core kernel: the SiLU activations (one MUFU tanh per pair) of
+    every hidden layer, against the measured MUFU rate x 148 SMs x the sampled SM clock."""
+    if head.activation != "silu":
+        return None
+    acts = float(sum(head.dims[1:-1]))
+    mhz = (clk or {}).get("sm_mhz") or 2032.0
+    achieved = N * acts / (enum_ms * 1e-3) / (148 * mhz * 1e6)
+    t_mufu = N * acts / MUFU_SILU_PER_CLK_SM / 148 / (mhz * 1e6)
+    t_tensor = N / 128 * 2851 / 148 / (mhz * 1e6)  # 2,221 (layer 2) + ~630 (layer 3) cycles per 128-row tile
+    return {"bound": "xu", "unit": "activations/clk/SM", "achieved": achieved, "peak": MUFU_SILU_PER_CLK_SM,
+            "frac": achieved / MUFU_SILU_PER_CLK_SM, "activations_per_compound": acts,
+            "tensor_frac_cap": t_tensor / t_mufu if t_mufu > t_tensor else 1.0,
+            "peak_kind": "measured tanh.approx.f16x2 rate x 2 elements"}
+
+
 def linear_roofline(N, q, lib, enum_ms, clk):
     """Linear head (Eq. apex): the work per compound is the scalar sums and compares, ALU-bound:
     (1 + m)(n - 1) additions + 2m comparisons (m constraints, n slots), against the FP32/INT
@@ -510,7 +531,7 @@ def main():
                      "traffic": recorded_traffic() if args.workload == "c2_10m" and args.precision == "fp16" else None,
                      "kernel": "k_tc_head (enumeration, layers 2-3 on tcgen05)",
                      "flop_per_compound": FLOP_PER_COMPOUND, "peak_kind": f"{kind} bf16 burst (fp16 dense rate equals bf16)",
-                     "kernel_ms_per_step": mean_enum},
+                     "kernel_ms_per_step": mean_enum, "mufu": mufu_bound(N, head, mean_enum, clk)},
         "fp32_plain": {"value": fp32_rate, "unit": "compounds/s", "same_topk_set_as_tc_pass": bool(same) if fp32_rate else None},
         "query": {k: last_stats[k] for k in ("n_candidates", "n_rescored_fp64", "n_restarts", "n_launches",
                                              "gpu_ms", "enumerate_ms", "queue_ms", "latency_ms", "host_start_ms",
