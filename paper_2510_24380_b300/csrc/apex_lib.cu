@@ -205,7 +205,18 @@ struct apex_library {
   size_t arena_cap = 0, arena_off = 0;
   char *pinned = nullptr;
   size_t pinned_cap = 0;
-  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  // Enumeration launches whose completion the worker has not observed yet. The worker keeps at
+  // most one launch queued behind the running one (it plans launch i + 1 while launch i runs) and
+  // reads each launch's kernel status word and duration from a pinned copy when it retires.
+  static constexpr int kRing = 4;
+  struct InFlight {
+    int ring;
+    std::vector<std::pair<int, long long>> queries;  // (slot, query id) served by the launch
+  };
+  cudaEvent_t ev_l0[kRing] = {}, ev_l1[kRing] = {}, ev_ls[kRing] = {};
+  int *status_pin = nullptr;
+  std::deque<InFlight> inflight;
+  long long launch_seq = 0;
 
   void *dalloc(size_t n, bool count = true) {
     if (count && budget && bytes + query_bytes + n > budget) throw BudgetFail();
@@ -402,6 +413,42 @@ static void check_kernel_status(apex_library &L) {
     int z = 0;
     CU(cudaMemcpy(L.d_err, &z, sizeof(int), cudaMemcpyHostToDevice));
     throw CudaFail(cudaErrorLaunchTimeout, "device-side bounded wait expired", e);
+  }
+}
+
+// Retires the oldest enumeration launch in flight: waits for its status copy, raises a device-side
+// wait timeout as an error, and adds the launch's duration to the queries it served.
+static void retire_launch(apex_library &L) {
+  apex_library::InFlight f = std::move(L.inflight.front());
+  L.inflight.pop_front();
+  CU(cudaEventSynchronize(L.ev_ls[f.ring]));
+  if (L.status_pin[f.ring]) {
+    L.inflight.clear();
+    int z = 0;
+    CU(cudaStreamSynchronize(L.st));
+    CU(cudaMemcpy(L.d_err, &z, sizeof(int), cudaMemcpyHostToDevice));
+    throw CudaFail(cudaErrorLaunchTimeout, "device-side bounded wait expired", L.status_pin[f.ring]);
+  }
+  float ms = 0;
+  CU(cudaEventElapsedTime(&ms, L.ev_l0[f.ring], L.ev_l1[f.ring]));
+  for (const auto &sq : f.queries) {
+    QueryRec *q = L.active[sq.first];
+    if (q && q->id == sq.second) q->stats.enumerate_ms += ms;
+  }
+}
+static void retire_all(apex_library &L) {
+  while (!L.inflight.empty()) retire_launch(L);
+}
+// Idle worker: launches of queries that are gone; only a stale timeout status is cleared.
+static void retire_quietly(apex_library &L) {
+  if (L.inflight.empty()) return;
+  cudaStreamSynchronize(L.st);
+  bool stale = false;
+  for (const auto &f : L.inflight) stale = stale || L.status_pin[f.ring] != 0;
+  L.inflight.clear();
+  if (stale) {
+    int z = 0;
+    cudaMemcpy(L.d_err, &z, sizeof(int), cudaMemcpyHostToDevice);
   }
 }
 
@@ -730,8 +777,12 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
     L->d_err = (int *)L->dalloc(sizeof(int));
     CU(cudaMemset(L->d_err, 0, sizeof(int)));
     L->d_slot_list = (int *)L->dalloc(sizeof(int) * APEX_MAX_ACTIVE);
-    CU(cudaEventCreate(&L->ev_a));
-    CU(cudaEventCreate(&L->ev_b));
+    for (int i = 0; i < apex_library::kRing; ++i) {
+      CU(cudaEventCreate(&L->ev_l0[i]));
+      CU(cudaEventCreate(&L->ev_l1[i]));
+      CU(cudaEventCreateWithFlags(&L->ev_ls[i], cudaEventDisableTiming));
+    }
+    CU(cudaMallocHost(&L->status_pin, sizeof(int) * apex_library::kRing));
     L->pin(1 << 20);
     CU(cudaStreamSynchronize(L->st));
     if (cal) {
@@ -785,8 +836,12 @@ extern "C" apex_status apex_free_library(apex_library *L) {
     }
   if (L->arena) cudaFree(L->arena);
   if (L->pinned) cudaFreeHost(L->pinned);
-  if (L->ev_a) cudaEventDestroy(L->ev_a);
-  if (L->ev_b) cudaEventDestroy(L->ev_b);
+  for (int i = 0; i < apex_library::kRing; ++i) {
+    if (L->ev_l0[i]) cudaEventDestroy(L->ev_l0[i]);
+    if (L->ev_l1[i]) cudaEventDestroy(L->ev_l1[i]);
+    if (L->ev_ls[i]) cudaEventDestroy(L->ev_ls[i]);
+  }
+  if (L->status_pin) cudaFreeHost(L->status_pin);
   L->release_all();
   if (L->own_stream) cudaStreamDestroy(L->st);
   delete L;
@@ -1121,6 +1176,7 @@ static bool finalize(apex_library &L, QueryRec *q) {
   QuerySlot *pS = (QuerySlot *)((char *)L.pinned + 64);
   CU(cudaMemcpyAsync(pS, L.d_slots + sl, sizeof(QuerySlot), cudaMemcpyDeviceToHost, L.st));
   CU(cudaStreamSynchronize(L.st));
+  retire_all(L);  // status of the pass's launches (all complete now)
   const QuerySlot S = *pS;
   const double t_f1 = now_ms();
   const bool spec_bad = std::isfinite(S.tau_spec) && (long long)S.n_sure_above_spec < q->k;
@@ -1374,10 +1430,10 @@ static void pass_step(apex_library &L) {
     QueryRec *q = L.active[s];
     if (q->stats.n_launches == 0 && q->stats.n_restarts == 0) CU(cudaEventRecord(q->ev0, L.st));
   }
-  cudaEvent_t e0 = L.ev_a, e1 = L.ev_b;
-  CU(cudaEventRecord(e0, L.st));
+  const int ring = (int)(L.launch_seq++ % apex_library::kRing);
+  CU(cudaEventRecord(L.ev_l0[ring], L.st));
   for (int p = 0; p < 5; ++p) launch_enum(L, pb[p].P, p);
-  CU(cudaEventRecord(e1, L.st));
+  CU(cudaEventRecord(L.ev_l1[ring], L.st));
   // select between launches only for queries with work left (a finished pass is selected by
   // its finalization right after)
   std::vector<int> cont;
@@ -1389,14 +1445,17 @@ static void pass_step(apex_library &L) {
     CU(cudaMemcpyAsync(L.d_slot_list, hl, sizeof(int) * cont.size(), cudaMemcpyHostToDevice, L.st));
     CU(apx_launch_slot_select(L.d_slots, L.d_slot_list, (int)cont.size(), 0, L.st));
   }
-  check_kernel_status(L);
-  float ms = 0;
-  CU(cudaEventElapsedTime(&ms, e0, e1));
+  // the kernel status word of this launch, read back without waiting for it
+  CU(cudaMemcpyAsync(L.status_pin + ring, L.d_err, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+  CU(cudaEventRecord(L.ev_ls[ring], L.st));
+  apex_library::InFlight f;
+  f.ring = ring;
+  for (int s : list) f.queries.emplace_back(s, L.active[s]->id);
+  L.inflight.push_back(std::move(f));
   for (int s : list) {
     QueryRec *q = L.active[s];
     q->remaining -= served[s];
     q->stats.n_launches++;
-    q->stats.enumerate_ms += ms;
     long long comp = 0;
     for (int p = 0; p < 5; ++p)
       for (int g = 0; g < pb[p].P.n_seg; ++g)
@@ -1406,6 +1465,7 @@ static void pass_step(apex_library &L) {
         }
     q->stats.n_scored += comp;
   }
+  while (L.inflight.size() > 1) retire_launch(L);  // the GPU keeps this launch queued
 }
 
 static void worker_main(apex_library *Lp) {
@@ -1460,6 +1520,7 @@ static void worker_main(apex_library *Lp) {
       for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
         if (L.active[s]) any = true;
       if (!any) {
+        retire_quietly(L);
         L.cv.wait_for(lk, std::chrono::milliseconds(20));
         continue;
       }
@@ -1500,6 +1561,8 @@ static void worker_main(apex_library *Lp) {
         }
       }
     } catch (const CudaFail &f) {
+      L.inflight.clear();
+      cudaStreamSynchronize(L.st);
       std::lock_guard<std::mutex> g(L.mu);
       const apex_status code = (f.e == cudaErrorLaunchTimeout) ? APEX_ETIMEDOUT : APEX_ECUDA;
       char buf[256];
@@ -1510,6 +1573,7 @@ static void worker_main(apex_library *Lp) {
     }
   }
   // shutdown: everything still pending is cancelled
+  retire_quietly(L);
   std::lock_guard<std::mutex> g(L.mu);
   for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
     if (L.active[s]) finish(L, L.active[s], Q_CANCELED, APEX_ECANCELED, "library freed");

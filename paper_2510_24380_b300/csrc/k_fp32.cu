@@ -117,24 +117,40 @@ __device__ void f32_build_layer1(F32Smem<TM> &S, const DevTables &T, int mode, c
   }
 }
 
+// acc = a * b + acc on two FP32 lanes at once (fma.rn.f32x2: each lane is an ordinary
+// round-to-nearest fused multiply-add, so results equal two fmaf calls)
+__device__ __forceinline__ void ffma2(float &c0, float &c1, float a0, float a1, float b0, float b1) {
+  asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%0, %1};\n"
+      " fma.rn.f32x2 rc, ra, rb, rc;\n mov.b64 {%0, %1}, rc;\n}"
+      : "+f"(c0), "+f"(c1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
 // out = act(W^T-chunked GEMM of AT) for layer l (1-based index into dims: K = dims[l], N = dims[l+1]).
-// Thread (rg, cg) owns RPT = TM / 16 rows and the 16 columns 64 jq + 4 cg + e. The next W^T chunk
-// is fetched into registers before the current chunk is consumed and stored to shared memory
-// after it, so its global-load latency overlaps the FMAs.
+// Thread (rg, cg) owns 8 rows (rg) and CPT columns 4 CG jq + 4 cg + e (CG = 256 / CPT column
+// groups; 16-byte conflict-free reads of W^T, broadcast reads of AT), two rows per packed FMA.
+// CPT = 16 for 128-row tiles, 4 for 32-row tiles. Column groups past N are skipped. The next W^T
+// chunk is fetched into registers before the current chunk is consumed and stored to shared
+// memory after it, so its global-load latency overlaps the FMAs.
 template <int TM>
 __device__ void f32_layer(F32Smem<TM> &S, const DevTables &T, int l) {
-  constexpr int RPT = TM / 16;
+  constexpr int RPT = 8;
+  constexpr int RG = TM / RPT;                    // row groups: 16 (TM 128) or 4 (TM 32)
+  constexpr int CG = APX_SIMT_THREADS / RG;       // column groups: 16 or 64
+  constexpr int CPT = 256 / CG;                   // columns per thread: 16 or 4
+  constexpr int JQ = CPT / 4;
   const int K = T.dims[l], N = T.dims[l + 1];
   const float *WT = T.WT[l];
   const float *B = T.B[l];
   const bool last = (l == T.n_layers - 1);
   const int t = threadIdx.x;
-  const int rg = t >> 4, cg = t & 15;
-  float acc[RPT][16];
+  const int rg = t / CG, cg = t % CG;
+  const int jq_n = min(JQ, (N + 4 * CG - 1) / (4 * CG));  // column groups that hold outputs
+  float acc[RPT][CPT];
 #pragma unroll
   for (int i = 0; i < RPT; ++i)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
   const int nk = (K + F32_KC - 1) / F32_KC;
   float pre[F32_KC * 256 / APX_SIMT_THREADS];
   auto fetch = [&](int kc) {
@@ -161,38 +177,27 @@ __device__ void f32_layer(F32Smem<TM> &S, const DevTables &T, int l) {
     if (kc + 1 < nk) fetch(kc + 1);
     const int kmax = min(F32_KC, K - kc * F32_KC);
     for (int kk = 0; kk < kmax; ++kk) {
-      float a[RPT];
-      if (RPT == 8) {
-        const float4 a0 = *reinterpret_cast<const float4 *>(&S.AT[kc * F32_KC + kk][rg * RPT]);
-        const float4 a1 = *reinterpret_cast<const float4 *>(&S.AT[kc * F32_KC + kk][rg * RPT + 4]);
-        a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
-        a[4 % RPT] = a1.x; a[5 % RPT] = a1.y; a[6 % RPT] = a1.z; a[7 % RPT] = a1.w;
-      } else {
-        const float2 a0 = *reinterpret_cast<const float2 *>(&S.AT[kc * F32_KC + kk][rg * RPT]);
-        a[0] = a0.x;
-        a[1 % RPT] = a0.y;
+      const float4 a0 = *reinterpret_cast<const float4 *>(&S.AT[kc * F32_KC + kk][rg * RPT]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&S.AT[kc * F32_KC + kk][rg * RPT + 4]);
+      const float a[RPT] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+      for (int jq = 0; jq < JQ; ++jq) {
+        if (jq >= jq_n) break;  // uniform
+        const float4 w4 = *reinterpret_cast<const float4 *>(&S.Wc[buf][kk][4 * CG * jq + 4 * cg]);
+        const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+          for (int i = 0; i < RPT; i += 2) ffma2(acc[i][4 * jq + e], acc[i + 1][4 * jq + e], a[i], a[i + 1], w[e], w[e]);
       }
-      float w[16];
-#pragma unroll
-      for (int jq = 0; jq < 4; ++jq) {  // thread cg owns columns 64 jq + 4 cg + e (conflict-free 16-byte reads)
-        const float4 w4 = *reinterpret_cast<const float4 *>(&S.Wc[buf][kk][64 * jq + 4 * cg]);
-        w[4 * jq + 0] = w4.x;
-        w[4 * jq + 1] = w4.y;
-        w[4 * jq + 2] = w4.z;
-        w[4 * jq + 3] = w4.w;
-      }
-#pragma unroll
-      for (int i = 0; i < RPT; ++i)
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
     }
     if (kc + 1 < nk) store(buf ^ 1);  // the other buffer was last read before the previous barrier
     __syncthreads();
   }
   // every thread has finished reading AT: overwrite it with this layer's output
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int n = 64 * (j >> 2) + 4 * cg + (j & 3);
+  for (int j = 0; j < CPT; ++j) {
+    const int n = 4 * CG * (j >> 2) + 4 * cg + (j & 3);
     if (n < N) {
       const float bn = __ldg(B + n);
 #pragma unroll
@@ -200,6 +205,49 @@ __device__ void f32_layer(F32Smem<TM> &S, const DevTables &T, int l) {
         const float z = acc[i][j] + bn;
         S.AT[n][rg * RPT + i] = last ? z : f32_act(T.act, z);
       }
+    }
+  }
+  __syncthreads();
+}
+
+// Last layer with at most 16 outputs (the usual head: a few objectives and properties): the
+// threads split K instead of N (tile row r, K slice sl of APX_SIMT_THREADS / TM slices), W^T of the
+// layer is staged in shared memory (broadcast reads), and the slices' partial sums are added
+// through shared memory. Reuses the W^T chunk buffers: K x 16 weights, then the partial sums.
+template <int TM>
+__device__ void f32_last_small(F32Smem<TM> &S, const DevTables &T, int l) {
+  constexpr int NS = APX_SIMT_THREADS / TM;
+  const int K = T.dims[l], N = T.dims[l + 1];
+  float *w = &S.Wc[0][0][0];   // [K][16]
+  float *part = w + 256 * 16;  // [NS][16][TM]
+  for (int e = threadIdx.x; e < K * 16; e += APX_SIMT_THREADS) {
+    const int k = e >> 4, n = e & 15;
+    w[e] = n < N ? __ldg(T.WT[l] + (long long)k * N + n) : 0.f;
+  }
+  __syncthreads();
+  const int r = threadIdx.x % TM, sl = threadIdx.x / TM;
+  const int k0 = sl * K / NS, k1 = (sl + 1) * K / NS;
+  float acc[16];
+#pragma unroll
+  for (int n = 0; n < 16; ++n) acc[n] = 0.f;
+  for (int k = k0; k < k1; ++k) {
+    const float a = S.AT[k][r];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = *reinterpret_cast<const float4 *>(w + k * 16 + 4 * q);
+      ffma2(acc[4 * q], acc[4 * q + 1], a, a, v.x, v.y);
+      ffma2(acc[4 * q + 2], acc[4 * q + 3], a, a, v.z, v.w);
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < 16; ++n) part[(sl * 16 + n) * TM + r] = acc[n];
+  __syncthreads();
+  for (int e = threadIdx.x; e < 16 * TM; e += APX_SIMT_THREADS) {
+    const int n = e / TM, rr = e % TM;
+    if (n < N) {
+      float z = 0.f;
+      for (int s2 = 0; s2 < NS; ++s2) z += part[(s2 * 16 + n) * TM + rr];
+      S.AT[n][rr] = z + __ldg(T.B[l] + n);
     }
   }
   __syncthreads();
@@ -237,7 +285,12 @@ __global__ void __launch_bounds__(APX_SIMT_THREADS, 1)
     for (long long o = o_begin; o < o_end; ++o) {
       f32_build_layer1<TM>(S, T, mode, rp, q0, o, ids, it * TM, n_ids, row_valid, row_id);
       __syncthreads();
-      for (int l = 1; l < T.n_layers; ++l) f32_layer<TM>(S, T, l);
+      for (int l = 1; l < T.n_layers; ++l) {
+        if (l == T.n_layers - 1 && T.dims[l + 1] <= 16)
+          f32_last_small<TM>(S, T, l);
+        else
+          f32_layer<TM>(S, T, l);
+      }
       if (threadIdx.x < TM) {
         const int r = threadIdx.x;
         float ov[APEX_MAX_OUTPUTS];
