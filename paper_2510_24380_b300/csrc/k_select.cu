@@ -63,24 +63,46 @@ __device__ bool block_kth_largest(const Src &src, long long n, long long k, unsi
       if (use && (int)lane == __ffs(grp) - 1) atomicAdd(&hist[dig], (unsigned)__popc(grp));
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      if (pass == 3) {
-        unsigned long long t = 0;
-        for (int d = 0; d < 256; ++d) t += hist[d];
-        total_s = t;
+    if (threadIdx.x < 32) {
+      // the digit of the kk-th largest key: bins from the top, 8 per lane (lane l holds digits
+      // 255 - 8l down to 248 - 8l), a warp prefix sum, then the one lane whose range crosses kk
+      // walks its bins. No crossing (fewer than kk keys): digit 0, every key counted.
+      const unsigned long long kk = (unsigned long long)kk_s;
+      unsigned c[8];
+      unsigned long long own = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        c[j] = hist[255 - 8 * (int)lane - j];
+        own += c[j];
       }
-      const long long kk = kk_s;
-      unsigned long long cum = 0;
-      int dsel = 0;
-      for (int d = 255; d >= 0; --d) {
-        if (cum + hist[d] >= (unsigned long long)kk) {
-          dsel = d;
-          break;
+      unsigned long long incl = own;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
+        if ((int)lane >= off) incl += v;
+      }
+      const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+      unsigned long long cum = incl - own;
+      const unsigned hit = __ballot_sync(0xffffffffu, cum < kk && incl >= kk);
+      if (lane == 0 && pass == 3) total_s = total;
+      if (hit == 0u) {
+        if (lane == 0) {
+          kk_s = (long long)(kk - total);
+          prefix_s = prefix;
         }
-        cum += hist[d];
+      } else if ((int)lane == __ffs(hit) - 1) {
+        int dsel = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (cum + c[j] >= kk) {
+            dsel = 255 - 8 * (int)lane - j;
+            break;
+          }
+          cum += c[j];
+        }
+        kk_s = (long long)(kk - cum);
+        prefix_s = prefix | ((unsigned)dsel << (8 * pass));
       }
-      kk_s = kk - (long long)cum;
-      prefix_s = prefix | ((unsigned)dsel << (8 * pass));
     }
     __syncthreads();
     mask |= 255u << (8 * pass);
@@ -310,31 +332,52 @@ __global__ void k_bitonic_global(RItem *R, unsigned n, unsigned j, unsigned kk) 
 }
 
 #define BITONIC_SMEM 2048
-// every (kk, j) step with j < block inside blocks of `block` (power of two <= BITONIC_SMEM) elements
+// every (kk, j) step with j < block inside blocks of `block` (power of two <= BITONIC_SMEM) elements.
+// The network runs on the sort keys only, as separate arrays in shared memory (conflict-free
+// 8-byte accesses): key (s, id) with dead items mapped to (-inf, max id), which reproduces the
+// (alive, s desc, id asc) order, plus the item's position; the items are permuted once at the end.
 __global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned block, unsigned kk_from, unsigned kk_to) {
-  __shared__ RItem s[BITONIC_SMEM];
+  __shared__ double ks[BITONIC_SMEM];
+  __shared__ long long kid[BITONIC_SMEM];
+  __shared__ unsigned short ix[BITONIC_SMEM];
   const unsigned base = blockIdx.x * block;
-  for (unsigned t = threadIdx.x; t < block; t += blockDim.x) s[t] = R[base + t];
+  for (unsigned t = threadIdx.x; t < block; t += blockDim.x) {
+    const RItem it = R[base + t];
+    ks[t] = it.alive ? it.s : -INFINITY;
+    kid[t] = it.alive ? it.id : 0x7fffffffffffffffLL;
+    ix[t] = (unsigned short)t;
+  }
   __syncthreads();
   for (unsigned kk = kk_from; kk <= kk_to; kk <<= 1) {
     for (unsigned j = min(kk >> 1, block >> 1); j > 0; j >>= 1) {
-      for (unsigned t = threadIdx.x; t < block; t += blockDim.x) {
-        const unsigned l = t ^ j;
-        if (l > t) {
-          const unsigned gi = base + t;
-          const bool up = ((gi & kk) == 0);
-          RItem a = s[t], b = s[l];
-          const bool swap = up ? r_before(b, a) : r_before(a, b);
-          if (swap) {
-            s[t] = b;
-            s[l] = a;
-          }
+      for (unsigned h = threadIdx.x; h < (block >> 1); h += blockDim.x) {
+        const unsigned t = ((h & ~(j - 1)) << 1) | (h & (j - 1));  // the pair (t, t + j)
+        const unsigned l = t + j;
+        const bool up = (((base + t) & kk) == 0);
+        const double sa = ks[t], sb = ks[l];
+        const long long ia = kid[t], ib = kid[l];
+        const bool b_first = (sb > sa) || (sb == sa && ib < ia);
+        const bool a_first = (sa > sb) || (sa == sb && ia < ib);
+        if (up ? b_first : a_first) {
+          ks[t] = sb;
+          ks[l] = sa;
+          kid[t] = ib;
+          kid[l] = ia;
+          const unsigned short x = ix[t];
+          ix[t] = ix[l];
+          ix[l] = x;
         }
       }
       __syncthreads();
     }
   }
-  for (unsigned t = threadIdx.x; t < block; t += blockDim.x) R[base + t] = s[t];
+  // permute the items: read every source first, then write
+  RItem mine[BITONIC_SMEM / 1024];
+  unsigned c = 0;
+  for (unsigned t = threadIdx.x; t < block; t += blockDim.x) mine[c++] = R[base + ix[t]];
+  __syncthreads();
+  c = 0;
+  for (unsigned t = threadIdx.x; t < block; t += blockDim.x) R[base + t] = mine[c++];
 }
 
 __global__ void k_pad_r(RItem *R, unsigned from, unsigned to) {
