@@ -54,9 +54,10 @@ cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *po
 cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, const unsigned *n64_dev,
                                int n_out, const QuerySlot *Q, const double *lo, const double *hi, double *out_rows,
                                cudaStream_t st);
-cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st);
+cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st, const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_mark(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked,
-                            cudaStream_t st);
+                            cudaStream_t st, const unsigned *n_used);
+cudaError_t apx_launch_pad_r_dev(RItem *R, const unsigned *n_used, unsigned to, cudaStream_t st);
 cudaError_t apx_launch_emit(const RItem *R, unsigned n_final, const unsigned *n_alive, const DevTables &T,
                             const float *out32, const double *out64_rows, long long *ids, int *rxn, long long *syn,
                             double *obj, double *outs, cudaStream_t st);
@@ -1270,18 +1271,18 @@ static bool finalize(apex_library &L, QueryRec *q) {
   unsigned *d_cnt = (unsigned *)B.get(sizeof(unsigned) * 8);
   CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned) * 8, L.st));
   CU(apx_launch_build_r(nc, q->ids, f32, maybe, sure, d_tau, (float)(2.0 * e32f * 1.0001), R, d_cnt, L.st));
-  unsigned *pin_u = (unsigned *)L.pin(64);
-  CU(cudaMemcpyAsync(pin_u, d_cnt, sizeof(unsigned), cudaMemcpyDeviceToHost, L.st));
-  CU(cudaStreamSynchronize(L.st));
-  const unsigned nr = *pin_u;
+  // |R| stays on the device: R is padded to n_pow2 with dead items from the device count and
+  // every later kernel covers n_pow2 entries (dead ones are skipped), with no host round trip
+  CU(apx_launch_pad_r_dev(R, d_cnt, n_pow2, L.st));
+  const unsigned nr = nc > 0 ? n_pow2 : 0;  // entries of R the kernels cover
+  const unsigned nc1 = (unsigned)std::max<long long>(nc, 1);
   const double t_f3 = now_ms();
   const double t_f2 = t_f3;
-  unsigned np = 1;
-  while (np < std::max(nr, 2u)) np <<= 1;
-  double *out64 = (double *)B.get(sizeof(double) * std::max<long long>(nc, 1) * no);
-  long long *ids64 = (long long *)B.get(sizeof(long long) * std::max(nr, 1u));
-  int *pos64 = (int *)B.get(sizeof(int) * std::max(nr, 1u));
-  double *o64 = (double *)B.get(sizeof(double) * std::max(nr, 1u) * no);
+  const unsigned np = n_pow2;
+  double *out64 = (double *)B.get(sizeof(double) * nc1 * no);
+  long long *ids64 = (long long *)B.get(sizeof(long long) * nc1);  // FP64 batches: at most |R| <= nc
+  int *pos64 = (int *)B.get(sizeof(int) * nc1);
+  double *o64 = (double *)B.get(sizeof(double) * nc1 * no);
   const double tol = 2.0 * e32f * 1.0001 + 1e-300;
   // FP64 rounds: rescore what is pending (near a box bound, or in the boundary band of the k-th
   // score), re-sort, re-mark the band. The band is marked once before the first round, so one
@@ -1291,13 +1292,13 @@ static bool finalize(apex_library &L, QueryRec *q) {
   auto fp64_round = [&]() {
     CU(cudaMemsetAsync(d_cnt + 1, 0, sizeof(unsigned) * 2, L.st));
     CU(apx_launch_collect64(R, nr, ids64, pos64, d_cnt + 1, L.st));
-    CU(apx_launch_fp64(L.T_, ids64, nr, o64, L.st, d_cnt + 1));
-    CU(apx_launch_apply64(R, pos64, o64, nr, d_cnt + 1, no, L.d_slots + sl, dlo, dhi, out64, L.st));
-    CU(apx_sort_r(R, nr, np, L.st));
-    CU(apx_launch_mark(R, nr, (unsigned)std::min<long long>(k + 1, nr), k, tol, d_cnt + 2, L.st));  // boundary band
+    CU(apx_launch_fp64(L.T_, ids64, nc1, o64, L.st, d_cnt + 1));
+    CU(apx_launch_apply64(R, pos64, o64, nc1, d_cnt + 1, no, L.d_slots + sl, dlo, dhi, out64, L.st));
+    CU(apx_sort_r(R, np, np, L.st, d_cnt));
+    CU(apx_launch_mark(R, nr, (unsigned)std::min<long long>(k + 1, nr), k, tol, d_cnt + 2, L.st, d_cnt));  // boundary band
   };
   // final rows: min(k, alive) of them, emitted on the device from the device count
-  const unsigned n_rows = (unsigned)std::min<long long>(k, nr);
+  const unsigned n_rows = (unsigned)std::min<long long>(k, nc);
   long long *e_ids = nullptr;
   int *e_rxn = nullptr;
   long long *e_syn = nullptr;
@@ -1354,7 +1355,7 @@ static bool finalize(apex_library &L, QueryRec *q) {
   }
   q->stats.n_feasible_lower = nf;
   TRACE("finalize q%lld: nc %lld nr %u rounds %d | select+read %.3f, rescore32+build_r %.3f, fp64 rounds+emit %.3f ms",
-        (long long)q->id, nc, nr, rounds, t_f1 - t_f0, t_f3 - t_f1, t_f4 - t_f2);
+        (long long)q->id, nc, nc > 0 ? h_cnt[0] : 0u, rounds, t_f1 - t_f0, t_f3 - t_f1, t_f4 - t_f2);
   return true;
 }
 

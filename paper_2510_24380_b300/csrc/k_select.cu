@@ -336,10 +336,19 @@ __global__ void k_bitonic_global(RItem *R, unsigned n, unsigned j, unsigned kk) 
 // The network runs on the sort keys only, as separate arrays in shared memory (conflict-free
 // 8-byte accesses): key (s, id) with dead items mapped to (-inf, max id), which reproduces the
 // (alive, s desc, id asc) order, plus the item's position; the items are permuted once at the end.
-__global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned block, unsigned kk_from, unsigned kk_to) {
+// n_used (optional, one block only): sort just the smallest power of two holding the *n_used
+// leading entries (the rest is dead padding, already in its place at the end).
+__global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned block, unsigned kk_from, unsigned kk_to,
+                                                         const unsigned *n_used) {
   __shared__ double ks[BITONIC_SMEM];
   __shared__ long long kid[BITONIC_SMEM];
   __shared__ unsigned short ix[BITONIC_SMEM];
+  if (n_used) {
+    unsigned p2 = 2;
+    while (p2 < *n_used && p2 < block) p2 <<= 1;
+    block = p2;
+    kk_to = min(kk_to, p2);
+  }
   const unsigned base = blockIdx.x * block;
   for (unsigned t = threadIdx.x; t < block; t += blockDim.x) {
     const RItem it = R[base + t];
@@ -394,8 +403,132 @@ __global__ void k_pad_r(RItem *R, unsigned from, unsigned to) {
   }
 }
 
+// One-block ordering of up to 2,048 items in registers: thread t holds elements t and t + 1024
+// (key (s, id), dead items mapped to (-inf, max id), and the item's position). Compare distances
+// below 32 exchange through warp shuffles, distance 1024 inside the thread, the others through
+// shared memory; the items are permuted once at the end. n_used (optional): only the smallest
+// power of two holding the *n_used leading entries is ordered (the rest is dead padding).
+__device__ __forceinline__ bool key_before(double sa, long long ia, double sb, long long ib) {
+  return sa > sb || (sa == sb && ia < ib);
+}
+__global__ void __launch_bounds__(1024) k_bitonic_reg(RItem *R, unsigned n, const unsigned *n_used) {
+  __shared__ double ks[BITONIC_SMEM];
+  __shared__ long long kid[BITONIC_SMEM];
+  __shared__ unsigned short kix[BITONIC_SMEM];
+  if (n_used) {
+    unsigned p2 = 2;
+    while (p2 < *n_used && p2 < n) p2 <<= 1;
+    n = p2;
+  }
+  const unsigned t = threadIdx.x;
+  double s[2];
+  long long id[2];
+  unsigned ix[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const unsigned e = t + 1024u * h;
+    s[h] = -INFINITY;
+    id[h] = 0x7fffffffffffffffLL;
+    ix[h] = e;
+    if (e < n) {
+      const RItem it = R[e];
+      if (it.alive) {
+        s[h] = it.s;
+        id[h] = it.id;
+      }
+    }
+  }
+  for (unsigned kk = 2; kk <= n; kk <<= 1) {
+    for (unsigned j = kk >> 1; j > 0; j >>= 1) {
+      if (j >= 32 && j < 1024) {  // partners in other warps: through shared memory
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const unsigned e = t + 1024u * h;
+          if (e < n) {
+            ks[e] = s[h];
+            kid[e] = id[h];
+            kix[e] = (unsigned short)ix[h];
+          }
+        }
+        __syncthreads();
+      }
+      const double s_old[2] = {s[0], s[1]};  // distance 1024 pairs a thread's two elements
+      const long long id_old[2] = {id[0], id[1]};
+      const unsigned ix_old[2] = {ix[0], ix[1]};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const unsigned e = t + 1024u * h;
+        double so;
+        long long io;
+        unsigned xo;
+        if (j < 32) {
+          so = __shfl_xor_sync(0xffffffffu, s[h], (int)j);
+          io = __shfl_xor_sync(0xffffffffu, id[h], (int)j);
+          xo = __shfl_xor_sync(0xffffffffu, ix[h], (int)j);
+        } else if (j == 1024) {
+          so = s_old[h ^ 1];
+          io = id_old[h ^ 1];
+          xo = ix_old[h ^ 1];
+        } else {
+          const unsigned pe = e ^ j;
+          so = pe < n ? ks[pe] : s[h];
+          io = pe < n ? kid[pe] : id[h];
+          xo = pe < n ? kix[pe] : ix[h];
+        }
+        if (e < n) {
+          const bool lower = (e & j) == 0, up = (e & kk) == 0;
+          const bool take =
+              (lower == up) ? key_before(so, io, s_old[h], id_old[h]) : key_before(s_old[h], id_old[h], so, io);
+          if (take) {
+            s[h] = so;
+            id[h] = io;
+            ix[h] = xo;
+          }
+        }
+      }
+    }
+  }
+  // permute the items: read every source first, then write
+  RItem mine[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const unsigned e = t + 1024u * h;
+    if (e < n) mine[h] = R[ix[h]];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const unsigned e = t + 1024u * h;
+    if (e < n) R[e] = mine[h];
+  }
+}
+
+// Pads R[*n_used, to) with dead items, the used count read on the device (no host round trip).
+__global__ void k_pad_r_dev(RItem *R, const unsigned *n_used, unsigned to) {
+  const unsigned from = *n_used;
+  for (unsigned i = from + blockIdx.x * blockDim.x + threadIdx.x; i < to; i += gridDim.x * blockDim.x) {
+    RItem it;
+    it.s = -INFINITY;
+    it.id = 0x3fffffffffffffffLL;
+    it.src = -1;
+    it.alive = 0;
+    it.is64 = 1;
+    it.need64 = 0;
+    it.pad = 0;
+    R[i] = it;
+  }
+}
+
+cudaError_t apx_launch_pad_r_dev(RItem *R, const unsigned *n_used, unsigned to, cudaStream_t st) {
+  if (to == 0) return cudaSuccess;
+  apx_count_launch();
+  k_pad_r_dev<<<std::min<unsigned>((to + 255) / 256, 148u * 4u), 256, 0, st>>>(R, n_used, to);
+  return cudaGetLastError();
+}
+
 // Sorts R[0, n_pow2) (n_pow2 a power of two) into (alive, s desc, id asc) order.
-cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st) {
+cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st, const unsigned *n_dev) {
   if (n_pow2 < 2) return cudaSuccess;
   if (n_used < n_pow2) {
     apx_count_launch();
@@ -403,19 +536,19 @@ cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t 
   }
   if (n_pow2 <= BITONIC_SMEM) {
     apx_count_launch();
-    k_bitonic_shared<<<1, 1024, 0, st>>>(R, n_pow2, 2, n_pow2);
+    k_bitonic_reg<<<1, 1024, 0, st>>>(R, n_pow2, n_dev);
     return cudaGetLastError();
   }
   const unsigned nb = n_pow2 / BITONIC_SMEM;
   apx_count_launch();
-  k_bitonic_shared<<<nb, 1024, 0, st>>>(R, BITONIC_SMEM, 2, BITONIC_SMEM);
+  k_bitonic_shared<<<nb, 1024, 0, st>>>(R, BITONIC_SMEM, 2, BITONIC_SMEM, nullptr);
   for (unsigned kk = BITONIC_SMEM * 2; kk <= n_pow2; kk <<= 1) {
     for (unsigned j = kk >> 1; j >= BITONIC_SMEM; j >>= 1) {
       apx_count_launch();
       k_bitonic_global<<<std::min<unsigned>(nb * 8, 148u * 16u), 256, 0, st>>>(R, n_pow2, j, kk);
     }
     apx_count_launch();
-    k_bitonic_shared<<<nb, 1024, 0, st>>>(R, BITONIC_SMEM, kk, kk);
+    k_bitonic_shared<<<nb, 1024, 0, st>>>(R, BITONIC_SMEM, kk, kk, nullptr);
   }
   return cudaGetLastError();
 }
@@ -423,11 +556,15 @@ cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t 
 // Marks for FP64 every alive, not-yet-FP64 item whose score is within tol of the k-th score (the
 // top-k boundary band, on either side of it): only those can change the returned set. Items
 // well inside keep their FP32 score; near-ties among them are ordered by it.
-__global__ void k_mark_ties(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked) {
+// n_used (optional, a device count <= n): entries of R that came from the candidates; the
+// rest is padding.
+__global__ void k_mark_ties(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked,
+                            const unsigned *n_used) {
   __shared__ double sk;
   if (threadIdx.x == 0) {
-    const unsigned kk = (unsigned)(k < (long long)n ? k : (long long)n) - 1u;
-    sk = (n > 0 && R[kk].alive) ? R[kk].s : -INFINITY;
+    const unsigned nu = n_used ? min(n, *n_used) : n;
+    const unsigned kk = (unsigned)(k < (long long)nu ? k : (long long)nu) - 1u;
+    sk = (nu > 0 && R[kk].alive) ? R[kk].s : -INFINITY;
   }
   __syncthreads();
   (void)kp1;
@@ -546,10 +683,11 @@ cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, 
   return cudaGetLastError();
 }
 cudaError_t apx_launch_mark(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked,
-                            cudaStream_t st) {
+                            cudaStream_t st, const unsigned *n_used) {
   if (n == 0) return cudaSuccess;
   apx_count_launch();
-  k_mark_ties<<<std::min<unsigned>((n + 255) / 256 + 1, 148u * 16u), 256, 0, st>>>(R, n, kp1, k, tol, n_marked);
+  k_mark_ties<<<std::min<unsigned>((n + 255) / 256 + 1, 148u * 16u), 256, 0, st>>>(R, n, kp1, k, tol, n_marked,
+                                                                                   n_used);
   return cudaGetLastError();
 }
 // rows emitted: min(n_final, *n_alive) (n_alive optional, a device count)

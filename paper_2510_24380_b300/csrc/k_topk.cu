@@ -134,7 +134,7 @@ __global__ void k_sel_write(const RItem *R, long long k, float *out_keys, long l
   }
 }
 
-cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st);
+cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st, const unsigned *n_dev = nullptr);
 
 // Runs the selection with caller-provided scratch (state + a RItem buffer of n_pow2 >= k entries).
 cudaError_t apx_topk_select_run(const float *keys, const long long *ids, long long n, long long k, float *out_keys,
