@@ -117,13 +117,20 @@ __device__ void f32_build_layer1(F32Smem<TM> &S, const DevTables &T, int mode, c
   }
 }
 
-// acc = a * b + acc on two FP32 lanes at once (fma.rn.f32x2: each lane is an ordinary
-// round-to-nearest fused multiply-add, so results equal two fmaf calls)
-__device__ __forceinline__ void ffma2(float &c0, float &c1, float a0, float a1, float b0, float b1) {
-  asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%0, %1};\n"
-      " fma.rn.f32x2 rc, ra, rb, rc;\n mov.b64 {%0, %1}, rc;\n}"
-      : "+f"(c0), "+f"(c1)
-      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+// Two FP32 lanes in one 64-bit register (lane 0 in the low half). fma.rn.f32x2: each lane is an
+// ordinary round-to-nearest fused multiply-add, so results equal two fmaf calls. Accumulators
+// stay packed for the whole layer; operands that are adjacent in shared memory load as pairs.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2dup(float v) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(f32x2 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ void ffma2(f32x2 &c, f32x2 a, f32x2 b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a), "l"(b));
 }
 
 // out = act(W^T-chunked GEMM of AT) for layer l (1-based index into dims: K = dims[l], N = dims[l+1]).
@@ -146,11 +153,11 @@ __device__ void f32_layer(F32Smem<TM> &S, const DevTables &T, int l) {
   const int t = threadIdx.x;
   const int rg = t / CG, cg = t % CG;
   const int jq_n = min(JQ, (N + 4 * CG - 1) / (4 * CG));  // column groups that hold outputs
-  float acc[RPT][CPT];
+  f32x2 acc[RPT / 2][CPT];  // rows (2i, 2i + 1) of column j
 #pragma unroll
-  for (int i = 0; i < RPT; ++i)
+  for (int i = 0; i < RPT / 2; ++i)
 #pragma unroll
-    for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < CPT; ++j) acc[i][j] = 0ull;
   const int nk = (K + F32_KC - 1) / F32_KC;
   float pre[F32_KC * 256 / APX_SIMT_THREADS];
   auto fetch = [&](int kc) {
@@ -177,18 +184,20 @@ __device__ void f32_layer(F32Smem<TM> &S, const DevTables &T, int l) {
     if (kc + 1 < nk) fetch(kc + 1);
     const int kmax = min(F32_KC, K - kc * F32_KC);
     for (int kk = 0; kk < kmax; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4 *>(&S.AT[kc * F32_KC + kk][rg * RPT]);
-      const float4 a1 = *reinterpret_cast<const float4 *>(&S.AT[kc * F32_KC + kk][rg * RPT + 4]);
-      const float a[RPT] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(&S.AT[kc * F32_KC + kk][rg * RPT]);
+      const ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(&S.AT[kc * F32_KC + kk][rg * RPT + 4]);
+      const f32x2 a[RPT / 2] = {a0.x, a0.y, a1.x, a1.y};
 #pragma unroll
       for (int jq = 0; jq < JQ; ++jq) {
         if (jq >= jq_n) break;  // uniform
         const float4 w4 = *reinterpret_cast<const float4 *>(&S.Wc[buf][kk][4 * CG * jq + 4 * cg]);
         const float w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
+        for (int e = 0; e < 4; ++e) {
+          const f32x2 wd = f2dup(w[e]);
 #pragma unroll
-          for (int i = 0; i < RPT; i += 2) ffma2(acc[i][4 * jq + e], acc[i + 1][4 * jq + e], a[i], a[i + 1], w[e], w[e]);
+          for (int i = 0; i < RPT / 2; ++i) ffma2(acc[i][4 * jq + e], a[i], wd);
+        }
       }
     }
     if (kc + 1 < nk) store(buf ^ 1);  // the other buffer was last read before the previous barrier
@@ -201,9 +210,13 @@ __device__ void f32_layer(F32Smem<TM> &S, const DevTables &T, int l) {
     if (n < N) {
       const float bn = __ldg(B + n);
 #pragma unroll
-      for (int i = 0; i < RPT; ++i) {
-        const float z = acc[i][j] + bn;
-        S.AT[n][rg * RPT + i] = last ? z : f32_act(T.act, z);
+      for (int i = 0; i < RPT / 2; ++i) {
+        float z0, z1;
+        f2unpack(acc[i][j], z0, z1);
+        z0 += bn;
+        z1 += bn;
+        S.AT[n][rg * RPT + 2 * i] = last ? z0 : f32_act(T.act, z0);
+        S.AT[n][rg * RPT + 2 * i + 1] = last ? z1 : f32_act(T.act, z1);
       }
     }
   }
@@ -227,20 +240,25 @@ __device__ void f32_last_small(F32Smem<TM> &S, const DevTables &T, int l) {
   __syncthreads();
   const int r = threadIdx.x % TM, sl = threadIdx.x / TM;
   const int k0 = sl * K / NS, k1 = (sl + 1) * K / NS;
-  float acc[16];
+  f32x2 acc[8];  // outputs (2m, 2m + 1)
 #pragma unroll
-  for (int n = 0; n < 16; ++n) acc[n] = 0.f;
+  for (int m = 0; m < 8; ++m) acc[m] = 0ull;
   for (int k = k0; k < k1; ++k) {
-    const float a = S.AT[k][r];
+    const f32x2 a = f2dup(S.AT[k][r]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float4 v = *reinterpret_cast<const float4 *>(w + k * 16 + 4 * q);
-      ffma2(acc[4 * q], acc[4 * q + 1], a, a, v.x, v.y);
-      ffma2(acc[4 * q + 2], acc[4 * q + 3], a, a, v.z, v.w);
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(w + k * 16 + 4 * q);
+      ffma2(acc[2 * q], a, v.x);
+      ffma2(acc[2 * q + 1], a, v.y);
     }
   }
 #pragma unroll
-  for (int n = 0; n < 16; ++n) part[(sl * 16 + n) * TM + r] = acc[n];
+  for (int m = 0; m < 8; ++m) {
+    float z0, z1;
+    f2unpack(acc[m], z0, z1);
+    part[(sl * 16 + 2 * m) * TM + r] = z0;
+    part[(sl * 16 + 2 * m + 1) * TM + r] = z1;
+  }
   __syncthreads();
   for (int e = threadIdx.x; e < 16 * TM; e += APX_SIMT_THREADS) {
     const int n = e / TM, rr = e % TM;

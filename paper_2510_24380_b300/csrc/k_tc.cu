@@ -53,7 +53,10 @@ struct SlotParams {
   float lo_s[16], hi_s[16];      // "sure" box (shrunk by the margin), per output
   float admit;
   unsigned cmask;
-  int n_obj, pad;
+  int n_obj;
+  unsigned cap;          // candidate buffer of the query (copied from its slot: no global loads
+  float *keys;           // on the append path)
+  long long *ids;
 };
 
 // Shared-memory map (offsets from a 1024-byte aligned base), per operand format FMT (0 = BF16,
@@ -78,7 +81,7 @@ struct TcL {
   static constexpr uint32_t QLIST = MISC + 64u;                  // per query warp: its run's query slots
   static constexpr uint32_t SMEM = QLIST + 4u * APEX_MAX_ACTIVE + 1024u;  // + alignment slack
 };
-static_assert(sizeof(SlotParams) == 336, "SlotParams layout");
+static_assert(sizeof(SlotParams) == 352, "SlotParams layout");
 static_assert(TcL<0>::SMEM <= 232448 && TcL<1>::SMEM <= 232448 && TcL<2>::SMEM <= 232448, "shared memory budget");
 static_assert(TcL<0>::A1 % 1024 == 0 && TcL<2>::A1 % 1024 == 0 && TcL<0>::QP % 16 == 0 && TcL<2>::QP % 16 == 0,
               "alignment");
@@ -285,19 +288,20 @@ __device__ __forceinline__ float2 unpack2(uint32_t w) {
 // append to the query's candidate buffer in global memory. Parameters come from shared memory.
 __device__ __forceinline__ void tc_apply_query_slow(const SlotParams &P, QuerySlot *Q, bool pass, float f, long long id,
                                                     const float (&o)[16]) {
-  bool sure = true;
   const unsigned cm = P.cmask;
 #pragma unroll
   for (int j = 0; j < 16; ++j)
-    if (cm & (1u << j)) {  // warp-uniform
-      pass = pass && (o[j] >= P.lo_w[j]) && (o[j] <= P.hi_w[j]);
-      sure = sure && (o[j] >= P.lo_s[j]) && (o[j] <= P.hi_s[j]);
-    }
+    if (cm & (1u << j)) pass = pass && (o[j] >= P.lo_w[j]) && (o[j] <= P.hi_w[j]);  // warp-uniform test
+  if (__ballot_sync(0xffffffffu, pass) == 0u) return;  // no lane inside the widened boxes
+  bool sure = true;
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if (cm & (1u << j)) sure = sure && (o[j] >= P.lo_s[j]) && (o[j] <= P.hi_s[j]);
   const unsigned pos = apx_warp_reserve(&Q->count, pass);
   if (pass) {
-    if (pos < Q->cap) {
-      Q->keys[pos] = f;
-      Q->ids[pos] = id | (sure ? 0LL : APX_UNSURE_BIT);
+    if (pos < P.cap) {
+      P.keys[pos] = f;
+      P.ids[pos] = id | (sure ? 0LL : APX_UNSURE_BIT);
     } else {
       apx_note_dropped(Q, f);
     }
@@ -452,6 +456,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (lane == 0) {
         P.admit = Q->admit;
         P.n_obj = Q->n_obj;
+        P.cap = Q->cap;
+        P.keys = Q->keys;
+        P.ids = Q->ids;
       }
     }
   }
