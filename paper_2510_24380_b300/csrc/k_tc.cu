@@ -352,15 +352,47 @@ __device__ __forceinline__ void tc_apply_queries_n(const SlotParams *qp, QuerySl
   }
 }
 
-__device__ __forceinline__ void tc_apply_queries(const SlotParams *qp, QuerySlot *slots, const unsigned char *qlist,
-                                                 int nq, bool valid, long long id, const float (&o)[16], int n_obj) {
-  if (n_obj <= 8)
-    tc_apply_queries_n<8>(qp, slots, qlist, nq, valid, id, o);
-  else
-    tc_apply_queries_n<16>(qp, slots, qlist, nq, valid, id, o);
+// Launches with at most TC_FEWQ queries: every objective first (branch-free, one admission bit
+// per query), one warp reduction, then the append path for the queries some lane admits. The
+// kernel is instantiated separately for this form, so its registers do not depend on the
+// many-query form's.
+#define TC_FEWQ 2
+template <int NW>
+__device__ __forceinline__ void tc_apply_queries_few(const SlotParams *qp, QuerySlot *slots, const unsigned char *qlist,
+                                                     int nq, bool valid, long long id, const float (&o)[16]) {
+  unsigned bits = 0u;
+  if (valid) {
+    for (int i = 0; i < nq; ++i) {
+      const SlotParams &P = qp[qlist[i]];
+      bits |= (unsigned)(tc_objective<NW>(P, o) >= P.admit) << i;
+    }
+  }
+  const unsigned any = __reduce_or_sync(0xffffffffu, bits);
+  for (int i = 0; i < nq; ++i)
+    if ((any >> i) & 1u) {  // warp-uniform
+      const int sq = qlist[i];
+      const SlotParams &P = qp[sq];
+      tc_apply_query_slow(P, slots + sq, ((bits >> i) & 1u) != 0u, tc_objective<NW>(P, o), id, o);
+    }
 }
 
-template <int ACT, int FMT>
+template <bool FEWQ>
+__device__ __forceinline__ void tc_apply_queries(const SlotParams *qp, QuerySlot *slots, const unsigned char *qlist,
+                                                 int nq, bool valid, long long id, const float (&o)[16], int n_obj) {
+  if (FEWQ) {
+    if (n_obj <= 8)
+      tc_apply_queries_few<8>(qp, slots, qlist, nq, valid, id, o);
+    else
+      tc_apply_queries_few<16>(qp, slots, qlist, nq, valid, id, o);
+  } else {
+    if (n_obj <= 8)
+      tc_apply_queries_n<8>(qp, slots, qlist, nq, valid, id, o);
+    else
+      tc_apply_queries_n<16>(qp, slots, qlist, nq, valid, id, o);
+  }
+}
+
+template <int ACT, int FMT, bool FEWQ>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_head(const __grid_constant__ LaunchPlan L, const __grid_constant__ DevTables T, QuerySlot *slots, int *err) {
   using LY = TcL<FMT>;
@@ -788,7 +820,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) mbar_arrive(bar(B_D2EMPTY(buf)));
         const long long id = id_row + o * ostride;
         if (L.mode == 0) {
-          tc_apply_queries(qp, slots, qlist, nq, valid, id, out, qp_n_obj);
+          tc_apply_queries<FEWQ>(qp, slots, qlist, nq, valid, id, out, qp_n_obj);
         } else if (L.mode == 1) {
           if (valid && id >= L.dump_base && id < L.dump_base + L.dump_n) {
 #pragma unroll
@@ -834,20 +866,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 size_t apx_tc_smem_bytes() { return TcL<1>::SMEM; }
 
-template <int ACT, int FMT>
-static cudaError_t tc_launch_one(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
-                                 cudaStream_t st) {
+template <int ACT, int FMT, bool FEWQ>
+static cudaError_t tc_launch_q(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
+                               cudaStream_t st) {
   static bool attr = false;  // per instantiation
   if (!attr) {
     const cudaError_t e =
-        cudaFuncSetAttribute(k_tc_head<ACT, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcL<FMT>::SMEM);
+        cudaFuncSetAttribute(k_tc_head<ACT, FMT, FEWQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcL<FMT>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   if (grid <= 0) return cudaSuccess;
   apx_count_launch();
-  k_tc_head<ACT, FMT><<<grid, TC_THREADS, TcL<FMT>::SMEM, st>>>(L, T, slots, err);
+  k_tc_head<ACT, FMT, FEWQ><<<grid, TC_THREADS, TcL<FMT>::SMEM, st>>>(L, T, slots, err);
   return cudaGetLastError();
+}
+template <int ACT, int FMT>
+static cudaError_t tc_launch_one(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
+                                 cudaStream_t st) {
+  if (__builtin_popcountll(L.qmask_all) <= TC_FEWQ) return tc_launch_q<ACT, FMT, true>(L, T, slots, err, grid, st);
+  return tc_launch_q<ACT, FMT, false>(L, T, slots, err, grid, st);
 }
 
 template <int FMT>
