@@ -403,107 +403,6 @@ __global__ void k_pad_r(RItem *R, unsigned from, unsigned to) {
   }
 }
 
-// One-block ordering of up to 2,048 items in registers: thread t holds elements t and t + 1024
-// (key (s, id), dead items mapped to (-inf, max id), and the item's position). Compare distances
-// below 32 exchange through warp shuffles, distance 1024 inside the thread, the others through
-// shared memory; the items are permuted once at the end. n_used (optional): only the smallest
-// power of two holding the *n_used leading entries is ordered (the rest is dead padding).
-__device__ __forceinline__ bool key_before(double sa, long long ia, double sb, long long ib) {
-  return sa > sb || (sa == sb && ia < ib);
-}
-__global__ void __launch_bounds__(1024) k_bitonic_reg(RItem *R, unsigned n, const unsigned *n_used) {
-  __shared__ double ks[BITONIC_SMEM];
-  __shared__ long long kid[BITONIC_SMEM];
-  __shared__ unsigned short kix[BITONIC_SMEM];
-  if (n_used) {
-    unsigned p2 = 2;
-    while (p2 < *n_used && p2 < n) p2 <<= 1;
-    n = p2;
-  }
-  const unsigned t = threadIdx.x;
-  double s[2];
-  long long id[2];
-  unsigned ix[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const unsigned e = t + 1024u * h;
-    s[h] = -INFINITY;
-    id[h] = 0x7fffffffffffffffLL;
-    ix[h] = e;
-    if (e < n) {
-      const RItem it = R[e];
-      if (it.alive) {
-        s[h] = it.s;
-        id[h] = it.id;
-      }
-    }
-  }
-  for (unsigned kk = 2; kk <= n; kk <<= 1) {
-    for (unsigned j = kk >> 1; j > 0; j >>= 1) {
-      if (j >= 32 && j < 1024) {  // partners in other warps: through shared memory
-        __syncthreads();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const unsigned e = t + 1024u * h;
-          if (e < n) {
-            ks[e] = s[h];
-            kid[e] = id[h];
-            kix[e] = (unsigned short)ix[h];
-          }
-        }
-        __syncthreads();
-      }
-      const double s_old[2] = {s[0], s[1]};  // distance 1024 pairs a thread's two elements
-      const long long id_old[2] = {id[0], id[1]};
-      const unsigned ix_old[2] = {ix[0], ix[1]};
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const unsigned e = t + 1024u * h;
-        double so;
-        long long io;
-        unsigned xo;
-        if (j < 32) {
-          so = __shfl_xor_sync(0xffffffffu, s[h], (int)j);
-          io = __shfl_xor_sync(0xffffffffu, id[h], (int)j);
-          xo = __shfl_xor_sync(0xffffffffu, ix[h], (int)j);
-        } else if (j == 1024) {
-          so = s_old[h ^ 1];
-          io = id_old[h ^ 1];
-          xo = ix_old[h ^ 1];
-        } else {
-          const unsigned pe = e ^ j;
-          so = pe < n ? ks[pe] : s[h];
-          io = pe < n ? kid[pe] : id[h];
-          xo = pe < n ? kix[pe] : ix[h];
-        }
-        if (e < n) {
-          const bool lower = (e & j) == 0, up = (e & kk) == 0;
-          const bool take =
-              (lower == up) ? key_before(so, io, s_old[h], id_old[h]) : key_before(s_old[h], id_old[h], so, io);
-          if (take) {
-            s[h] = so;
-            id[h] = io;
-            ix[h] = xo;
-          }
-        }
-      }
-    }
-  }
-  // permute the items: read every source first, then write
-  RItem mine[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const unsigned e = t + 1024u * h;
-    if (e < n) mine[h] = R[ix[h]];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const unsigned e = t + 1024u * h;
-    if (e < n) R[e] = mine[h];
-  }
-}
-
 // Pads R[*n_used, to) with dead items, the used count read on the device (no host round trip).
 __global__ void k_pad_r_dev(RItem *R, const unsigned *n_used, unsigned to) {
   const unsigned from = *n_used;
@@ -536,7 +435,7 @@ cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t 
   }
   if (n_pow2 <= BITONIC_SMEM) {
     apx_count_launch();
-    k_bitonic_reg<<<1, 1024, 0, st>>>(R, n_pow2, n_dev);
+    k_bitonic_shared<<<1, 1024, 0, st>>>(R, n_pow2, 2, n_pow2, n_dev);
     return cudaGetLastError();
   }
   const unsigned nb = n_pow2 / BITONIC_SMEM;
