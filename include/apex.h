@@ -187,8 +187,12 @@ apex_status apex_cancel(apex_library *lib, apex_query_id id);
 apex_status apex_query_stats(apex_library *lib, apex_query_id id, apex_query_stats_t *out);
 
 /* Scores given compounds (host ids [n]) through the gather kernels: precision APEX_FP32
- * (CUDA cores) or APEX_FP64 (plain form g = sum u, then the head). outputs: host [n x n_outputs].
- * Synchronous. Used for calibration checks and parity tests. */
+ * (CUDA cores), APEX_FP64 (plain form g = sum u, then the head), or a reduced precision the
+ * library was built with (APEX_BF16, APEX_FP16, APEX_FP8: the tensor-core kernel over the id
+ * list, every slot's P row summed per compound; the path of a query's start-threshold sample).
+ * outputs: host [n x n_outputs]. Synchronous. Returns APEX_EINVAL for an unknown precision or an
+ * id out of range, APEX_EUNSUPPORTED for a reduced precision the library does not hold. Used for
+ * calibration checks and parity tests. */
 apex_status apex_score_ids(apex_library *lib, int32_t precision, int64_t n, const int64_t *ids,
                            double *outputs);
 

@@ -40,6 +40,8 @@ cudaError_t apx_launch_p16(const float *P32, long long n, float scale, int fmt, 
 cudaError_t apx_launch_image(const float *W, int rows_used, int rows, int fmt, void *img, cudaStream_t st);
 cudaError_t apx_launch_image_e4m3(const float *W, const float *scale, int rows_used, int rows, void *img,
                                   cudaStream_t st);
+cudaError_t apx_launch_tc_ids(const DevTables &T, const long long *ids, long long n, float *out, int *err, int n_sm,
+                              cudaStream_t st, int fmt);
 cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
                           cudaStream_t st, int fmt);
 cudaError_t apx_launch_slot_select(QuerySlot *slots, const int *slot_list, int n_slots, int mode, cudaStream_t st);
@@ -417,6 +419,19 @@ static void check_kernel_status(apex_library &L) {
   }
 }
 
+static bool trace_on() {
+  static int on = -1;
+  if (on < 0) on = getenv("APEX_TRACE") ? 1 : 0;
+  return on == 1;
+}
+#define TRACE(...)                          \
+  do {                                      \
+    if (trace_on()) {                       \
+      fprintf(stderr, "[apex] " __VA_ARGS__); \
+      fputc('\n', stderr);                 \
+    }                                       \
+  } while (0)
+
 // Retires the oldest enumeration launch in flight: waits for its status copy, raises a device-side
 // wait timeout as an error, and adds the launch's duration to the queries it served.
 static void retire_launch(apex_library &L) {
@@ -436,6 +451,7 @@ static void retire_launch(apex_library &L) {
     QueryRec *q = L.active[sq.first];
     if (q && q->id == sq.second) q->stats.enumerate_ms += ms;
   }
+  TRACE("launch %d queries: %.3f ms", (int)f.queries.size(), (double)ms);
 }
 static void retire_all(apex_library &L) {
   while (!L.inflight.empty()) retire_launch(L);
@@ -1011,30 +1027,22 @@ static void write_slot(apex_library &L, QueryRec *q, float admit) {
   CU(cudaMemcpyAsync(L.d_slots + q->slot, &S, sizeof(S), cudaMemcpyHostToDevice, L.st));
 }
 
-static bool trace_on() {
-  static int on = -1;
-  if (on < 0) on = getenv("APEX_TRACE") ? 1 : 0;
-  return on == 1;
-}
-#define TRACE(...)                          \
-  do {                                      \
-    if (trace_on()) {                       \
-      fprintf(stderr, "[apex] " __VA_ARGS__); \
-      fputc('\n', stderr);                 \
-    }                                       \
-  } while (0)
 
 // Start threshold guess, computed on the device without a host round trip: the rank-r best
-// objective among the feasible compounds (exact boxes, FP32 outputs) of a uniform sample of the
-// query's scope, r chosen so that ~3k scope compounds are expected above it. The kernel writes
-// the slot's start threshold and admission threshold (start - 2 delta_f) in stream order before
+// objective among the feasible compounds (exact boxes, outputs of the pass's precision) of a
+// uniform sample of the query's scope, r chosen so that ~3k scope compounds are expected above
+// it. The kernel writes the slot's start threshold and admission threshold (start - 2 delta_f)
+// in stream order before
 // the enumeration launch. Only a guess: finalization verifies it (>= k sure entries at or above
 // it) or restarts lower. Returns false (and leaves the slot's -inf thresholds) when the sample
 // cannot hold rank r.
 static bool speculative_start(apex_library &L, QueryRec *q, double margin2) {
   if (q->spec_rank < 0) return false;
   const double t_a = now_ms();
-  const long long S = std::min<long long>(4096, q->scope_n);
+  // the sample is scored by the pass's own kernel when it runs on the tensor cores (a 16,384-id
+  // sample costs one tile per CTA), else by the FP32 kernel (4,096 ids)
+  const int fmt = tc_format(q->precision);
+  const long long S = std::min<long long>(fmt >= 0 ? 16384 : 4096, q->scope_n);
   const double expect = (double)S * (double)q->k / (double)q->scope_n;
   long long r = q->spec_rank > 0 ? q->spec_rank : (long long)std::ceil(3.0 * expect + 5.0);
   q->spec_rank = (int)std::min<long long>(r, 1 << 30);
@@ -1058,10 +1066,14 @@ static bool speculative_start(apex_library &L, QueryRec *q, double margin2) {
   CU(cudaMemcpyAsync(d_rxn, q->subset.data(), sizeof(int) * n_sub, cudaMemcpyHostToDevice, L.st));
   CU(cudaMemcpyAsync(d_pre, pre.data(), sizeof(long long) * (n_sub + 1), cudaMemcpyHostToDevice, L.st));
   CU(apx_launch_spec_ids(d_rxn, d_pre, n_sub, L.T_.id_first, q->scope_n, L.rng(), S, d_ids, L.st));
-  LaunchPlan dummy;
-  memset(&dummy, 0, sizeof(dummy));
-  CU(apx_launch_fp32(dummy, L.T_, nullptr, d_ids, S, d_out, grid_for(L, (S + APX_TILE - 1) / APX_TILE), L.st,
-                     L.fp32_id_tile.load()));
+  if (fmt >= 0) {
+    CU(apx_launch_tc_ids(L.T_, d_ids, S, d_out, L.d_err, L.n_sm, L.st, fmt));
+  } else {
+    LaunchPlan dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    CU(apx_launch_fp32(dummy, L.T_, nullptr, d_ids, S, d_out, grid_for(L, (S + APX_TILE - 1) / APX_TILE), L.st,
+                       L.fp32_id_tile.load()));
+  }
   SpecArgs a;
   memset(&a, 0, sizeof(a));
   for (int j = 0; j < L.n_obj; ++j) a.w[j] = q->w[j];
@@ -1636,7 +1648,9 @@ extern "C" apex_status apex_query_stats(apex_library *L, apex_query_id id, apex_
 extern "C" apex_status apex_score_ids(apex_library *L, int32_t precision, int64_t n, const int64_t *ids,
                                       double *outputs) {
   if (!L || n < 0 || (n > 0 && (!ids || !outputs))) return fail(APEX_EINVAL, "bad arguments");
-  if (precision != APEX_FP32 && precision != APEX_FP64) return fail(APEX_EINVAL, "precision must be APEX_FP32 or APEX_FP64");
+  const int fmt = tc_format(precision);
+  if (precision != APEX_FP32 && precision != APEX_FP64 && fmt < 0) return fail(APEX_EINVAL, "unknown precision");
+  if (fmt >= 0 && !((L->precisions >> precision) & 1u)) return fail(APEX_EUNSUPPORTED, "precision not built");
   for (int64_t i = 0; i < n; ++i)
     if (ids[i] < 0 || ids[i] >= L->N) return fail(APEX_EINVAL, "id %lld out of range", (long long)ids[i]);
   if (n == 0) return APEX_OK;
@@ -1647,11 +1661,16 @@ extern "C" apex_status apex_score_ids(apex_library *L, int32_t precision, int64_
     DevBuf B;
     long long *d_ids = (long long *)B.get(sizeof(long long) * n);
     CU(cudaMemcpyAsync(d_ids, ids, sizeof(long long) * n, cudaMemcpyHostToDevice, L->st));
-    if (precision == APEX_FP32) {
+    if (precision != APEX_FP64) {
       float *d = (float *)B.get(sizeof(float) * n * no);
-      LaunchPlan dummy;
-      memset(&dummy, 0, sizeof(dummy));
-      CU(apx_launch_fp32(dummy, L->T_, nullptr, d_ids, n, d, grid_for(*L, (n + APX_TILE - 1) / APX_TILE), L->st));
+      if (fmt >= 0) {  // the tensor-core kernel over the id list (the start-threshold sample's path)
+        CU(apx_launch_tc_ids(L->T_, d_ids, n, d, L->d_err, L->n_sm, L->st, fmt));
+        check_kernel_status(*L);
+      } else {
+        LaunchPlan dummy;
+        memset(&dummy, 0, sizeof(dummy));
+        CU(apx_launch_fp32(dummy, L->T_, nullptr, d_ids, n, d, grid_for(*L, (n + APX_TILE - 1) / APX_TILE), L->st));
+      }
       std::vector<float> h(n * no);
       CU(cudaMemcpyAsync(h.data(), d, sizeof(float) * n * no, cudaMemcpyDeviceToHost, L->st));
       CU(cudaStreamSynchronize(L->st));

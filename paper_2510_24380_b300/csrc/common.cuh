@@ -43,7 +43,8 @@ struct Segment {
 // One enumeration launch: a list of item ranges, passed by value as a kernel parameter.
 struct LaunchPlan {
   int n_seg;
-  int mode;                                  // 0 = queries, 1 = dump by id, 2 = dump by launch tile
+  int mode;                                  // 0 = queries, 1 = dump by id, 2 = dump by launch tile,
+                                             // 3 = outputs of an id list (tensor-core kernel)
   int pad;
   long long total_items;
   long long seg_first[APX_MAX_SEG + 1];      // prefix of items
@@ -54,7 +55,7 @@ struct LaunchPlan {
   // dump mode
   float *dump;                               // [dump_n x n_out]
   long long *dump_ids;                       // mode 2: [dump_n], row r of launch tile t at t * 128 + r,
-                                             // -1 = padding row
+                                             // -1 = padding row; mode 3: the input ids [dump_n]
   long long dump_base, dump_n;
 };
 

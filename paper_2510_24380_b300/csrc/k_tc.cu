@@ -28,6 +28,8 @@
 // columns [64g, 64g + 32) of its buffer, the four layer-3 partial sums use [32, 64) and [96, 128).
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel records
 // APX_ERR_TIMEOUT in the status word, every role leaves its loop, and TMEM is released.
+#include <algorithm>
+#include <cstring>
 #include "common.cuh"
 #include "tc_sync.cuh"
 
@@ -392,7 +394,10 @@ __device__ __forceinline__ void tc_apply_queries(const SlotParams *qp, QuerySlot
   }
 }
 
-template <int ACT, int FMT, bool FEWQ>
+// IDS: the rows of the launch are a list of compound ids (L.dump_ids[0, L.dump_n)), 128 per tile,
+// each row summing the P rows of all its slots; the FP32 outputs go to L.dump (the start-
+// threshold sample of a query). Otherwise the tiles come from the launch plan.
+template <int ACT, int FMT, bool FEWQ, bool IDS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_head(const __grid_constant__ LaunchPlan L, const __grid_constant__ DevTables T, QuerySlot *slots, int *err) {
   using LY = TcL<FMT>;
@@ -525,17 +530,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const bool produce = more;
       if (produce) {
         if (need_r) {
-          const TileRun I = apx_tile_run(L, T.rx, tile, (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x);
-          const RxnPlan *rp = I.rp;
-          left = (int)(I.o_end - I.o_begin);
-          has_outer = rp->outer_row >= 0;
-          const long long q = I.q0 + m;
-          if (q < rp->n_inner) {
-            // the row's synthon of every inner slot (mixed radix, last slot fastest); unrolled
-            // over the slot count so that the row pointers stay in registers
-            const unsigned short *src[APEX_MAX_SLOTS];
+          // the row's synthon of every summed slot (mixed radix, last slot fastest); unrolled over
+          // the slot count so that the row pointers stay in registers
+          const unsigned short *src[APEX_MAX_SLOTS];
+          int ni = 0;
+          bool row_ok;
+          if constexpr (IDS) {  // every slot of the listed compound; each tile is its own run
+            left = 1;
+            has_outer = false;
+            const long long i = tile * APX_TILE + m;
+            row_ok = i < L.dump_n;
+            const long long id = row_ok ? (L.dump_ids[i] & APX_ID_MASK) : 0;
+            int lo = 0, hi = T.n_rx - 1;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (T.id_first[mid] <= id) lo = mid; else hi = mid - 1;
+            }
+            const RxnPlan *rp = T.rx + lo;
+            long long rem = id - rp->id_first;
+            ni = row_ok ? rp->n_slots : 0;
+#pragma unroll
+            for (int sl = APEX_MAX_SLOTS - 1; sl >= 0; --sl) {
+              src[sl] = T.P16[PF] + g * 64;
+              if (sl < ni) {
+                const long long sz = rp->slot_size[sl];
+                src[sl] += (rp->slot_row[sl] + rem % sz) * 256;
+                rem /= sz;
+              }
+            }
+          } else {  // the inner slots of the tile's work item
+            const TileRun I = apx_tile_run(L, T.rx, tile, (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x);
+            const RxnPlan *rp = I.rp;
+            left = (int)(I.o_end - I.o_begin);
+            has_outer = rp->outer_row >= 0;
+            const long long q = I.q0 + m;
+            row_ok = q < rp->n_inner;
             long long rem = q;
-            const int ni = rp->n_inner_slots;
+            ni = row_ok ? rp->n_inner_slots : 0;
 #pragma unroll
             for (int sl = APEX_MAX_SLOTS - 1; sl >= 0; --sl) {
               src[sl] = T.P16[PF] + g * 64;
@@ -545,6 +576,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 rem /= sz;
               }
             }
+          }
+          if (row_ok) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -679,7 +712,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp == TC_LOAD_WARP) {
     // ------------------------------------------------------------ outer-row loader (bulk TMA)
-    if (lane == 0) {
+    if (lane == 0 && IDS) {  // id lists have no outer rows: keep the ring's phases
+      for (long long j = 0; j < t_end - t_begin; ++j) {
+        const int rs = (int)(j & (TC_OROW_SLOTS - 1));
+        if (!mbar_wait(bar(B_OEMPTY(rs)), (uint32_t)(((j / TC_OROW_SLOTS) & 1) ^ 1), abort_flag, err)) break;
+        mbar_arrive(bar(B_OFULL(rs)));
+      }
+    } else if (lane == 0) {
       long long j = 0;
       bool ok = true;
       for (long long tile = t_begin; ok && tile < t_end;) {
@@ -712,12 +751,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (mbar_wait(bar(B_W), 0, abort_flag, err)) {
         tc_fence_after();
         const uint32_t a1 = sbase + LY::A1, w2 = sbase + LY::W2;
-        long long j = 0;
         bool ok = true;
-        for (long long tile = t_begin; ok && tile < t_end;) {
-          const TileRun I = apx_tile_run(L, T.rx, tile, t_end);
-          tile += I.o_end - I.o_begin;
-          for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
+        {
+          for (long long j = 0; j < t_end - t_begin; ++j) {  // this CTA's tiles, in order
             const int buf = (int)(j & 1);
             if (!mbar_wait(bar(B_D2EMPTY(buf)), (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
             tc_fence_after();
@@ -780,8 +816,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // every query of a library has the library's objective count
     const int qp_n_obj = L.qmask_all ? qp[__ffsll((long long)L.qmask_all) - 1].n_obj : APEX_MAX_OBJECTIVES;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    if constexpr (IDS) {  // outputs of the listed compounds, FP32, row-major [n x n_out]
+      for (long long j = 0; j < t_end - t_begin; ++j) {
+        const int buf = (int)(j & 1);
+        if (!mbar_wait(bar(B_D3FULL(buf)), (uint32_t)((j >> 1) & 1), abort_flag, err)) break;
+        tc_fence_after();
+        float out[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) out[n] = b3s[n];
+#pragma unroll
+        for (int c = 0; c < TC_L3_CHAINS; ++c) {
+          uint32_t pa[16];
+          tmem_ld16(lane_base + (uint32_t)buf * 256u + tc_d3_col(c), pa);
+          tmem_wait_ld_dep16(pa);
+#pragma unroll
+          for (int n = 0; n < 16; ++n) out[n] += __uint_as_float(pa[n]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(B_D2EMPTY(buf)));
+        const long long i = (t_begin + j) * APX_TILE + r;
+        if (i < L.dump_n) {
+#pragma unroll
+          for (int n = 0; n < 16; ++n)
+            if (n < T.n_out) L.dump[i * T.n_out + n] = out[n];
+        }
+      }
+    }
     long long j = 0;
-    bool ok = true;
+    bool ok = !IDS;
     for (long long tile = t_begin; ok && tile < t_end;) {
       const TileRun I = apx_tile_run(L, T.rx, tile, t_end);
       const long long run_tile0 = tile - I.o_begin;  // launch tile of outer index o: run_tile0 + o
@@ -866,19 +929,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 size_t apx_tc_smem_bytes() { return TcL<1>::SMEM; }
 
-template <int ACT, int FMT, bool FEWQ>
+template <int ACT, int FMT, bool FEWQ, bool IDS = false>
 static cudaError_t tc_launch_q(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
                                cudaStream_t st) {
   static bool attr = false;  // per instantiation
   if (!attr) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_tc_head<ACT, FMT, FEWQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcL<FMT>::SMEM);
+    const cudaError_t e = cudaFuncSetAttribute(k_tc_head<ACT, FMT, FEWQ, IDS>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, TcL<FMT>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   if (grid <= 0) return cudaSuccess;
   apx_count_launch();
-  k_tc_head<ACT, FMT, FEWQ><<<grid, TC_THREADS, TcL<FMT>::SMEM, st>>>(L, T, slots, err);
+  k_tc_head<ACT, FMT, FEWQ, IDS><<<grid, TC_THREADS, TcL<FMT>::SMEM, st>>>(L, T, slots, err);
   return cudaGetLastError();
 }
 template <int ACT, int FMT>
@@ -902,4 +965,29 @@ cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *sl
   if (fmt == 0) return tc_launch_fmt<0>(L, T, slots, err, grid, st);
   if (fmt == 1) return tc_launch_fmt<1>(L, T, slots, err, grid, st);
   return tc_launch_fmt<2>(L, T, slots, err, grid, st);
+}
+
+template <int FMT>
+static cudaError_t tc_launch_ids_fmt(const LaunchPlan &L, const DevTables &T, int *err, int grid, cudaStream_t st) {
+  if (T.act == APEX_ACT_SILU) return tc_launch_q<APEX_ACT_SILU, FMT, true, true>(L, T, nullptr, err, grid, st);
+  if (T.act == APEX_ACT_RELU) return tc_launch_q<APEX_ACT_RELU, FMT, true, true>(L, T, nullptr, err, grid, st);
+  return tc_launch_q<APEX_ACT_IDENTITY, FMT, true, true>(L, T, nullptr, err, grid, st);
+}
+
+// Outputs of n listed compounds (ids: device, bit 62 ignored) in the reduced-precision pass format
+// fmt, as FP32 rows out[n x n_out] (device). One tile of 128 ids per CTA step.
+cudaError_t apx_launch_tc_ids(const DevTables &T, const long long *ids, long long n, float *out, int *err, int n_sm,
+                              cudaStream_t st, int fmt) {
+  if (n <= 0) return cudaSuccess;
+  LaunchPlan L;
+  memset(&L, 0, sizeof(L));
+  L.mode = 3;
+  L.total_tiles = (n + APX_TILE - 1) / APX_TILE;
+  L.dump = out;
+  L.dump_ids = const_cast<long long *>(ids);
+  L.dump_n = n;
+  const int grid = (int)std::min<long long>(L.total_tiles, n_sm);
+  if (fmt == 0) return tc_launch_ids_fmt<0>(L, T, err, grid, st);
+  if (fmt == 1) return tc_launch_ids_fmt<1>(L, T, err, grid, st);
+  return tc_launch_ids_fmt<2>(L, T, err, grid, st);
 }

@@ -56,6 +56,31 @@ def test_score_ids_fp32_and_fp64(ragged):
     assert np.max(np.abs(o64 - ref) / rms) <= 1e-12
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8"])
+def test_score_ids_tensor_core_id_list(ragged, precision):
+    """The tensor-core kernel over an id list (the start-threshold sample's path): every slot of
+    each listed compound summed per row, tiles of 128 ids with a ragged last tile, ids from every
+    reaction (1- to 4-slot) in random order and repeated; outputs within the pass bound of the
+    FP64 oracle and within rounding of the enumeration kernel's outputs of the same compounds."""
+    lib, head, spec, L, rms = ragged
+    N = O.count(lib)
+    firsts = np.cumsum([0] + [int(np.prod(lib.sizes_of(t))) for t in range(lib.n_reactions)])
+    ids = np.concatenate([np.random.default_rng(3).integers(0, N, 1000), [0, N - 1, 0], firsts[:-1]])
+    ref = O.score_ids(lib, head, ids)
+    got = L.score_ids(ids, precision)
+    assert got.shape == ref.shape
+    assert np.abs(got - ref).max() <= BF16_ABS
+    # the same compounds from the enumeration kernel (same format, same weights)
+    t = int(np.argmax([np.prod(lib.sizes_of(t)) for t in range(lib.n_reactions)]))
+    nt = int(np.prod(lib.sizes_of(t)))
+    pick = np.arange(0, nt, 7)
+    enum = L.dump_outputs(t, nt, precision).astype(np.float64)[pick]
+    sc = L.score_ids(firsts[t] + pick, precision)
+    assert np.abs(sc - enum).max() <= BF16_ABS
+    # repeated ids give identical rows
+    assert np.array_equal(got[1000], got[1002])
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16", "fp8"])
 def test_raw_outputs_of_every_compound(ragged, precision):
     """The production enumeration kernel's raw outputs for every compound of every reaction."""
