@@ -223,50 +223,40 @@ __device__ void f32_layer(F32Smem<TM> &S, const DevTables &T, int l) {
   __syncthreads();
 }
 
-// Last layer with at most 16 outputs (the usual head: a few objectives and properties): the
-// threads split K instead of N (tile row r, K slice sl of APX_SIMT_THREADS / TM slices), W^T of the
-// layer is staged in shared memory (broadcast reads), and the slices' partial sums are added
-// through shared memory. Reuses the W^T chunk buffers: K x 16 weights, then the partial sums.
+// Last layer with at most 16 outputs (the usual head: a few objectives and properties): thread
+// (row r, output group grp) accumulates OPG outputs over the whole K range in order, so every
+// output is the same fmaf chain whatever the tile height (results do not depend on the id tile
+// chosen by the autotuner); W^T of the layer is staged in shared memory (broadcast reads),
+// reusing the W^T chunk buffers, instead of computing 256 padded columns.
 template <int TM>
 __device__ void f32_last_small(F32Smem<TM> &S, const DevTables &T, int l) {
-  constexpr int NS = APX_SIMT_THREADS / TM;
+  constexpr int NG = APX_SIMT_THREADS / TM;  // output groups: 2 (128-row tiles) or 8 (32-row tiles)
+  constexpr int OPG = 16 / NG;               // outputs per group: 8 or 2
   const int K = T.dims[l], N = T.dims[l + 1];
-  float *w = &S.Wc[0][0][0];   // [K][16]
-  float *part = w + 256 * 16;  // [NS][16][TM]
+  float *w = &S.Wc[0][0][0];  // [K][16]
   for (int e = threadIdx.x; e < K * 16; e += APX_SIMT_THREADS) {
     const int k = e >> 4, n = e & 15;
     w[e] = n < N ? __ldg(T.WT[l] + (long long)k * N + n) : 0.f;
   }
   __syncthreads();
-  const int r = threadIdx.x % TM, sl = threadIdx.x / TM;
-  const int k0 = sl * K / NS, k1 = (sl + 1) * K / NS;
-  f32x2 acc[8];  // outputs (2m, 2m + 1)
+  const int r = threadIdx.x % TM, grp = threadIdx.x / TM;
+  f32x2 acc[OPG / 2];  // outputs (grp OPG + 2m, grp OPG + 2m + 1)
 #pragma unroll
-  for (int m = 0; m < 8; ++m) acc[m] = 0ull;
-  for (int k = k0; k < k1; ++k) {
+  for (int m = 0; m < OPG / 2; ++m) acc[m] = 0ull;
+  for (int k = 0; k < K; ++k) {
     const f32x2 a = f2dup(S.AT[k][r]);
+    const f32x2 *wk = reinterpret_cast<const f32x2 *>(w + k * 16 + grp * OPG);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(w + k * 16 + 4 * q);
-      ffma2(acc[2 * q], a, v.x);
-      ffma2(acc[2 * q + 1], a, v.y);
-    }
+    for (int m = 0; m < OPG / 2; ++m) ffma2(acc[m], a, wk[m]);
   }
+  __syncthreads();  // every thread has read AT
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
+  for (int m = 0; m < OPG / 2; ++m) {
     float z0, z1;
     f2unpack(acc[m], z0, z1);
-    part[(sl * 16 + 2 * m) * TM + r] = z0;
-    part[(sl * 16 + 2 * m + 1) * TM + r] = z1;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < 16 * TM; e += APX_SIMT_THREADS) {
-    const int n = e / TM, rr = e % TM;
-    if (n < N) {
-      float z = 0.f;
-      for (int s2 = 0; s2 < NS; ++s2) z += part[(s2 * 16 + n) * TM + rr];
-      S.AT[n][rr] = z + __ldg(T.B[l] + n);
-    }
+    const int n = grp * OPG + 2 * m;
+    if (n < N) S.AT[n][r] = z0 + __ldg(T.B[l] + n);
+    if (n + 1 < N) S.AT[n + 1][r] = z1 + __ldg(T.B[l] + n + 1);
   }
   __syncthreads();
 }

@@ -666,19 +666,29 @@ __global__ void k_spec_ids(const int *rxn, const long long *pre, int n_sub, cons
   }
 }
 
-// Objective of the feasible sample entries (exact boxes on FP32 outputs), its rank-th largest
-// value, and the query slot's start and admission thresholds (-inf when fewer than rank sample
-// entries are feasible). One CTA.
+// Objective of the feasible sample entries (exact boxes on the sample's outputs), its rank-th
+// largest value, and the query slot's start and admission thresholds (-inf when fewer than rank
+// sample entries are feasible). One CTA; samples of up to SPEC_SMEM_KEYS entries are selected
+// from shared memory.
+#define SPEC_SMEM_KEYS 16384
 __global__ void __launch_bounds__(SEL_THREADS) k_spec_select(const float *out, long long S, const __grid_constant__ SpecArgs a,
                                                              float *keys, unsigned char *flag, QuerySlot *slot) {
-  __shared__ unsigned spec_bits[4096];  // the sample's objective bits, 0 = infeasible
-  const bool in_smem = S <= 4096;
+  extern __shared__ unsigned spec_bits[];  // the sample's objective bits, 0 = infeasible
+  const bool in_smem = S <= SPEC_SMEM_KEYS;
+  // the boxes as FP32 bounds that decide exactly like the FP64 ones for FP32 values: the smallest
+  // float >= lo and the largest float <= hi (FP64 compares run at a small fraction of the FP32 rate)
+  __shared__ float lo_f[APEX_MAX_CONSTRAINTS], hi_f[APEX_MAX_CONSTRAINTS];
+  if (threadIdx.x < (unsigned)a.n_cons) {
+    lo_f[threadIdx.x] = __double2float_ru(a.lo[threadIdx.x]);
+    hi_f[threadIdx.x] = __double2float_rd(a.hi[threadIdx.x]);
+  }
+  __syncthreads();
   for (long long i = threadIdx.x; i < S; i += blockDim.x) {
     const float *o = out + i * a.n_out;
     bool ok = true;
     for (int c = 0; c < a.n_cons; ++c) {
-      const double v = (double)o[a.cons_idx[c]];
-      ok = ok && v >= a.lo[c] && v <= a.hi[c];
+      const float v = o[a.cons_idx[c]];
+      ok = ok && v >= lo_f[c] && v <= hi_f[c];
     }
     float f = 0.f;
     for (int j = 0; j < a.n_obj; ++j) f = fmaf(a.w[j], o[j], f);
@@ -711,7 +721,15 @@ cudaError_t apx_launch_spec_ids(const int *rxn, const long long *pre, int n_sub,
 
 cudaError_t apx_launch_spec_select(const float *out, long long S, const SpecArgs &a, float *keys, unsigned char *flag,
                                    QuerySlot *slot, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_spec_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(SPEC_SMEM_KEYS * sizeof(unsigned)));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   apx_count_launch();
-  k_spec_select<<<1, SEL_THREADS, 0, st>>>(out, S, a, keys, flag, slot);
+  const size_t smem = S <= SPEC_SMEM_KEYS ? (size_t)S * sizeof(unsigned) : 0;
+  k_spec_select<<<1, SEL_THREADS, smem, st>>>(out, S, a, keys, flag, slot);
   return cudaGetLastError();
 }
