@@ -509,7 +509,7 @@ def main():
     peak = P.get("bf16_tflops", 1800.0)
     linear = len(head.dims) == 2
     d2h = int(res["n"]) * (8 + 4 + 8 * 4 + 8 + 8 * L.n_outputs)
-    h2d = 4 * len(q.weights) + (4 + 8 + 8) * q.m + 752  # query weights/boxes + the device query slot
+    h2d = 4 * len(q.weights) + (4 + 8 + 8) * q.m + 880  # query weights/boxes + the device query slot
     value = world * N * args.steps / (t_dev * 1e-3)
     line = {
         "metric": "compounds scored per second (exhaustive top-k query)",

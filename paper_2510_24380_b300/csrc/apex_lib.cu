@@ -41,7 +41,7 @@ cudaError_t apx_launch_image(const float *W, int rows_used, int rows, int fmt, v
 cudaError_t apx_launch_image_e4m3(const float *W, const float *scale, int rows_used, int rows, void *img,
                                   cudaStream_t st);
 cudaError_t apx_launch_tc_ids(const DevTables &T, const long long *ids, long long n, float *out, int *err, int n_sm,
-                              cudaStream_t st, int fmt);
+                              cudaStream_t st, int fmt, QuerySlot *slots, int spec_slot);
 cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
                           cudaStream_t st, int fmt);
 cudaError_t apx_launch_slot_select(QuerySlot *slots, const int *slot_list, int n_slots, int mode, cudaStream_t st);
@@ -1013,6 +1013,11 @@ static void write_slot(apex_library &L, QueryRec *q, float admit) {
     S.hi_w[c] = (float)(q->hi[c] + err[p]);
     S.lo_s[c] = (float)(q->lo[c] + err[p]);
     S.hi_s[c] = (float)(q->hi[c] - err[p]);
+    float lx = (float)q->lo[c], hx = (float)q->hi[c];  // exact decisions for FP32 values
+    if ((double)lx < q->lo[c]) lx = std::nextafter(lx, INFINITY);
+    if ((double)hx > q->hi[c]) hx = std::nextafter(hx, -INFINITY);
+    S.lo_x[c] = lx;
+    S.hi_x[c] = hx;
   }
   S.delta_f = (float)(df * 1.0001 + 1e-12);
   S.admit = admit;
@@ -1066,8 +1071,8 @@ static bool speculative_start(apex_library &L, QueryRec *q, double margin2) {
   CU(cudaMemcpyAsync(d_rxn, q->subset.data(), sizeof(int) * n_sub, cudaMemcpyHostToDevice, L.st));
   CU(cudaMemcpyAsync(d_pre, pre.data(), sizeof(long long) * (n_sub + 1), cudaMemcpyHostToDevice, L.st));
   CU(apx_launch_spec_ids(d_rxn, d_pre, n_sub, L.T_.id_first, q->scope_n, L.rng(), S, d_ids, L.st));
-  if (fmt >= 0) {
-    CU(apx_launch_tc_ids(L.T_, d_ids, S, d_out, L.d_err, L.n_sm, L.st, fmt));
+  if (fmt >= 0) {  // the kernel applies the query's exact boxes and objective: one key per sample
+    CU(apx_launch_tc_ids(L.T_, d_ids, S, d_out, L.d_err, L.n_sm, L.st, fmt, L.d_slots, q->slot));
   } else {
     LaunchPlan dummy;
     memset(&dummy, 0, sizeof(dummy));
@@ -1087,6 +1092,7 @@ static bool speculative_start(apex_library &L, QueryRec *q, double margin2) {
   }
   a.rank = r;
   a.margin2 = (float)margin2;
+  a.bits_in = fmt >= 0 ? 1 : 0;
   CU(apx_launch_spec_select(d_out, S, a, d_keys, d_flag, L.d_slots + q->slot, L.st));
   TRACE("start q%lld: host %.3f ms (sample of %lld, rank %lld)", (long long)q->id, now_ms() - t_a, S, r);
   return true;
@@ -1664,7 +1670,7 @@ extern "C" apex_status apex_score_ids(apex_library *L, int32_t precision, int64_
     if (precision != APEX_FP64) {
       float *d = (float *)B.get(sizeof(float) * n * no);
       if (fmt >= 0) {  // the tensor-core kernel over the id list (the start-threshold sample's path)
-        CU(apx_launch_tc_ids(L->T_, d_ids, n, d, L->d_err, L->n_sm, L->st, fmt));
+        CU(apx_launch_tc_ids(L->T_, d_ids, n, d, L->d_err, L->n_sm, L->st, fmt, nullptr, -1));
         check_kernel_status(*L);
       } else {
         LaunchPlan dummy;

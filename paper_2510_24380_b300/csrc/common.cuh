@@ -67,6 +67,8 @@ struct QuerySlot {
   int cons_idx[APEX_MAX_CONSTRAINTS];
   float lo_w[APEX_MAX_CONSTRAINTS], hi_w[APEX_MAX_CONSTRAINTS];  // admission box (widened by the pass margin)
   float lo_s[APEX_MAX_CONSTRAINTS], hi_s[APEX_MAX_CONSTRAINTS];  // sure box (shrunk by the margin)
+  float lo_x[APEX_MAX_CONSTRAINTS], hi_x[APEX_MAX_CONSTRAINTS];  // exact box as FP32 bounds: smallest
+                                                                 // float >= lo, largest float <= hi
   float admit;        // admission threshold on the pass objective
   float delta_f;      // objective margin of the pass
   float tau;          // k-th largest sure key seen so far (-inf until k sure keys exist)
@@ -84,10 +86,11 @@ struct QuerySlot {
 };
 
 // Speculative start threshold of one query, evaluated on the device: the rank-th best objective
-// (exact boxes, FP32 outputs) of a uniform sample of the query's scope.
+// (exact boxes) of a uniform sample of the query's scope.
 struct SpecArgs {
   float w[APEX_MAX_OBJECTIVES];
-  int n_obj, n_cons, n_out, pad;
+  int n_obj, n_cons, n_out;
+  int bits_in;  // 1: the sample's keys come as order-preserving objective bits (0 = infeasible)
   int cons_idx[APEX_MAX_CONSTRAINTS];
   double lo[APEX_MAX_CONSTRAINTS], hi[APEX_MAX_CONSTRAINTS];
   long long rank;

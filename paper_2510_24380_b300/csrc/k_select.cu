@@ -684,6 +684,16 @@ __global__ void __launch_bounds__(SEL_THREADS) k_spec_select(const float *out, l
   }
   __syncthreads();
   for (long long i = threadIdx.x; i < S; i += blockDim.x) {
+    if (a.bits_in) {  // keys already formed by the scoring kernel
+      const unsigned kb = reinterpret_cast<const unsigned *>(out)[i];
+      if (in_smem) {
+        spec_bits[i] = kb;
+      } else {
+        keys[i] = kb ? apx_bits_key(kb) : 0.f;
+        flag[i] = kb != 0u;
+      }
+      continue;
+    }
     const float *o = out + i * a.n_out;
     bool ok = true;
     for (int c = 0; c < a.n_cons; ++c) {

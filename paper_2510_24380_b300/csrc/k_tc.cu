@@ -837,9 +837,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) mbar_arrive(bar(B_D2EMPTY(buf)));
         const long long i = (t_begin + j) * APX_TILE + r;
         if (i < L.dump_n) {
+          if (L.dump_base >= 0) {  // start-threshold sample of query slot dump_base: its key
+            const QuerySlot *Q = slots + L.dump_base;
+            const int n_obj = Q->n_obj;
+            float f = 0.f;
 #pragma unroll
-          for (int n = 0; n < 16; ++n)
-            if (n < T.n_out) L.dump[i * T.n_out + n] = out[n];
+            for (int o = 0; o < 16; ++o)
+              if (o < n_obj) f = fmaf(Q->w[o], out[o], f);
+            bool feasible = true;
+            for (int c = 0; c < Q->n_cons; ++c) {
+              const float v = apx_sel(out, Q->cons_idx[c]);
+              feasible = feasible && v >= Q->lo_x[c] && v <= Q->hi_x[c];
+            }
+            reinterpret_cast<unsigned *>(L.dump)[i] = feasible ? apx_key_bits(f) : 0u;
+          } else {
+#pragma unroll
+            for (int n = 0; n < 16; ++n)
+              if (n < T.n_out) L.dump[i * T.n_out + n] = out[n];
+          }
         }
       }
     }
@@ -968,16 +983,19 @@ cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *sl
 }
 
 template <int FMT>
-static cudaError_t tc_launch_ids_fmt(const LaunchPlan &L, const DevTables &T, int *err, int grid, cudaStream_t st) {
-  if (T.act == APEX_ACT_SILU) return tc_launch_q<APEX_ACT_SILU, FMT, true, true>(L, T, nullptr, err, grid, st);
-  if (T.act == APEX_ACT_RELU) return tc_launch_q<APEX_ACT_RELU, FMT, true, true>(L, T, nullptr, err, grid, st);
-  return tc_launch_q<APEX_ACT_IDENTITY, FMT, true, true>(L, T, nullptr, err, grid, st);
+static cudaError_t tc_launch_ids_fmt(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
+                                     cudaStream_t st) {
+  if (T.act == APEX_ACT_SILU) return tc_launch_q<APEX_ACT_SILU, FMT, true, true>(L, T, slots, err, grid, st);
+  if (T.act == APEX_ACT_RELU) return tc_launch_q<APEX_ACT_RELU, FMT, true, true>(L, T, slots, err, grid, st);
+  return tc_launch_q<APEX_ACT_IDENTITY, FMT, true, true>(L, T, slots, err, grid, st);
 }
 
 // Outputs of n listed compounds (ids: device, bit 62 ignored) in the reduced-precision pass format
-// fmt, as FP32 rows out[n x n_out] (device). One tile of 128 ids per CTA step.
+// fmt, as FP32 rows out[n x n_out] (device). One tile of 128 ids per CTA step. With spec_slot >= 0
+// the kernel applies that query slot's exact boxes and objective instead and writes one key per
+// compound into out (as unsigned: order-preserving objective bits, 0 = infeasible).
 cudaError_t apx_launch_tc_ids(const DevTables &T, const long long *ids, long long n, float *out, int *err, int n_sm,
-                              cudaStream_t st, int fmt) {
+                              cudaStream_t st, int fmt, QuerySlot *slots, int spec_slot) {
   if (n <= 0) return cudaSuccess;
   LaunchPlan L;
   memset(&L, 0, sizeof(L));
@@ -986,8 +1004,9 @@ cudaError_t apx_launch_tc_ids(const DevTables &T, const long long *ids, long lon
   L.dump = out;
   L.dump_ids = const_cast<long long *>(ids);
   L.dump_n = n;
+  L.dump_base = spec_slot >= 0 && slots ? spec_slot : -1;
   const int grid = (int)std::min<long long>(L.total_tiles, n_sm);
-  if (fmt == 0) return tc_launch_ids_fmt<0>(L, T, err, grid, st);
-  if (fmt == 1) return tc_launch_ids_fmt<1>(L, T, err, grid, st);
-  return tc_launch_ids_fmt<2>(L, T, err, grid, st);
+  if (fmt == 0) return tc_launch_ids_fmt<0>(L, T, slots, err, grid, st);
+  if (fmt == 1) return tc_launch_ids_fmt<1>(L, T, slots, err, grid, st);
+  return tc_launch_ids_fmt<2>(L, T, slots, err, grid, st);
 }
