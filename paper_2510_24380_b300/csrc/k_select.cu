@@ -209,17 +209,28 @@ cudaError_t apx_launch_slot_select(QuerySlot *slots, const int *slot_list, int n
 // margin eps) and sure-feasible (box shrunk by eps).
 
 __global__ void k_eval32(EvalArgs a, long long n, float *f32, unsigned char *maybe, unsigned char *sure) {
+  // the widened and shrunk boxes as FP32 bounds deciding exactly like the FP64 arithmetic for FP32
+  // values (FP64 compares run at a small fraction of the FP32 rate)
+  __shared__ float mlo[APEX_MAX_CONSTRAINTS], mhi[APEX_MAX_CONSTRAINTS], slo[APEX_MAX_CONSTRAINTS],
+      shi[APEX_MAX_CONSTRAINTS];
+  const int m = a.Q->n_cons;
+  if (threadIdx.x < (unsigned)m) {
+    const int c = threadIdx.x, p = a.Q->cons_idx[c];
+    mlo[c] = __double2float_ru(a.lo[c] - a.eps[p]);
+    mhi[c] = __double2float_rd(a.hi[c] + a.eps[p]);
+    slo[c] = __double2float_ru(a.lo[c] + a.eps[p]);
+    shi[c] = __double2float_rd(a.hi[c] - a.eps[p]);
+  }
+  __syncthreads();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float *o = a.out32 + i * a.n_out;
     float f = 0.f;
     for (int j = 0; j < a.Q->n_obj; ++j) f = fmaf(a.Q->w[j], o[j], f);
     bool mb = true, sr = true;
-    for (int c = 0; c < a.Q->n_cons; ++c) {
-      const int p = a.Q->cons_idx[c];
-      const float v = o[p];
-      const double lo = a.lo[c], hi = a.hi[c];
-      mb = mb && ((double)v >= lo - a.eps[p]) && ((double)v <= hi + a.eps[p]);
-      sr = sr && ((double)v >= lo + a.eps[p]) && ((double)v <= hi - a.eps[p]);
+    for (int c = 0; c < m; ++c) {
+      const float v = o[a.Q->cons_idx[c]];
+      mb = mb && v >= mlo[c] && v <= mhi[c];
+      sr = sr && v >= slo[c] && v <= shi[c];
     }
     f32[i] = f;
     maybe[i] = mb;
@@ -310,9 +321,18 @@ __global__ void k_apply64(RItem *R, const int *pos64, const double *out64, unsig
 
 // ------------------------------------------------------------------ bitonic sort of R
 // order: alive first, then s desc, then id asc
+// Order-preserving 64-bit key of a score (larger score, larger key; -0 and +0 equal), so the
+// orderings compare integers: FP64 comparisons issue at a small fraction of the integer rate
+// on this part. Dead items take key 0, below every score (-inf included).
+__device__ __forceinline__ unsigned long long r_key(double s) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(s);
+  if (b == 0x8000000000000000ull) b = 0ull;
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
 __device__ __forceinline__ bool r_before(const RItem &a, const RItem &b) {
+  const unsigned long long ka = a.alive ? r_key(a.s) : 0ull, kb = b.alive ? r_key(b.s) : 0ull;
   if (a.alive != b.alive) return a.alive > b.alive;
-  if (a.s != b.s) return a.s > b.s;
+  if (ka != kb) return ka > kb;
   return a.id < b.id;
 }
 
@@ -334,13 +354,13 @@ __global__ void k_bitonic_global(RItem *R, unsigned n, unsigned j, unsigned kk) 
 #define BITONIC_SMEM 2048
 // every (kk, j) step with j < block inside blocks of `block` (power of two <= BITONIC_SMEM) elements.
 // The network runs on the sort keys only, as separate arrays in shared memory (conflict-free
-// 8-byte accesses): key (s, id) with dead items mapped to (-inf, max id), which reproduces the
+// 8-byte accesses): key (r_key(s), id) with dead items mapped to (0, max id), which reproduces the
 // (alive, s desc, id asc) order, plus the item's position; the items are permuted once at the end.
 // n_used (optional, one block only): sort just the smallest power of two holding the *n_used
 // leading entries (the rest is dead padding, already in its place at the end).
 __global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned block, unsigned kk_from, unsigned kk_to,
                                                          const unsigned *n_used) {
-  __shared__ double ks[BITONIC_SMEM];
+  __shared__ unsigned long long ks[BITONIC_SMEM];
   __shared__ long long kid[BITONIC_SMEM];
   __shared__ unsigned short ix[BITONIC_SMEM];
   if (n_used) {
@@ -352,7 +372,7 @@ __global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned bloc
   const unsigned base = blockIdx.x * block;
   for (unsigned t = threadIdx.x; t < block; t += blockDim.x) {
     const RItem it = R[base + t];
-    ks[t] = it.alive ? it.s : -INFINITY;
+    ks[t] = it.alive ? r_key(it.s) : 0ull;
     kid[t] = it.alive ? it.id : 0x7fffffffffffffffLL;
     ix[t] = (unsigned short)t;
   }
@@ -363,7 +383,7 @@ __global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned bloc
         const unsigned t = ((h & ~(j - 1)) << 1) | (h & (j - 1));  // the pair (t, t + j)
         const unsigned l = t + j;
         const bool up = (((base + t) & kk) == 0);
-        const double sa = ks[t], sb = ks[l];
+        const unsigned long long sa = ks[t], sb = ks[l];
         const long long ia = kid[t], ib = kid[l];
         const bool b_first = (sb > sa) || (sb == sa && ib < ia);
         const bool a_first = (sa > sb) || (sa == sb && ia < ib);
@@ -435,7 +455,8 @@ cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t 
   }
   if (n_pow2 <= BITONIC_SMEM) {
     apx_count_launch();
-    k_bitonic_shared<<<1, 1024, 0, st>>>(R, n_pow2, 2, n_pow2, n_dev);
+    // one thread per compare-exchange pair (fewer idle warps at every barrier)
+    k_bitonic_shared<<<1, std::max(32u, n_pow2 / 2), 0, st>>>(R, n_pow2, 2, n_pow2, n_dev);
     return cudaGetLastError();
   }
   const unsigned nb = n_pow2 / BITONIC_SMEM;
