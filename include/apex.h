@@ -283,6 +283,13 @@ typedef struct {
 } apex_autotune_result_t;
 apex_status apex_autotune(apex_library *lib, const apex_autotune_desc *desc, apex_autotune_result_t *out);
 
+/* Sets the launch shape by hand (the two values apex_autotune picks): compounds per enumeration
+ * launch of the circular pass (chunk_compounds >= 128; the planner rounds it to whole work items,
+ * and a query's first launches stay at most 2^24, 2^26, ... compounds) and rows per CTA tile of
+ * the FP32 kernel over id lists (fp32_id_tile: 32 or 128). Affects launches planned after the call.
+ * APEX_EINVAL for other values. */
+apex_status apex_set_launch_shape(apex_library *lib, int64_t chunk_compounds, int32_t fp32_id_tile);
+
 /* Failure-detection self-test of the bounded device waits. Every wait inside this library's
  * kernels (mbarrier phases between warp roles) gives up after a time limit (2 s in production
  * kernels), records a timeout in the launch's status word and returns; the host then fails the

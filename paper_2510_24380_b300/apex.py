@@ -110,6 +110,7 @@ SYMBOLS = {
     "apex_kernel_launches": [C.POINTER(C.c_int64)],
     "apex_selftest_wait_timeout": [C.c_void_p, C.c_int32],
     "apex_autotune": [C.c_void_p, C.POINTER(AutotuneDesc), C.POINTER(AutotuneResult)],
+    "apex_set_launch_shape": [C.c_void_p, C.c_int64, C.c_int32],
     "apex_save_library": [C.c_void_p, C.c_char_p],
     "apex_load_library_file": [C.c_char_p, C.c_int32, C.c_void_p, C.c_uint64, C.POINTER(C.c_void_p)],
     "apex_associative_embeddings": [C.c_int64, C.POINTER(C.c_int64), C.c_int32, C.c_int32, C.POINTER(C.c_float),
@@ -332,6 +333,10 @@ class Library:
         return {"chunk_compounds": list(r.chunk_compounds)[:n], "chunk_ms": [round(x, 3) for x in list(r.chunk_ms)[:n]],
                 "fp32_id_tile_ms": [round(x, 3) for x in r.fp32_id_tile_ms],
                 "chosen_chunk_compounds": int(r.chosen_chunk_compounds), "chosen_fp32_id_tile": int(r.chosen_fp32_id_tile)}
+
+    def set_launch_shape(self, chunk_compounds: int, fp32_id_tile: int = 32):
+        """Compounds per enumeration launch and FP32 id-list tile rows, by hand (what autotune picks)."""
+        _check(load().apex_set_launch_shape(self.h, int(chunk_compounds), int(fp32_id_tile)), "apex_set_launch_shape")
 
     def selftest_wait_timeout(self, limit_ms: int = 50) -> int:
         """Runs the device-wait self-test; returns the status code (APEX_ETIMEDOUT = -5 expected)."""

@@ -11,6 +11,7 @@
 //           finalized: exact selection (FP32 rescore of the candidates, FP64 rescore of the
 //           boundary band and of near-ties), ordering by (objective desc, id asc), decode.
 #include <algorithm>
+#include <climits>
 #include <atomic>
 #include <cstdarg>
 #include <chrono>
@@ -1416,17 +1417,24 @@ static void pass_step(apex_library &L) {
     const int t = (int)(std::upper_bound(L.item_first.begin(), L.item_first.end(), cur) - L.item_first.begin()) - 1;
     const long long b = cur - L.item_first[t];
     const long long e = L.rx[t].n_items;
+    // a query is served only the items it still lacks: its unvisited items are exactly the next
+    // `remaining` items of its reactions in circular order from the cursor, so a segment never
+    // reaches past the end of its cycle (no compound is enumerated twice for it)
     unsigned long long mask[5] = {0, 0, 0, 0, 0};
+    long long lack = LLONG_MAX;
     for (int s = 0; s < APEX_MAX_ACTIVE; ++s) {
       QueryRec *q = L.active[s];
-      if (q && q->remaining > 0 && q->need[t]) mask[q->precision] |= 1ull << s;
+      if (q && q->remaining > served[s] && q->need[t]) {
+        mask[q->precision] |= 1ull << s;
+        lack = std::min(lack, q->remaining - served[s]);
+      }
     }
     long long take = e - b;
     const unsigned long long any = mask[0] | mask[1] | mask[3] | mask[4];
     if (any) {
       const long long per_item = (long long)L.rx[t].L_o * APX_TILE;
       const long long room = std::max<long long>(1, (chunk_compounds - served_compounds + per_item - 1) / per_item);
-      take = std::min(take, room);
+      take = std::min(std::min(take, room), lack);
       bool ok = true;
       for (int p = 0; p < 5; ++p)
         if (mask[p] && pb[p].P.n_seg >= APX_MAX_SEG) ok = false;
@@ -1793,6 +1801,15 @@ static double autotune_run(apex_library *L, const apex_autotune_desc *d, uint64_
     if (r != APEX_OK && *rc == APEX_OK) *rc = r;
   }
   return now_ms() - t0;
+}
+
+extern "C" apex_status apex_set_launch_shape(apex_library *L, int64_t chunk_compounds, int32_t fp32_id_tile) {
+  if (!L) return fail(APEX_EINVAL, "NULL library");
+  if (chunk_compounds < APX_TILE) return fail(APEX_EINVAL, "chunk_compounds %lld < %d", (long long)chunk_compounds, APX_TILE);
+  if (fp32_id_tile != 32 && fp32_id_tile != 128) return fail(APEX_EINVAL, "fp32_id_tile must be 32 or 128");
+  L->chunk_compounds.store(chunk_compounds);
+  L->fp32_id_tile.store(fp32_id_tile);
+  return APEX_OK;
 }
 
 extern "C" apex_status apex_autotune(apex_library *L, const apex_autotune_desc *d, apex_autotune_result_t *out) {

@@ -109,6 +109,7 @@ def test_null_arguments(dll):
     assert dll.apex_free_library(None) == 0
     n = C.c_int64()
     assert dll.apex_topk_select(None, None, 10, 0, None, None, C.byref(n), None) == -1
+    assert dll.apex_set_launch_shape(None, 1 << 20, 32) == -1
 
 
 def test_library_file_rejected_before_the_gpu(dll, tmp_path):

@@ -331,6 +331,31 @@ def test_associative_embeddings_match_oracle():
     assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), scale)) <= FP32_REL
 
 
+def test_many_launch_pass_matches_one_launch(ragged):
+    """A pass cut into many small launches (launch ramp, selects between launches, launches retired
+    without a host synchronization each) returns exactly what one launch returns, alone and with a
+    second query in the same launches; bad shapes are rejected."""
+    lib, head, spec, L, rms = ragged
+    stats = csl_gen.load_stats("t_ragged")
+    qa = csl_gen.query_single("t_ragged", spec, stats, precision="fp16")
+    qb = csl_gen.Query(qa.weights[::-1].copy(), qa.cons_idx, qa.lo, qa.hi, 37, None, "fp16")
+    ref_a, ref_b = L.run(qa), L.run(qb)
+    try:
+        L.set_launch_shape(2048, 32)
+        ra = L.run(qa)
+        assert L.stats(-1)["n_launches"] > 4
+        assert np.array_equal(ra["ids"], ref_a["ids"]) and np.array_equal(ra["objective"], ref_a["objective"])
+        ia, ib = L.query(qa), L.query(qb)
+        ra, rb = L.fetch(ia, qa.k), L.fetch(ib, qb.k)
+        assert np.array_equal(ra["ids"], ref_a["ids"]) and np.array_equal(rb["ids"], ref_b["ids"])
+        with pytest.raises(apex.ApexError):
+            L.set_launch_shape(64, 32)
+        with pytest.raises(apex.ApexError):
+            L.set_launch_shape(1 << 20, 48)
+    finally:
+        L.set_launch_shape(1 << 25, 32)
+
+
 def test_library_file_round_trip(ragged, tmp_path):
     """save -> load from file: same margins (restored, not recalibrated) and identical results."""
     lib, head, spec, L, rms = ragged
