@@ -1397,6 +1397,7 @@ static void finish(apex_library &L, QueryRec *q, QState st, apex_status err, con
 // One step of the circular pass: a launch over the next chunk of items needed by any active
 // query (per precision), then the conditional select of the served queries.
 static void pass_step(apex_library &L) {
+  const double t_p0 = trace_on() ? now_ms() : 0.0;
   // a linear head costs ~100x less per compound than the MLP: larger launches. A query's first
   // launches are small and grow 4x per launch (2^24, 2^26, ...): its admission threshold is only
   // a sampled guess until the select after a launch raises it, and a large first launch at a loose
@@ -1458,9 +1459,11 @@ static void pass_step(apex_library &L) {
     if (q->stats.n_launches == 0 && q->stats.n_restarts == 0) CU(cudaEventRecord(q->ev0, L.st));
   }
   const int ring = (int)(L.launch_seq++ % apex_library::kRing);
+  const double t_p1 = trace_on() ? now_ms() : 0.0;
   CU(cudaEventRecord(L.ev_l0[ring], L.st));
   for (int p = 0; p < 5; ++p) launch_enum(L, pb[p].P, p);
   CU(cudaEventRecord(L.ev_l1[ring], L.st));
+  TRACE("pass step: plan %.3f ms, launch %.3f ms", t_p1 - t_p0, now_ms() - t_p1);
   // select between launches only for queries with work left (a finished pass is selected by
   // its finalization right after)
   std::vector<int> cont;
