@@ -23,7 +23,9 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <pthread.h>
 #include <random>
+#include <sched.h>
 #include <string>
 #include <thread>
 #include <vector>
@@ -32,7 +34,8 @@
 
 // ------------------------------------------------------------------ kernels (other files)
 cudaError_t apx_launch_fp32(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, const long long *ids,
-                            long long n_ids, float *out, int grid, cudaStream_t st, int id_tile = 32);
+                            long long n_ids, float *out, int grid, cudaStream_t st, int id_tile = 32,
+                            const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_fp64(const DevTables &T, const long long *ids, long long n, double *out, cudaStream_t st,
                             const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_prep(const float *U, const float *W1, const float *b1, const unsigned char *bias_row,
@@ -47,12 +50,12 @@ cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *sl
                           cudaStream_t st, int fmt);
 cudaError_t apx_launch_slot_select(QuerySlot *slots, const int *slot_list, int n_slots, int mode, cudaStream_t st);
 cudaError_t apx_launch_eval32(const EvalArgs &a, long long n, float *f32, unsigned char *maybe, unsigned char *sure,
-                              cudaStream_t st);
+                              cudaStream_t st, const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_kth(const float *keys, const unsigned char *flag, long long n, long long k, float *out_tau,
-                           int *out_ok, cudaStream_t st);
+                           int *out_ok, cudaStream_t st, const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
                                const unsigned char *sure, const float *tau32, float margin2, RItem *R, unsigned *n_r,
-                               cudaStream_t st);
+                               cudaStream_t st, const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64, cudaStream_t st);
 cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, const unsigned *n64_dev,
                                int n_out, const QuerySlot *Q, const double *lo, const double *hi, double *out_rows,
@@ -112,6 +115,39 @@ void apx_count_launch(long long n) { g_launches += n; }
 
 static double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static inline void cpu_relax() {
+#if defined(__x86_64__) || defined(__i386__)
+  __builtin_ia32_pause();
+#endif
+}
+// Watches an atomic counter until it moves away from seq (true) or limit_ms pass (false). The CPU
+// is offered to other threads every yield_mask + 1 checks.
+static bool watch(const std::atomic<unsigned long long> &c, unsigned long long seq, double limit_ms, int yield_mask) {
+  const double t0 = now_ms();
+  for (int i = 0;; ++i) {
+    if (c.load(std::memory_order_acquire) != seq) return true;
+    if ((i & yield_mask) == yield_mask) {
+      if (now_ms() - t0 >= limit_ms) return false;
+      sched_yield();
+    }
+    cpu_relax();
+  }
+}
+static double env_ms(const char *name, double dflt) {
+  const char *e = getenv(name);
+  return e ? std::max(0.0, atof(e)) : dflt;
+}
+// How long the idle worker watches for work before it sleeps (APEX_WORKER_SPIN_MS, default 3) and
+// how long a fetcher watches for completions before it sleeps (APEX_FETCH_SPIN_MS, default 20).
+static double worker_spin_ms() {
+  static const double v = env_ms("APEX_WORKER_SPIN_MS", 3.0);
+  return v;
+}
+static double fetch_spin_ms() {
+  static const double v = env_ms("APEX_FETCH_SPIN_MS", 20.0);
+  return v;
 }
 
 // ------------------------------------------------------------------ query record
@@ -195,6 +231,12 @@ struct apex_library {
   std::map<apex_query_id, std::unique_ptr<QueryRec>> queries;
   QueryRec *active[APEX_MAX_ACTIVE] = {nullptr};
   std::atomic<long long> next_id{1};
+  // Wake-ups without a sleep on the short path: the idle worker watches work_seq (bumped under mu
+  // with every submission, cancellation and shutdown) for a few milliseconds before it sleeps on
+  // cv, and up to two fetchers watch done_seq (bumped under mu when a query finishes) before they
+  // sleep on cv_done. A thread woken from a sleep starts tens of microseconds later.
+  std::atomic<unsigned long long> work_seq{0}, done_seq{0};
+  int spinners = 0;  // fetchers watching done_seq (under mu)
   long long cursor = 0;  // global item index of the circular pass
   apex_query_stats_t last_stats{};
   std::mt19937_64 rng;
@@ -209,6 +251,15 @@ struct apex_library {
   size_t arena_cap = 0, arena_off = 0;
   char *pinned = nullptr;
   size_t pinned_cap = 0;
+  // Pinned upload ring: every small host-to-device copy of the worker (slot parameters, slot
+  // lists, sample scope, boxes) is staged in its own region, so a copy still queued behind a
+  // running launch never sees a later overwrite; the ring wraps only after a stream sync.
+  char *up = nullptr;
+  size_t up_cap = 0, up_off = 0;
+  // Pinned download area of one batch of finalizations (results land here; each query of the
+  // batch owns its region until the host has taken its rows).
+  char *dl = nullptr;
+  size_t dl_cap = 0, dl_off = 0;
   // Enumeration launches whose completion the worker has not observed yet. The worker keeps at
   // most one launch queued behind the running one (it plans launch i + 1 while launch i runs) and
   // reads each launch's kernel status word and duration from a pinned copy when it retires.
@@ -219,6 +270,7 @@ struct apex_library {
   };
   cudaEvent_t ev_l0[kRing] = {}, ev_l1[kRing] = {}, ev_ls[kRing] = {};
   int *status_pin = nullptr;
+  cudaEvent_t ev_tr[8] = {};  // GPU timeline marks of a query's phases (APEX_TRACE only)
   std::deque<InFlight> inflight;
   long long launch_seq = 0;
 
@@ -255,6 +307,40 @@ struct apex_library {
     CU(cudaMalloc(&arena, want));
     query_bytes += want - arena_cap;
     arena_cap = want;
+  }
+  void upload(void *dst, const void *src, size_t n) {
+    if (n == 0) return;
+    const size_t a = (n + 63) & ~(size_t)63;
+    if (a > up_cap) {
+      CU(cudaStreamSynchronize(st));
+      if (up) cudaFreeHost(up);
+      up = nullptr;
+      up_cap = std::max(a, (size_t)(1u << 20));
+      CU(cudaMallocHost(&up, up_cap));
+      up_off = 0;
+    } else if (up_off + a > up_cap) {
+      CU(cudaStreamSynchronize(st));
+      up_off = 0;
+    }
+    memcpy(up + up_off, src, n);
+    CU(cudaMemcpyAsync(dst, up + up_off, n, cudaMemcpyHostToDevice, st));
+    up_off += a;
+  }
+  void dl_reserve(size_t n) {
+    dl_off = 0;
+    if (n <= dl_cap) return;
+    CU(cudaStreamSynchronize(st));
+    if (dl) cudaFreeHost(dl);
+    dl = nullptr;
+    dl_cap = std::max(n + (n >> 1), (size_t)(1u << 20));
+    CU(cudaMallocHost(&dl, dl_cap));
+  }
+  void *dl_get(size_t n) {
+    n = (n + 63) & ~(size_t)63;
+    if (dl_off + n > dl_cap) throw CudaFail(cudaErrorMemoryAllocation, "download area exhausted", __LINE__);
+    void *p = dl + dl_off;
+    dl_off += n;
+    return p;
   }
   void *pin(size_t n) {
     if (n > pinned_cap) {
@@ -432,6 +518,16 @@ static bool trace_on() {
       fputc('\n', stderr);                 \
     }                                       \
   } while (0)
+
+// GPU timeline mark i of the current query (APEX_TRACE only)
+static void tmark(apex_library &L, int i) {
+  if (L.ev_tr[i]) CU(cudaEventRecord(L.ev_tr[i], L.st));
+}
+static float tspan(apex_library &L, cudaEvent_t a, cudaEvent_t b) {
+  float ms = -1.f;
+  if (a && b && cudaEventElapsedTime(&ms, a, b) != cudaSuccess) ms = -1.f;
+  return ms;
+}
 
 // Retires the oldest enumeration launch in flight: waits for its status copy, raises a device-side
 // wait timeout as an error, and adds the launch's duration to the queries it served.
@@ -801,6 +897,8 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
       CU(cudaEventCreateWithFlags(&L->ev_ls[i], cudaEventDisableTiming));
     }
     CU(cudaMallocHost(&L->status_pin, sizeof(int) * apex_library::kRing));
+    if (trace_on())
+      for (auto &e : L->ev_tr) CU(cudaEventCreate(&e));
     L->pin(1 << 20);
     CU(cudaStreamSynchronize(L->st));
     if (cal) {
@@ -835,6 +933,7 @@ extern "C" apex_status apex_free_library(apex_library *L) {
   {
     std::lock_guard<std::mutex> g(L->mu);
     L->stop = true;
+    L->work_seq++;
   }
   L->cv.notify_all();
   if (L->worker.joinable()) L->worker.join();
@@ -854,12 +953,16 @@ extern "C" apex_status apex_free_library(apex_library *L) {
     }
   if (L->arena) cudaFree(L->arena);
   if (L->pinned) cudaFreeHost(L->pinned);
+  if (L->up) cudaFreeHost(L->up);
+  if (L->dl) cudaFreeHost(L->dl);
   for (int i = 0; i < apex_library::kRing; ++i) {
     if (L->ev_l0[i]) cudaEventDestroy(L->ev_l0[i]);
     if (L->ev_l1[i]) cudaEventDestroy(L->ev_l1[i]);
     if (L->ev_ls[i]) cudaEventDestroy(L->ev_ls[i]);
   }
   if (L->status_pin) cudaFreeHost(L->status_pin);
+  for (auto &e : L->ev_tr)
+    if (e) cudaEventDestroy(e);
   L->release_all();
   if (L->own_stream) cudaStreamDestroy(L->st);
   delete L;
@@ -971,6 +1074,7 @@ extern "C" apex_status apex_query(apex_library *L, const apex_query_desc *Dq, ap
     if (L->stop) return fail(APEX_ECANCELED, "library is shutting down");
     L->queued.push_back(q.get());
     L->queries[id] = std::move(q);
+    L->work_seq++;
   }
   L->cv.notify_all();
   *out = id;
@@ -983,6 +1087,7 @@ extern "C" apex_status apex_cancel(apex_library *L, apex_query_id id) {
   auto it = L->queries.find(id);
   if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found", (long long)id);
   it->second->cancel = true;
+  L->work_seq++;
   L->cv.notify_all();
   return APEX_OK;
 }
@@ -1030,7 +1135,7 @@ static void write_slot(apex_library &L, QueryRec *q, float admit) {
   S.ids = q->ids;
   S.keys2 = q->keys2;
   S.ids2 = q->ids2;
-  CU(cudaMemcpyAsync(L.d_slots + q->slot, &S, sizeof(S), cudaMemcpyHostToDevice, L.st));
+  L.upload(L.d_slots + q->slot, &S, sizeof(S));
 }
 
 
@@ -1068,9 +1173,8 @@ static bool speculative_start(apex_library &L, QueryRec *q, double margin2) {
   float *d_out = (float *)L.aget(sizeof(float) * S * no);
   float *d_keys = (float *)L.aget(sizeof(float) * S);
   unsigned char *d_flag = (unsigned char *)L.aget(S);
-  // pageable sources: the copies are staged before the calls return
-  CU(cudaMemcpyAsync(d_rxn, q->subset.data(), sizeof(int) * n_sub, cudaMemcpyHostToDevice, L.st));
-  CU(cudaMemcpyAsync(d_pre, pre.data(), sizeof(long long) * (n_sub + 1), cudaMemcpyHostToDevice, L.st));
+  L.upload(d_rxn, q->subset.data(), sizeof(int) * n_sub);
+  L.upload(d_pre, pre.data(), sizeof(long long) * (n_sub + 1));
   CU(apx_launch_spec_ids(d_rxn, d_pre, n_sub, L.T_.id_first, q->scope_n, L.rng(), S, d_ids, L.st));
   if (fmt >= 0) {  // the kernel applies the query's exact boxes and objective: one key per sample
     CU(apx_launch_tc_ids(L.T_, d_ids, S, d_out, L.d_err, L.n_sm, L.st, fmt, L.d_slots, q->slot));
@@ -1107,10 +1211,12 @@ static double pass_delta_f(const apex_library &L, const QueryRec *q) {
 }
 
 static void start_query(apex_library &L, QueryRec *q) {
+  tmark(L, 0);
   const double df = pass_delta_f(L, q);
   q->tau_spec = -INFINITY;  // the device-side guess lands in the slot; finalization reads it back
   write_slot(L, q, -INFINITY);
   speculative_start(L, q, 2.0 * df * 1.0001);
+  tmark(L, 1);
   q->remaining = q->scope_items;
   q->started = true;
 }
@@ -1184,21 +1290,194 @@ struct DevBuf {
   }
 };
 
-// returns false when the query must restart (start guess too high or candidate overflow)
-static bool finalize(apex_library &L, QueryRec *q) {
-  const double t_f0 = now_ms();
+// A query's finalization after its pass: the slot's last select (threshold raise and
+// compaction), then on the device the FP32 rescore of the candidates, their FP32 decisions, the
+// result set R, the FP64 rescore of R's boundary band, the ordering of R and the final rows,
+// copied to pinned host memory. The chain is queued right behind the pass's last launch, before
+// the candidate count is known: it covers up to `cover` candidates and every kernel reads the
+// actual count from the slot, so the host waits once per query. After that wait the host checks
+// the count and the exactness conditions; a chain that did not fit (count > cover) or whose
+// boundary band moved during its FP64 round is queued again, sized exactly, with further rounds
+// as needed.
+struct FinChain {
+  QueryRec *q = nullptr;
+  int sl = -1;
+  unsigned cover = 0, nr = 0, np = 2, nc1 = 1, n_rows = 0;
+  long long k = 0;
+  double tol = 0;
+  float *out32 = nullptr, *d_tau = nullptr;
+  RItem *R = nullptr;
+  unsigned *d_cnt = nullptr;  // [0] |R|, [1] FP64 batch, [2] newly marked, [3] alive, [4] FP64-rescored
+  long long *ids64 = nullptr;
+  int *pos64 = nullptr;
+  double *o64 = nullptr, *out64 = nullptr, *dlo = nullptr, *dhi = nullptr;
+  long long *e_ids = nullptr, *e_syn = nullptr;
+  int *e_rxn = nullptr;
+  double *e_obj = nullptr, *e_out = nullptr;
+  size_t span = 0;
+  char *h = nullptr;          // pinned copy of the rows [e_ids, e_out + n_rows * n_out)
+  unsigned *h_cnt = nullptr;  // pinned copy of d_cnt
+  QuerySlot *hS = nullptr;    // pinned copy of the slot after its last select
+  int rounds = 0;
+};
+
+static unsigned fin_pow2(unsigned n) {
+  unsigned p = 2;
+  while (p < n) p <<= 1;
+  return p;
+}
+static size_t fin_row_bytes(const apex_library &L) {
+  return 8 + 4 + 8 * APEX_MAX_SLOTS + 8 + 8 * (size_t)L.n_out;
+}
+// device scratch of a chain covering `cover` candidates (256-byte roundings in the slack)
+static size_t fin_arena_bytes(const apex_library &L, const QueryRec *q, unsigned cover) {
+  const size_t ncx = std::max(cover, 1u), no = L.n_out;
+  const size_t kx = (size_t)std::min<long long>(q->k, (long long)ncx);
+  return ncx * (4 * no + 4 + 2 + 8 * no + 8 + 4 + 8 * no) + fin_pow2((unsigned)ncx) * sizeof(RItem) +
+         kx * fin_row_bytes(L) + 64 * 1024;
+}
+// pinned host memory of the same chain: its rows, counters and slot copy
+static size_t fin_pinned_bytes(const apex_library &L, const QueryRec *q, unsigned cover) {
+  const size_t kx = (size_t)std::min<long long>(q->k, (long long)cover);
+  return kx * fin_row_bytes(L) + 5 * 64 + 64 + sizeof(QuerySlot) + 64;
+}
+// candidates an optimistic chain covers: the usual candidate set is a small multiple of k
+static unsigned fin_cover(const QueryRec *q) {
+  const long long c = std::max<long long>(4096, 4 * q->k);
+  return (unsigned)std::min<long long>(c, (long long)q->cap);
+}
+
+// One FP64 round: rescore what is pending (near a box bound, or in the boundary band of the k-th
+// score), re-sort, re-mark the band (the FP64 launch reads its batch size on the device).
+static void fin_round(apex_library &L, FinChain &C) {
+  CU(cudaMemsetAsync(C.d_cnt + 1, 0, sizeof(unsigned) * 2, L.st));
+  CU(apx_launch_collect64(C.R, C.nr, C.ids64, C.pos64, C.d_cnt + 1, L.st));
+  CU(apx_launch_fp64(L.T_, C.ids64, C.nc1, C.o64, L.st, C.d_cnt + 1));
+  CU(apx_launch_apply64(C.R, C.pos64, C.o64, C.nc1, C.d_cnt + 1, L.n_out, L.d_slots + C.sl, C.dlo, C.dhi, C.out64,
+                        L.st));
+  CU(apx_sort_r(C.R, C.np, C.np, L.st, C.d_cnt));
+  CU(apx_launch_mark(C.R, C.nr, (unsigned)std::min<long long>(C.k + 1, C.nr), C.k, C.tol, C.d_cnt + 2, L.st,
+                     C.d_cnt));  // boundary band
+  C.rounds++;
+}
+
+// The final rows, min(k, alive) of them, emitted on the device from the device count, and their
+// copy (with the counters) to pinned host memory. No wait.
+static void fin_emit(apex_library &L, FinChain &C) {
+  CU(cudaMemsetAsync(C.d_cnt + 3, 0, sizeof(unsigned) * 2, L.st));
+  CU(apx_launch_count_alive(C.R, C.nr, C.d_cnt + 3, L.st));
+  CU(apx_launch_emit(C.R, C.n_rows, C.d_cnt + 3, L.T_, C.out32, C.out64, C.e_ids, C.e_rxn, C.e_syn, C.e_obj,
+                     C.e_out, L.st));
+  CU(cudaEventRecord(C.q->ev1, L.st));
+  if (C.span) CU(cudaMemcpyAsync(C.h, C.e_ids, C.span, cudaMemcpyDeviceToHost, L.st));
+  CU(cudaMemcpyAsync(C.h_cnt, C.d_cnt, sizeof(unsigned) * 8, cudaMemcpyDeviceToHost, L.st));
+}
+
+// Queues the chain of query q over up to `cover` candidates (the slot's count, read on the device,
+// decides how many are used). Arena and download area must hold fin_arena_bytes /
+// fin_pinned_bytes for it.
+static void fin_queue(apex_library &L, QueryRec *q, FinChain &C, unsigned cover) {
   const int no = L.n_out;
-  const int sl = q->slot;
-  int *pin_sl = (int *)L.pin(sizeof(QuerySlot) + 64);
-  *pin_sl = sl;
-  CU(cudaMemcpyAsync(L.d_slot_list, pin_sl, sizeof(int), cudaMemcpyHostToDevice, L.st));
-  CU(apx_launch_slot_select(L.d_slots, L.d_slot_list, 1, 1, L.st));
-  QuerySlot *pS = (QuerySlot *)((char *)L.pinned + 64);
-  CU(cudaMemcpyAsync(pS, L.d_slots + sl, sizeof(QuerySlot), cudaMemcpyDeviceToHost, L.st));
-  CU(cudaStreamSynchronize(L.st));
-  retire_all(L);  // status of the pass's launches (all complete now)
-  const QuerySlot S = *pS;
-  const double t_f1 = now_ms();
+  C.q = q;
+  C.sl = q->slot;
+  C.cover = cover;
+  C.k = q->k;
+  C.rounds = 0;
+  const unsigned *d_n = &L.d_slots[C.sl].count;
+  const unsigned n1 = std::max(cover, 1u);
+  C.nc1 = n1;
+  // FP32 rescore of the candidates
+  C.out32 = (float *)L.aget(sizeof(float) * n1 * no);
+  if (cover > 0) {
+    LaunchPlan dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    CU(apx_launch_fp32(dummy, L.T_, nullptr, q->ids, cover, C.out32, grid_for(L, (cover + APX_TILE - 1) / APX_TILE),
+                       L.st, L.fp32_id_tile.load(), d_n));
+  }
+  float *f32 = (float *)L.aget(sizeof(float) * n1);
+  unsigned char *maybe = (unsigned char *)L.aget(n1);
+  unsigned char *sure = (unsigned char *)L.aget(n1);
+  const int m = (int)q->cidx.size();
+  C.dlo = (double *)L.aget(sizeof(double) * std::max(m, 1));
+  C.dhi = (double *)L.aget(sizeof(double) * std::max(m, 1));
+  if (m > 0) {
+    L.upload(C.dlo, q->lo.data(), sizeof(double) * m);
+    L.upload(C.dhi, q->hi.data(), sizeof(double) * m);
+  }
+  double e32f = 0;
+  for (int j = 0; j < L.n_obj; ++j) e32f += std::fabs((double)q->w[j]) * L.err32[j];
+  EvalArgs ea{C.out32, no, L.d_slots + C.sl, L.d_err32f, (float)e32f, C.dlo, C.dhi};
+  CU(apx_launch_eval32(ea, cover, f32, maybe, sure, L.st, d_n));
+  C.d_tau = (float *)L.aget(sizeof(float));
+  int *d_ok = (int *)L.aget(sizeof(int));
+  CU(apx_launch_kth(f32, sure, cover, C.k, C.d_tau, d_ok, L.st, d_n));
+  // R = the candidates that may reach the FP32 top-k band (threshold taken on the device); |R|
+  // stays on the device: R is padded to np with dead items from the device count and every later
+  // kernel covers np entries (dead ones are skipped)
+  C.np = fin_pow2(n1);
+  C.R = (RItem *)L.aget(sizeof(RItem) * C.np);
+  C.d_cnt = (unsigned *)L.aget(sizeof(unsigned) * 8);
+  CU(cudaMemsetAsync(C.d_cnt, 0, sizeof(unsigned) * 8, L.st));
+  CU(apx_launch_build_r(cover, q->ids, f32, maybe, sure, C.d_tau, (float)(2.0 * e32f * 1.0001), C.R, C.d_cnt, L.st,
+                        d_n));
+  CU(apx_launch_pad_r_dev(C.R, C.d_cnt, C.np, L.st));
+  tmark(L, 3);
+  C.nr = cover > 0 ? C.np : 0;
+  C.out64 = (double *)L.aget(sizeof(double) * n1 * no);
+  C.ids64 = (long long *)L.aget(sizeof(long long) * n1);  // FP64 batches: at most |R| <= count
+  C.pos64 = (int *)L.aget(sizeof(int) * n1);
+  C.o64 = (double *)L.aget(sizeof(double) * n1 * no);
+  C.tol = 2.0 * e32f * 1.0001 + 1e-300;
+  C.n_rows = (unsigned)std::min<long long>(C.k, cover);
+  C.span = 0;
+  if (C.n_rows > 0) {
+    C.e_ids = (long long *)L.aget(sizeof(long long) * C.n_rows);
+    C.e_rxn = (int *)L.aget(sizeof(int) * C.n_rows);
+    C.e_syn = (long long *)L.aget(sizeof(long long) * C.n_rows * APEX_MAX_SLOTS);
+    C.e_obj = (double *)L.aget(sizeof(double) * C.n_rows);
+    C.e_out = (double *)L.aget(sizeof(double) * C.n_rows * no);
+    C.span = (size_t)((char *)(C.e_out + (size_t)C.n_rows * no) - (char *)C.e_ids);
+  }
+  C.h = (char *)L.dl_get(std::max<size_t>(C.span, 1));
+  C.h_cnt = (unsigned *)L.dl_get(sizeof(unsigned) * 8);
+  // the band around the FP32 k-th score is marked before the first round, so one round usually
+  // settles it
+  if (C.nr > 0) {
+    CU(apx_launch_mark_near(C.R, C.nr, C.d_tau, C.tol, C.d_cnt + 2, L.st));
+    fin_round(L, C);
+  }
+  tmark(L, 4);
+  fin_emit(L, C);
+}
+
+// Copies the rows of a finished chain into the query record.
+static void fin_take(apex_library &L, FinChain &C) {
+  QueryRec *q = C.q;
+  const int no = L.n_out;
+  q->stats.n_rescored_fp64 = C.nr > 0 ? (long long)C.h_cnt[4] : 0;
+  const long long alive = C.nr > 0 ? (long long)C.h_cnt[3] : 0;
+  const long long nf = std::min<long long>(C.k, alive);
+  q->r_ids.resize(nf);
+  q->r_rxn.resize(nf);
+  q->r_syn.resize(nf * APEX_MAX_SLOTS);
+  q->r_obj.resize(nf);
+  q->r_out.resize(nf * no);
+  if (nf > 0) {
+    const char *b = (const char *)C.e_ids;
+    memcpy(q->r_ids.data(), C.h, sizeof(long long) * nf);
+    memcpy(q->r_rxn.data(), C.h + ((const char *)C.e_rxn - b), sizeof(int) * nf);
+    memcpy(q->r_syn.data(), C.h + ((const char *)C.e_syn - b), sizeof(long long) * nf * APEX_MAX_SLOTS);
+    memcpy(q->r_obj.data(), C.h + ((const char *)C.e_obj - b), sizeof(double) * nf);
+    memcpy(q->r_out.data(), C.h + ((const char *)C.e_out - b), sizeof(double) * nf * no);
+  }
+  q->stats.n_feasible_lower = nf;
+}
+
+// Decides from the slot after its last select whether the query must run its pass again: the
+// start guess was too high (fewer than k sure entries reach it) or the candidate buffer
+// overflowed with a possible member of the top-k dropped.
+static bool fin_needs_restart(const apex_library &L, const QueryRec *q, const QuerySlot &S, bool *spec_bad_out,
+                              bool *overflow_out) {
   const bool spec_bad = std::isfinite(S.tau_spec) && (long long)S.n_sure_above_spec < q->k;
   // An overflow is harmless when every dropped candidate's pass key lies below tau - 2 delta_f:
   // every member of the exact top-k has a pass key at or above that (k surely feasible compounds
@@ -1213,169 +1492,127 @@ static bool finalize(apex_library &L, QueryRec *q) {
     TRACE("overflow q%lld: dropped max %g, tau %g -> %s", (long long)q->id, (double)dropped_max, (double)S.tau,
           overflow ? "rerun" : "harmless");
   }
-  if (overflow || spec_bad) {
-    q->stats.n_restarts++;
-    const double df = pass_delta_f(L, q);
-    bool device_guess = false;
-    if (overflow) {
-      // the band above the best valid threshold did not fit: more room, and restart from the
-      // largest valid threshold found (k real, surely feasible compounds reach S.tau)
-      q->cap = (unsigned)std::min<unsigned long long>((unsigned long long)q->cap * 4ull, 1ull << 30);
-      bind_slot(L, q);
-      if (std::isfinite(S.tau) && !spec_bad) {
-        q->tau_spec = S.tau;
-      } else {
-        q->tau_spec = -INFINITY;
-        q->spec_rank = -1;
-      }
+  *spec_bad_out = spec_bad;
+  *overflow_out = overflow;
+  return spec_bad || overflow;
+}
+
+// Prepares the restart of a query's pass (after fin_needs_restart said so).
+static void fin_restart(apex_library &L, QueryRec *q, const QuerySlot &S, bool spec_bad, bool overflow) {
+  q->stats.n_restarts++;
+  const double df = pass_delta_f(L, q);
+  bool device_guess = false;
+  if (overflow) {
+    // the band above the best valid threshold did not fit: more room, and restart from the
+    // largest valid threshold found (k real, surely feasible compounds reach S.tau)
+    q->cap = (unsigned)std::min<unsigned long long>((unsigned long long)q->cap * 4ull, 1ull << 30);
+    bind_slot(L, q);
+    if (std::isfinite(S.tau) && !spec_bad) {
+      q->tau_spec = S.tau;
     } else {
-      q->spec_rank = q->spec_rank > 0 ? q->spec_rank * 8 : -1;  // the start guess was too high: lower it
       q->tau_spec = -INFINITY;
-      device_guess = q->spec_rank > 0;
+      q->spec_rank = -1;
     }
-    write_slot(L, q, std::isfinite(q->tau_spec) ? (float)(q->tau_spec - 2.0 * df * 1.0001) : -INFINITY);
-    if (device_guess) speculative_start(L, q, 2.0 * df * 1.0001);
-    q->remaining = q->scope_items;
-    TRACE("restart q%lld: overflow=%u spec_bad=%d cap=%u tau_spec=%g rank=%d", (long long)q->id, S.overflow,
-          (int)spec_bad, q->cap, (double)S.tau_spec, q->spec_rank);
-    return false;
+  } else {
+    q->spec_rank = q->spec_rank > 0 ? q->spec_rank * 8 : -1;  // the start guess was too high: lower it
+    q->tau_spec = -INFINITY;
+    device_guess = q->spec_rank > 0;
   }
-  const long long nc = S.count;
-  {
-    // worst-case scratch of this finalization, reserved before anything is queued on it
-    const size_t ncx = (size_t)std::max<long long>(nc, 1);
-    size_t np2 = 2;
-    while (np2 < ncx) np2 <<= 1;
-    const size_t kx = (size_t)std::min<long long>(q->k, (long long)ncx);
-    L.arena_reserve(ncx * (4 * L.n_out + 4 + 2 + 8 * L.n_out + 8 + 4 + 8 * L.n_out) + np2 * sizeof(RItem) +
-                    kx * (8 + 4 + 8 * APEX_MAX_SLOTS + 8 + 8 * L.n_out) + 64 * 1024);
-  }
-  struct ArenaBuf {
-    apex_library &L;
-    void *get(size_t n) { return L.aget(n); }
-  } B{L};
-  q->stats.n_candidates = nc;
-  const long long k = q->k;
-  // FP32 rescore of the candidates
-  float *out32 = (float *)B.get(sizeof(float) * std::max<long long>(nc, 1) * no);
-  if (nc > 0) {
-    LaunchPlan dummy;
-    memset(&dummy, 0, sizeof(dummy));
-    CU(apx_launch_fp32(dummy, L.T_, nullptr, q->ids, nc, out32, grid_for(L, (nc + APX_TILE - 1) / APX_TILE), L.st,
-                       L.fp32_id_tile.load()));
-  }
-  float *f32 = (float *)B.get(sizeof(float) * std::max<long long>(nc, 1));
-  unsigned char *maybe = (unsigned char *)B.get(std::max<long long>(nc, 1));
-  unsigned char *sure = (unsigned char *)B.get(std::max<long long>(nc, 1));
-  const int m = (int)q->cidx.size();
-  double *dlo = (double *)B.get(sizeof(double) * std::max(m, 1));
-  double *dhi = (double *)B.get(sizeof(double) * std::max(m, 1));
-  if (m > 0) {
-    CU(cudaMemcpyAsync(dlo, q->lo.data(), sizeof(double) * m, cudaMemcpyHostToDevice, L.st));
-    CU(cudaMemcpyAsync(dhi, q->hi.data(), sizeof(double) * m, cudaMemcpyHostToDevice, L.st));
-  }
-  double e32f = 0;
-  for (int j = 0; j < L.n_obj; ++j) e32f += std::fabs((double)q->w[j]) * L.err32[j];
-  EvalArgs ea{out32, no, L.d_slots + sl, L.d_err32f, (float)e32f, dlo, dhi};
-  CU(apx_launch_eval32(ea, nc, f32, maybe, sure, L.st));
-  float *d_tau = (float *)B.get(sizeof(float));
-  int *d_ok = (int *)B.get(sizeof(int));
-  CU(apx_launch_kth(f32, sure, nc, k, d_tau, d_ok, L.st));
-  // R = the candidates that may reach the FP32 top-k band (threshold taken on the device)
-  unsigned n_pow2 = 1;
-  while (n_pow2 < (unsigned)std::max<long long>(nc, 1)) n_pow2 <<= 1;
-  n_pow2 = std::max(n_pow2, 2u);
-  RItem *R = (RItem *)B.get(sizeof(RItem) * n_pow2);
-  // device counters: [0] |R|, [1] FP64 batch, [2] newly marked, [3] alive, [4] FP64-rescored
-  unsigned *d_cnt = (unsigned *)B.get(sizeof(unsigned) * 8);
-  CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned) * 8, L.st));
-  CU(apx_launch_build_r(nc, q->ids, f32, maybe, sure, d_tau, (float)(2.0 * e32f * 1.0001), R, d_cnt, L.st));
-  // |R| stays on the device: R is padded to n_pow2 with dead items from the device count and
-  // every later kernel covers n_pow2 entries (dead ones are skipped), with no host round trip
-  CU(apx_launch_pad_r_dev(R, d_cnt, n_pow2, L.st));
-  const unsigned nr = nc > 0 ? n_pow2 : 0;  // entries of R the kernels cover
-  const unsigned nc1 = (unsigned)std::max<long long>(nc, 1);
-  const double t_f3 = now_ms();
-  const double t_f2 = t_f3;
-  const unsigned np = n_pow2;
-  double *out64 = (double *)B.get(sizeof(double) * nc1 * no);
-  long long *ids64 = (long long *)B.get(sizeof(long long) * nc1);  // FP64 batches: at most |R| <= nc
-  int *pos64 = (int *)B.get(sizeof(int) * nc1);
-  double *o64 = (double *)B.get(sizeof(double) * nc1 * no);
-  const double tol = 2.0 * e32f * 1.0001 + 1e-300;
-  // FP64 rounds: rescore what is pending (near a box bound, or in the boundary band of the k-th
-  // score), re-sort, re-mark the band. The band is marked once before the first round, so one
-  // round usually settles it; that round is queued without host synchronization (the FP64
-  // launch reads its batch size on the device), and further rounds run only when the last one
-  // still marked new entries.
-  auto fp64_round = [&]() {
-    CU(cudaMemsetAsync(d_cnt + 1, 0, sizeof(unsigned) * 2, L.st));
-    CU(apx_launch_collect64(R, nr, ids64, pos64, d_cnt + 1, L.st));
-    CU(apx_launch_fp64(L.T_, ids64, nc1, o64, L.st, d_cnt + 1));
-    CU(apx_launch_apply64(R, pos64, o64, nc1, d_cnt + 1, no, L.d_slots + sl, dlo, dhi, out64, L.st));
-    CU(apx_sort_r(R, np, np, L.st, d_cnt));
-    CU(apx_launch_mark(R, nr, (unsigned)std::min<long long>(k + 1, nr), k, tol, d_cnt + 2, L.st, d_cnt));  // boundary band
-  };
-  // final rows: min(k, alive) of them, emitted on the device from the device count
-  const unsigned n_rows = (unsigned)std::min<long long>(k, nc);
-  long long *e_ids = nullptr;
-  int *e_rxn = nullptr;
-  long long *e_syn = nullptr;
-  double *e_obj = nullptr, *e_out = nullptr;
-  char *e_base = nullptr, *e_end = nullptr;
-  if (n_rows > 0) {
-    e_ids = (long long *)B.get(sizeof(long long) * n_rows);
-    e_rxn = (int *)B.get(sizeof(int) * n_rows);
-    e_syn = (long long *)B.get(sizeof(long long) * n_rows * APEX_MAX_SLOTS);
-    e_obj = (double *)B.get(sizeof(double) * n_rows);
-    e_out = (double *)B.get(sizeof(double) * n_rows * no);
-    e_base = (char *)e_ids;
-    e_end = (char *)e_out + sizeof(double) * n_rows * no;
-  }
-  const size_t span = (size_t)(e_end - e_base);
-  char *h = (char *)L.pin(span + 128);
-  unsigned *h_cnt = (unsigned *)(h + ((span + 63) & ~(size_t)63));  // counters land after the rows
-  auto emit_and_read = [&]() {
-    CU(cudaMemsetAsync(d_cnt + 3, 0, sizeof(unsigned) * 2, L.st));
-    CU(apx_launch_count_alive(R, nr, d_cnt + 3, L.st));
-    CU(apx_launch_emit(R, n_rows, d_cnt + 3, L.T_, out32, out64, e_ids, e_rxn, e_syn, e_obj, e_out, L.st));
-    CU(cudaEventRecord(q->ev1, L.st));
-    if (span) CU(cudaMemcpyAsync(h, e_base, span, cudaMemcpyDeviceToHost, L.st));
-    CU(cudaMemcpyAsync(h_cnt, d_cnt, sizeof(unsigned) * 8, cudaMemcpyDeviceToHost, L.st));
+  write_slot(L, q, std::isfinite(q->tau_spec) ? (float)(q->tau_spec - 2.0 * df * 1.0001) : -INFINITY);
+  if (device_guess) speculative_start(L, q, 2.0 * df * 1.0001);
+  q->remaining = q->scope_items;
+  TRACE("restart q%lld: overflow=%u spec_bad=%d cap=%u tau_spec=%g rank=%d", (long long)q->id, S.overflow,
+        (int)spec_bad, q->cap, (double)S.tau_spec, q->spec_rank);
+}
+
+// The chain of one query sized exactly (its count known), waited for, with further FP64 rounds
+// while the boundary band still moves.
+static void fin_exact(apex_library &L, QueryRec *q, unsigned nc) {
+  L.arena_reserve(fin_arena_bytes(L, q, nc));
+  L.dl_reserve(fin_pinned_bytes(L, q, nc));
+  FinChain C;
+  fin_queue(L, q, C, nc);
+  CU(cudaStreamSynchronize(L.st));
+  while (C.nr > 0 && C.h_cnt[2] > 0 && C.rounds < 8) {  // rare: the band moved in the last round
+    fin_round(L, C);
+    fin_emit(L, C);
     CU(cudaStreamSynchronize(L.st));
-  };
-  int rounds = 0;
-  if (nr > 0) {
-    CU(apx_launch_mark_near(R, nr, d_tau, tol, d_cnt + 2, L.st));  // band around the FP32 k-th score
-    fp64_round();
-    rounds = 1;
   }
-  emit_and_read();
-  while (nr > 0 && h_cnt[2] > 0 && rounds < 8) {  // rare: the band moved in the last round
-    fp64_round();
-    ++rounds;
-    emit_and_read();
+  fin_take(L, C);
+  TRACE("finalize q%lld exactly: nc %u rounds %d", (long long)q->id, nc, C.rounds);
+}
+
+// Finalizes the queries whose pass has ended (all slots in one select launch, every chain queued,
+// one wait). done[i] = true when qs[i] has its rows, false when it restarts its pass.
+static void finalize_batch(apex_library &L, const std::vector<QueryRec *> &qs, std::vector<char> &done) {
+  const double t_f0 = now_ms();
+  const size_t n = qs.size();
+  done.assign(n, 0);
+  if (n == 0) return;
+  std::vector<unsigned> cover(n);
+  size_t ab = 0, pb = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cover[i] = fin_cover(qs[i]);
+    ab += fin_arena_bytes(L, qs[i], cover[i]);
+    pb += fin_pinned_bytes(L, qs[i], cover[i]);
   }
-  const double t_f4 = now_ms();
-  q->stats.n_rescored_fp64 = nr > 0 ? (long long)h_cnt[4] : 0;
-  const long long alive = nr > 0 ? (long long)h_cnt[3] : 0;
-  const long long nf = std::min<long long>(k, alive);
-  q->r_ids.resize(nf);
-  q->r_rxn.resize(nf);
-  q->r_syn.resize(nf * APEX_MAX_SLOTS);
-  q->r_obj.resize(nf);
-  q->r_out.resize(nf * no);
-  if (nf > 0) {
-    memcpy(q->r_ids.data(), h + ((char *)e_ids - e_base), sizeof(long long) * nf);
-    memcpy(q->r_rxn.data(), h + ((char *)e_rxn - e_base), sizeof(int) * nf);
-    memcpy(q->r_syn.data(), h + ((char *)e_syn - e_base), sizeof(long long) * nf * APEX_MAX_SLOTS);
-    memcpy(q->r_obj.data(), h + ((char *)e_obj - e_base), sizeof(double) * nf);
-    memcpy(q->r_out.data(), h + ((char *)e_out - e_base), sizeof(double) * nf * no);
+  L.arena_reserve(ab);
+  L.dl_reserve(pb);
+  std::vector<int> slots(n);
+  for (size_t i = 0; i < n; ++i) slots[i] = qs[i]->slot;
+  L.upload(L.d_slot_list, slots.data(), sizeof(int) * n);
+  CU(apx_launch_slot_select(L.d_slots, L.d_slot_list, (int)n, 1, L.st));
+  tmark(L, 2);
+  std::vector<FinChain> C(n);
+  for (size_t i = 0; i < n; ++i) {
+    C[i].hS = (QuerySlot *)L.dl_get(sizeof(QuerySlot));
+    CU(cudaMemcpyAsync(C[i].hS, L.d_slots + slots[i], sizeof(QuerySlot), cudaMemcpyDeviceToHost, L.st));
   }
-  q->stats.n_feasible_lower = nf;
-  TRACE("finalize q%lld: nc %lld nr %u rounds %d | select+read %.3f, rescore32+build_r %.3f, fp64 rounds+emit %.3f ms",
-        (long long)q->id, nc, nc > 0 ? h_cnt[0] : 0u, rounds, t_f1 - t_f0, t_f3 - t_f1, t_f4 - t_f2);
-  return true;
+  for (size_t i = 0; i < n; ++i) fin_queue(L, qs[i], C[i], cover[i]);
+  const double t_f1 = now_ms();
+  CU(cudaStreamSynchronize(L.st));
+  const int last_ring = L.inflight.empty() ? -1 : L.inflight.back().ring;
+  retire_all(L);  // status of the pass's launches (all complete now)
+  const double t_f2 = now_ms();
+  // rows first: a restart or an exact rerun below reuses the arena and the download area
+  std::vector<char> redo(n, 0), sbad(n, 0), ovf(n, 0);
+  std::vector<QuerySlot> Ss(n);
+  std::vector<unsigned> n_r(n, 0);
+  for (size_t i = 0; i < n; ++i) {
+    Ss[i] = *C[i].hS;
+    n_r[i] = C[i].nr > 0 ? C[i].h_cnt[0] : 0u;
+    qs[i]->stats.n_candidates = Ss[i].count;
+    bool sb = false, of = false;
+    if (fin_needs_restart(L, qs[i], Ss[i], &sb, &of)) {
+      redo[i] = 2;
+      sbad[i] = sb;
+      ovf[i] = of;
+    } else if (Ss[i].count > C[i].cover || (C[i].nr > 0 && C[i].h_cnt[2] > 0)) {
+      redo[i] = 1;
+    } else {
+      fin_take(L, C[i]);
+      done[i] = 1;
+    }
+  }
+  for (size_t i = 0; i < n; ++i) {
+    if (redo[i] == 2) {
+      fin_restart(L, qs[i], Ss[i], sbad[i], ovf[i]);
+    } else if (redo[i] == 1) {
+      fin_exact(L, qs[i], Ss[i].count);
+      done[i] = 1;
+    }
+  }
+  if (trace_on())
+    for (size_t i = 0; i < n; ++i) {
+      TRACE("finalize q%lld: nc %u nr %u rounds %d redo %d | queue %.3f, wait %.3f, rest %.3f ms", (long long)qs[i]->id,
+            Ss[i].count, n_r[i], C[i].rounds, (int)redo[i], t_f1 - t_f0, t_f2 - t_f1, now_ms() - t_f2);
+      if (n == 1 && last_ring >= 0)
+        TRACE("gpu q%lld: start %.3f | to enum %.3f | enum %.3f | to select end %.3f | rescore32 %.3f | fp64 %.3f | "
+              "emit %.3f ms",
+              (long long)qs[i]->id, tspan(L, L.ev_tr[0], L.ev_tr[1]), tspan(L, L.ev_tr[1], L.ev_l0[last_ring]),
+              tspan(L, L.ev_l0[last_ring], L.ev_l1[last_ring]), tspan(L, L.ev_l1[last_ring], L.ev_tr[2]),
+              tspan(L, L.ev_tr[2], L.ev_tr[3]), tspan(L, L.ev_tr[3], L.ev_tr[4]), tspan(L, L.ev_tr[4], qs[i]->ev1));
+    }
 }
 
 // ------------------------------------------------------------------ worker: main loop
@@ -1392,6 +1629,7 @@ static void finish(apex_library &L, QueryRec *q, QState st, apex_status err, con
   q->stats.queue_ms = q->t_admit > 0 ? q->t_admit - q->t_submit : 0;
   q->stats.latency_ms = q->t_done - q->t_submit;
   q->stats.n_scope = q->scope_n;
+  L.done_seq++;
 }
 
 // One step of the circular pass: a launch over the next chunk of items needed by any active
@@ -1470,9 +1708,7 @@ static void pass_step(apex_library &L) {
   for (int s : list)
     if (L.active[s]->remaining > served[s]) cont.push_back(s);
   if (!cont.empty()) {
-    int *hl = (int *)L.pin(sizeof(int) * APEX_MAX_ACTIVE + 64);
-    memcpy(hl, cont.data(), sizeof(int) * cont.size());
-    CU(cudaMemcpyAsync(L.d_slot_list, hl, sizeof(int) * cont.size(), cudaMemcpyHostToDevice, L.st));
+    L.upload(L.d_slot_list, cont.data(), sizeof(int) * cont.size());
     CU(apx_launch_slot_select(L.d_slots, L.d_slot_list, (int)cont.size(), 0, L.st));
   }
   // the kernel status word of this launch, read back without waiting for it
@@ -1551,7 +1787,11 @@ static void worker_main(apex_library *Lp) {
         if (L.active[s]) any = true;
       if (!any) {
         retire_quietly(L);
-        L.cv.wait_for(lk, std::chrono::milliseconds(20));
+        const unsigned long long seq = L.work_seq.load();
+        lk.unlock();
+        const bool moved = worker_spin_ms() > 0 && watch(L.work_seq, seq, worker_spin_ms(), 63);
+        lk.lock();
+        if (!moved && L.work_seq.load() == seq) L.cv.wait_for(lk, std::chrono::milliseconds(20));
         continue;
       }
     }
@@ -1568,6 +1808,7 @@ static void worker_main(apex_library *Lp) {
         for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
           if (L.active[s]) L.active[s]->stats.host_pass_ms += dt;
       }
+      std::vector<QueryRec *> ended;
       for (int s = 0; s < APEX_MAX_ACTIVE; ++s) {
         QueryRec *q = L.active[s];
         if (!q || q->remaining > 0) continue;
@@ -1579,16 +1820,23 @@ static void worker_main(apex_library *Lp) {
             continue;
           }
         }
+        ended.push_back(q);
+      }
+      if (!ended.empty()) {
         const double t0 = now_ms();
-        const bool fin = finalize(L, q);
-        q->stats.host_finalize_ms += now_ms() - t0;
-        if (fin) {
+        std::vector<char> done;
+        finalize_batch(L, ended, done);
+        const double dt = now_ms() - t0;
+        std::lock_guard<std::mutex> g(L.mu);
+        for (size_t i = 0; i < ended.size(); ++i) {
+          QueryRec *q = ended[i];
+          q->stats.host_finalize_ms += dt;
+          if (!done[i]) continue;
           float ms = 0;
           if (cudaEventElapsedTime(&ms, q->ev0, q->ev1) == cudaSuccess) q->stats.gpu_ms = ms;
-          std::lock_guard<std::mutex> g(L.mu);
           finish(L, q, Q_DONE, APEX_OK, "");
-          L.cv_done.notify_all();
         }
+        L.cv_done.notify_all();
       }
     } catch (const CudaFail &f) {
       L.inflight.clear();
@@ -1623,10 +1871,29 @@ extern "C" apex_status apex_topk_fetch(apex_library *L, apex_query_id id, int64_
   if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found", (long long)id);
   QueryRec *q = it->second.get();
   auto done = [&] { return q->state == Q_DONE || q->state == Q_CANCELED || q->state == Q_FAILED; };
-  if (timeout_ms < 0)
+  // watch for completions first (no sleep), for at most fetch_spin_ms() or the timeout
+  const double t_w0 = now_ms();
+  const double spin_ms = timeout_ms < 0 ? fetch_spin_ms() : std::min(fetch_spin_ms(), (double)timeout_ms);
+  while (!done() && L->spinners < 2) {
+    const double left = spin_ms - (now_ms() - t_w0);
+    if (left <= 0) break;
+    const unsigned long long seq = L->done_seq.load();
+    L->spinners++;
+    lk.unlock();
+    watch(L->done_seq, seq, left, 63);
+    lk.lock();
+    L->spinners--;
+    it = L->queries.find(id);  // another fetcher of the same id may have taken it meanwhile
+    if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found", (long long)id);
+    q = it->second.get();
+  }
+  if (timeout_ms < 0) {
     L->cv_done.wait(lk, done);
-  else if (!L->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
-    return fail(APEX_EAGAIN, "query %lld not finished", (long long)id);
+  } else {
+    const double left_ms = std::max(0.0, timeout_ms - (now_ms() - t_w0));
+    if (!L->cv_done.wait_for(lk, std::chrono::microseconds((long long)(1000.0 * left_ms)), done))
+      return fail(APEX_EAGAIN, "query %lld not finished", (long long)id);
+  }
   apex_status rc = q->err;
   if (q->state == Q_DONE) {
     const long long n = (long long)q->r_ids.size();

@@ -261,16 +261,18 @@ __device__ void f32_last_small(F32Smem<TM> &S, const DevTables &T, int l) {
   __syncthreads();
 }
 
-// mode 0: enumeration (LaunchPlan); mode 1: ids[0, n_ids) -> out[n_ids x n_out] (FP32 outputs)
+// mode 0: enumeration (LaunchPlan); mode 1: ids[0, n) -> out[n x n_out] (FP32 outputs), n = n_ids, or
+// min(n_ids, *n_dev) when the list's length is a device count
 template <int TM>
 __global__ void __launch_bounds__(APX_SIMT_THREADS, 1)
     k_fp32_head(const __grid_constant__ LaunchPlan L, const __grid_constant__ DevTables T, QuerySlot *slots,
-                const long long *ids, long long n_ids, float *out) {
+                const long long *ids, long long n_ids, float *out, const unsigned *n_dev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   F32Smem<TM> &S = *reinterpret_cast<F32Smem<TM> *>(smem_raw);
   __shared__ bool row_valid[TM];
   __shared__ long long row_id[TM];
   const int mode = (ids != nullptr) ? 1 : 0;
+  if (n_dev && (long long)*n_dev < n_ids) n_ids = *n_dev;  // id list sized on the device
   const int n_out = T.n_out;
   long long n_work = mode == 0 ? L.total_items : (n_ids + TM - 1) / TM;
   for (long long it = blockIdx.x; it < n_work; it += gridDim.x) {
@@ -340,7 +342,7 @@ size_t apx_fp32_smem_bytes() { return sizeof(F32Smem<128>); }
 // Enumeration (ids == nullptr) runs 128-row tiles; id lists run id_tile-row tiles (32 or 128,
 // chosen by the autotuner), min(tiles, 148 * 2) CTAs.
 cudaError_t apx_launch_fp32(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, const long long *ids,
-                            long long n_ids, float *out, int grid, cudaStream_t st, int id_tile) {
+                            long long n_ids, float *out, int grid, cudaStream_t st, int id_tile, const unsigned *n_dev) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_fp32_head<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -353,19 +355,19 @@ cudaError_t apx_launch_fp32(const LaunchPlan &L, const DevTables &T, QuerySlot *
   if (ids == nullptr) {
     if (grid <= 0) return cudaSuccess;
     apx_count_launch();
-    k_fp32_head<128><<<grid, APX_SIMT_THREADS, sizeof(F32Smem<128>), st>>>(L, T, slots, ids, n_ids, out);
+    k_fp32_head<128><<<grid, APX_SIMT_THREADS, sizeof(F32Smem<128>), st>>>(L, T, slots, ids, n_ids, out, n_dev);
   } else if (id_tile == 128) {
     const long long tiles = (n_ids + 127) / 128;
     if (tiles <= 0) return cudaSuccess;
     const int g = (int)(tiles < 148 * 2 ? tiles : 148 * 2);
     apx_count_launch();
-    k_fp32_head<128><<<g, APX_SIMT_THREADS, sizeof(F32Smem<128>), st>>>(L, T, slots, ids, n_ids, out);
+    k_fp32_head<128><<<g, APX_SIMT_THREADS, sizeof(F32Smem<128>), st>>>(L, T, slots, ids, n_ids, out, n_dev);
   } else {
     const long long tiles = (n_ids + 31) / 32;
     if (tiles <= 0) return cudaSuccess;
     const int g = (int)(tiles < 148 * 2 ? tiles : 148 * 2);
     apx_count_launch();
-    k_fp32_head<32><<<g, APX_SIMT_THREADS, sizeof(F32Smem<32>), st>>>(L, T, slots, ids, n_ids, out);
+    k_fp32_head<32><<<g, APX_SIMT_THREADS, sizeof(F32Smem<32>), st>>>(L, T, slots, ids, n_ids, out, n_dev);
   }
   return cudaGetLastError();
 }

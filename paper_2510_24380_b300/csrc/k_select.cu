@@ -208,7 +208,9 @@ cudaError_t apx_launch_slot_select(QuerySlot *slots, const int *slot_list, int n
 // From FP32 outputs of the candidates: objective, maybe-feasible (box widened by the FP32
 // margin eps) and sure-feasible (box shrunk by eps).
 
-__global__ void k_eval32(EvalArgs a, long long n, float *f32, unsigned char *maybe, unsigned char *sure) {
+__global__ void k_eval32(EvalArgs a, long long n, float *f32, unsigned char *maybe, unsigned char *sure,
+                         const unsigned *n_dev) {
+  if (n_dev && (long long)*n_dev < n) n = *n_dev;  // candidate count on the device
   // the widened and shrunk boxes as FP32 bounds deciding exactly like the FP64 arithmetic for FP32
   // values (FP64 compares run at a small fraction of the FP32 rate)
   __shared__ float mlo[APEX_MAX_CONSTRAINTS], mhi[APEX_MAX_CONSTRAINTS], slo[APEX_MAX_CONSTRAINTS],
@@ -240,8 +242,9 @@ __global__ void k_eval32(EvalArgs a, long long n, float *f32, unsigned char *may
 
 // tau32 = k-th largest f32 among sure entries (one CTA)
 __global__ void __launch_bounds__(SEL_THREADS) k_kth(const float *keys, const unsigned char *flag, long long n, long long k,
-                                                     float *out_tau, int *out_ok) {
+                                                     float *out_tau, int *out_ok, const unsigned *n_dev) {
   extern __shared__ unsigned sel_bits[];
+  if (n_dev && (long long)*n_dev < n) n = *n_dev;
   unsigned bits;
   bool ok;
   if (n <= SEL_SMEM_KEYS) {  // stage once, select from shared memory
@@ -262,7 +265,9 @@ __global__ void __launch_bounds__(SEL_THREADS) k_kth(const float *keys, const un
 // R = {maybe && f32 >= thr}, thr = tau32 - margin2 (-inf when fewer than k sure entries exist);
 // need64 = !sure
 __global__ void k_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
-                          const unsigned char *sure, const float *tau32, float margin2, RItem *R, unsigned *n_r) {
+                          const unsigned char *sure, const float *tau32, float margin2, RItem *R, unsigned *n_r,
+                          const unsigned *n_dev) {
+  if (n_dev && (long long)*n_dev < n) n = *n_dev;
   const float tau = *tau32;
   const float thr = isfinite(tau) ? tau - margin2 : -INFINITY;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -336,7 +341,13 @@ __device__ __forceinline__ bool r_before(const RItem &a, const RItem &b) {
   return a.id < b.id;
 }
 
-__global__ void k_bitonic_global(RItem *R, unsigned n, unsigned j, unsigned kk) {
+__global__ void k_bitonic_global(RItem *R, unsigned n, unsigned j, unsigned kk, const unsigned *n_used) {
+  if (n_used) {  // only the power-of-two prefix holding the used entries is sorted
+    unsigned p2 = 2;
+    while (p2 < *n_used) p2 <<= 1;
+    if (kk > p2) return;
+    n = min(n, p2);
+  }
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const unsigned l = i ^ j;
     if (l > i) {
@@ -356,8 +367,9 @@ __global__ void k_bitonic_global(RItem *R, unsigned n, unsigned j, unsigned kk) 
 // The network runs on the sort keys only, as separate arrays in shared memory (conflict-free
 // 8-byte accesses): key (r_key(s), id) with dead items mapped to (0, max id), which reproduces the
 // (alive, s desc, id asc) order, plus the item's position; the items are permuted once at the end.
-// n_used (optional, one block only): sort just the smallest power of two holding the *n_used
-// leading entries (the rest is dead padding, already in its place at the end).
+// n_used (optional): sort just the smallest power of two p2 holding the *n_used leading entries
+// (the rest is dead padding, already in its place at the end): blocks past p2 and stages past
+// p2 do nothing, a block longer than p2 sorts its first p2 entries.
 __global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned block, unsigned kk_from, unsigned kk_to,
                                                          const unsigned *n_used) {
   __shared__ unsigned long long ks[BITONIC_SMEM];
@@ -365,8 +377,9 @@ __global__ void __launch_bounds__(1024) k_bitonic_shared(RItem *R, unsigned bloc
   __shared__ unsigned short ix[BITONIC_SMEM];
   if (n_used) {
     unsigned p2 = 2;
-    while (p2 < *n_used && p2 < block) p2 <<= 1;
-    block = p2;
+    while (p2 < *n_used) p2 <<= 1;
+    if (blockIdx.x * block >= p2 || kk_from > p2) return;
+    if (p2 < block) block = p2;
     kk_to = min(kk_to, p2);
   }
   const unsigned base = blockIdx.x * block;
@@ -446,7 +459,9 @@ cudaError_t apx_launch_pad_r_dev(RItem *R, const unsigned *n_used, unsigned to, 
   return cudaGetLastError();
 }
 
-// Sorts R[0, n_pow2) (n_pow2 a power of two) into (alive, s desc, id asc) order.
+// Sorts R[0, n_pow2) (n_pow2 a power of two) into (alive, s desc, id asc) order. With n_dev (a
+// device count of leading used entries; the rest dead padding) only the power-of-two prefix that
+// holds them is sorted, whatever n_pow2 the launches were sized for.
 cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st, const unsigned *n_dev) {
   if (n_pow2 < 2) return cudaSuccess;
   if (n_used < n_pow2) {
@@ -461,14 +476,14 @@ cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t 
   }
   const unsigned nb = n_pow2 / BITONIC_SMEM;
   apx_count_launch();
-  k_bitonic_shared<<<nb, 1024, 0, st>>>(R, BITONIC_SMEM, 2, BITONIC_SMEM, nullptr);
+  k_bitonic_shared<<<nb, 1024, 0, st>>>(R, BITONIC_SMEM, 2, BITONIC_SMEM, n_dev);
   for (unsigned kk = BITONIC_SMEM * 2; kk <= n_pow2; kk <<= 1) {
     for (unsigned j = kk >> 1; j >= BITONIC_SMEM; j >>= 1) {
       apx_count_launch();
-      k_bitonic_global<<<std::min<unsigned>(nb * 8, 148u * 16u), 256, 0, st>>>(R, n_pow2, j, kk);
+      k_bitonic_global<<<std::min<unsigned>(nb * 8, 148u * 16u), 256, 0, st>>>(R, n_pow2, j, kk, n_dev);
     }
     apx_count_launch();
-    k_bitonic_shared<<<nb, 1024, 0, st>>>(R, BITONIC_SMEM, kk, kk, nullptr);
+    k_bitonic_shared<<<nb, 1024, 0, st>>>(R, BITONIC_SMEM, kk, kk, n_dev);
   }
   return cudaGetLastError();
 }
@@ -557,15 +572,16 @@ __global__ void k_emit(const RItem *R, unsigned n_max, const unsigned *n_alive, 
   }
 }
 
+// n_dev (optional): the actual count on the device, at most n (grids are sized for n)
 cudaError_t apx_launch_eval32(const EvalArgs &a, long long n, float *f32, unsigned char *maybe, unsigned char *sure,
-                              cudaStream_t st) {
+                              cudaStream_t st, const unsigned *n_dev) {
   if (n <= 0) return cudaSuccess;
   apx_count_launch();
-  k_eval32<<<(unsigned)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0, st>>>(a, n, f32, maybe, sure);
+  k_eval32<<<(unsigned)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0, st>>>(a, n, f32, maybe, sure, n_dev);
   return cudaGetLastError();
 }
 cudaError_t apx_launch_kth(const float *keys, const unsigned char *flag, long long n, long long k, float *out_tau,
-                           int *out_ok, cudaStream_t st) {
+                           int *out_ok, cudaStream_t st, const unsigned *n_dev) {
   static bool attr = false;
   if (!attr) {
     const cudaError_t e =
@@ -574,16 +590,16 @@ cudaError_t apx_launch_kth(const float *keys, const unsigned char *flag, long lo
     attr = true;
   }
   apx_count_launch();
-  k_kth<<<1, SEL_THREADS, SEL_SMEM_KEYS * sizeof(unsigned), st>>>(keys, flag, n, k, out_tau, out_ok);
+  k_kth<<<1, SEL_THREADS, SEL_SMEM_KEYS * sizeof(unsigned), st>>>(keys, flag, n, k, out_tau, out_ok, n_dev);
   return cudaGetLastError();
 }
 cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
                                const unsigned char *sure, const float *tau32, float margin2, RItem *R, unsigned *n_r,
-                               cudaStream_t st) {
+                               cudaStream_t st, const unsigned *n_dev) {
   if (n <= 0) return cudaSuccess;
   apx_count_launch();
   k_build_r<<<(unsigned)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0, st>>>(n, cand_ids, f32, maybe, sure, tau32,
-                                                                                 margin2, R, n_r);
+                                                                                 margin2, R, n_r, n_dev);
   return cudaGetLastError();
 }
 cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64, cudaStream_t st) {
