@@ -214,6 +214,9 @@ struct apex_library {
   QuerySlot *d_slots = nullptr;
   int *d_err = nullptr;
   int *d_slot_list = nullptr;
+  // start-threshold sample of whole-library queries: drawn once (uniform, seeded) and kept
+  long long *d_spec_full = nullptr;
+  long long spec_full_n = 0;
   std::vector<std::vector<float>> hW, hb;  // host copies of the head (for apex_save_library)
   uint32_t precisions_requested = 1u;
   // calibration
@@ -891,6 +894,7 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
     L->d_err = (int *)L->dalloc(sizeof(int));
     CU(cudaMemset(L->d_err, 0, sizeof(int)));
     L->d_slot_list = (int *)L->dalloc(sizeof(int) * APEX_MAX_ACTIVE);
+    L->d_spec_full = (long long *)L->dalloc(sizeof(long long) * 16384);
     for (int i = 0; i < apex_library::kRing; ++i) {
       CU(cudaEventCreate(&L->ev_l0[i]));
       CU(cudaEventCreate(&L->ev_l1[i]));
@@ -1162,20 +1166,28 @@ static bool speculative_start(apex_library &L, QueryRec *q, double margin2) {
     return false;
   }
   const int n_sub = (int)q->subset.size();
-  std::vector<long long> pre(n_sub + 1, 0);
-  for (int i = 0; i < n_sub; ++i) pre[i + 1] = pre[i] + (L.id_first[q->subset[i] + 1] - L.id_first[q->subset[i]]);
   const int no = L.n_out;
   L.arena_reserve(sizeof(int) * n_sub + sizeof(long long) * (n_sub + 1) + sizeof(long long) * S +
                   sizeof(float) * S * (no + 1) + S + 8 * 256);
-  int *d_rxn = (int *)L.aget(sizeof(int) * n_sub);
-  long long *d_pre = (long long *)L.aget(sizeof(long long) * (n_sub + 1));
-  long long *d_ids = (long long *)L.aget(sizeof(long long) * S);
   float *d_out = (float *)L.aget(sizeof(float) * S * no);
   float *d_keys = (float *)L.aget(sizeof(float) * S);
   unsigned char *d_flag = (unsigned char *)L.aget(S);
-  L.upload(d_rxn, q->subset.data(), sizeof(int) * n_sub);
-  L.upload(d_pre, pre.data(), sizeof(long long) * (n_sub + 1));
-  CU(apx_launch_spec_ids(d_rxn, d_pre, n_sub, L.T_.id_first, q->scope_n, L.rng(), S, d_ids, L.st));
+  // a whole-library query reuses the library's own sample (the threshold is a guess that the
+  // finalization verifies, so any uniform sample serves); a subset draws one from its scope
+  const bool full = n_sub == L.T;
+  long long *d_ids = full ? L.d_spec_full : nullptr;
+  if (!full || L.spec_full_n < S) {
+    std::vector<long long> pre(n_sub + 1, 0);
+    for (int i = 0; i < n_sub; ++i) pre[i + 1] = pre[i] + (L.id_first[q->subset[i] + 1] - L.id_first[q->subset[i]]);
+    int *d_rxn = (int *)L.aget(sizeof(int) * n_sub);
+    long long *d_pre = (long long *)L.aget(sizeof(long long) * (n_sub + 1));
+    if (!full) d_ids = (long long *)L.aget(sizeof(long long) * S);
+    const long long n_draw = full ? std::min<long long>(16384, q->scope_n) : S;
+    L.upload(d_rxn, q->subset.data(), sizeof(int) * n_sub);
+    L.upload(d_pre, pre.data(), sizeof(long long) * (n_sub + 1));
+    CU(apx_launch_spec_ids(d_rxn, d_pre, n_sub, L.T_.id_first, q->scope_n, L.rng(), n_draw, d_ids, L.st));
+    if (full) L.spec_full_n = n_draw;
+  }
   if (fmt >= 0) {  // the kernel applies the query's exact boxes and objective: one key per sample
     CU(apx_launch_tc_ids(L.T_, d_ids, S, d_out, L.d_err, L.n_sm, L.st, fmt, L.d_slots, q->slot));
   } else {
