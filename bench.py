@@ -442,6 +442,8 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
     L = apex.Library(lib, head, precisions=("fp32", args.precision), device=dev, stream=stream.cuda_stream, seed=0)
+    cpus0 = os.sched_getaffinity(0)
+    worker_cpu = L.keep_caller_off_worker_cpu()  # this thread polls for results: not on the worker's CPU
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
 
     def step(query):
@@ -545,6 +547,8 @@ def main():
                     "err_fp32": [float("%.3g" % x) for x in list(L.info().err_fp32)[:L.n_outputs]],
                     "rms": [round(x, 4) for x in list(L.info().rms)[:L.n_outputs]]},
     }
+    line["host"] = {"worker_cpu": worker_cpu, "caller_cpus": len(os.sched_getaffinity(0))}
+    os.sched_setaffinity(0, cpus0)  # the oracle baseline runs on every core
     if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
         cb = run_cpu_baseline(lib, head, q)
         # GPU answer on the same sampled reactions, checked against the oracle's

@@ -290,6 +290,16 @@ apex_status apex_autotune(apex_library *lib, const apex_autotune_desc *desc, ape
  * APEX_EINVAL for other values. */
 apex_status apex_set_launch_shape(apex_library *lib, int64_t chunk_compounds, int32_t fp32_id_tile);
 
+/* CPU the library's worker thread is pinned to (-1: not pinned), waiting up to 2 s for the worker
+ * to choose it after the load. The worker issues every CUDA call of the query path; CUDA calls from
+ * the CPU that created the device context were measured about three times cheaper than from any
+ * other CPU. The worker is not pinned unless the environment says so at load: APEX_WORKER_CPU=auto
+ * pins it to the CPU with the cheapest calls when one is clearly cheaper, APEX_WORKER_CPU=n to CPU
+ * n. An application thread that busy-polls or computes on a pinned worker's CPU slows the worker
+ * down: keep such threads off it.
+ * APEX_EINVAL for a NULL argument. */
+apex_status apex_worker_cpu(const apex_library *lib, int32_t *cpu);
+
 /* Failure-detection self-test of the bounded device waits. Every wait inside this library's
  * kernels (mbarrier phases between warp roles) gives up after a time limit (2 s in production
  * kernels), records a timeout in the launch's status word and returns; the host then fails the

@@ -100,6 +100,7 @@ SYMBOLS = {
                         C.c_int32],
     "apex_cancel": [C.c_void_p, C.c_int64],
     "apex_query_stats": [C.c_void_p, C.c_int64, C.POINTER(QueryStats)],
+    "apex_worker_cpu": [C.c_void_p, C.POINTER(C.c_int32)],
     "apex_score_ids": [C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
     "apex_dump_outputs": [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_float), C.c_int64],
     "apex_decode_ids": [C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int64)],
@@ -337,6 +338,23 @@ class Library:
     def set_launch_shape(self, chunk_compounds: int, fp32_id_tile: int = 32):
         """Compounds per enumeration launch and FP32 id-list tile rows, by hand (what autotune picks)."""
         _check(load().apex_set_launch_shape(self.h, int(chunk_compounds), int(fp32_id_tile)), "apex_set_launch_shape")
+
+    def worker_cpu(self) -> int:
+        """CPU the library's worker thread is pinned to (-1: not pinned)."""
+        c = C.c_int32()
+        _check(load().apex_worker_cpu(self.h, C.byref(c)), "apex_worker_cpu")
+        return c.value
+
+    def keep_caller_off_worker_cpu(self) -> int:
+        """Moves the calling thread off the worker's CPU (when it is pinned and other CPUs are
+        allowed), so that the caller's polling and Python work never share a core with the thread
+        that issues the CUDA calls. Returns the worker's CPU."""
+        cpu = self.worker_cpu()
+        if cpu >= 0 and hasattr(os, "sched_getaffinity"):
+            allowed = os.sched_getaffinity(0)
+            if cpu in allowed and len(allowed) > 1:
+                os.sched_setaffinity(0, allowed - {cpu})
+        return cpu
 
     def selftest_wait_timeout(self, limit_ms: int = 50) -> int:
         """Runs the device-wait self-test; returns the status code (APEX_ETIMEDOUT = -5 expected)."""

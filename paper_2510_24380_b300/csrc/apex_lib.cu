@@ -135,6 +135,16 @@ static bool watch(const std::atomic<unsigned long long> &c, unsigned long long s
     cpu_relax();
   }
 }
+// Takes the lock right after a watched counter moved: the thread that moved it still holds the
+// lock for a moment, and a blocking lock would put this thread to sleep (its wake-up then costs
+// the other thread a wake call and this one tens of microseconds), so it tries for a while first.
+static void lock_spin(std::unique_lock<std::mutex> &lk) {
+  for (int i = 0; i < 20000; ++i) {
+    if (lk.try_lock()) return;
+    cpu_relax();
+  }
+  lk.lock();
+}
 static double env_ms(const char *name, double dflt) {
   const char *e = getenv(name);
   return e ? std::max(0.0, atof(e)) : dflt;
@@ -240,6 +250,7 @@ struct apex_library {
   // sleep on cv_done. A thread woken from a sleep starts tens of microseconds later.
   std::atomic<unsigned long long> work_seq{0}, done_seq{0};
   int spinners = 0;  // fetchers watching done_seq (under mu)
+  std::atomic<int> worker_cpu{-2};  // CPU the worker is pinned to, -1 none, -2 not chosen yet
   long long cursor = 0;  // global item index of the circular pass
   apex_query_stats_t last_stats{};
   std::mt19937_64 rng;
@@ -928,6 +939,11 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
   }
   apex_library *lib = L.release();
   lib->worker = std::thread(worker_main, lib);
+  // the worker chooses its CPU before the first query (the caller is blocked here meanwhile, so
+  // it does not disturb the timing of the candidate CPUs)
+  const double t_w = now_ms();
+  while (lib->worker_cpu.load() == -2 && now_ms() - t_w < 5000.0)
+    std::this_thread::sleep_for(std::chrono::microseconds(100));
   *out = lib;
   return APEX_OK;
 }
@@ -1074,7 +1090,8 @@ extern "C" apex_status apex_query(apex_library *L, const apex_query_desc *Dq, ap
   q->id = L->next_id++;
   const apex_query_id id = q->id;
   {
-    std::lock_guard<std::mutex> g(L->mu);
+    std::unique_lock<std::mutex> g(L->mu, std::defer_lock);
+    lock_spin(g);
     if (L->stop) return fail(APEX_ECANCELED, "library is shutting down");
     L->queued.push_back(q.get());
     L->queries[id] = std::move(q);
@@ -1746,9 +1763,62 @@ static void pass_step(apex_library &L) {
   while (L.inflight.size() > 1) retire_launch(L);  // the GPU keeps this launch queued
 }
 
+// The CPU the worker runs on. On the hosts this library was measured on, CUDA calls issued from
+// the CPU that created the device context cost about a third of what they cost from any other CPU
+// (kernel launch ~3.5 us against ~9-10 us), and a query's host path issues a few dozen of them.
+// With APEX_WORKER_CPU=auto the worker times a burst of event records from every allowed CPU and
+// stays on the fastest one when it is clearly faster than the typical one; APEX_WORKER_CPU=n pins
+// it to CPU n. By default it is not pinned: pinned, it shares its CPU with whatever application
+// thread the scheduler puts there, and on the measured hosts the mean query time gained about 1 %
+// while the tail grew.
+static int pick_worker_cpu(apex_library &L) {
+  const char *e = getenv("APEX_WORKER_CPU");
+  if (!e) return -1;
+  if (strcmp(e, "auto") != 0) return atoi(e);
+  cpu_set_t allowed;
+  if (sched_getaffinity(0, sizeof(allowed), &allowed) != 0) return -1;
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return -1;
+  std::vector<std::pair<double, int>> t;
+  for (int c = 0; c < CPU_SETSIZE && c < 256; ++c) {
+    if (!CPU_ISSET(c, &allowed)) continue;
+    cpu_set_t one;
+    CPU_ZERO(&one);
+    CPU_SET(c, &one);
+    if (pthread_setaffinity_np(pthread_self(), sizeof(one), &one) != 0) continue;
+    double best = 1e30;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaStreamSynchronize(L.st);
+      const double t0 = now_ms();
+      for (int j = 0; j < 8; ++j) cudaEventRecord(ev, L.st);
+      best = std::min(best, now_ms() - t0);
+    }
+    t.emplace_back(best, c);
+  }
+  cudaStreamSynchronize(L.st);
+  cudaEventDestroy(ev);
+  pthread_setaffinity_np(pthread_self(), sizeof(allowed), &allowed);
+  if (t.size() < 2) return -1;
+  std::sort(t.begin(), t.end());
+  const double median = t[t.size() / 2].first;
+  TRACE("worker cpu probe: fastest cpus %d %.2f, %d %.2f us/call, median %.2f us/call", t[0].second,
+        1e3 * t[0].first / 8, t[1].second, 1e3 * t[1].first / 8, 1e3 * median / 8);
+  return t[0].first < 0.6 * median ? t[0].second : -1;
+}
+
 static void worker_main(apex_library *Lp) {
   apex_library &L = *Lp;
   cudaSetDevice(L.device);
+  int cpu = pick_worker_cpu(L);
+  if (cpu >= 0 && cpu < CPU_SETSIZE) {
+    cpu_set_t one;
+    CPU_ZERO(&one);
+    CPU_SET(cpu, &one);
+    if (pthread_setaffinity_np(pthread_self(), sizeof(one), &one) != 0) cpu = -1;
+  } else {
+    cpu = -1;
+  }
+  L.worker_cpu.store(cpu);
   for (;;) {
     std::vector<QueryRec *> fresh;
     {
@@ -1802,7 +1872,7 @@ static void worker_main(apex_library *Lp) {
         const unsigned long long seq = L.work_seq.load();
         lk.unlock();
         const bool moved = worker_spin_ms() > 0 && watch(L.work_seq, seq, worker_spin_ms(), 63);
-        lk.lock();
+        lock_spin(lk);
         if (!moved && L.work_seq.load() == seq) L.cv.wait_for(lk, std::chrono::milliseconds(20));
         continue;
       }
@@ -1878,7 +1948,8 @@ extern "C" apex_status apex_topk_fetch(apex_library *L, apex_query_id id, int64_
                                        int64_t *n_out, int32_t timeout_ms) {
   if (!L) return fail(APEX_EINVAL, "NULL library");
   if (capacity < 0) return fail(APEX_EINVAL, "negative capacity");
-  std::unique_lock<std::mutex> lk(L->mu);
+  std::unique_lock<std::mutex> lk(L->mu, std::defer_lock);
+  lock_spin(lk);
   auto it = L->queries.find(id);
   if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found", (long long)id);
   QueryRec *q = it->second.get();
@@ -1893,7 +1964,7 @@ extern "C" apex_status apex_topk_fetch(apex_library *L, apex_query_id id, int64_
     L->spinners++;
     lk.unlock();
     watch(L->done_seq, seq, left, 63);
-    lk.lock();
+    lock_spin(lk);
     L->spinners--;
     it = L->queries.find(id);  // another fetcher of the same id may have taken it meanwhile
     if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found", (long long)id);
@@ -2302,6 +2373,16 @@ extern "C" apex_status apex_load_library_file(const char *path, int32_t device, 
 extern "C" apex_status apex_kernel_launches(int64_t *out) {
   if (!out) return fail(APEX_EINVAL, "NULL argument");
   *out = g_launches.load();
+  return APEX_OK;
+}
+
+extern "C" apex_status apex_worker_cpu(const apex_library *L, int32_t *cpu) {
+  if (!L || !cpu) return fail(APEX_EINVAL, "NULL argument");
+  const double t0 = now_ms();
+  while (L->worker_cpu.load() == -2 && now_ms() - t0 < 2000.0)
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  const int c = L->worker_cpu.load();
+  *cpu = c < 0 ? -1 : c;
   return APEX_OK;
 }
 

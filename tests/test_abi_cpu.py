@@ -110,6 +110,8 @@ def test_null_arguments(dll):
     n = C.c_int64()
     assert dll.apex_topk_select(None, None, 10, 0, None, None, C.byref(n), None) == -1
     assert dll.apex_set_launch_shape(None, 1 << 20, 32) == -1
+    cpu = C.c_int32()
+    assert dll.apex_worker_cpu(None, C.byref(cpu)) == -1
 
 
 def test_library_file_rejected_before_the_gpu(dll, tmp_path):
