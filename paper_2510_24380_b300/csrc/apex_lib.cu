@@ -497,15 +497,60 @@ static inline const double *pass_err(const apex_library &L, int precision) {
   return f >= 0 ? L.err16[f] : L.err32;
 }
 
+// Launch tile ranges of equal estimated cost for the CTAs of the tensor-core kernel. A tile costs 1
+// and every run of tiles (consecutive tiles of one inner block: the kernel gathers the block's
+// inner rows again at its start and its pipeline refills) costs kRunCost more, about two tiles as
+// measured per CTA on B300 (a reaction whose outer slot has 19 synthons ran ~10 % slower per tile
+// than one with long runs, and equal tile counts left its CTAs last). Every CTA gets >= 1 tile.
+static void tc_partition(const apex_library &L, LaunchPlan &P, int grid) {
+  P.cta_n = 0;
+  if (grid < 2 || grid > APX_MAX_CTA || P.total_tiles < grid) return;
+  constexpr double kRunCost = 2.0;
+  std::vector<std::pair<long long, long long>> runs;  // (first launch tile, tiles)
+  for (int g = 0; g < P.n_seg; ++g) {
+    const Segment &sg = P.seg[g];
+    const RxnPlan &p = L.rx[sg.rxn];
+    const long long x0 = apx_tiles_before(p, sg.item_begin), x1 = apx_tiles_before(p, sg.item_end);
+    for (long long x = x0; x < x1;) {
+      const long long e = std::min(x1, (x / p.n_outer + 1) * p.n_outer);
+      runs.emplace_back(P.seg_tile_first[g] + (x - x0), e - x);
+      x = e;
+    }
+  }
+  double total = 0;
+  for (const auto &r : runs) total += kRunCost + (double)r.second;
+  const double per = total / grid;
+  P.cta_first[0] = 0;
+  int c = 1;
+  double cum = 0;
+  for (const auto &r : runs) {
+    while (c < grid && (double)c * per <= cum + kRunCost + (double)r.second) {
+      const double into = std::max(0.0, (double)c * per - cum - kRunCost);  // tiles into the run
+      long long t = r.first + std::min(r.second, (long long)std::ceil(into));
+      t = std::max(t, P.cta_first[c - 1] + 1);
+      t = std::min(t, P.total_tiles - (grid - c));
+      P.cta_first[c++] = t;
+    }
+    cum += kRunCost + (double)r.second;
+  }
+  for (; c < grid; ++c) P.cta_first[c] = std::min(P.total_tiles - (grid - c), P.cta_first[c - 1] + 1);
+  P.cta_first[grid] = P.total_tiles;
+  P.cta_n = grid;
+}
+
 static void launch_enum(apex_library &L, const LaunchPlan &P, int precision) {
   if (P.total_items == 0) return;
   const int fmt = tc_format(precision);
-  if (fmt >= 0)  // every CTA takes an equal share of the launch's tiles
-    CU(apx_launch_tc(P, L.T_, L.d_slots, L.d_err, grid_for(L, P.total_tiles), L.st, fmt));
-  else if (L.n_layers == 1 && P.mode == 0)  // linear head: per-synthon scalar sums (Eq. apex)
+  if (fmt >= 0) {  // CTAs take tile ranges of equal estimated cost
+    const int grid = grid_for(L, P.total_tiles);
+    LaunchPlan Q = P;
+    tc_partition(L, Q, grid);
+    CU(apx_launch_tc(Q, L.T_, L.d_slots, L.d_err, grid, L.st, fmt));
+  } else if (L.n_layers == 1 && P.mode == 0) {  // linear head: per-synthon scalar sums (Eq. apex)
     CU(apx_launch_linear(P, L.T_, L.d_slots, L.n_sm, L.st));
-  else
+  } else {
     CU(apx_launch_fp32(P, L.T_, L.d_slots, nullptr, 0, nullptr, grid_for(L, P.total_items), L.st));
+  }
 }
 
 static void check_kernel_status(apex_library &L) {

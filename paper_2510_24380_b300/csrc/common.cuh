@@ -14,6 +14,7 @@
 
 #define APX_TILE 128
 #define APX_MAX_SEG 160
+#define APX_MAX_CTA 160  // CTAs of a launch that can take cost-weighted tile ranges
 #define APX_SIMT_THREADS 256
 
 struct RxnPlan {
@@ -57,6 +58,10 @@ struct LaunchPlan {
   long long *dump_ids;                       // mode 2: [dump_n], row r of launch tile t at t * 128 + r,
                                              // -1 = padding row; mode 3: the input ids [dump_n]
   long long dump_base, dump_n;
+  // tensor-core kernel: CTA c takes launch tiles [cta_first[c], cta_first[c + 1]) when cta_n equals
+  // the launch's grid (ranges of equal estimated cost), else an equal count of tiles
+  int cta_n;
+  long long cta_first[APX_MAX_CTA + 1];
 };
 
 // Per-query device state (one per active slot).
@@ -190,12 +195,28 @@ __device__ __forceinline__ unsigned apx_warp_reserve(unsigned *counter, bool tak
   return base + __popc(m & ((1u << lane) - 1u));
 }
 
+// a / b (returned) and a % b (*rem) for a >= 0, b > 0: in 32-bit arithmetic when both fit, the
+// usual case (a 64-bit integer division is a long instruction sequence, and every role of the
+// enumeration kernel divides at the start of each run of tiles).
+__host__ __device__ __forceinline__ long long apx_divmod(long long a, long long b, long long *rem) {
+  if (((unsigned long long)a | (unsigned long long)b) < 4294967296ull) {
+    const unsigned q = (unsigned)a / (unsigned)b;
+    *rem = (long long)((unsigned)a - q * (unsigned)b);
+    return (long long)q;
+  }
+  const long long q = a / b;
+  *rem = a - q * b;
+  return q;
+}
+
 // Locates item `it` of a launch: segment (binary search) and local item index.
 // Tiles of a reaction before its item i, in (inner block b, outer index o) order: item
 // b * n_oc + oc covers the tiles b * n_outer + [oc * L_o, min((oc + 1) * L_o, n_outer)).
 __host__ __device__ __forceinline__ long long apx_tiles_before(const RxnPlan &p, long long i) {
-  const long long r = (i % p.n_oc) * p.L_o;
-  return (i / p.n_oc) * p.n_outer + (r < p.n_outer ? r : p.n_outer);
+  long long oc;
+  const long long b = apx_divmod(i, p.n_oc, &oc);
+  const long long r = oc * p.L_o;
+  return b * p.n_outer + (r < p.n_outer ? r : p.n_outer);
 }
 
 // A run of consecutive tiles of one segment that share their inner block: rows q0 + [0, 128),
@@ -222,8 +243,7 @@ __device__ __forceinline__ TileRun apx_tile_run(const LaunchPlan &L, const RxnPl
   r.rp = rx + seg.rxn;
   const long long x = apx_tiles_before(*r.rp, seg.item_begin) + (tile - L.seg_tile_first[lo]);
   const long long x_end = apx_tiles_before(*r.rp, seg.item_end);
-  r.b = x / r.rp->n_outer;
-  r.o_begin = x - r.b * r.rp->n_outer;
+  r.b = apx_divmod(x, r.rp->n_outer, &r.o_begin);
   long long n = r.rp->n_outer - r.o_begin;
   if (x_end - x < n) n = x_end - x;
   if (t_end - tile < n) n = t_end - tile;

@@ -414,10 +414,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   auto bar = [&](int i) { return sbase + LY::BAR + 8u * (uint32_t)i; };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // this CTA's share of the launch: tiles [t_begin, t_end), equal counts across CTAs (every tile
-  // costs the same), walked by every role in the same order of runs
-  const long long t_begin = (long long)blockIdx.x * L.total_tiles / gridDim.x;
-  const long long t_end = (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x;
+  // this CTA's share of the launch: tiles [t_begin, t_end), from the launch plan's cost-weighted
+  // ranges when it has them (a tile that starts a run of tiles costs more), else equal counts;
+  // walked by every role in the same order of runs
+#define TC_CTA_END()                                                        \
+  (L.cta_n == (int)gridDim.x ? L.cta_first[blockIdx.x + 1]                  \
+                             : (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x)
+  const long long t_begin = L.cta_n == (int)gridDim.x ? L.cta_first[blockIdx.x]
+                                                      : (long long)blockIdx.x * L.total_tiles / gridDim.x;
+  const long long t_end = TC_CTA_END();
   if (tid == 0) {
     for (int s = 0; s < 4; ++s) {  // FP8: a K-half stage is written by the warps of two K quarters
       mbar_init(bar(B_FULL(s)), F8 ? 8 : 4);
@@ -523,7 +528,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     long long tile = t_begin;
     int left = 0;            // tiles left in the current run
     bool has_outer = false;  // per-run fields kept in registers (no per-tile global loads)
-    bool more = tile < (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x;
+    bool more = tile < TC_CTA_END();
     bool need_r = more;
     bool ok = true;
     for (unsigned s = 0; ok; ++s) {
@@ -554,12 +559,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               src[sl] = T.P16[PF] + g * 64;
               if (sl < ni) {
                 const long long sz = rp->slot_size[sl];
-                src[sl] += (rp->slot_row[sl] + rem % sz) * 256;
-                rem /= sz;
+                long long dig;
+                rem = apx_divmod(rem, sz, &dig);
+                src[sl] += (rp->slot_row[sl] + dig) * 256;
               }
             }
           } else {  // the inner slots of the tile's work item
-            const TileRun I = apx_tile_run(L, T.rx, tile, (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x);
+            const TileRun I = apx_tile_run(L, T.rx, tile, TC_CTA_END());
             const RxnPlan *rp = I.rp;
             left = (int)(I.o_end - I.o_begin);
             has_outer = rp->outer_row >= 0;
@@ -572,8 +578,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               src[sl] = T.P16[PF] + g * 64;
               if (sl < ni) {
                 const long long sz = rp->inner_size[sl];
-                src[sl] += (rp->inner_row[sl] + rem % sz) * 256;
-                rem /= sz;
+                long long dig;
+                rem = apx_divmod(rem, sz, &dig);
+                src[sl] += (rp->inner_row[sl] + dig) * 256;
               }
             }
           }
@@ -651,7 +658,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         ++tile;
         if (--left == 0) {
-          more = tile < (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x;
+          more = tile < TC_CTA_END();
           need_r = more;
         }
       }
