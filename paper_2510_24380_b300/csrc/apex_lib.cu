@@ -499,13 +499,13 @@ static inline const double *pass_err(const apex_library &L, int precision) {
 
 // Launch tile ranges of equal estimated cost for the CTAs of the tensor-core kernel. A tile costs 1
 // and every run of tiles (consecutive tiles of one inner block: the kernel gathers the block's
-// inner rows again at its start and its pipeline refills) costs kRunCost more, about two tiles as
+// inner rows again at its start and its pipeline refills) costs kRunCost more, about 2.4 tiles as
 // measured per CTA on B300 (a reaction whose outer slot has 19 synthons ran ~10 % slower per tile
 // than one with long runs, and equal tile counts left its CTAs last). Every CTA gets >= 1 tile.
 static void tc_partition(const apex_library &L, LaunchPlan &P, int grid) {
   P.cta_n = 0;
   if (grid < 2 || grid > APX_MAX_CTA || P.total_tiles < grid) return;
-  constexpr double kRunCost = 2.0;
+  constexpr double kRunCost = 2.4;
   std::vector<std::pair<long long, long long>> runs;  // (first launch tile, tiles)
   for (int g = 0; g < P.n_seg; ++g) {
     const Segment &sg = P.seg[g];
