@@ -290,6 +290,14 @@ apex_status apex_autotune(apex_library *lib, const apex_autotune_desc *desc, ape
  * APEX_EINVAL for other values. */
 apex_status apex_set_launch_shape(apex_library *lib, int64_t chunk_compounds, int32_t fp32_id_tile);
 
+/* Candidates covered by the finalization chain that is queued behind a query's last enumeration
+ * launch before its candidate count is known (0 restores the default, max(4096, 4 k), capped by
+ * the query's candidate buffer). A query with more candidates than that has its chain queued
+ * again, sized exactly, after one more host wait: a smaller cover trades device scratch for that
+ * rerun; results do not depend on it. Affects finalizations that start after the call.
+ * APEX_EINVAL for a NULL library or a cover outside 0..2^30. */
+apex_status apex_set_finalize_cover(apex_library *lib, int64_t cover);
+
 /* CPU the library's worker thread is pinned to (-1: not pinned), waiting up to 2 s for the worker
  * to choose it after the load. The worker issues every CUDA call of the query path; CUDA calls from
  * the CPU that created the device context were measured about three times cheaper than from any

@@ -101,6 +101,7 @@ SYMBOLS = {
     "apex_cancel": [C.c_void_p, C.c_int64],
     "apex_query_stats": [C.c_void_p, C.c_int64, C.POINTER(QueryStats)],
     "apex_worker_cpu": [C.c_void_p, C.POINTER(C.c_int32)],
+    "apex_set_finalize_cover": [C.c_void_p, C.c_int64],
     "apex_score_ids": [C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
     "apex_dump_outputs": [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_float), C.c_int64],
     "apex_decode_ids": [C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int64)],
@@ -338,6 +339,10 @@ class Library:
     def set_launch_shape(self, chunk_compounds: int, fp32_id_tile: int = 32):
         """Compounds per enumeration launch and FP32 id-list tile rows, by hand (what autotune picks)."""
         _check(load().apex_set_launch_shape(self.h, int(chunk_compounds), int(fp32_id_tile)), "apex_set_launch_shape")
+
+    def set_finalize_cover(self, cover: int = 0):
+        """Candidates the queued finalization covers before the count is known (0: default)."""
+        _check(load().apex_set_finalize_cover(self.h, int(cover)), "apex_set_finalize_cover")
 
     def worker_cpu(self) -> int:
         """CPU the library's worker thread is pinned to (-1: not pinned)."""

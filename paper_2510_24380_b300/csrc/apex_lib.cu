@@ -251,6 +251,7 @@ struct apex_library {
   std::atomic<unsigned long long> work_seq{0}, done_seq{0};
   int spinners = 0;  // fetchers watching done_seq (under mu)
   std::atomic<int> worker_cpu{-2};  // CPU the worker is pinned to, -1 none, -2 not chosen yet
+  std::atomic<long long> fin_cover_set{0};  // candidates a queued finalization covers (0: default)
   long long cursor = 0;  // global item index of the circular pass
   apex_query_stats_t last_stats{};
   std::mt19937_64 rng;
@@ -1416,8 +1417,9 @@ static size_t fin_pinned_bytes(const apex_library &L, const QueryRec *q, unsigne
   return kx * fin_row_bytes(L) + 5 * 64 + 64 + sizeof(QuerySlot) + 64;
 }
 // candidates an optimistic chain covers: the usual candidate set is a small multiple of k
-static unsigned fin_cover(const QueryRec *q) {
-  const long long c = std::max<long long>(4096, 4 * q->k);
+static unsigned fin_cover(const apex_library &L, const QueryRec *q) {
+  const long long set = L.fin_cover_set.load();
+  const long long c = set > 0 ? set : std::max<long long>(4096, 4 * q->k);
   return (unsigned)std::min<long long>(c, (long long)q->cap);
 }
 
@@ -1531,19 +1533,19 @@ static void fin_take(apex_library &L, FinChain &C) {
   q->stats.n_rescored_fp64 = C.nr > 0 ? (long long)C.h_cnt[4] : 0;
   const long long alive = C.nr > 0 ? (long long)C.h_cnt[3] : 0;
   const long long nf = std::min<long long>(C.k, alive);
-  q->r_ids.resize(nf);
-  q->r_rxn.resize(nf);
-  q->r_syn.resize(nf * APEX_MAX_SLOTS);
-  q->r_obj.resize(nf);
-  q->r_out.resize(nf * no);
-  if (nf > 0) {
-    const char *b = (const char *)C.e_ids;
-    memcpy(q->r_ids.data(), C.h, sizeof(long long) * nf);
-    memcpy(q->r_rxn.data(), C.h + ((const char *)C.e_rxn - b), sizeof(int) * nf);
-    memcpy(q->r_syn.data(), C.h + ((const char *)C.e_syn - b), sizeof(long long) * nf * APEX_MAX_SLOTS);
-    memcpy(q->r_obj.data(), C.h + ((const char *)C.e_obj - b), sizeof(double) * nf);
-    memcpy(q->r_out.data(), C.h + ((const char *)C.e_out - b), sizeof(double) * nf * no);
-  }
+  // copied straight from the pinned rows (no zero-fill first)
+  const char *b = (const char *)C.e_ids;
+  auto at = [&](const void *dev) { return C.h + ((const char *)dev - b); };
+  const long long *ids = nf > 0 ? (const long long *)C.h : nullptr;
+  const int *rxn = nf > 0 ? (const int *)at(C.e_rxn) : nullptr;
+  const long long *syn = nf > 0 ? (const long long *)at(C.e_syn) : nullptr;
+  const double *obj = nf > 0 ? (const double *)at(C.e_obj) : nullptr;
+  const double *out = nf > 0 ? (const double *)at(C.e_out) : nullptr;
+  q->r_ids.assign(ids, ids + (nf > 0 ? nf : 0));
+  q->r_rxn.assign(rxn, rxn + (nf > 0 ? nf : 0));
+  q->r_syn.assign(syn, syn + (nf > 0 ? nf * APEX_MAX_SLOTS : 0));
+  q->r_obj.assign(obj, obj + (nf > 0 ? nf : 0));
+  q->r_out.assign(out, out + (nf > 0 ? nf * no : 0));
   q->stats.n_feasible_lower = nf;
 }
 
@@ -1626,7 +1628,7 @@ static void finalize_batch(apex_library &L, const std::vector<QueryRec *> &qs, s
   std::vector<unsigned> cover(n);
   size_t ab = 0, pb = 0;
   for (size_t i = 0; i < n; ++i) {
-    cover[i] = fin_cover(qs[i]);
+    cover[i] = fin_cover(L, qs[i]);
     ab += fin_arena_bytes(L, qs[i], cover[i]);
     pb += fin_pinned_bytes(L, qs[i], cover[i]);
   }
@@ -2418,6 +2420,13 @@ extern "C" apex_status apex_load_library_file(const char *path, int32_t device, 
 extern "C" apex_status apex_kernel_launches(int64_t *out) {
   if (!out) return fail(APEX_EINVAL, "NULL argument");
   *out = g_launches.load();
+  return APEX_OK;
+}
+
+extern "C" apex_status apex_set_finalize_cover(apex_library *L, int64_t cover) {
+  if (!L) return fail(APEX_EINVAL, "NULL library");
+  if (cover < 0 || cover > (1LL << 30)) return fail(APEX_EINVAL, "cover outside 0..2^30");
+  L->fin_cover_set.store(cover);
   return APEX_OK;
 }
 

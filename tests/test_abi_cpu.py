@@ -112,6 +112,7 @@ def test_null_arguments(dll):
     assert dll.apex_set_launch_shape(None, 1 << 20, 32) == -1
     cpu = C.c_int32()
     assert dll.apex_worker_cpu(None, C.byref(cpu)) == -1
+    assert dll.apex_set_finalize_cover(None, 0) == -1
 
 
 def test_library_file_rejected_before_the_gpu(dll, tmp_path):

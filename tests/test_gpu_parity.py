@@ -356,6 +356,33 @@ def test_many_launch_pass_matches_one_launch(ragged):
         L.set_launch_shape(1 << 25, 32)
 
 
+def test_exact_finalization_rerun_matches(ragged):
+    """With a finalization cover far below the candidate count, every query's queued rescore chain
+    is too short and the host queues it again sized exactly (and runs further FP64 rounds there if
+    needed): the rows must be exactly those of the default path, for a reduced-precision and an
+    FP32 pass, alone and with two queries finalized in one batch."""
+    lib, head, spec, L, rms = ragged
+    stats = csl_gen.load_stats("t_ragged")
+    qa = csl_gen.query_single("t_ragged", spec, stats, precision="fp16")
+    qb = csl_gen.Query(qa.weights[::-1].copy(), qa.cons_idx, qa.lo, qa.hi, 37, None, "fp16")
+    q32 = csl_gen.query_single("t_ragged", spec, stats, precision="fp32")
+    refs = [L.run(q) for q in (qa, qb, q32)]
+    try:
+        L.set_finalize_cover(8)
+        for q, ref in zip((qa, qb, q32), refs):
+            r = L.run(q)
+            assert L.stats(-1)["n_candidates"] > 8
+            assert np.array_equal(r["ids"], ref["ids"]) and np.array_equal(r["objective"], ref["objective"])
+            assert np.array_equal(r["outputs"], ref["outputs"])
+        ia, ib = L.query(qa), L.query(qb)
+        ra, rb = L.fetch(ia, qa.k), L.fetch(ib, qb.k)
+        assert np.array_equal(ra["ids"], refs[0]["ids"]) and np.array_equal(rb["ids"], refs[1]["ids"])
+        with pytest.raises(apex.ApexError):
+            L.set_finalize_cover(-1)
+    finally:
+        L.set_finalize_cover(0)
+
+
 def test_library_file_round_trip(ragged, tmp_path):
     """save -> load from file: same margins (restored, not recalibrated) and identical results."""
     lib, head, spec, L, rms = ragged
