@@ -1416,10 +1416,11 @@ static size_t fin_pinned_bytes(const apex_library &L, const QueryRec *q, unsigne
   const size_t kx = (size_t)std::min<long long>(q->k, (long long)cover);
   return kx * fin_row_bytes(L) + 5 * 64 + 64 + sizeof(QuerySlot) + 64;
 }
-// candidates an optimistic chain covers: the usual candidate set is a small multiple of k
+// candidates an optimistic chain covers: the usual candidate set is a small multiple of k (at most
+// 2^20 by default: the scratch grows ~280 bytes per covered candidate)
 static unsigned fin_cover(const apex_library &L, const QueryRec *q) {
   const long long set = L.fin_cover_set.load();
-  const long long c = set > 0 ? set : std::max<long long>(4096, 4 * q->k);
+  const long long c = set > 0 ? set : std::max<long long>(4096, std::min<long long>(4 * q->k, 1LL << 20));
   return (unsigned)std::min<long long>(c, (long long)q->cap);
 }
 
@@ -1632,8 +1633,15 @@ static void finalize_batch(apex_library &L, const std::vector<QueryRec *> &qs, s
     ab += fin_arena_bytes(L, qs[i], cover[i]);
     pb += fin_pinned_bytes(L, qs[i], cover[i]);
   }
-  L.arena_reserve(ab);
-  L.dl_reserve(pb);
+  // the queued chains' scratch must fit the device budget (and stay below 8 GB without one);
+  // otherwise every query takes the exact path after the wait
+  const bool queue = ab <= (8ull << 30) && !(L.budget && L.bytes + L.query_bytes - L.arena_cap + ab > L.budget);
+  if (queue) {
+    L.arena_reserve(ab);
+    L.dl_reserve(pb);
+  } else {
+    L.dl_reserve(n * (sizeof(QuerySlot) + 64));
+  }
   std::vector<int> slots(n);
   for (size_t i = 0; i < n; ++i) slots[i] = qs[i]->slot;
   L.upload(L.d_slot_list, slots.data(), sizeof(int) * n);
@@ -1644,7 +1652,8 @@ static void finalize_batch(apex_library &L, const std::vector<QueryRec *> &qs, s
     C[i].hS = (QuerySlot *)L.dl_get(sizeof(QuerySlot));
     CU(cudaMemcpyAsync(C[i].hS, L.d_slots + slots[i], sizeof(QuerySlot), cudaMemcpyDeviceToHost, L.st));
   }
-  for (size_t i = 0; i < n; ++i) fin_queue(L, qs[i], C[i], cover[i]);
+  if (queue)
+    for (size_t i = 0; i < n; ++i) fin_queue(L, qs[i], C[i], cover[i]);
   const double t_f1 = now_ms();
   CU(cudaStreamSynchronize(L.st));
   const int last_ring = L.inflight.empty() ? -1 : L.inflight.back().ring;
@@ -1663,7 +1672,7 @@ static void finalize_batch(apex_library &L, const std::vector<QueryRec *> &qs, s
       redo[i] = 2;
       sbad[i] = sb;
       ovf[i] = of;
-    } else if (Ss[i].count > C[i].cover || (C[i].nr > 0 && C[i].h_cnt[2] > 0)) {
+    } else if (!queue || Ss[i].count > C[i].cover || (C[i].nr > 0 && C[i].h_cnt[2] > 0)) {
       redo[i] = 1;
     } else {
       fin_take(L, C[i]);
