@@ -708,8 +708,76 @@ __global__ void k_spec_ids(const int *rxn, const long long *pre, int n_sub, cons
 // sample entries are feasible). One CTA; samples of up to SPEC_SMEM_KEYS entries are selected
 // from shared memory.
 #define SPEC_SMEM_KEYS 16384
+// Rank-r largest of at most 16 * SEL_THREADS keys (order-preserving bits, 0 = excluded) for a small
+// rank: r rounds of a block-wide maximum, each removing one instance of it (so equal keys count
+// with their multiplicity). Keys stay in registers. Returns false when fewer than r keys are
+// non-zero.
+#define SPEC_FAST_RANK 32
+__device__ bool block_rank_small(const unsigned *bits, long long n, long long r, unsigned *out_bits) {
+  __shared__ unsigned wmax[SEL_THREADS / 32];
+  __shared__ unsigned bmax;
+  __shared__ int claimed;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const long long i = (long long)tid + (long long)j * SEL_THREADS;
+    v[j] = i < n ? bits[i] : 0u;
+  }
+  unsigned last = 0;
+  bool ok = true;
+  for (long long round = 0; round < r; ++round) {
+    unsigned m = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) m = max(m, v[j]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) wmax[warp] = m;
+    if (tid == 0) claimed = 0;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned x = lane < (int)(blockDim.x >> 5) ? wmax[lane] : 0u;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, off));
+      if (lane == 0) bmax = x;
+    }
+    __syncthreads();
+    const unsigned M = bmax;
+    if (M == 0u) {  // uniform: fewer than r keys
+      ok = false;
+      break;
+    }
+    last = M;
+    bool has = false;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) has = has || v[j] == M;
+    if (has && atomicCAS(&claimed, 0, 1) == 0) {  // one instance leaves
+      bool gone = false;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (!gone && v[j] == M) {
+          v[j] = 0u;
+          gone = true;
+        }
+    }
+    __syncthreads();
+  }
+  *out_bits = last;
+  return ok;
+}
+
 __global__ void __launch_bounds__(SEL_THREADS) k_spec_select(const float *out, long long S, const __grid_constant__ SpecArgs a,
                                                              float *keys, unsigned char *flag, QuerySlot *slot) {
+  if (a.bits_in && S <= 16LL * SEL_THREADS && a.rank <= SPEC_FAST_RANK && blockDim.x == SEL_THREADS) {
+    unsigned bits;  // keys already formed by the scoring kernel; a small rank
+    const bool ok = block_rank_small(reinterpret_cast<const unsigned *>(out), S, a.rank, &bits);
+    if (threadIdx.x == 0) {
+      const float t = ok ? apx_bits_key(bits) : -INFINITY;
+      slot->tau_spec = t;
+      slot->admit = ok ? t - a.margin2 : -INFINITY;
+    }
+    return;
+  }
   extern __shared__ unsigned spec_bits[];  // the sample's objective bits, 0 = infeasible
   const bool in_smem = S <= SPEC_SMEM_KEYS;
   // the boxes as FP32 bounds that decide exactly like the FP64 ones for FP32 values: the smallest
