@@ -251,6 +251,9 @@ struct apex_library {
   std::atomic<unsigned long long> work_seq{0}, done_seq{0};
   int spinners = 0;  // fetchers watching done_seq (under mu)
   std::atomic<int> worker_cpu{-2};  // CPU the worker is pinned to, -1 none, -2 not chosen yet
+  // timing event pairs of finished queries, reused by the next ones (under mu): creating and
+  // destroying two events per query were four CUDA calls on the query's path
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   std::atomic<long long> fin_cover_set{0};  // candidates a queued finalization covers (0: default)
   long long cursor = 0;  // global item index of the circular pass
   apex_query_stats_t last_stats{};
@@ -1010,6 +1013,10 @@ extern "C" apex_status apex_free_library(apex_library *L) {
     if (q->ev0) cudaEventDestroy(q->ev0);
     if (q->ev1) cudaEventDestroy(q->ev1);
   }
+  for (auto &e : L->ev_pool) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   for (auto &B : L->slotbuf)
     if (B.cap) {
       cudaFree(B.keys);
@@ -1344,6 +1351,11 @@ static bool admit_one(apex_library &L, QueryRec *q) {
   L.active[slot] = q;
   q->state = Q_ACTIVE;
   q->t_admit = now_ms();
+  if (!q->ev0 && !L.ev_pool.empty()) {
+    q->ev0 = L.ev_pool.back().first;
+    q->ev1 = L.ev_pool.back().second;
+    L.ev_pool.pop_back();
+  }
   if (!q->ev0) {
     CU(cudaEventCreate(&q->ev0));
     CU(cudaEventCreate(&q->ev1));
@@ -2047,8 +2059,12 @@ extern "C" apex_status apex_topk_fetch(apex_library *L, apex_query_id id, int64_
     if (n_out) *n_out = 0;
     fail(rc, "query %lld: %s", (long long)id, q->err_msg.c_str());
   }
-  if (q->ev0) cudaEventDestroy(q->ev0);
-  if (q->ev1) cudaEventDestroy(q->ev1);
+  if (q->ev0 && q->ev1 && L->ev_pool.size() < 256) {
+    L->ev_pool.emplace_back(q->ev0, q->ev1);
+  } else {
+    if (q->ev0) cudaEventDestroy(q->ev0);
+    if (q->ev1) cudaEventDestroy(q->ev1);
+  }
   L->last_stats = q->stats;
   L->queries.erase(it);
   return rc;
