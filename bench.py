@@ -2,8 +2,9 @@
 
 A step = one query through the C ABI over the whole synthetic library: enumeration of every
 compound (FP16 tensor-core head by default; --precision bf16 or fp32), streaming top-k, FP32
-rescore of the candidates, FP64 rescore of the boundary band and ties, ordering and decode. Workloads come from csl_gen (seeded,
-synthetic; the paper's libraries and labels are not available).
+rescore of the candidates, FP64 rescore of the boundary band and ties, ordering and decode.
+Workloads come from csl_gen (seeded, synthetic; the paper's libraries and labels are not
+available).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2_10m] [--impl ours|reference]
 
