@@ -383,6 +383,37 @@ def test_exact_finalization_rerun_matches(ragged):
         L.set_finalize_cover(0)
 
 
+def test_restarts_when_no_candidate_is_surely_feasible():
+    """A property that is constant (its last-layer row is zero) and a box whose lower bound is that
+    constant: every compound is feasible, none is surely feasible within the pass margin. The start
+    threshold is then never confirmed (no sure entries above it), so the query restarts with lower
+    ranks until it runs without one; its candidates all go through the FP64 decision. The rows
+    must equal the FP64 oracle's, alone and while a second query completes in the same batches."""
+    lib = library_from_sizes([[50, 60]], d=64, seed=7, name="const_property")
+    head = make_head([64, 64, 5], "relu", seed=11, n_objectives=1, n_properties=4)
+    head.W[-1][1, :] = 0.0
+    head.b[-1][1] = 0.25
+    L = apex.Library(lib, head, precisions=("fp32",), seed=1)
+    try:
+        qa = _q([1.0], [1], [0.25], [1.0], k=10, precision="fp32")
+        qb = _q([1.0], k=10, precision="fp32")
+        for q in (qa, qb):
+            ref = O.topk(lib, head, q)
+            r = L.run(q)
+            assert set(r["ids"].tolist()) == set(ref.ids.tolist())
+            np.testing.assert_allclose(r["objective"], ref.scores, rtol=FP32_REL, atol=0)  # FP64 where rescored
+            if q is qa:
+                st = L.stats(-1)
+                assert st["n_restarts"] >= 1 and st["n_rescored_fp64"] >= 10
+        ref_a, ref_b = O.topk(lib, head, qa), O.topk(lib, head, qb)
+        ia, ib = L.query(qa), L.query(qb)
+        ra, rb = L.fetch(ia, qa.k), L.fetch(ib, qb.k)
+        assert set(ra["ids"].tolist()) == set(ref_a.ids.tolist())
+        assert set(rb["ids"].tolist()) == set(ref_b.ids.tolist())
+    finally:
+        L.close()
+
+
 def test_library_file_round_trip(ragged, tmp_path):
     """save -> load from file: same margins (restored, not recalibrated) and identical results."""
     lib, head, spec, L, rms = ragged
