@@ -175,7 +175,10 @@ apex_status apex_query(apex_library *lib, const apex_query_desc *desc, apex_quer
  * top-k boundary band (within the FP32 margin of the k-th objective) or within the FP32 margin
  * of a constraint bound; the returned set is the FP64 top-k, and results whose FP32 objectives
  * are closer than the FP32 margin are ordered by those. *n_out = n.
- * EAGAIN: not done yet (the query stays alive); otherwise the query is released. */
+ * EAGAIN: not done yet (the query stays alive); otherwise the query is released.
+ * Waiting: up to two concurrent callers first watch a completion counter (busy, yielding the CPU
+ * every few microseconds) for at most APEX_FETCH_SPIN_MS (default 20) of the timeout, then sleep
+ * until the query finishes; more callers sleep at once. */
 apex_status apex_topk_fetch(apex_library *lib, apex_query_id id, int64_t capacity, int64_t *ids,
                             int32_t *reaction, int64_t *synthons, double *objective, double *outputs,
                             int64_t *n_out, int32_t timeout_ms);
