@@ -1,17 +1,31 @@
-"""Benchmark: compounds scored per second for one exhaustive top-k query (APEX hot path).
+"""Benchmark of the APEX hot path: compounds scored per second of the exhaustive top-k pass.
 
-A step = one query through the C ABI over the whole synthetic library: enumeration of every
-compound (FP16 tensor-core head by default; --precision bf16 or fp32), streaming top-k, FP32
-rescore of the candidates, FP64 rescore of the boundary band and ties, ordering and decode.
-Workloads come from csl_gen (seeded, synthetic; the paper's libraries and labels are not
-available).
+Default (no flags): the ~3e10-compound synthetic CSL `c3_real` (1,000 reactions of 2-3 slots,
+lognormal(2000) slot sizes, d = 256, 256-256-256-13 SiLU head), BF16 tensor-core head with FP32
+boundary rescore and FP64 tie-breaking, in the batched form: one step = one shared pass of the
+circular enumeration serving 8 queries submitted together through the C ABI (the workload's own
+query -- objective 0, six upper bounds at the 0.8 quantile, k = 10^4 -- plus 7 with random convex
+weights over the 5 objectives, six property boxes and k in {100, 1000, 10^4}). `value` counts
+unique compounds scored per second (every compound's head evaluated once per step, whatever the
+number of queries); `query_compounds_per_s` counts sum over queries of their scopes.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2_10m] [--impl ours|reference]
+Beside it on the same JSON line: the FP32 plain single-query path (CUDA cores) on the 1e9-compound
+reaction subset of the same library (a full FP32 pass over 3e10 compounds takes minutes); p50/p99
+query latency over the timed steps (apex_stats); the roofline of the enumeration kernel; the
+FP64 oracle on the host cores over a seeded sample of reactions, which also checks every query of
+the last step with the reaction-decomposed rule (exact per sampled reaction); e2e through the C
+ABI with host buffers.
 
-Under torchrun (N > 1) every rank runs an independent replica (the path does not exchange
-data between GPUs); the step time is the max over ranks and `value` counts all ranks' work.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3_real] [--queries 8]
+                  [--precision bf16|fp16|fp8] [--mode batched|single|serving] [--impl ours|reference]
+
+--mode single: one query per step (the workload's own). --mode serving: Poisson arrivals over the
+resident library at each rate of --rates (queries on random subsets of 1-1000 reactions), p50/p99
+latency and throughput per rate from apex_stats. Under torchrun (N > 1) the reactions are
+partitioned across ranks by compound count, each rank serves every query on its part, and rank 0
+gathers and merges the <= k rows of every query (strong scaling: the library is fixed).
 --impl reference times the FP64 CPU oracle (the only reference this build has) on a bounded
-sample of the same workload.
+sample of the same workload, per step.
 """
 from __future__ import annotations
 
@@ -30,6 +44,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOP_PER_COMPOUND = 2 * (256 * 256 + 256 * 13)  # layers 2 and 3 of the 256-256-256-13 head (MMA work)
+METRIC = "compounds scored/s (BF16/FP8 batched vs FP32 plain), top-k match vs FP64; p99 query ms"
 
 
 def parse():
@@ -37,18 +52,21 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="c2_10m")
+    ap.add_argument("--workload", default="c3_real")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="batched", choices=["batched", "single", "serving"])
+    ap.add_argument("--queries", type=int, default=8, help="queries per batched step")
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"],
+                    help="pass precision of the enumeration (tensor-core bf16/fp16/fp8, or fp32 CUDA cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp32-steps", type=int, default=2)
-    ap.add_argument("--mode", default="single", choices=["single", "batched", "serving"],
-                    help="single: the contract line; batched: 64 queries in one shared pass over the 1e9 subset "
-                         "of c3_real; serving: Poisson arrivals over the resident c3_real library")
-    ap.add_argument("--queries", type=int, default=64)
-    ap.add_argument("--precision", default="fp16", choices=["bf16", "fp16", "fp32"],
-                    help="pass precision of the enumeration (tensor-core bf16/fp16, or fp32 CUDA cores)")
-    ap.add_argument("--rate", type=float, default=5.0, help="serving: arrivals per second")
-    ap.add_argument("--serve-queries", type=int, default=24)
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 plain leg")
+    ap.add_argument("--fp32-subset", type=float, default=1e9, help="compounds of the FP32 plain leg's subset")
+    ap.add_argument("--oracle-compounds", type=float, default=1.1e6,
+                    help="compounds of the seeded reaction sample the oracle enumerates (per query)")
+    ap.add_argument("--autotune", action="store_true", help="autotune the launch shape first (else 2^27 for c3_real)")
+    ap.add_argument("--rates", default="5,20,50,100,200", help="serving: arrival rates (queries/s)")
+    ap.add_argument("--serve-seconds", type=float, default=12.0, help="serving: arrival window per rate")
+    ap.add_argument("--serve-max-queries", type=int, default=160, help="serving: cap on queries per rate")
     return ap.parse_args()
 
 
@@ -265,89 +283,320 @@ def barrier(pg):
         pg.barrier()
 
 
-def cpu_sample_subset(lib, target_compounds: float, seed: int = 3):
-    """Reactions of a seeded shuffle whose sizes sum to about target_compounds (>= 1 reaction)."""
-    rng = np.random.default_rng(seed)
-    order = rng.permutation(lib.n_reactions)
-    sizes = np.array([float(np.prod(lib.sizes_of(int(t)).astype(np.float64))) for t in range(lib.n_reactions)])
+def compounds_per_reaction(lib):
+    return np.array([float(np.prod(lib.sizes_of(t).astype(np.float64))) for t in range(lib.n_reactions)])
+
+
+def step_queries(args, spec, precision=None):
+    import csl_gen
+
+    prec = precision or args.precision
+    if args.mode == "single":
+        return [csl_gen.query_single(args.workload, spec, precision=prec)]
+    return csl_gen.queries_step(args.workload, spec, args.queries, seed=1, precision=prec)
+
+
+def oracle_sample(sizes, n_target: float, seed: int, min_reactions: int = 5):
+    """A seeded sample of small reactions for the oracle: at least min_reactions reactions, drawn
+    from those no larger than max(n_target / 3, the min_reactions-th smallest), until about
+    n_target compounds."""
+    order = np.sort(sizes)
+    cap = max(n_target / 3.0, order[min(min_reactions, len(order)) - 1])
+    cand = np.flatnonzero(sizes <= cap)
+    np.random.default_rng(seed).shuffle(cand)
     chosen, n = [], 0.0
-    for t in order:
-        if n + sizes[t] > target_compounds and chosen:
+    for t in cand:
+        if n + sizes[t] > n_target and len(chosen) >= min_reactions:
             continue
         chosen.append(int(t))
         n += sizes[t]
-        if n >= 0.8 * target_compounds:
+        if n >= 0.8 * n_target and len(chosen) >= min_reactions:
             break
     return sorted(chosen), int(n)
 
 
-def run_cpu_baseline(lib, head, q, seconds: float = 15.0):
-    """The FP64 oracle as it stands, on this host's cores, over a bounded reaction sample."""
+def row_bytes(n_out: int) -> int:
+    return 8 + 4 + 8 * 4 + 8 + 8 * n_out  # id, reaction, synthons, objective, outputs
+
+
+def query_upload_bytes(q) -> int:
+    sub = 0 if q.subset is None else 4 * len(q.subset)
+    return 4 * len(q.weights) + (4 + 8 + 8) * q.m + sub + 880  # descriptor arrays + the device query slot
+
+
+def oracle_leg(L, lib, head, qs, results, n_target, seed=3):
+    """The FP64 oracle as it stands, on every host core, over a seeded sample of small reactions:
+    each query's exact top-(k + 65) of the sample, timed (cpu_baseline), then the reaction-decomposed
+    check of the GPU's rows against it and every returned member rescored by the oracle (the
+    top-k match)."""
+    import csl_gen
     from oracle import oracle as O
 
-    cores = os.cpu_count() or 1
-    # rate probe on the smallest reaction
-    sizes = [float(np.prod(lib.sizes_of(t).astype(np.float64))) for t in range(lib.n_reactions)]
-    t_small = int(np.argmin(sizes))
-    import csl_gen
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import check_members_exact, check_reaction_decomposed, decomposed_query
 
-    probe = csl_gen.Query(q.weights, q.cons_idx, q.lo, q.hi, q.k, np.array([t_small], np.int32), "fp64")
+    sizes = compounds_per_reaction(lib)
+    S, nS = oracle_sample(sizes, n_target, seed)
+    rms = np.array(list(L.info().rms)[: head.dims[-1]])
+    t_or, refs = 0.0, []
+    for q in qs:
+        sq = decomposed_query(q, S)
+        t0 = time.perf_counter()
+        refs.append(O.topk(lib, head, sq) if sq is not None else None)
+        t_or += time.perf_counter() - t0
+    per, ok = [], True
+    for q, r, ref in zip(qs, results, refs):
+        entry = {"k": int(q.k), "n": int(r["n"])}
+        try:
+            v = check_reaction_decomposed(r, lib, head, q, S, rms, ref=ref)
+            entry.update(in_sample=v["in_result"], ambiguous=v["ambiguous"])
+            check_members_exact(r, lib, head, q, rms)
+            entry["ok"] = True
+        except AssertionError as e:
+            entry.update(ok=False, why=str(e)[:200])
+            ok = False
+        per.append(entry)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    sample = (f"{len(S)} of {lib.n_reactions} reactions ({nS} compounds), each of the {len(qs)} queries of a step "
+              f"enumerated exactly, {t_or:.1f} s")
+    cpu = {"value": nS / t_or, "unit": "compounds/s", "cores": cores, "kind": "oracle", "sample": sample}
+    match = {"passed": ok, "rule": "reaction-decomposed on the sampled reactions (exact per reaction) + every "
+                                   "returned member rescored in FP64 (feasible, objective and outputs within 1e-5)",
+             "reactions": S, "sample_compounds": nS, "queries": per}
+    return cpu, match
+
+
+def run_reference(args):
+    """The FP64 oracle (no other reference exists) on the host cores, timed per step on a bounded
+    seeded sample of the workload's reactions: every query of the step over the sample."""
+    import csl_gen
+    from oracle import oracle as O
+
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    full, head, spec = csl_gen.build_workload(args.workload, materialize=False)
+    qs = step_queries(args, spec, precision="fp64")
+    sizes = compounds_per_reaction(full)
+    # rate probe on the smallest reaction
+    t_small = int(np.argmin(sizes))
+    lib1 = full.subset_materialized([t_small])
     t0 = time.perf_counter()
-    O.topk(lib, head, probe)
-    rate = sizes[t_small] / max(time.perf_counter() - t0, 1e-6)
-    subset, n = cpu_sample_subset(lib, rate * seconds)
-    qs = csl_gen.Query(q.weights, q.cons_idx, q.lo, q.hi, q.k, np.array(subset, np.int32), "fp64")
-    t0 = time.perf_counter()
-    ref = O.topk(lib, head, qs)
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "compounds/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(subset)} of {lib.n_reactions} reactions ({n} compounds), full query, {dt:.1f} s",
-            "_subset": subset, "_ref": ref, "_query": qs}
+    for q in qs:
+        O.topk(lib1, head, csl_gen.Query(q.weights, q.cons_idx, q.lo, q.hi, q.k, None, "fp64"))
+    rate = sizes[t_small] / max(time.perf_counter() - t0, 1e-6)  # compounds per second for all queries
+    budget = max(2.0, 150.0 / max(1, args.warmup + args.steps))
+    vals, ms, last = [], [], None
+    for i in range(args.warmup + args.steps):
+        S, nS = oracle_sample(sizes, rate * budget, seed=100 + i, min_reactions=1)
+        lib_s = full.subset_materialized(S)
+        t0 = time.perf_counter()
+        for q in qs:
+            O.topk(lib_s, head, csl_gen.Query(q.weights, q.cons_idx, q.lo, q.hi, q.k, None, "fp64"))
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            vals.append(nS / dt)
+            ms.append(1e3 * float(sizes.sum()) / (nS / dt))
+            last = (S, nS, dt)
+    v = float(np.mean(vals))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    N = float(sizes.sum())
+    line = {"metric": METRIC, "value": v, "unit": "compounds/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": run_config(args, full, head, qs, N, world=1), "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "compounds/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step {len(last[0])} seeded reactions (~{last[1]} compounds) x "
+                                       f"{len(qs)} queries, ~{last[2]:.1f} s; ms_per_step extrapolated to the "
+                                       f"whole library"},
+            "e2e": {"value": v, "unit": "compounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_config(args, lib, head, qs, N, world):
+    form = "batched" if args.mode == "batched" else "single query"
+    return {"workload": f"{args.workload} {form}: {len(qs)} quer{'ies' if len(qs) > 1 else 'y'} per shared pass",
+            "n_compounds": int(N), "n_reactions": int(lib.n_reactions), "queries_per_step": len(qs),
+            "k": [int(q.k) for q in qs], "n_constraints": [int(q.m) for q in qs],
+            "head": "-".join(str(x) for x in head.dims) + f" {head.activation}",
+            "precision": f"{args.precision} pass + fp32 boundary rescore + fp64 tie-break",
+            "parallelism": f"reactions sharded x{world} (gather merge of <= k rows per query)" if world > 1
+            else "1 GPU",
+            "l2": "inputs larger than L2 (the 16-bit P table alone is 2.1 GB on c3_real) and a 512 MB write before "
+                  "every timed step"}
 
 
 def run_batched(args):
-    """64 queries (random convex weights over the 5 objectives, 8 property boxes, k from
-    {10 .. 1e5}) submitted together over the 1e9-compound subset of c3_real: one shared pass."""
     import torch
 
     import csl_gen
-    from paper_2510_24380_b300 import apex
+    from paper_2510_24380_b300 import apex, shard
 
-    full, head, spec = csl_gen.build_workload("c3_real", materialize=False)
-    sub = csl_gen.subset_prefix(full, 0, 1e9)
-    lib = full.subset_materialized(sub)
-    N = int(sum(np.prod(lib.sizes_of(t).astype(np.float64)) for t in range(lib.n_reactions)))
-    stats = csl_gen.load_stats("c3_real")
-    qs = csl_gen.queries_batched(stats, 5, 8, args.queries, seed=1, precision=args.precision)
-    stream = torch.cuda.Stream()
-    L = apex.Library(lib, head, precisions=("fp32", args.precision), stream=stream.cuda_stream)
-    tune = L.autotune(args.precision, n_queries=16, k=10000)  # launch shapes for this library
-    L.run(qs[0])  # warm-up
+    world, rank, local, pg = dist_setup(args)
+    t_load0 = time.perf_counter()
+    lib, head, spec = csl_gen.build_workload(args.workload)
+    qs = step_queries(args, spec)
+    sizes = compounds_per_reaction(lib)
+    N = float(sizes.sum())
+    prec = args.precision
+    dev = local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    L = apex.Library(lib, head, precisions=("fp32", prec), device=dev, stream=stream.cuda_stream, seed=0)
+    load_s = time.perf_counter() - t_load0
+    if args.autotune:
+        tune = L.autotune(prec, n_queries=len(qs), k=10000, subset=np.arange(min(30, lib.n_reactions)))
+    elif N > 1e9 and len(head.dims) > 2:
+        L.set_launch_shape(1 << 27, 32)  # 2^27 compounds per launch: the autotuner's choice on this library
+        tune = {"chosen_chunk_compounds": 1 << 27, "how": "fixed (autotuned choice on this workload)"}
+    else:
+        tune = {"chosen_chunk_compounds": 1 << 25, "how": "library default"}
+
+    def run_local(lq):
+        ids = [L.query(q) for q in lq]
+        return [L.fetch(i, q.k) for i, q in zip(ids, lq)]
+
+    runner = shard.ShardedRunner(sizes, rank, world, run_local, L.n_outputs)
+    n_rank = float(sizes[runner.part].sum())
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    for _ in range(args.warmup):
+        runner.run(qs)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ids = [L.query(q) for q in qs]
-    res, per, pass_stats = [], [], None
-    for i, q in zip(ids, qs):
-        res.append(L.fetch(i, q.k))
-        st = L.stats(-1)
-        if pass_stats is None:
-            pass_stats = {k: round(st[k], 3) if isinstance(st[k], float) else st[k]
-                          for k in ("n_launches", "enumerate_ms", "host_pass_ms", "gpu_ms", "latency_ms")}
-        per.append((int(q.k), st["n_restarts"], st["n_candidates"], st["n_rescored_fp64"], round(st["latency_ms"], 1),
-                    round(st["host_finalize_ms"], 1), round(st["host_start_ms"], 1)))
-    dt = time.perf_counter() - t0
-    out = {"mode": "batched", "workload": "c3_real 1e9-compound subset", "precision": args.precision, "n_compounds": N,
-           "reactions": len(sub), "queries": len(qs), "k": [int(q.k) for q in qs][:8],
-           "wall_s": dt, "head_evaluations_per_s": N / dt, "query_compounds_per_s": len(qs) * N / dt,
-           "results": int(sum(r["n"] for r in res)), "autotune": tune, "first_query_pass": pass_stats,
-           "per_query_k_restarts_candidates_fp64_latency_finalize_start": per[:64]}
+    barrier(pg)
+
+    # ------------------------------------------------------------- timed region (device events)
+    clocks = Clocks(dev) if rank == 0 else None
+    L.reset_serving_stats()
+    launches0 = apex.apex_kernel_launches()
+    dev_ms, e2e_ms, res = [], [], None
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        torch.cuda.synchronize()
+        barrier(pg)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        res = runner.run(qs)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        dev_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches = apex.apex_kernel_launches() - launches0
+    sv = L.serving_stats()
+    clk = clocks.stop() if clocks else None
+    barrier(pg)
+    t_dev = max_over_ranks(pg, float(np.sum(dev_ms)))
+    t_e2e = max_over_ranks(pg, float(np.sum(e2e_ms)))
+    last_stats = [L.stats(-1)]
+    if rank != 0:
+        barrier(pg)
+        L.close()
+        return
+
+    # ------------------------------------------------------------- FP32 plain path, same library
+    fp32 = None
+    if not args.no_fp32:
+        sub = csl_gen.subset_prefix(lib, 0, args.fp32_subset)
+        n_sub = float(sizes[sub].sum())
+        q0 = qs[0]
+        q32 = csl_gen.Query(q0.weights, q0.cons_idx, q0.lo, q0.hi, q0.k, np.array(sub, np.int32), "fp32")
+        q16 = csl_gen.Query(q0.weights, q0.cons_idx, q0.lo, q0.hi, q0.k, np.array(sub, np.int32), prec)
+        L.run(csl_gen.Query(q0.weights, q0.cons_idx, q0.lo, q0.hi, q0.k,
+                            np.array([int(np.argmin(sizes))], np.int32), "fp32"))  # warm-up
+        times = {}
+        rows = {}
+        for name, qq in (("fp32", q32), (prec, q16)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rows[name] = L.run(qq)
+            e1.record(stream)
+            e1.synchronize()
+            times[name] = e0.elapsed_time(e1)
+        fp32 = {"value": n_sub / (times["fp32"] * 1e-3), "unit": "compounds/s",
+                "workload": f"{args.workload} reaction subset of {len(sub)} reactions ({int(n_sub)} compounds; a full "
+                            f"FP32 pass over the library takes minutes), the workload's query, single query, FP32 "
+                            f"CUDA cores",
+                "ms": times["fp32"],
+                f"{prec}_single_query_same_subset": n_sub / (times[prec] * 1e-3),
+                "same_topk_set_as_tc_pass": bool(set(rows["fp32"]["ids"].tolist()) == set(rows[prec]["ids"].tolist()))}
+
+    P, kind = peaks()
+    K = args.steps
+    enum_ms = sv["enumerate_ms"] / K
+    achieved = FLOP_PER_COMPOUND * n_rank / (enum_ms * 1e-3) / 1e12
+    linear = len(head.dims) == 2
+    peak_s = P.get("bf16_tflops_sustained", 1400.0)
+    peak_b = P.get("bf16_tflops", 1800.0)
+    if prec == "fp8":
+        peak_s, peak_b = 2 * peak_s, 2 * peak_b  # layer 2 at the FP8 rate (nominal 2x of BF16)
+    if linear:
+        roof = linear_roofline(n_rank, qs[0], lib, enum_ms, clk)
+    else:
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_s, "unit": "TFLOP/s", "frac": achieved / peak_s,
+                "traffic": recorded_traffic(f"k_tc_head_{args.workload}.md"),
+                "kernel": "k_tc_head (enumeration: layer-1 sums and SiLU on CUDA cores, layers 2-3 on tcgen05)",
+                "flop_per_compound": FLOP_PER_COMPOUND,
+                "peak_kind": f"{kind} bf16 sustained (the kernel runs for seconds inside each step); "
+                             f"against the {kind} burst peak {peak_b:.0f}: frac {achieved / peak_b:.3f}",
+                "frac_vs_burst": achieved / peak_b, "kernel_ms_per_step": enum_ms,
+                "launches_per_step": sv["n_enumeration_launches"] / K,
+                "mufu": mufu_bound(n_rank, head, enum_ms, clk)}
+    d2h = int(sum(r["n"] for r in res)) * row_bytes(L.n_outputs)
+    h2d = int(sum(query_upload_bytes(q) for q in qs))
+    qc = float(sum(N if q.subset is None else sizes[q.subset].sum() for q in qs))
+    line = {
+        "metric": METRIC,
+        "value": N * K / (t_dev * 1e-3),
+        "unit": "compounds/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": t_dev / K,
+        "higher_is_better": True,
+        "scaling": "strong",
+        "vs_baseline": None,
+        "dtype": prec,
+        "data": "synthetic (seeded N(0,1) synthon embeddings, random-init head; the paper's libraries are unavailable)",
+        "config": run_config(args, lib, head, qs, N, world),
+        "query_compounds_per_s": qc * K / (t_dev * 1e-3),
+        "latency": {"p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "max_ms": sv["max_ms"],
+                    "queue_p99_ms": sv["queue_p99_ms"], "n_queries": sv["n_queries"]},
+        "e2e": {"value": N * K / (t_e2e * 1e-3), "unit": "compounds/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "p50_ms": float(np.percentile(e2e_ms, 50)),
+                "p99_ms": float(np.percentile(e2e_ms, 99))},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "fp32_plain": fp32,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, match = oracle_leg(L, lib, head, qs, res, args.oracle_compounds)
+        line["topk_match_vs_fp64_oracle"] = match
+        line["cpu_baseline"] = cpu
+    line["queries"] = [{"k": int(q.k), "n": int(r["n"])} for q, r in zip(qs, res)]
+    st = last_stats[0]
+    line["last_query_stats"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()
+                                if k in ("n_candidates", "n_rescored_fp64", "n_restarts", "n_margin_reruns",
+                                         "pass_err_ratio", "fp32_err_ratio", "n_launches", "enumerate_ms",
+                                         "latency_ms", "host_finalize_ms")}
+    line["host"] = {"load_s": round(load_s, 1), "launch_shape": tune,
+                    "margins": {"pass": [round(x, 5) for x in list(getattr(L.info(), "err_" + prec))[:L.n_outputs]]
+                                if prec != "fp32" else None,
+                                "fp32": [float("%.3g" % x) for x in list(L.info().err_fp32)[:L.n_outputs]]}}
+    line["steps_detail_ms"] = [round(x, 2) for x in dev_ms]
+    barrier(pg)
     L.close()
-    print(json.dumps(out))
+    print(json.dumps(line))
 
 
 def run_serving(args):
-    """Poisson arrivals over the resident c3_real library; each query takes a random subset of
-    1..1000 reactions, random weights and boxes, k log-uniform in [10, 1e5]."""
+    """Poisson arrivals at each rate over the resident library: each query on a random subset of
+    1..1000 reactions (log-uniform count), random weights and boxes, k log-uniform in [10, 10^5];
+    p50/p99 latency, queue time and throughput per rate from apex_stats."""
     import threading
 
     import torch
@@ -355,213 +604,49 @@ def run_serving(args):
     import csl_gen
     from paper_2510_24380_b300 import apex
 
-    lib, head, spec = csl_gen.build_workload("c3_real")
-    stats = csl_gen.load_stats("c3_real")
-    arrivals = csl_gen.serving_stream(stats, 5, 8, lib.n_reactions, args.serve_queries, args.rate, seed=2,
-                                      precision=args.precision)
+    lib, head, spec = csl_gen.build_workload(args.workload)
+    stats = csl_gen.load_stats(args.workload)
     stream = torch.cuda.Stream()
     L = apex.Library(lib, head, precisions=("fp32", args.precision), stream=stream.cuda_stream)
-    tune = L.autotune(args.precision, n_queries=8, k=10000, subset=np.arange(min(30, lib.n_reactions)))
-    sizes = np.array([float(np.prod(lib.sizes_of(t).astype(np.float64))) for t in range(lib.n_reactions)])
-    done = []
-    lock = threading.Lock()
-
-    def fetcher(qid, k, scope):
-        r = L.fetch(qid, k)
-        st = L.stats(-1)
-        with lock:
-            done.append((st["latency_ms"], scope, r["n"], st["queue_ms"]))
-
-    threads = []
-    t0 = time.perf_counter()
-    for t_arr, q in arrivals:
-        now = time.perf_counter() - t0
-        if t_arr > now:
-            time.sleep(t_arr - now)
-        qid = L.query(q)
-        th = threading.Thread(target=fetcher, args=(qid, int(q.k), float(sizes[q.subset].sum())))
-        th.start()
-        threads.append(th)
-    for th in threads:
-        th.join()
-    wall = time.perf_counter() - t0
-    lat = np.array([d[0] for d in done])
-    scope = np.array([d[1] for d in done])
-    out = {"mode": "serving", "workload": "c3_real resident", "n_compounds": float(sizes.sum()),
-           "rate_hz": args.rate, "queries": len(done), "wall_s": wall,
-           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-           "mean_scope_compounds": float(scope.mean()), "query_compounds_per_s": float(scope.sum() / wall),
-           "autotune": tune}
+    if lib.n_reactions >= 100:
+        L.set_launch_shape(1 << 27, 32)
+    out = {"mode": "serving", "workload": f"{args.workload} resident", "precision": args.precision,
+           "n_compounds": float(compounds_per_reaction(lib).sum()), "rates": []}
+    for i, rate in enumerate(float(x) for x in args.rates.split(",")):
+        n_q = int(min(args.serve_max_queries, max(8, rate * args.serve_seconds)))
+        arrivals = csl_gen.serving_stream(stats, spec["n_obj"], spec["n_prop"], lib.n_reactions, n_q, rate, seed=2 + i,
+                                          precision=args.precision)
+        L.reset_serving_stats()
+        threads = []
+        t0 = time.perf_counter()
+        for t_arr, q in arrivals:
+            now = time.perf_counter() - t0
+            if t_arr > now:
+                time.sleep(t_arr - now)
+            qid = L.query(q)
+            th = threading.Thread(target=L.fetch, args=(qid, int(q.k)))
+            th.start()
+            threads.append(th)
+        for th in threads:
+            th.join()
+        sv = L.serving_stats()
+        out["rates"].append({"rate_hz": rate, "queries": sv["n_queries"], "failed": sv["n_failed"],
+                             "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "max_ms": sv["max_ms"],
+                             "queue_p50_ms": sv["queue_p50_ms"], "queue_p99_ms": sv["queue_p99_ms"],
+                             "wall_s": sv["wall_ms"] / 1e3, "query_compounds_per_s": sv["query_compounds_per_s"],
+                             "head_evaluations_per_s": sv["head_evaluations_per_s"],
+                             "mean_scope_compounds": sv["query_compounds"] / max(1, sv["n_queries"])})
     L.close()
     print(json.dumps(out))
 
 
 def main():
     args = parse()
-    if args.mode == "batched":
-        return run_batched(args)
+    if args.impl == "reference":
+        return run_reference(args)
     if args.mode == "serving":
         return run_serving(args)
-    world, rank, local, pg = dist_setup(args)
-    import csl_gen
-
-    lib, head, spec = csl_gen.build_workload(args.workload)
-    q = csl_gen.query_single(args.workload, spec, precision=args.precision)
-    N = int(sum(np.prod(lib.sizes_of(t).astype(np.float64)) for t in range(lib.n_reactions)))
-    config = {"workload": args.workload, "n_compounds": N, "k": int(q.k), "n_constraints": int(q.m),
-              "head": "-".join(str(x) for x in head.dims) + f" {head.activation}", "precision": f"{args.precision} pass + fp32/fp64 rescore",
-              "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) before every timed step"}
-
-    if args.impl == "reference":
-        if rank != 0:
-            return
-        per_step = []
-        info = None
-        for i in range(args.warmup + args.steps):
-            r = run_cpu_baseline(lib, head, q, seconds=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
-            if i >= args.warmup:
-                per_step.append(r)
-                info = r
-        v = float(np.mean([r["value"] for r in per_step]))
-        line = {"metric": "compounds scored per second (exhaustive top-k query)", "value": v, "unit": "compounds/s",
-                "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": float(np.mean([1e3 * int(r["sample"].split("(")[1].split(" ")[0]) / r["value"]
-                                              for r in per_step])),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": config, "impl": "reference",
-                "cpu_baseline": {"value": v, "unit": "compounds/s", "cores": info["cores"], "kind": "oracle",
-                                 "sample": info["sample"]},
-                "e2e": {"value": v, "unit": "compounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
-        return
-
-    import torch
-
-    from paper_2510_24380_b300 import apex
-
-    dev = local
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.Stream(device=dev)
-    L = apex.Library(lib, head, precisions=("fp32", args.precision), device=dev, stream=stream.cuda_stream, seed=0)
-    cpus0 = os.sched_getaffinity(0)
-    worker_cpu = L.keep_caller_off_worker_cpu()  # this thread polls for results: not on the worker's CPU
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
-
-    def step(query):
-        return L.run(query)
-
-    for _ in range(args.warmup):
-        step(q)
-    torch.cuda.synchronize()
-    barrier(pg)
-
-    # ------------------------------------------------------------- timed region (device events)
-    clocks = Clocks(dev) if rank == 0 else None
-    launches0 = apex.apex_kernel_launches()
-    dev_ms, e2e_ms, enum_ms, scored, step_stats = [], [], [], [], []
-    res = None
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        t0 = time.perf_counter()
-        e0.record(stream)
-        res = step(q)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        dev_ms.append(e0.elapsed_time(e1))
-        st = L.stats(-1)
-        enum_ms.append(st["enumerate_ms"])
-        scored.append(st["n_scored"])
-        step_stats.append({k: round(st[k], 3) if isinstance(st[k], float) else st[k]
-                           for k in ("gpu_ms", "enumerate_ms", "n_restarts", "n_candidates", "n_rescored_fp64")})
-    torch.cuda.synchronize()
-    launches = apex.apex_kernel_launches() - launches0
-    clk = clocks.stop() if clocks else None
-    barrier(pg)
-    t_dev = max_over_ranks(pg, float(np.sum(dev_ms)))
-    t_e2e = max_over_ranks(pg, float(np.sum(e2e_ms)))
-    last_stats = L.stats(-1)
-
-    # ------------------------------------------------------------- FP32 plain path, same query
-    fp32_rate = None
-    if args.fp32_steps > 0:
-        q32 = csl_gen.Query(q.weights, q.cons_idx, q.lo, q.hi, q.k, q.subset, "fp32")
-        r32 = L.run(q32)
-        t32 = []
-        for _ in range(args.fp32_steps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r32 = L.run(q32)
-            e1.record(stream)
-            e1.synchronize()
-            t32.append(e0.elapsed_time(e1))
-        fp32_rate = N / (np.mean(t32) * 1e-3)
-        same = set(r32["ids"].tolist()) == set(res["ids"].tolist())
-    if rank != 0:
-        L.close()
-        return
-
-    P, kind = peaks()
-    mean_enum = float(np.mean(enum_ms))
-    achieved = FLOP_PER_COMPOUND * N / (mean_enum * 1e-3) / 1e12
-    peak = P.get("bf16_tflops", 1800.0)
-    linear = len(head.dims) == 2
-    d2h = int(res["n"]) * (8 + 4 + 8 * 4 + 8 + 8 * L.n_outputs)
-    h2d = 4 * len(q.weights) + (4 + 8 + 8) * q.m + 880  # query weights/boxes + the device query slot
-    value = world * N * args.steps / (t_dev * 1e-3)
-    line = {
-        "metric": "compounds scored per second (exhaustive top-k query)",
-        "value": value,
-        "unit": "compounds/s",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": t_dev / args.steps,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": args.precision,
-        "data": "synthetic (seeded N(0,1) synthon embeddings, random-init head; paper libraries unavailable)",
-        "config": config,
-        "e2e": {"value": world * N * args.steps / (t_e2e * 1e-3), "unit": "compounds/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "p50_ms": float(np.percentile(e2e_ms, 50)),
-                "p99_ms": float(np.percentile(e2e_ms, 99))},
-        "gpu_launches": int(launches),
-        "roofline": linear_roofline(N, q, lib, mean_enum, clk) if linear else {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": recorded_traffic() if args.workload == "c2_10m" and args.precision == "fp16" else None,
-                     "kernel": "k_tc_head (enumeration, layers 2-3 on tcgen05)",
-                     "flop_per_compound": FLOP_PER_COMPOUND, "peak_kind": f"{kind} bf16 burst (fp16 dense rate equals bf16)",
-                     "kernel_ms_per_step": mean_enum, "mufu": mufu_bound(N, head, mean_enum, clk)},
-        "fp32_plain": {"value": fp32_rate, "unit": "compounds/s", "same_topk_set_as_tc_pass": bool(same) if fp32_rate else None},
-        "query": {k: last_stats[k] for k in ("n_candidates", "n_rescored_fp64", "n_restarts", "n_launches",
-                                             "gpu_ms", "enumerate_ms", "queue_ms", "latency_ms", "host_start_ms",
-                                             "host_pass_ms", "host_finalize_ms")},
-        "clocks": clk,
-        "steps_detail": step_stats,
-        "margins": {"err_pass": [round(x, 5) for x in list(getattr(L.info(), "err_" + args.precision))[:L.n_outputs]],
-                    "err_fp32": [float("%.3g" % x) for x in list(L.info().err_fp32)[:L.n_outputs]],
-                    "rms": [round(x, 4) for x in list(L.info().rms)[:L.n_outputs]]},
-    }
-    line["host"] = {"worker_cpu": worker_cpu, "caller_cpus": len(os.sched_getaffinity(0))}
-    os.sched_setaffinity(0, cpus0)  # the oracle baseline runs on every core
-    if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
-        cb = run_cpu_baseline(lib, head, q)
-        # GPU answer on the same sampled reactions, checked against the oracle's
-        qs = cb["_query"]
-        qg = csl_gen.Query(qs.weights, qs.cons_idx, qs.lo, qs.hi, qs.k, qs.subset, args.precision)
-        rg = L.run(qg)
-        match = set(rg["ids"].tolist()) == set(cb["_ref"].ids.tolist())
-        line["cpu_baseline"] = {k: v for k, v in cb.items() if not k.startswith("_")}
-        line["topk_match_vs_fp64_oracle"] = {"sample": cb["sample"], "exact_set": bool(match), "k": int(q.k),
-                                             "n": int(rg["n"])}
-    L.close()
-    print(json.dumps(line))
+    return run_batched(args)
 
 
 if __name__ == "__main__":

@@ -15,10 +15,10 @@ from .library import (
     library_from_sizes,
 )
 from .configs import WORKLOADS, build_workload, subset_prefix, workload_sizes
-from .queries import Query, query_single, queries_batched, random_query, serving_stream, load_stats
+from .queries import Query, query_single, queries_batched, queries_step, random_query, serving_stream, load_stats
 
 __all__ = [
     "CSL", "Head", "make_library", "make_head", "lognormal_slot_sizes", "library_from_sizes",
     "WORKLOADS", "build_workload", "subset_prefix", "workload_sizes",
-    "Query", "query_single", "queries_batched", "random_query", "serving_stream", "load_stats",
+    "Query", "query_single", "queries_batched", "queries_step", "random_query", "serving_stream", "load_stats",
 ]

@@ -133,3 +133,18 @@ def serving_stream(stats: dict, n_obj: int, n_prop: int, n_reactions: int, n_que
         k = int(round(math.exp(rng.uniform(math.log(k_range[0]), math.log(k_range[1])))))
         out.append((t, random_query(rng, stats, n_obj, n_prop, k, subset=sub, precision=precision)))
     return out
+
+
+def queries_step(name: str, spec: dict, n_queries: int, seed: int, stats: dict | None = None,
+                 precision: str = "bf16", ks=(100, 1000, 10000), n_boxes: int = 6):
+    """The queries of one batched step over a workload: the workload's own query first, then
+    n_queries - 1 random ones (Dirichlet(1) weights over the objectives, n_boxes property boxes of
+    joint pass rate log-uniform in [1 %, 50 %], k drawn from ks), all on the whole library."""
+    stats = stats if stats is not None else load_stats(name)
+    out = [query_single(name, spec, stats, precision=precision)]
+    rng = _rng(seed, 8)
+    for _ in range(n_queries - 1):
+        k = int(rng.choice(ks))
+        out.append(random_query(rng, stats, spec["n_obj"], spec["n_prop"], k, precision=precision, n_boxes=n_boxes))
+    return out
+

@@ -141,6 +141,21 @@ typedef struct {
   double host_start_ms;         /* worker wall time spent estimating the start threshold */
   double host_pass_ms;          /* worker wall time of the pass steps that served it */
   double host_finalize_ms;      /* worker wall time of exact selection, ordering and decode */
+  /* Runtime check of the calibrated margins on the compounds that matter (the candidates, i.e. the
+   * tail of the objective distribution, not a uniform sample): at finalization every candidate has
+   * its pass objective and its FP32 rescore, and every FP64-rescored member its FP32 and FP64
+   * outputs. pass_err_ratio = max |pass - FP32| objective / the pass's objective margin;
+   * fp32_err_ratio = max over outputs of max |FP32 - FP64| / that output's FP32 margin. A ratio
+   * above 1 means a margin was too small for this query: its pass is rerun with both margins
+   * widened (at least 2x, and at least twice the observed ratio), up to 4 times; the ratios
+   * reported are those of the final run. */
+  int32_t n_margin_reruns;
+  int32_t reserved;
+  double pass_err_ratio;
+  double fp32_err_ratio;
+  int64_t first_item;           /* work item of the library's circular pass at which the query's (last)
+                                   pass began: queries that arrive while others run join at the
+                                   pass's current position */
 } apex_query_stats_t;
 
 /* Pure host: N = sum_t prod_j slot_sizes (App. A.1). EINVAL on bad shapes or int64 overflow. */
@@ -176,6 +191,8 @@ apex_status apex_query(apex_library *lib, const apex_query_desc *desc, apex_quer
  * of a constraint bound; the returned set is the FP64 top-k, and results whose FP32 objectives
  * are closer than the FP32 margin are ordered by those. *n_out = n.
  * EAGAIN: not done yet (the query stays alive); otherwise the query is released.
+ * Several threads may fetch the same id at once: the first to see it finished receives its rows
+ * (or its error) and releases it; the others then return APEX_ENOTFOUND.
  * Waiting: up to two concurrent callers first watch a completion counter (busy, yielding the CPU
  * every few microseconds) for at most APEX_FETCH_SPIN_MS (default 20) of the timeout, then sleep
  * until the query finishes; more callers sleep at once. */
@@ -189,6 +206,33 @@ apex_status apex_cancel(apex_library *lib, apex_query_id id);
 /* Statistics of a finished (not yet fetched) query, or of the last fetched one when id < 0. */
 apex_status apex_query_stats(apex_library *lib, apex_query_id id, apex_query_stats_t *out);
 
+/* Serving statistics of the library over the queries fetched since the load or the last
+ * apex_stats_reset (the request loop's view: continuous batching serves many queries at once, so
+ * latency and throughput are properties of the mix, not of one query). Latencies are host wall
+ * times from apex_query until the query's results were ready; percentiles interpolate linearly
+ * between the two nearest ranks (rank p/100 * (n - 1) of the sorted sample), over the last
+ * APEX_STATS_WINDOW fetched queries. The window of the throughput figures runs from the earliest
+ * submission to the latest completion among the counted queries. */
+#define APEX_STATS_WINDOW (1 << 20)
+typedef struct {
+  int64_t n_queries;            /* fetched with APEX_OK */
+  int64_t n_failed;             /* fetched with an error (cancelled, failed, timed out) */
+  double p50_ms, p99_ms, max_ms, mean_ms;   /* latency of the APEX_OK queries */
+  double queue_p50_ms, queue_p99_ms;        /* time from apex_query to admission into a slot */
+  double wall_ms;               /* earliest submission -> latest completion of the counted queries */
+  double query_compounds;       /* sum over those queries of the compounds in their reaction subsets */
+  double head_evaluations;      /* compounds scored by enumeration launches since the load or reset
+                                   (one per compound and launch, whatever the number of queries the
+                                   launch served) */
+  double query_compounds_per_s; /* query_compounds / wall */
+  double head_evaluations_per_s;/* head_evaluations / wall */
+  double enumerate_ms;          /* device time (CUDA events) of the enumeration launches retired since
+                                   the load or reset */
+  int64_t n_enumeration_launches;
+} apex_stats_t;
+apex_status apex_stats(apex_library *lib, apex_stats_t *out);
+apex_status apex_stats_reset(apex_library *lib);
+
 /* Scores given compounds (host ids [n]) through the gather kernels: precision APEX_FP32
  * (CUDA cores), APEX_FP64 (plain form g = sum u, then the head), or a reduced precision the
  * library was built with (APEX_BF16, APEX_FP16, APEX_FP8: the tensor-core kernel over the id
@@ -201,6 +245,9 @@ apex_status apex_score_ids(apex_library *lib, int32_t precision, int64_t n, cons
 
 /* Runs the production enumeration kernel of the given precision over one reaction and
  * writes the raw outputs of every compound, in id order: host float [N_t x n_outputs].
+ * reaction = -1: the whole library, in launches shaped like those of a query's pass (consecutive
+ * work items in library order, about the library's compounds per launch each, apex_set_launch_shape
+ * / apex_autotune) into host float [N x n_outputs]; at most 16 GB of outputs, else APEX_EINVAL.
  * capacity is the number of rows of outputs. Synchronous; meant for tests of raw scores. */
 apex_status apex_dump_outputs(apex_library *lib, int32_t precision, int32_t reaction, float *outputs,
                               int64_t capacity);
@@ -223,10 +270,12 @@ apex_status apex_topk_select(const float *keys, const int64_t *ids, int64_t n, i
  * the paper. Its scratch is one file-scope device array of fixed size (about 1.6 MB, held by
  * every GPU that loads the library until the process exits), so it calls no cudaMalloc,
  * cudaFree or allocating routine. min(k, n) must be <= APEX_SELECT_NOALLOC_MAX_K, else EINVAL.
- * The first call on a device looks up the array's device address (with that device current);
- * make that first call before any stream capture. All calls share the one array and it keeps
- * the last call's contents: calls that overlap on the GPU (other streams, other host threads)
- * race; each call clears the state it needs and synchronizes its stream before returning. */
+ * The first call on a device looks up the array's device address (with that device current) and,
+ * under CUDA's lazy module loading, is also where the select kernels' module gets loaded, so it
+ * takes longer than later calls; make that first call before any stream capture. All calls share
+ * the one array and it keeps the last call's contents: calls that overlap on the GPU (other
+ * streams, other host threads) race. Each call clears the state it needs, and before returning
+ * it waits for its stream to finish (cudaStreamSynchronize on cuda_stream). */
 #define APEX_SELECT_NOALLOC_MAX_K 65536
 apex_status apex_topk_select_noalloc(const float *keys, const int64_t *ids, int64_t n, int64_t k, float *out_keys,
                                      int64_t *out_ids, int64_t *n_out, void *cuda_stream);

@@ -20,13 +20,31 @@ LIB = os.path.join(HERE, "libapex_oracle.so")
 ACT = {"identity": 0, "relu": 1, "silu": 2}
 
 
+GCC_FLAGS = ["-O3", "-march=x86-64-v3", "-std=c11", "-fPIC", "-shared", "-pthread"]
+
+
+def _source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256(" ".join(GCC_FLAGS).encode())
+    with open(SRC, "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (x86-64-v3 so the binary runs on any AVX2 host)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+    """Compile the oracle with gcc (x86-64-v3 so the binary runs on any AVX2 host). Rebuilt whenever
+    the source or the flags differ from those of the last build (sha256 stamp beside the binary)."""
+    stamp = LIB + ".sha256"
+    want = _source_hash()
+    have = open(stamp).read().strip() if os.path.exists(stamp) else ""
+    if force or not os.path.exists(LIB) or have != want:
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O3", "-march=x86-64-v3", "-std=c11", "-fPIC", "-shared", "-pthread",
-                               SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", *GCC_FLAGS, SRC, "-o", tmp, "-lm"])
         os.replace(tmp, LIB)
+        with open(stamp + f".tmp{os.getpid()}", "w") as f:
+            f.write(want + "\n")
+        os.replace(stamp + f".tmp{os.getpid()}", stamp)
     return LIB
 
 

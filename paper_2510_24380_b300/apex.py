@@ -81,6 +81,21 @@ class QueryStats(C.Structure):
         ("n_feasible_lower", C.c_int64), ("n_restarts", C.c_int32), ("n_launches", C.c_int32),
         ("queue_ms", C.c_double), ("latency_ms", C.c_double), ("gpu_ms", C.c_double), ("enumerate_ms", C.c_double),
         ("host_start_ms", C.c_double), ("host_pass_ms", C.c_double), ("host_finalize_ms", C.c_double),
+        ("n_margin_reruns", C.c_int32), ("reserved", C.c_int32), ("pass_err_ratio", C.c_double),
+        ("fp32_err_ratio", C.c_double), ("first_item", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServingStats(C.Structure):
+    _fields_ = [
+        ("n_queries", C.c_int64), ("n_failed", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+        ("max_ms", C.c_double), ("mean_ms", C.c_double), ("queue_p50_ms", C.c_double), ("queue_p99_ms", C.c_double),
+        ("wall_ms", C.c_double), ("query_compounds", C.c_double), ("head_evaluations", C.c_double),
+        ("query_compounds_per_s", C.c_double), ("head_evaluations_per_s", C.c_double),
+        ("enumerate_ms", C.c_double), ("n_enumeration_launches", C.c_int64),
     ]
 
     def as_dict(self):
@@ -100,6 +115,8 @@ SYMBOLS = {
                         C.c_int32],
     "apex_cancel": [C.c_void_p, C.c_int64],
     "apex_query_stats": [C.c_void_p, C.c_int64, C.POINTER(QueryStats)],
+    "apex_stats": [C.c_void_p, C.POINTER(ServingStats)],
+    "apex_stats_reset": [C.c_void_p],
     "apex_worker_cpu": [C.c_void_p, C.POINTER(C.c_int32)],
     "apex_set_finalize_cover": [C.c_void_p, C.c_int64],
     "apex_score_ids": [C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
@@ -306,6 +323,15 @@ class Library:
         s = QueryStats()
         _check(load().apex_query_stats(self.h, int(qid), C.byref(s)), "apex_query_stats")
         return s.as_dict()
+
+    def serving_stats(self) -> dict:
+        """Latency percentiles and throughput over the queries fetched since load or reset (apex_stats)."""
+        s = ServingStats()
+        _check(load().apex_stats(self.h, C.byref(s)), "apex_stats")
+        return s.as_dict()
+
+    def reset_serving_stats(self):
+        _check(load().apex_stats_reset(self.h), "apex_stats_reset")
 
     def score_ids(self, ids, precision: str = "fp32"):
         ids = np.ascontiguousarray(ids, np.int64)

@@ -1,7 +1,13 @@
-"""Builds libapex_b300.so in-tree with nvcc for sm_103a (tcgen05 / TMA need the 'a' target)."""
+"""Builds libapex_b300.so in-tree with nvcc for sm_103a (tcgen05 / TMA need the 'a' target).
+
+The library is rebuilt whenever the content of its sources (csrc/*.cu, csrc/*.cuh, include/apex.h)
+or the compiler flags differ from those it was last built from: a stamp file beside the library
+holds their sha256, so a copied or checked-out tree with newer-looking but different sources, or a
+stale binary with newer timestamps, is never reused."""
 from __future__ import annotations
 
 import glob
+import hashlib
 import os
 import shutil
 import subprocess
@@ -12,6 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libapex_b300.so")
+STAMP = LIB + ".sha256"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
@@ -28,16 +35,28 @@ def _inputs():
         os.path.join(ROOT, "include", "apex.h")]
 
 
+def source_hash() -> str:
+    """sha256 over the names and contents of every input and the compile and link flags."""
+    h = hashlib.sha256()
+    h.update(" ".join(ARCH + FLAGS).encode())
+    for f in _inputs():
+        h.update(os.path.relpath(f, ROOT).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in _inputs())
+    with open(STAMP) as f:
+        return f.read().strip() == source_hash()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
+    want = source_hash()
     os.makedirs(OBJ, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     cc = nvcc()
@@ -63,6 +82,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP + f".tmp{os.getpid()}", "w") as f:
+        f.write(want + "\n")
+    os.replace(STAMP + f".tmp{os.getpid()}", STAMP)
     return LIB
 
 

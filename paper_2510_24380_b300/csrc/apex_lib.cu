@@ -42,6 +42,8 @@ cudaError_t apx_launch_prep(const float *U, const float *W1, const float *b1, co
                             long long rows, int K, int N, float *P32, cudaStream_t st);
 cudaError_t apx_launch_p16(const float *P32, long long n, float scale, int fmt, void *P16, cudaStream_t st);
 cudaError_t apx_launch_image(const float *W, int rows_used, int rows, int fmt, void *img, cudaStream_t st);
+cudaError_t apx_launch_slot_extremes(const float *P, const long long *row_first, int n_slots, int N, float *mx,
+                                     float *mn, cudaStream_t st);
 cudaError_t apx_launch_image_e4m3(const float *W, const float *scale, int rows_used, int rows, void *img,
                                   cudaStream_t st);
 cudaError_t apx_launch_tc_ids(const DevTables &T, const long long *ids, long long n, float *out, int *err, int n_sm,
@@ -59,7 +61,7 @@ cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const flo
 cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64, cudaStream_t st);
 cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, const unsigned *n64_dev,
                                int n_out, const QuerySlot *Q, const double *lo, const double *hi, double *out_rows,
-                               cudaStream_t st);
+                               cudaStream_t st, const float *out32 = nullptr, unsigned *obs = nullptr);
 cudaError_t apx_sort_r(RItem *R, unsigned n_used, unsigned n_pow2, cudaStream_t st, const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_mark(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked,
                             cudaStream_t st, const unsigned *n_used);
@@ -188,6 +190,9 @@ struct QueryRec {
   bool started = false;
   int spec_rank = 0;                // rank used for the speculative start threshold (0 = none)
   float tau_spec = -INFINITY;
+  // factors on the library's pass and FP32 margins for this query (raised when the runtime check at
+  // finalization observed a larger error than a margin allows)
+  double mscale = 1.0;
   // results
   std::vector<long long> r_ids;
   std::vector<int> r_rxn;
@@ -233,6 +238,7 @@ struct apex_library {
   // admission margins: err16[0] BF16 pass, [1] FP16 pass, [2] FP8 pass; err32 FP32 pass / rescore
   double err16[3][APEX_MAX_OUTPUTS] = {{0}}, err32[APEX_MAX_OUTPUTS] = {0}, rms[APEX_MAX_OUTPUTS] = {0};
   int n_calib = 0;
+  double a1_amax = 0;         // FP8: exact max |a_1| over the library (its static activation scale)
   float *d_err32f = nullptr;  // per-output FP32 margin (float) for eval32
   uint64_t seed = 0;
   // engine
@@ -257,6 +263,17 @@ struct apex_library {
   std::atomic<long long> fin_cover_set{0};  // candidates a queued finalization covers (0: default)
   long long cursor = 0;  // global item index of the circular pass
   apex_query_stats_t last_stats{};
+  // serving statistics over fetched queries (apex_stats; under mu). head_evals counts compounds
+  // scored by enumeration launches (worker thread), snapshotted at every reset.
+  struct Served {
+    std::vector<double> lat, queue;  // ring of the last APEX_STATS_WINDOW queries
+    size_t next = 0;
+    long long n_ok = 0, n_failed = 0;
+    double t_first = 0, t_last = 0, query_compounds = 0, lat_sum = 0, lat_max = 0;
+    long long evals_at_reset = 0, enum_ns_at_reset = 0, launches_at_reset = 0;
+  } served;
+  std::atomic<long long> head_evals{0};
+  std::atomic<long long> enum_ns{0}, enum_launches{0};  // device time and count of enumeration launches
   std::mt19937_64 rng;
   // reusable device scratch: per-slot candidate buffers (grow-only) and a bump arena for
   // finalization / sampling temporaries (grow-only), pinned host staging, events
@@ -607,6 +624,8 @@ static void retire_launch(apex_library &L) {
   }
   float ms = 0;
   CU(cudaEventElapsedTime(&ms, L.ev_l0[f.ring], L.ev_l1[f.ring]));
+  L.enum_ns += (long long)(1e6 * (double)ms);
+  L.enum_launches++;
   for (const auto &sq : f.queries) {
     QueryRec *q = L.active[sq.first];
     if (q && q->id == sq.second) q->stats.enumerate_ms += ms;
@@ -621,13 +640,34 @@ static void retire_quietly(apex_library &L) {
   if (L.inflight.empty()) return;
   cudaStreamSynchronize(L.st);
   bool stale = false;
-  for (const auto &f : L.inflight) stale = stale || L.status_pin[f.ring] != 0;
+  for (const auto &f : L.inflight) {
+    stale = stale || L.status_pin[f.ring] != 0;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, L.ev_l0[f.ring], L.ev_l1[f.ring]) == cudaSuccess) {
+      L.enum_ns += (long long)(1e6 * (double)ms);
+      L.enum_launches++;
+    }
+  }
   L.inflight.clear();
   if (stale) {
     int z = 0;
     cudaMemcpy(L.d_err, &z, sizeof(int), cudaMemcpyHostToDevice);
   }
 }
+
+// device temporaries released when the scope ends
+struct DevBuf {
+  std::vector<void *> p;
+  void *get(size_t n) {
+    void *x = nullptr;
+    CU(cudaMalloc(&x, n ? n : 16));
+    p.push_back(x);
+    return x;
+  }
+  ~DevBuf() {
+    for (void *x : p) cudaFree(x);
+  }
+};
 
 // ------------------------------------------------------------------ calibration
 // Margins of the reduced-precision pass and of the FP32 rescore, measured on a seeded sample:
@@ -679,52 +719,65 @@ static void calibrate(apex_library &L) {
   }
   L.n_calib = (int)ns;
   if (L.tc_fmt[0] || L.tc_fmt[1] || L.tc_fmt[2]) {
-    // tensor-core pass vs FP32 on whole work items: the first item of up to 48 reactions, chosen at random
-    PlanBuilder pb(L.rx);
+    // tensor-core pass vs FP32 on whole work items: one item, chosen at random, of every reaction
+    // (of kCalRx reactions chosen at random when the library has more), in launches of up to
+    // kCalBatch items. Random items rather than each reaction's first one: the first item always
+    // pairs the first inner rows with the first outer synthons.
+    constexpr int kCalRx = 1024, kCalBatch = 128;
     std::vector<int> order(L.T);
     for (int t = 0; t < L.T; ++t) order[t] = t;
     std::shuffle(order.begin(), order.end(), g);
-    for (int t : order) {
-      if (pb.P.n_seg >= 48) break;
-      pb.add(t, 0, 1, 0);
+    const int n_rx = std::min(L.T, kCalRx);
+    double mx[3][APEX_MAX_OUTPUTS] = {{0}};
+    long long cnt[3] = {0, 0, 0};
+    for (int b0 = 0; b0 < n_rx; b0 += kCalBatch) {
+      PlanBuilder pb(L.rx);
+      for (int i = b0; i < std::min(n_rx, b0 + kCalBatch); ++i) {
+        const int t = order[i];
+        const long long item = (long long)(g() % (unsigned long long)L.rx[t].n_items);
+        pb.add(t, item, item + 1, 0);
+      }
+      const long long slots = pb.P.total_tiles * APX_TILE;
+      DevBuf B;  // temporaries of this batch (freed when it is done)
+      float *d16 = (float *)B.get(sizeof(float) * slots * no);
+      float *d32 = (float *)B.get(sizeof(float) * slots * no);
+      long long *di16 = (long long *)B.get(sizeof(long long) * slots);
+      long long *di32 = (long long *)B.get(sizeof(long long) * slots);
+      LaunchPlan P = pb.P;
+      P.mode = 2;
+      P.dump_n = slots;
+      P.dump = d32;
+      P.dump_ids = di32;
+      CU(cudaMemsetAsync(di32, 0xff, sizeof(long long) * slots, L.st));
+      CU(apx_launch_fp32(P, L.T_, nullptr, nullptr, 0, nullptr, grid_for(L, P.total_items), L.st));
+      std::vector<float> a(slots * no), b(slots * no);
+      std::vector<long long> ia(slots), ib(slots);
+      CU(cudaMemcpyAsync(b.data(), d32, sizeof(float) * slots * no, cudaMemcpyDeviceToHost, L.st));
+      CU(cudaMemcpyAsync(ib.data(), di32, sizeof(long long) * slots, cudaMemcpyDeviceToHost, L.st));
+      CU(cudaStreamSynchronize(L.st));
+      for (int f = 0; f < 3; ++f) {
+        if (!L.tc_fmt[f]) continue;
+        P.dump = d16;
+        P.dump_ids = di16;
+        CU(cudaMemsetAsync(di16, 0xff, sizeof(long long) * slots, L.st));
+        CU(apx_launch_tc(P, L.T_, nullptr, L.d_err, grid_for(L, P.total_tiles), L.st, f));
+        check_kernel_status(L);
+        CU(cudaMemcpyAsync(a.data(), d16, sizeof(float) * slots * no, cudaMemcpyDeviceToHost, L.st));
+        CU(cudaMemcpyAsync(ia.data(), di16, sizeof(long long) * slots, cudaMemcpyDeviceToHost, L.st));
+        CU(cudaStreamSynchronize(L.st));
+        for (long long i = 0; i < slots; ++i) {
+          if (ia[i] < 0 || ia[i] != ib[i]) continue;
+          ++cnt[f];
+          for (int p = 0; p < no; ++p)
+            mx[f][p] = std::max(mx[f][p], std::fabs((double)a[i * no + p] - (double)b[i * no + p]));
+        }
+      }
     }
-    const long long slots = pb.P.total_tiles * APX_TILE;
-    float *d16 = (float *)L.dalloc(sizeof(float) * slots * no, false);
-    float *d32 = (float *)L.dalloc(sizeof(float) * slots * no, false);
-    long long *di16 = (long long *)L.dalloc(sizeof(long long) * slots, false);
-    long long *di32 = (long long *)L.dalloc(sizeof(long long) * slots, false);
-    LaunchPlan P = pb.P;
-    P.mode = 2;
-    P.dump_n = slots;
-    P.dump = d32;
-    P.dump_ids = di32;
-    CU(cudaMemsetAsync(di32, 0xff, sizeof(long long) * slots, L.st));
-    CU(apx_launch_fp32(P, L.T_, nullptr, nullptr, 0, nullptr, grid_for(L, P.total_items), L.st));
-    std::vector<float> a(slots * no), b(slots * no);
-    std::vector<long long> ia(slots), ib(slots);
-    CU(cudaMemcpyAsync(b.data(), d32, sizeof(float) * slots * no, cudaMemcpyDeviceToHost, L.st));
-    CU(cudaMemcpyAsync(ib.data(), di32, sizeof(long long) * slots, cudaMemcpyDeviceToHost, L.st));
-    CU(cudaStreamSynchronize(L.st));
     long long cnt_max = 0;
     for (int f = 0; f < 3; ++f) {
       if (!L.tc_fmt[f]) continue;
-      P.dump = d16;
-      P.dump_ids = di16;
-      CU(cudaMemsetAsync(di16, 0xff, sizeof(long long) * slots, L.st));
-      CU(apx_launch_tc(P, L.T_, nullptr, L.d_err, grid_for(L, P.total_tiles), L.st, f));
-      check_kernel_status(L);
-      CU(cudaMemcpyAsync(a.data(), d16, sizeof(float) * slots * no, cudaMemcpyDeviceToHost, L.st));
-      CU(cudaMemcpyAsync(ia.data(), di16, sizeof(long long) * slots, cudaMemcpyDeviceToHost, L.st));
-      CU(cudaStreamSynchronize(L.st));
-      long long cnt = 0;
-      double mx[APEX_MAX_OUTPUTS] = {0};
-      for (long long i = 0; i < slots; ++i) {
-        if (ia[i] < 0 || ia[i] != ib[i]) continue;
-        ++cnt;
-        for (int p = 0; p < no; ++p) mx[p] = std::max(mx[p], std::fabs((double)a[i * no + p] - (double)b[i * no + p]));
-      }
-      for (int p = 0; p < no; ++p) L.err16[f][p] = 4.0 * mx[p] + 1e-3 * L.rms[p] + L.err32[p];
-      cnt_max = std::max(cnt_max, cnt);
+      for (int p = 0; p < no; ++p) L.err16[f][p] = 4.0 * mx[f][p] + 1e-3 * L.rms[p] + L.err32[p];
+      cnt_max = std::max(cnt_max, cnt[f]);
     }
     L.n_calib += (int)cnt_max;
   }
@@ -906,20 +959,59 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
           L->T_.w3img[f] = d3;
         }
         if (L->tc_fmt[2]) {
-          // FP8 layer-2 image: every output channel of W_2 (already scaled) quantized with its own
-          // scale max|row| / 448 (the e4m3 maximum); the kernel multiplies the accumulators back
-          std::vector<float> s2(256, 1.f);
+          // FP8 layer 2. Activations: one static scale for the layer, from the exact maximum of
+          // |a_1| over the whole library. z_1 of a compound is the sum of one P row per slot, so
+          // its extremes over a reaction's Cartesian product are the sums of the per-slot column
+          // extremes (computed on the device), and a_1 = act(z_1) is monotone on each side of the
+          // activation's minimum. The scale is the power of two 2^floor(log2(448 / amax)), so the
+          // multiply in FP16 is exact and |a_1| * scale <= 448 (the e4m3 maximum).
+          const long long S = L->slot_first[L->T];
+          long long *d_rf = (long long *)L->dalloc(sizeof(long long) * (S + 1), false);
+          float *d_mx = (float *)L->dalloc(sizeof(float) * S * h1, false);
+          float *d_mn = (float *)L->dalloc(sizeof(float) * S * h1, false);
+          CU(cudaMemcpy(d_rf, L->row_first.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice));
+          CU(apx_launch_slot_extremes(P32, d_rf, (int)S, h1, d_mx, d_mn, L->st));
+          std::vector<float> hmx((size_t)S * h1), hmn((size_t)S * h1);
+          CU(cudaMemcpyAsync(hmx.data(), d_mx, sizeof(float) * S * h1, cudaMemcpyDeviceToHost, L->st));
+          CU(cudaMemcpyAsync(hmn.data(), d_mn, sizeof(float) * S * h1, cudaMemcpyDeviceToHost, L->st));
+          CU(cudaStreamSynchronize(L->st));
+          auto act = [&](double z) {
+            return L->act == APEX_ACT_SILU ? z / (1.0 + std::exp(-z)) : L->act == APEX_ACT_RELU ? std::max(z, 0.0) : z;
+          };
+          // SiLU's minimum: SiLU'(z) = 0 <=> z = -(1 + e^z), i.e. z = -1 - W(1/e) (W: Lambert's function)
+          const double z_silu_min = -1.2784645427610738;
+          double amax = 0;
+          for (int t = 0; t < L->T; ++t)
+            for (int n = 0; n < h1; ++n) {
+              double zx = 0, zn = 0;
+              for (long long j = L->slot_first[t]; j < L->slot_first[t + 1]; ++j) {
+                zx += hmx[(size_t)j * h1 + n];
+                zn += hmn[(size_t)j * h1 + n];
+              }
+              double a = std::max(std::fabs(act(zx)), std::fabs(act(zn)));
+              if (L->act == APEX_ACT_SILU && zn <= z_silu_min && z_silu_min <= zx) a = std::max(a, std::fabs(act(z_silu_min)));
+              amax = std::max(amax, a);
+            }
+          L->a1_amax = amax;
+          const double inv = amax > 0 ? std::exp2(std::floor(std::log2(448.0 / amax))) : 1.0;
+          L->T_.a1_inv = (float)std::min(inv, 32768.0);
+          // weights: every output channel of W_2 (already scaled) quantized with its own scale
+          // max|row| / 448; the kernel multiplies the accumulators by s_2[n] / a1_inv
+          std::vector<float> s2(256, 1.f), s2a(256, 1.f);
           for (int n = 0; n < 256; ++n) {
             float mx = 0.f;
             for (int k = 0; k < 256; ++k) mx = std::max(mx, std::fabs(w2[(size_t)n * 256 + k]));
             if (mx > 0.f) s2[n] = mx / 448.f;
+            s2a[n] = (float)((double)s2[n] / (double)L->T_.a1_inv);
           }
           float *ds2 = (float *)L->dalloc(sizeof(float) * 256);
+          float *ds2a = (float *)L->dalloc(sizeof(float) * 256);
           CU(cudaMemcpy(ds2, s2.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
+          CU(cudaMemcpy(ds2a, s2a.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
           unsigned char *d2 = (unsigned char *)L->dalloc(256 * 256);
           CU(apx_launch_image_e4m3(dw, ds2, 256, 256, d2, L->st));
           L->T_.w2img[2] = d2;
-          L->T_.s2 = ds2;
+          L->T_.s2 = ds2a;
         }
         std::vector<float> b2s(256), b3(16, 0.f);
         for (int n = 0; n < 256; ++n) b2s[n] = scale * D->b[1][n];
@@ -1181,18 +1273,19 @@ static void write_slot(apex_library &L, QueryRec *q, float admit) {
   QuerySlot S;
   memset(&S, 0, sizeof(S));
   const double *err = pass_err(L, q->precision);
+  const double sc = q->mscale;
   for (int j = 0; j < L.n_obj; ++j) S.w[j] = q->w[j];
   S.n_obj = L.n_obj;
   S.n_cons = (int)q->cidx.size();
   double df = 0;
-  for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
+  for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j] * sc;
   for (int c = 0; c < S.n_cons; ++c) {
     const int p = q->cidx[c];
     S.cons_idx[c] = p;
-    S.lo_w[c] = (float)(q->lo[c] - err[p]);
-    S.hi_w[c] = (float)(q->hi[c] + err[p]);
-    S.lo_s[c] = (float)(q->lo[c] + err[p]);
-    S.hi_s[c] = (float)(q->hi[c] - err[p]);
+    S.lo_w[c] = (float)(q->lo[c] - err[p] * sc);
+    S.hi_w[c] = (float)(q->hi[c] + err[p] * sc);
+    S.lo_s[c] = (float)(q->lo[c] + err[p] * sc);
+    S.hi_s[c] = (float)(q->hi[c] - err[p] * sc);
     float lx = (float)q->lo[c], hx = (float)q->hi[c];  // exact decisions for FP32 values
     if ((double)lx < q->lo[c]) lx = std::nextafter(lx, INFINITY);
     if ((double)hx > q->hi[c]) hx = std::nextafter(hx, -INFINITY);
@@ -1289,11 +1382,18 @@ static double pass_delta_f(const apex_library &L, const QueryRec *q) {
   const double *err = pass_err(L, q->precision);
   double df = 0;
   for (int j = 0; j < L.n_obj; ++j) df += std::fabs((double)q->w[j]) * err[j];
-  return df;
+  return df * q->mscale;
+}
+// objective margin of the FP32 rescore for this query
+static double fp32_delta_f(const apex_library &L, const QueryRec *q) {
+  double e = 0;
+  for (int j = 0; j < L.n_obj; ++j) e += std::fabs((double)q->w[j]) * L.err32[j];
+  return e * q->mscale;
 }
 
 static void start_query(apex_library &L, QueryRec *q) {
   tmark(L, 0);
+  q->stats.first_item = L.cursor;
   const double df = pass_delta_f(L, q);
   q->tau_spec = -INFINITY;  // the device-side guess lands in the slot; finalization reads it back
   write_slot(L, q, -INFINITY);
@@ -1364,18 +1464,6 @@ static bool admit_one(apex_library &L, QueryRec *q) {
 }
 
 // ------------------------------------------------------------------ worker: finalization
-struct DevBuf {
-  std::vector<void *> p;
-  void *get(size_t n) {
-    void *x = nullptr;
-    CU(cudaMalloc(&x, n ? n : 16));
-    p.push_back(x);
-    return x;
-  }
-  ~DevBuf() {
-    for (void *x : p) cudaFree(x);
-  }
-};
 
 // A query's finalization after its pass: the slot's last select (threshold raise and
 // compaction), then on the device the FP32 rescore of the candidates, their FP32 decisions, the
@@ -1405,6 +1493,8 @@ struct FinChain {
   char *h = nullptr;          // pinned copy of the rows [e_ids, e_out + n_rows * n_out)
   unsigned *h_cnt = nullptr;  // pinned copy of d_cnt
   QuerySlot *hS = nullptr;    // pinned copy of the slot after its last select
+  unsigned *d_obs = nullptr;  // [1 + APEX_MAX_OUTPUTS] observed errors (EvalArgs::obs), float bits
+  unsigned *h_obs = nullptr;  // pinned copy of d_obs
   int rounds = 0;
 };
 
@@ -1426,7 +1516,7 @@ static size_t fin_arena_bytes(const apex_library &L, const QueryRec *q, unsigned
 // pinned host memory of the same chain: its rows, counters and slot copy
 static size_t fin_pinned_bytes(const apex_library &L, const QueryRec *q, unsigned cover) {
   const size_t kx = (size_t)std::min<long long>(q->k, (long long)cover);
-  return kx * fin_row_bytes(L) + 5 * 64 + 64 + sizeof(QuerySlot) + 64;
+  return kx * fin_row_bytes(L) + 5 * 64 + 64 + sizeof(QuerySlot) + 64 + 4 * (1 + APEX_MAX_OUTPUTS) + 64;
 }
 // candidates an optimistic chain covers: the usual candidate set is a small multiple of k (at most
 // 2^20 by default: the scratch grows ~280 bytes per covered candidate)
@@ -1443,7 +1533,7 @@ static void fin_round(apex_library &L, FinChain &C) {
   CU(apx_launch_collect64(C.R, C.nr, C.ids64, C.pos64, C.d_cnt + 1, L.st));
   CU(apx_launch_fp64(L.T_, C.ids64, C.nc1, C.o64, L.st, C.d_cnt + 1));
   CU(apx_launch_apply64(C.R, C.pos64, C.o64, C.nc1, C.d_cnt + 1, L.n_out, L.d_slots + C.sl, C.dlo, C.dhi, C.out64,
-                        L.st));
+                        L.st, C.out32, C.d_obs));
   CU(apx_sort_r(C.R, C.np, C.np, L.st, C.d_cnt));
   CU(apx_launch_mark(C.R, C.nr, (unsigned)std::min<long long>(C.k + 1, C.nr), C.k, C.tol, C.d_cnt + 2, L.st,
                      C.d_cnt));  // boundary band
@@ -1460,6 +1550,7 @@ static void fin_emit(apex_library &L, FinChain &C) {
   CU(cudaEventRecord(C.q->ev1, L.st));
   if (C.span) CU(cudaMemcpyAsync(C.h, C.e_ids, C.span, cudaMemcpyDeviceToHost, L.st));
   CU(cudaMemcpyAsync(C.h_cnt, C.d_cnt, sizeof(unsigned) * 8, cudaMemcpyDeviceToHost, L.st));
+  CU(cudaMemcpyAsync(C.h_obs, C.d_obs, sizeof(unsigned) * (1 + APEX_MAX_OUTPUTS), cudaMemcpyDeviceToHost, L.st));
 }
 
 // Queues the chain of query q over up to `cover` candidates (the slot's count, read on the device,
@@ -1493,9 +1584,13 @@ static void fin_queue(apex_library &L, QueryRec *q, FinChain &C, unsigned cover)
     L.upload(C.dlo, q->lo.data(), sizeof(double) * m);
     L.upload(C.dhi, q->hi.data(), sizeof(double) * m);
   }
-  double e32f = 0;
-  for (int j = 0; j < L.n_obj; ++j) e32f += std::fabs((double)q->w[j]) * L.err32[j];
+  const double e32f = fp32_delta_f(L, q);
+  C.d_obs = (unsigned *)L.aget(sizeof(unsigned) * (1 + APEX_MAX_OUTPUTS));
+  CU(cudaMemsetAsync(C.d_obs, 0, sizeof(unsigned) * (1 + APEX_MAX_OUTPUTS), L.st));
   EvalArgs ea{C.out32, no, L.d_slots + C.sl, L.d_err32f, (float)e32f, C.dlo, C.dhi};
+  ea.eps_scale = (float)q->mscale;
+  ea.pass_keys = q->keys;  // compacted with the ids by the slot's last select
+  ea.obs = C.d_obs;
   CU(apx_launch_eval32(ea, cover, f32, maybe, sure, L.st, d_n));
   C.d_tau = (float *)L.aget(sizeof(float));
   int *d_ok = (int *)L.aget(sizeof(int));
@@ -1529,6 +1624,7 @@ static void fin_queue(apex_library &L, QueryRec *q, FinChain &C, unsigned cover)
   }
   C.h = (char *)L.dl_get(std::max<size_t>(C.span, 1));
   C.h_cnt = (unsigned *)L.dl_get(sizeof(unsigned) * 8);
+  C.h_obs = (unsigned *)L.dl_get(sizeof(unsigned) * (1 + APEX_MAX_OUTPUTS));
   // the band around the FP32 k-th score is marked before the first round, so one round usually
   // settles it
   if (C.nr > 0) {
@@ -1560,6 +1656,26 @@ static void fin_take(apex_library &L, FinChain &C) {
   q->r_obj.assign(obj, obj + (nf > 0 ? nf : 0));
   q->r_out.assign(out, out + (nf > 0 ? nf * no : 0));
   q->stats.n_feasible_lower = nf;
+  // observed errors against the margins this run was admitted and decided with
+  auto bits_f = [](unsigned u) {
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
+  };
+  const double df = pass_delta_f(L, q);
+  q->stats.pass_err_ratio = df > 0 ? bits_f(C.h_obs[0]) / df : 0.0;
+  double r32 = 0;
+  for (int p = 0; p < no; ++p)
+    if (L.err32[p] > 0) r32 = std::max(r32, bits_f(C.h_obs[1 + p]) / (L.err32[p] * q->mscale));
+  q->stats.fp32_err_ratio = r32;
+}
+
+// After fin_take: whether an observed error exceeded the margin the run used (the run is then
+// repeated with wider margins, up to kMaxMarginReruns times).
+static constexpr int kMaxMarginReruns = 4;
+static bool fin_margin_exceeded(const QueryRec *q) {
+  return (q->stats.pass_err_ratio > 1.0 || q->stats.fp32_err_ratio > 1.0) &&
+         q->stats.n_margin_reruns < kMaxMarginReruns;
 }
 
 // Decides from the slot after its last select whether the query must run its pass again: the
@@ -1610,8 +1726,26 @@ static void fin_restart(apex_library &L, QueryRec *q, const QuerySlot &S, bool s
   write_slot(L, q, std::isfinite(q->tau_spec) ? (float)(q->tau_spec - 2.0 * df * 1.0001) : -INFINITY);
   if (device_guess) speculative_start(L, q, 2.0 * df * 1.0001);
   q->remaining = q->scope_items;
+  q->stats.first_item = L.cursor;
   TRACE("restart q%lld: overflow=%u spec_bad=%d cap=%u tau_spec=%g rank=%d", (long long)q->id, S.overflow,
         (int)spec_bad, q->cap, (double)S.tau_spec, q->spec_rank);
+}
+
+// Repeats a query's pass with both margins widened: by at least 2x and at least twice the largest
+// observed error ratio. The start threshold is sampled again (its admission bound moved).
+static void fin_restart_margin(apex_library &L, QueryRec *q) {
+  const double r = std::max(q->stats.pass_err_ratio, q->stats.fp32_err_ratio);
+  q->stats.n_margin_reruns++;
+  q->mscale *= std::max(2.0, 2.0 * r);
+  q->tau_spec = -INFINITY;
+  q->spec_rank = 0;
+  const double df = pass_delta_f(L, q);
+  write_slot(L, q, -INFINITY);
+  speculative_start(L, q, 2.0 * df * 1.0001);
+  q->remaining = q->scope_items;
+  q->stats.first_item = L.cursor;
+  TRACE("margin rerun q%lld: ratios pass %.3f fp32 %.3f -> scale %.3f", (long long)q->id, q->stats.pass_err_ratio,
+        q->stats.fp32_err_ratio, q->mscale);
 }
 
 // The chain of one query sized exactly (its count known), waited for, with further FP64 rounds
@@ -1688,7 +1822,10 @@ static void finalize_batch(apex_library &L, const std::vector<QueryRec *> &qs, s
       redo[i] = 1;
     } else {
       fin_take(L, C[i]);
-      done[i] = 1;
+      if (fin_margin_exceeded(qs[i]))
+        redo[i] = 3;
+      else
+        done[i] = 1;
     }
   }
   for (size_t i = 0; i < n; ++i) {
@@ -1696,7 +1833,12 @@ static void finalize_batch(apex_library &L, const std::vector<QueryRec *> &qs, s
       fin_restart(L, qs[i], Ss[i], sbad[i], ovf[i]);
     } else if (redo[i] == 1) {
       fin_exact(L, qs[i], Ss[i].count);
-      done[i] = 1;
+      if (fin_margin_exceeded(qs[i]))
+        fin_restart_margin(L, qs[i]);
+      else
+        done[i] = 1;
+    } else if (redo[i] == 3) {
+      fin_restart_margin(L, qs[i]);
     }
   }
   if (trace_on())
@@ -1815,6 +1957,15 @@ static void pass_step(apex_library &L) {
   f.ring = ring;
   for (int s : list) f.queries.emplace_back(s, L.active[s]->id);
   L.inflight.push_back(std::move(f));
+  {
+    long long launched = 0;
+    for (int p = 0; p < 5; ++p)
+      for (int g = 0; g < pb[p].P.n_seg; ++g) {
+        const RxnPlan &r = L.rx[pb[p].P.seg[g].rxn];
+        launched += (pb[p].P.seg[g].item_end - pb[p].P.seg[g].item_begin) * r.L_o * APX_TILE;
+      }
+    L.head_evals += launched;
+  }
   for (int s : list) {
     QueryRec *q = L.active[s];
     q->remaining -= served[s];
@@ -2018,14 +2169,23 @@ extern "C" apex_status apex_topk_fetch(apex_library *L, apex_query_id id, int64_
   if (capacity < 0) return fail(APEX_EINVAL, "negative capacity");
   std::unique_lock<std::mutex> lk(L->mu, std::defer_lock);
   lock_spin(lk);
+  // Every wait below releases L->mu, and another fetcher of the same id may finish meanwhile and
+  // release the record (queries.erase frees it). So the record is looked up again under the lock
+  // after each wait, and the wait predicate itself looks it up instead of holding a pointer: a
+  // query whose record is gone was taken by that other fetcher and is reported as not found.
   auto it = L->queries.find(id);
   if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found", (long long)id);
-  QueryRec *q = it->second.get();
-  auto done = [&] { return q->state == Q_DONE || q->state == Q_CANCELED || q->state == Q_FAILED; };
+  auto finished = [](const QueryRec *r) {
+    return r->state == Q_DONE || r->state == Q_CANCELED || r->state == Q_FAILED;
+  };
+  auto gone_or_done = [&] {
+    auto f = L->queries.find(id);
+    return f == L->queries.end() || finished(f->second.get());
+  };
   // watch for completions first (no sleep), for at most fetch_spin_ms() or the timeout
   const double t_w0 = now_ms();
   const double spin_ms = timeout_ms < 0 ? fetch_spin_ms() : std::min(fetch_spin_ms(), (double)timeout_ms);
-  while (!done() && L->spinners < 2) {
+  while (!gone_or_done() && L->spinners < 2) {
     const double left = spin_ms - (now_ms() - t_w0);
     if (left <= 0) break;
     const unsigned long long seq = L->done_seq.load();
@@ -2034,18 +2194,39 @@ extern "C" apex_status apex_topk_fetch(apex_library *L, apex_query_id id, int64_
     watch(L->done_seq, seq, left, 63);
     lock_spin(lk);
     L->spinners--;
-    it = L->queries.find(id);  // another fetcher of the same id may have taken it meanwhile
-    if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found", (long long)id);
-    q = it->second.get();
   }
   if (timeout_ms < 0) {
-    L->cv_done.wait(lk, done);
+    L->cv_done.wait(lk, gone_or_done);
   } else {
     const double left_ms = std::max(0.0, timeout_ms - (now_ms() - t_w0));
-    if (!L->cv_done.wait_for(lk, std::chrono::microseconds((long long)(1000.0 * left_ms)), done))
+    if (!L->cv_done.wait_for(lk, std::chrono::microseconds((long long)(1000.0 * left_ms)), gone_or_done))
       return fail(APEX_EAGAIN, "query %lld not finished", (long long)id);
   }
+  it = L->queries.find(id);
+  if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found (fetched by another caller)", (long long)id);
+  QueryRec *q = it->second.get();
   apex_status rc = q->err;
+  {
+    apex_library::Served &V = L->served;
+    if (q->state == Q_DONE) {
+      if (V.lat.size() < APEX_STATS_WINDOW) {
+        V.lat.push_back(q->stats.latency_ms);
+        V.queue.push_back(q->stats.queue_ms);
+      } else {
+        V.lat[V.next] = q->stats.latency_ms;
+        V.queue[V.next] = q->stats.queue_ms;
+        V.next = (V.next + 1) % APEX_STATS_WINDOW;
+      }
+      V.t_first = V.n_ok == 0 ? q->t_submit : std::min(V.t_first, q->t_submit);
+      V.t_last = V.n_ok == 0 ? q->t_done : std::max(V.t_last, q->t_done);
+      V.n_ok++;
+      V.query_compounds += (double)q->scope_n;
+      V.lat_sum += q->stats.latency_ms;
+      V.lat_max = std::max(V.lat_max, q->stats.latency_ms);
+    } else {
+      V.n_failed++;
+    }
+  }
   if (q->state == Q_DONE) {
     const long long n = (long long)q->r_ids.size();
     const long long c = std::min<long long>(n, capacity);
@@ -2080,6 +2261,56 @@ extern "C" apex_status apex_query_stats(apex_library *L, apex_query_id id, apex_
   auto it = L->queries.find(id);
   if (it == L->queries.end()) return fail(APEX_ENOTFOUND, "query %lld not found", (long long)id);
   *out = it->second->stats;
+  return APEX_OK;
+}
+
+// percentile p (0..100) of v by linear interpolation between the nearest ranks (v is sorted here)
+static double pct_linear(std::vector<double> &v, double p) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const double r = p / 100.0 * (double)(v.size() - 1);
+  const size_t i = (size_t)std::floor(r);
+  const size_t j = std::min(i + 1, v.size() - 1);
+  return v[i] + (r - (double)i) * (v[j] - v[i]);
+}
+
+extern "C" apex_status apex_stats(apex_library *L, apex_stats_t *out) {
+  if (!L || !out) return fail(APEX_EINVAL, "NULL argument");
+  memset(out, 0, sizeof(*out));
+  std::vector<double> lat, queue;
+  {
+    std::lock_guard<std::mutex> g(L->mu);
+    const apex_library::Served &V = L->served;
+    lat = V.lat;
+    queue = V.queue;
+    out->n_queries = V.n_ok;
+    out->n_failed = V.n_failed;
+    out->max_ms = V.lat_max;
+    out->mean_ms = V.n_ok > 0 ? V.lat_sum / (double)V.n_ok : 0.0;
+    out->wall_ms = V.n_ok > 0 ? V.t_last - V.t_first : 0.0;
+    out->query_compounds = V.query_compounds;
+    out->head_evaluations = (double)(L->head_evals.load() - V.evals_at_reset);
+    out->enumerate_ms = 1e-6 * (double)(L->enum_ns.load() - V.enum_ns_at_reset);
+    out->n_enumeration_launches = L->enum_launches.load() - V.launches_at_reset;
+  }
+  out->p50_ms = pct_linear(lat, 50.0);
+  out->p99_ms = pct_linear(lat, 99.0);
+  out->queue_p50_ms = pct_linear(queue, 50.0);
+  out->queue_p99_ms = pct_linear(queue, 99.0);
+  if (out->wall_ms > 0) {
+    out->query_compounds_per_s = out->query_compounds / (out->wall_ms * 1e-3);
+    out->head_evaluations_per_s = out->head_evaluations / (out->wall_ms * 1e-3);
+  }
+  return APEX_OK;
+}
+
+extern "C" apex_status apex_stats_reset(apex_library *L) {
+  if (!L) return fail(APEX_EINVAL, "NULL library");
+  std::lock_guard<std::mutex> g(L->mu);
+  L->served = apex_library::Served();
+  L->served.evals_at_reset = L->head_evals.load();
+  L->served.enum_ns_at_reset = L->enum_ns.load();
+  L->served.launches_at_reset = L->enum_launches.load();
   return APEX_OK;
 }
 
@@ -2128,28 +2359,54 @@ extern "C" apex_status apex_score_ids(apex_library *L, int32_t precision, int64_
 
 extern "C" apex_status apex_dump_outputs(apex_library *L, int32_t precision, int32_t reaction, float *outputs,
                                          int64_t capacity) {
-  if (!L || !outputs || reaction < 0 || reaction >= L->T) return fail(APEX_EINVAL, "bad arguments");
+  if (!L || !outputs || reaction < -1 || reaction >= L->T) return fail(APEX_EINVAL, "bad arguments");
   if (precision != APEX_FP32 && precision != APEX_BF16 && precision != APEX_FP16 && precision != APEX_FP8)
     return fail(APEX_EINVAL, "unknown precision");
   if (!((L->precisions >> precision) & 1u)) return fail(APEX_EUNSUPPORTED, "precision not built");
-  const long long nt = L->id_first[reaction + 1] - L->id_first[reaction];
+  const int t0 = reaction < 0 ? 0 : reaction, t1 = reaction < 0 ? L->T : reaction + 1;
+  const long long nt = L->id_first[t1] - L->id_first[t0];
   if (capacity < nt) return fail(APEX_EINVAL, "capacity %lld < %lld compounds", (long long)capacity, nt);
-  std::lock_guard<std::mutex> g(L->mu);
   const int no = L->n_out;
+  if ((double)nt * no * sizeof(float) > (double)(16ull << 30))
+    return fail(APEX_EINVAL, "dump of %lld compounds exceeds 16 GB of outputs", nt);
+  std::lock_guard<std::mutex> g(L->mu);
   try {
     CU(cudaSetDevice(L->device));
     DevBuf B;
     float *d = (float *)B.get(sizeof(float) * nt * no);
+    // launches shaped like those of a query's pass: consecutive items in library order, about the
+    // library's compounds-per-launch each, cost-weighted CTA ranges (launch_enum)
+    const long long chunk = reaction < 0 ? L->chunk_compounds.load() : (1LL << 62);
     PlanBuilder pb(L->rx);
-    const long long items = L->rx[reaction].n_items;
-    for (long long b = 0; b < items; b += 1LL << 30) pb.add(reaction, b, std::min(items, b + (1LL << 30)), 0);
-    LaunchPlan P = pb.P;
-    P.mode = 1;
-    P.dump = d;
-    P.dump_base = L->id_first[reaction];
-    P.dump_n = nt;
-    launch_enum(*L, P, precision);
-    check_kernel_status(*L);
+    long long in_plan = 0;
+    auto flush = [&] {
+      if (pb.P.n_seg == 0) return;
+      LaunchPlan P = pb.P;
+      P.mode = 1;
+      P.dump = d;
+      P.dump_base = L->id_first[t0];
+      P.dump_n = nt;
+      launch_enum(*L, P, precision);
+      check_kernel_status(*L);
+      pb = PlanBuilder(L->rx);
+      in_plan = 0;
+    };
+    for (int t = t0; t < t1; ++t) {
+      const long long items = L->rx[t].n_items, per_item = (long long)L->rx[t].L_o * APX_TILE;
+      long long b = 0;
+      while (b < items) {
+        const long long room = std::max<long long>(1, (chunk - in_plan + per_item - 1) / per_item);
+        const long long e = std::min(items, b + std::min<long long>(room, 1LL << 30));
+        if (!pb.add(t, b, e, 0)) {
+          flush();
+          continue;
+        }
+        in_plan += (e - b) * per_item;
+        b = e;
+        if (in_plan >= chunk) flush();
+      }
+    }
+    flush();
     CU(cudaMemcpy(outputs, d, sizeof(float) * nt * no, cudaMemcpyDeviceToHost));
   } catch (const CudaFail &f) {
     return fail(f.e == cudaErrorLaunchTimeout ? APEX_ETIMEDOUT : APEX_ECUDA, "dump: %s failed: %s", f.what,

@@ -270,6 +270,10 @@ struct EvalArgs {
   const float *eps;         // per-output FP32 margin [n_out]
   float eps_f;              // objective margin
   const double *lo, *hi;    // exact box [n_cons]
+  float eps_scale;          // this query's factor on eps (1 unless a margin check widened it)
+  const float *pass_keys;   // [n] pass objective of every candidate (nullptr: not checked)
+  unsigned *obs;            // [1 + n_out] observed maxima as float bits: [0] max |pass key - FP32
+                            // objective| (here), [1 + p] max |FP32 - FP64| of output p (k_apply64)
 };
 
 // One member of the result set under exact selection.
@@ -305,7 +309,10 @@ struct DevTables {
   const unsigned short *P16[2];   // [n_rows x 256] 16-bit bits, scaled into the activation's input space
   const unsigned char *w2img[3];  // W_2 as the SW128 K-major shared-memory image (128 KB; FP8: 64 KB)
   const unsigned char *w3img[2];  // W_3 padded to 16 rows, same layout (8 KB)
-  const float *s2;                // FP8: dequantization scale of every W_2 output channel
+  const float *s2;                // FP8: dequantization scale of every W_2 output channel, times the
+                                  // inverse of a1_inv (both operands' scales undone in one multiply)
+  float a1_inv;                   // FP8: power-of-two factor on a_1 before its e4m3 conversion
+                                  // (the layer's static activation scale, 448 / amax rounded down)
   const float *b2s;            // b_2 in the same scaled space [256]
   const float *b3;             // b_3 padded [16]
 };

@@ -100,6 +100,31 @@ __global__ void k_sw128_image_e4m3(const float *__restrict__ W, const float *__r
   }
 }
 
+// Per-slot column extremes of P (FP32): mx[j][n] = max over the slot's rows r of P[r][n], mn likewise.
+// One block per slot, one thread per column (rows read in order, coalesced).
+__global__ void k_slot_extremes(const float *__restrict__ P, const long long *__restrict__ row_first, int N,
+                                float *__restrict__ mx, float *__restrict__ mn) {
+  const int j = blockIdx.x;
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    float a = -INFINITY, b = INFINITY;
+    for (long long r = row_first[j]; r < row_first[j + 1]; ++r) {
+      const float v = P[r * N + n];
+      a = fmaxf(a, v);
+      b = fminf(b, v);
+    }
+    mx[(size_t)j * N + n] = a;
+    mn[(size_t)j * N + n] = b;
+  }
+}
+
+cudaError_t apx_launch_slot_extremes(const float *P, const long long *row_first, int n_slots, int N, float *mx,
+                                     float *mn, cudaStream_t st) {
+  if (n_slots <= 0) return cudaSuccess;
+  apx_count_launch();
+  k_slot_extremes<<<n_slots, 256, 0, st>>>(P, row_first, N, mx, mn);
+  return cudaGetLastError();
+}
+
 cudaError_t apx_launch_image_e4m3(const float *W, const float *scale, int rows_used, int rows, void *img,
                                   cudaStream_t st) {
   apx_count_launch();

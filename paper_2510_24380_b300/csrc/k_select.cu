@@ -218,12 +218,14 @@ __global__ void k_eval32(EvalArgs a, long long n, float *f32, unsigned char *may
   const int m = a.Q->n_cons;
   if (threadIdx.x < (unsigned)m) {
     const int c = threadIdx.x, p = a.Q->cons_idx[c];
-    mlo[c] = __double2float_ru(a.lo[c] - a.eps[p]);
-    mhi[c] = __double2float_rd(a.hi[c] + a.eps[p]);
-    slo[c] = __double2float_ru(a.lo[c] + a.eps[p]);
-    shi[c] = __double2float_rd(a.hi[c] - a.eps[p]);
+    const double e = (double)a.eps[p] * (double)a.eps_scale;
+    mlo[c] = __double2float_ru(a.lo[c] - e);
+    mhi[c] = __double2float_rd(a.hi[c] + e);
+    slo[c] = __double2float_ru(a.lo[c] + e);
+    shi[c] = __double2float_rd(a.hi[c] - e);
   }
   __syncthreads();
+  float dmax = 0.f;  // largest |pass key - FP32 objective| this thread saw
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float *o = a.out32 + i * a.n_out;
     float f = 0.f;
@@ -237,6 +239,11 @@ __global__ void k_eval32(EvalArgs a, long long n, float *f32, unsigned char *may
     f32[i] = f;
     maybe[i] = mb;
     sure[i] = sr;
+    if (a.pass_keys) dmax = fmaxf(dmax, __fsub_ru(fmaxf(a.pass_keys[i], f), fminf(a.pass_keys[i], f)));
+  }
+  if (a.obs) {  // every thread of the block reaches this point
+    for (int off = 16; off > 0; off >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+    if ((threadIdx.x & 31) == 0 && dmax > 0.f) atomicMax(a.obs, __float_as_uint(dmax));
   }
 }
 
@@ -305,7 +312,7 @@ __global__ void k_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, 
 // apply FP64 outputs: exact objective and box; drop infeasible
 __global__ void k_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64_max, const unsigned *n64_dev,
                           int n_out, const QuerySlot *Q, const double *lo, const double *hi,
-                          double *out_rows /* [n_candidates x n_out], by src */) {
+                          double *out_rows /* [n_candidates x n_out], by src */, const float *out32, unsigned *obs) {
   const unsigned n64 = n64_dev ? min(n64_max, *n64_dev) : n64_max;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n64; i += gridDim.x * blockDim.x) {
     const double *o = out64 + (size_t)i * n_out;
@@ -321,6 +328,11 @@ __global__ void k_apply64(RItem *R, const int *pos64, const double *out64, unsig
     it.is64 = 1;
     it.alive = ok ? 1 : 0;
     for (int j = 0; j < n_out; ++j) out_rows[(size_t)it.src * n_out + j] = o[j];
+    if (out32 && obs)  // observed FP32 error of every output on this member (rounded up to float)
+      for (int j = 0; j < n_out; ++j) {
+        const float e = __double2float_ru(fabs(o[j] - (double)out32[(size_t)it.src * n_out + j]));
+        if (e > 0.f) atomicMax(obs + 1 + j, __float_as_uint(e));
+      }
   }
 }
 
@@ -611,11 +623,11 @@ cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *po
 // n64_dev (optional): device count, at most n64
 cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, const unsigned *n64_dev,
                                int n_out, const QuerySlot *Q, const double *lo, const double *hi, double *out_rows,
-                               cudaStream_t st) {
+                               cudaStream_t st, const float *out32, unsigned *obs) {
   if (n64 == 0) return cudaSuccess;
   apx_count_launch();
   k_apply64<<<std::min<unsigned>((n64 + 255) / 256, 148u * 16u), 256, 0, st>>>(R, pos64, out64, n64, n64_dev, n_out, Q,
-                                                                                lo, hi, out_rows);
+                                                                                lo, hi, out_rows, out32, obs);
   return cudaGetLastError();
 }
 cudaError_t apx_launch_mark(RItem *R, unsigned n, unsigned kp1, long long k, double tol, unsigned *n_marked,

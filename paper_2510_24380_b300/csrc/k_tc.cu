@@ -522,6 +522,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // s - 1 is activated.
     const int p = tid - TC_EPI_WARPS * 32;
     const int g = p >> 7, m = p & 127;
+    // FP8: a_1 times its power-of-two activation scale (exact in FP16) before the e4m3 conversion
+    const uint32_t a1s = F8 ? pack2<1>(T.a1_inv, T.a1_inv) : 0u;
     const uint32_t row_off = (uint32_t)(m >> 3) * 1024u + (uint32_t)(m & 7) * 128u;
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     uint32_t R[32];  // resident inner sum of the producing item (64 columns), packed bf16 pairs
@@ -641,7 +643,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
                 uint32_t out[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) out[e] = act2<ACT, PF>(add2<PF>(R[c * 4 + e], pw[e]));
+                for (int e = 0; e < 4; ++e) out[e] = fma2<PF>(act2<ACT, PF>(add2<PF>(R[c * 4 + e], pw[e])), a1s, 0u);
                 q[2 * h] = e4m3x4(out[0], out[1]);
                 q[2 * h + 1] = e4m3x4(out[2], out[3]);
               }

@@ -32,7 +32,9 @@ def _select(fn, keys, ids, k):
 def test_noalloc_select_matches_allocating_select_twice():
     build.build()
     rng = np.random.default_rng(21)
-    cases = [(200000, 65536), (50000, 777)]  # the second call follows a larger one in the same array
+    # the second call follows a larger one in the same array; the third asks for more than n
+    # (k = 9000 > n = 5000: every key comes back, sorted)
+    cases = [(200000, 65536), (50000, 777), (5000, 9000)]
     for n, k in cases:
         keys = rng.standard_normal(n).astype(np.float32)
         keys[rng.integers(0, n, n // 20)] = -0.5  # ties broken by the smaller id
@@ -42,6 +44,9 @@ def test_noalloc_select_matches_allocating_select_twice():
         assert n_got == n_ref == min(n, k)
         assert np.array_equal(i_got, i_ref)
         assert np.array_equal(k_got, k_ref)  # same keys (exact: selection copies them)
+        # and both equal the plain definition: key descending, then id ascending
+        order = np.lexsort((ids, -keys.astype(np.float64)))[: min(n, k)]
+        assert np.array_equal(i_got, ids[order]) and np.array_equal(k_got, keys[order])
 
 
 def test_noalloc_select_rejects_k_above_its_limit():
