@@ -81,7 +81,7 @@ class QueryStats(C.Structure):
         ("n_feasible_lower", C.c_int64), ("n_restarts", C.c_int32), ("n_launches", C.c_int32),
         ("queue_ms", C.c_double), ("latency_ms", C.c_double), ("gpu_ms", C.c_double), ("enumerate_ms", C.c_double),
         ("host_start_ms", C.c_double), ("host_pass_ms", C.c_double), ("host_finalize_ms", C.c_double),
-        ("n_margin_reruns", C.c_int32), ("reserved", C.c_int32), ("pass_err_ratio", C.c_double),
+        ("n_margin_reruns", C.c_int32), ("n_compactions", C.c_int32), ("pass_err_ratio", C.c_double),
         ("fp32_err_ratio", C.c_double), ("first_item", C.c_int64),
     ]
 

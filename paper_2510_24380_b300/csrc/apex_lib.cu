@@ -59,6 +59,9 @@ cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const flo
                                const unsigned char *sure, const float *tau32, float margin2, RItem *R, unsigned *n_r,
                                cudaStream_t st, const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64, cudaStream_t st);
+cudaError_t apx_launch_compact(QuerySlot *Q, const float *f32, const unsigned char *maybe, const unsigned char *sure,
+                               const float *tau32, const int *ok, float margin2, float eps_f, unsigned *kept,
+                               unsigned n_max, int n_sm, cudaStream_t st);
 cudaError_t apx_launch_apply64(RItem *R, const int *pos64, const double *out64, unsigned n64, const unsigned *n64_dev,
                                int n_out, const QuerySlot *Q, const double *lo, const double *hi, double *out_rows,
                                cudaStream_t st, const float *out32 = nullptr, unsigned *obs = nullptr);
@@ -193,6 +196,9 @@ struct QueryRec {
   // factors on the library's pass and FP32 margins for this query (raised when the runtime check at
   // finalization observed a larger error than a margin allows)
   double mscale = 1.0;
+  // in-pass FP32 compaction of the candidate buffer wanted before the next launch (set when a
+  // retired launch showed the buffer above the trigger)
+  bool want_compact = false;
   // results
   std::vector<long long> r_ids;
   std::vector<int> r_rxn;
@@ -305,6 +311,13 @@ struct apex_library {
   };
   cudaEvent_t ev_l0[kRing] = {}, ev_l1[kRing] = {}, ev_ls[kRing] = {};
   int *status_pin = nullptr;
+  // per ring entry: (count, count_compacted) of every slot after the launch's select and
+  // compactions (pinned), read when the launch retires to decide the next compactions
+  unsigned *cnt_pin = nullptr;
+  // per slot: observed errors of the running query (EvalArgs::obs: [0] max |pass key - FP32
+  // objective| over every candidate rescored in the pass or at its end, [1 + p] max |FP32 - FP64|
+  // of output p), zeroed whenever the slot's parameters are written
+  unsigned *d_obs_slots = nullptr;
   cudaEvent_t ev_tr[8] = {};  // GPU timeline marks of a query's phases (APEX_TRACE only)
   std::deque<InFlight> inflight;
   long long launch_seq = 0;
@@ -609,8 +622,21 @@ static float tspan(apex_library &L, cudaEvent_t a, cudaEvent_t b) {
   return ms;
 }
 
+static unsigned fin_cover(const apex_library &L, const QueryRec *q);
+
+// Candidate count above which a query's buffer is compacted in FP32 before the next launch: about
+// what its end-of-pass finalization covers in one queued chain (so that chain rarely needs its exact
+// rerun), at least 2k, at least twice what the last compaction kept (a query with few surely
+// feasible candidates cannot shrink its buffer much: no compaction every launch), and at most half
+// the buffer (two launches are queued before the compaction runs).
+static unsigned compact_trigger(const apex_library &L, const QueryRec *q, unsigned last_kept) {
+  const long long base = std::max<long long>(std::min<long long>(q->cap / 4, fin_cover(L, q) / 2), 2 * q->k);
+  return (unsigned)std::min<long long>(std::max<long long>(base, 2LL * last_kept), q->cap / 2);
+}
+
 // Retires the oldest enumeration launch in flight: waits for its status copy, raises a device-side
-// wait timeout as an error, and adds the launch's duration to the queries it served.
+// wait timeout as an error, adds the launch's duration to the queries it served, and marks for an
+// FP32 compaction the queries whose candidate buffer it left above their trigger.
 static void retire_launch(apex_library &L) {
   apex_library::InFlight f = std::move(L.inflight.front());
   L.inflight.pop_front();
@@ -626,9 +652,14 @@ static void retire_launch(apex_library &L) {
   CU(cudaEventElapsedTime(&ms, L.ev_l0[f.ring], L.ev_l1[f.ring]));
   L.enum_ns += (long long)(1e6 * (double)ms);
   L.enum_launches++;
+  const unsigned *cnt = L.cnt_pin + (size_t)f.ring * 2 * APEX_MAX_ACTIVE;
   for (const auto &sq : f.queries) {
     QueryRec *q = L.active[sq.first];
-    if (q && q->id == sq.second) q->stats.enumerate_ms += ms;
+    if (q && q->id == sq.second) {
+      q->stats.enumerate_ms += ms;
+      const unsigned c = cnt[2 * sq.first], kept = cnt[2 * sq.first + 1];
+      if (q->remaining > 0 && !q->want_compact && c > compact_trigger(L, q, kept)) q->want_compact = true;
+    }
   }
   TRACE("launch %d queries: %.3f ms", (int)f.queries.size(), (double)ms);
 }
@@ -1053,6 +1084,9 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
       CU(cudaEventCreateWithFlags(&L->ev_ls[i], cudaEventDisableTiming));
     }
     CU(cudaMallocHost(&L->status_pin, sizeof(int) * apex_library::kRing));
+    CU(cudaMallocHost(&L->cnt_pin, sizeof(unsigned) * 2 * APEX_MAX_ACTIVE * apex_library::kRing));
+    memset(L->cnt_pin, 0, sizeof(unsigned) * 2 * APEX_MAX_ACTIVE * apex_library::kRing);
+    L->d_obs_slots = (unsigned *)L->dalloc(sizeof(unsigned) * (1 + APEX_MAX_OUTPUTS) * APEX_MAX_ACTIVE);
     if (trace_on())
       for (auto &e : L->ev_tr) CU(cudaEventCreate(&e));
     L->pin(1 << 20);
@@ -1126,6 +1160,7 @@ extern "C" apex_status apex_free_library(apex_library *L) {
     if (L->ev_ls[i]) cudaEventDestroy(L->ev_ls[i]);
   }
   if (L->status_pin) cudaFreeHost(L->status_pin);
+  if (L->cnt_pin) cudaFreeHost(L->cnt_pin);
   for (auto &e : L->ev_tr)
     if (e) cudaEventDestroy(e);
   L->release_all();
@@ -1268,6 +1303,8 @@ static void free_query_device(apex_library &L, QueryRec *q) {
   q->dev_bytes = 0;
 }
 
+static unsigned *slot_obs(apex_library &L, int slot) { return L.d_obs_slots + (size_t)slot * (1 + APEX_MAX_OUTPUTS); }
+
 // Writes the query's slot parameters (boxes widened / shrunk by the pass margin).
 static void write_slot(apex_library &L, QueryRec *q, float admit) {
   QuerySlot S;
@@ -1303,6 +1340,8 @@ static void write_slot(apex_library &L, QueryRec *q, float admit) {
   S.keys2 = q->keys2;
   S.ids2 = q->ids2;
   L.upload(L.d_slots + q->slot, &S, sizeof(S));
+  CU(cudaMemsetAsync(slot_obs(L, q->slot), 0, sizeof(unsigned) * (1 + APEX_MAX_OUTPUTS), L.st));
+  q->want_compact = false;
 }
 
 
@@ -1440,7 +1479,11 @@ static bool admit_one(apex_library &L, QueryRec *q) {
       break;
     }
   if (slot < 0) return false;
-  if (q->cap == 0) q->cap = (unsigned)std::min<long long>(std::max<long long>(1LL << 18, 8 * q->k), 1LL << 30);
+  // candidate buffer: 2^18 entries (2^20 for scopes above 2^31 compounds, where the loose start
+  // threshold meets launches of 2^26 - 2^27 compounds) or 8k, grown 4x after an overflow
+  if (q->cap == 0)
+    q->cap = (unsigned)std::min<long long>(std::max<long long>(q->scope_n > (1LL << 31) ? 1LL << 20 : 1LL << 18, 8 * q->k),
+                                           1LL << 30);
   const unsigned have = L.slotbuf[slot].cap;
   if (have < q->cap) {
     const size_t need = query_bytes_for(q->cap) - query_bytes_for(have);
@@ -1585,8 +1628,7 @@ static void fin_queue(apex_library &L, QueryRec *q, FinChain &C, unsigned cover)
     L.upload(C.dhi, q->hi.data(), sizeof(double) * m);
   }
   const double e32f = fp32_delta_f(L, q);
-  C.d_obs = (unsigned *)L.aget(sizeof(unsigned) * (1 + APEX_MAX_OUTPUTS));
-  CU(cudaMemsetAsync(C.d_obs, 0, sizeof(unsigned) * (1 + APEX_MAX_OUTPUTS), L.st));
+  C.d_obs = slot_obs(L, C.sl);  // accumulates over the pass's compactions and this chain
   EvalArgs ea{C.out32, no, L.d_slots + C.sl, L.d_err32f, (float)e32f, C.dlo, C.dhi};
   ea.eps_scale = (float)q->mscale;
   ea.pass_keys = q->keys;  // compacted with the ids by the slot's last select
@@ -1873,8 +1915,51 @@ static void finish(apex_library &L, QueryRec *q, QState st, apex_status err, con
 
 // One step of the circular pass: a launch over the next chunk of items needed by any active
 // query (per precision), then the conditional select of the served queries.
+// In-pass FP32 compaction of query q's candidate buffer (queued behind the select that follows an
+// enumeration launch; no host wait): FP32 rescore of the buffer's entries, their FP32 decisions
+// and the k-th FP32-sure objective, then the buffer keeps only what can still reach the top-k and
+// the admission threshold rises to the FP32-certified floor (k_compact_keep / k_compact_apply).
+static void compact_query(apex_library &L, QueryRec *q) {
+  const int no = L.n_out, m = (int)q->cidx.size();
+  const unsigned cover = q->cap;
+  const unsigned *d_n = &L.d_slots[q->slot].count;
+  L.arena_reserve(sizeof(float) * (size_t)cover * (no + 1) + 2 * (size_t)cover + 16 * (size_t)(m + 1) + 8 * 256);
+  float *out32 = (float *)L.aget(sizeof(float) * (size_t)cover * no);
+  float *f32 = (float *)L.aget(sizeof(float) * cover);
+  unsigned char *maybe = (unsigned char *)L.aget(cover);
+  unsigned char *sure = (unsigned char *)L.aget(cover);
+  double *dlo = (double *)L.aget(sizeof(double) * std::max(m, 1));
+  double *dhi = (double *)L.aget(sizeof(double) * std::max(m, 1));
+  float *d_tau = (float *)L.aget(sizeof(float));
+  int *d_ok = (int *)L.aget(sizeof(int));
+  unsigned *kept = (unsigned *)L.aget(sizeof(unsigned));
+  if (m > 0) {
+    L.upload(dlo, q->lo.data(), sizeof(double) * m);
+    L.upload(dhi, q->hi.data(), sizeof(double) * m);
+  }
+  LaunchPlan dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  CU(apx_launch_fp32(dummy, L.T_, nullptr, q->ids, cover, out32, grid_for(L, (cover + APX_TILE - 1) / APX_TILE), L.st,
+                     L.fp32_id_tile.load(), d_n));
+  const double e32f = fp32_delta_f(L, q);
+  EvalArgs ea{out32, no, L.d_slots + q->slot, L.d_err32f, (float)e32f, dlo, dhi};
+  ea.eps_scale = (float)q->mscale;
+  ea.pass_keys = q->keys;
+  ea.obs = slot_obs(L, q->slot);
+  CU(apx_launch_eval32(ea, cover, f32, maybe, sure, L.st, d_n));
+  CU(apx_launch_kth(f32, sure, cover, q->k, d_tau, d_ok, L.st, d_n));
+  CU(apx_launch_compact(L.d_slots + q->slot, f32, maybe, sure, d_tau, d_ok, (float)(2.0 * e32f * 1.0001),
+                        (float)(e32f * 1.0001), kept, cover, L.n_sm, L.st));
+  q->want_compact = false;
+  q->stats.n_compactions++;
+}
+
 static void pass_step(apex_library &L) {
   const double t_p0 = trace_on() ? now_ms() : 0.0;
+  // compactions wanted by the launch retired last: queued before this step's launch, so they run
+  // right behind the select of the launch still in flight (one launch of lag)
+  for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+    if (L.active[s] && L.active[s]->want_compact && L.active[s]->remaining > 0) compact_query(L, L.active[s]);
   // a linear head costs ~100x less per compound than the MLP: larger launches. A query's first
   // launches are small and grow 4x per launch (2^24, 2^26, ...): its admission threshold is only
   // a sampled guess until the select after a launch raises it, and a large first launch at a loose
@@ -1949,6 +2034,9 @@ static void pass_step(apex_library &L) {
   if (!cont.empty()) {
     L.upload(L.d_slot_list, cont.data(), sizeof(int) * cont.size());
     CU(apx_launch_slot_select(L.d_slots, L.d_slot_list, (int)cont.size(), 0, L.st));
+    // every slot's (count, count_compacted) after the select, for the compaction trigger
+    CU(cudaMemcpy2DAsync(L.cnt_pin + (size_t)ring * 2 * APEX_MAX_ACTIVE, 2 * sizeof(unsigned), &L.d_slots[0].count,
+                         sizeof(QuerySlot), 2 * sizeof(unsigned), APEX_MAX_ACTIVE, cudaMemcpyDeviceToHost, L.st));
   }
   // the kernel status word of this launch, read back without waiting for it
   CU(cudaMemcpyAsync(L.status_pin + ring, L.d_err, sizeof(int), cudaMemcpyDeviceToHost, L.st));

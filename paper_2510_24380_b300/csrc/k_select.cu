@@ -296,6 +296,57 @@ __global__ void k_build_r(long long n, const long long *cand_ids, const float *f
   }
 }
 
+// ------------------------------------------------------------------ in-pass FP32 compaction
+// Between the launches of a pass, a query whose candidate buffer fills up has its candidates
+// rescored in FP32 (k_eval32, k_kth: tau32 = k-th largest FP32 objective among FP32-sure entries).
+// k surely feasible compounds then have exact objectives >= B = tau32 - eps_f, so the final k-th
+// exact objective is >= B: a candidate can still be a member only if its FP32 objective is >=
+// B - eps_f = tau32 - 2 eps_f and its FP32 outputs lie in the box widened by eps, and a compound
+// of a later launch only if its pass objective is >= B - delta_f. The buffer keeps the first kind
+// (pass keys unchanged; an entry becomes "sure" when it is FP32-sure) and the admission threshold
+// rises to the second, so the buffer holds about k entries plus the FP32 band after every
+// compaction, whatever the width of the pass margin (Sec. 3.3 queue with the precision pattern's
+// FP32 rescore moved into the pass).
+// Keep step: surviving entries -> keys2/ids2 (order not kept), their count -> *kept.
+__global__ void k_compact_keep(QuerySlot *Q, const float *f32, const unsigned char *maybe, const unsigned char *sure,
+                               const float *tau32, const int *ok, float margin2, unsigned *kept, unsigned n_max) {
+  const unsigned n = min(Q->count, min(Q->cap, n_max));
+  const float tau = *tau32;
+  const float thr = (*ok && isfinite(tau)) ? __fsub_rd(tau, margin2) : -INFINITY;
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned b = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < n; b += stride) {
+    const unsigned i = b + (threadIdx.x & 31);
+    const bool take = (i < n) && maybe[i] && f32[i] >= thr;
+    const unsigned p = apx_warp_reserve(kept, take);
+    if (take) {
+      const long long id = Q->ids[i];
+      Q->keys2[p] = Q->keys[i];
+      Q->ids2[p] = sure[i] ? (id & APX_ID_MASK) : id;
+    }
+  }
+}
+// Apply step: keys2/ids2 [0, kept) back into the buffer, the new count, the admission floor
+// B - delta_f, and the start guess marked verified when its admission threshold (tau_spec -
+// 2 delta_f) was at or below that floor (every member of the top-k was then admitted).
+__global__ void k_compact_apply(QuerySlot *Q, const unsigned *kept, const float *tau32, const int *ok, float eps_f) {
+  const unsigned m = *kept;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    Q->keys[i] = Q->keys2[i];
+    Q->ids[i] = Q->ids2[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Q->count = m;
+    Q->count_compacted = m;
+    const float tau = *tau32;
+    if (*ok && isfinite(tau)) {
+      const float B = __fsub_rd(tau, eps_f);
+      const float floor_adm = __fsub_rd(B, Q->delta_f);
+      if (floor_adm > Q->admit) Q->admit = floor_adm;
+      if (isfinite(Q->tau_spec) && __fadd_rd(B, Q->delta_f) >= Q->tau_spec) Q->tau_spec = -INFINITY;
+    }
+  }
+}
+
 // list of R positions whose FP64 rescore is pending
 __global__ void k_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64) {
   for (unsigned b = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < n; b += gridDim.x * blockDim.x) {
@@ -612,6 +663,19 @@ cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const flo
   apx_count_launch();
   k_build_r<<<(unsigned)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0, st>>>(n, cand_ids, f32, maybe, sure, tau32,
                                                                                  margin2, R, n_r, n_dev);
+  return cudaGetLastError();
+}
+// n_max: entries the scratch arrays (f32, maybe, sure) cover; the slot's count decides how many
+// are used. kept: a device counter, zeroed here.
+cudaError_t apx_launch_compact(QuerySlot *Q, const float *f32, const unsigned char *maybe, const unsigned char *sure,
+                               const float *tau32, const int *ok, float margin2, float eps_f, unsigned *kept,
+                               unsigned n_max, int n_sm, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(kept, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = std::max(1u, std::min<unsigned>((n_max + 255) / 256, (unsigned)n_sm * 4u));
+  apx_count_launch(2);
+  k_compact_keep<<<grid, 256, 0, st>>>(Q, f32, maybe, sure, tau32, ok, margin2, kept, n_max);
+  k_compact_apply<<<grid, 256, 0, st>>>(Q, kept, tau32, ok, eps_f);
   return cudaGetLastError();
 }
 cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64, cudaStream_t st) {

@@ -393,6 +393,40 @@ def test_exact_finalization_rerun_matches(ragged):
         L.set_finalize_cover(0)
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_in_pass_compaction_matches(ragged, precision):
+    """Small launches and a small finalization cover make every query's candidate buffer pass its
+    trigger between launches: it is rescored in FP32 and cut to what can still reach the top-k, and
+    the admission threshold rises to the FP32-certified floor. The rows must equal those of the
+    default path (no compaction) and the FP64 oracle, alone and with a second query sharing the
+    launches; the pass error observed on the compacted candidates stays inside the margin. (The
+    FP16 pass, with margins ~10x tighter, keeps too few candidates here to reach the trigger.)"""
+    lib, head, spec, L, rms = ragged
+    stats = csl_gen.load_stats("t_ragged")
+    qa = csl_gen.query_single("t_ragged", spec, stats, precision=precision)
+    qb = csl_gen.Query(qa.weights[::-1].copy(), qa.cons_idx, qa.lo, qa.hi, 37, None, precision)
+    refs = [L.run(q) for q in (qa, qb)]
+    assert L.stats(-1)["n_compactions"] == 0
+    try:
+        L.set_launch_shape(2048, 32)
+        L.set_finalize_cover(16)
+        for q, ref in zip((qa, qb), refs):
+            r = L.run(q)
+            st = L.stats(-1)
+            assert st["n_compactions"] > 0, st
+            assert st["n_restarts"] == 0 and st["n_margin_reruns"] == 0, st
+            assert 0.0 < st["pass_err_ratio"] <= 1.0, st
+            assert np.array_equal(r["ids"], ref["ids"]) and np.array_equal(r["objective"], ref["objective"])
+            assert np.array_equal(r["outputs"], ref["outputs"])
+            check_topk(r, O.topk(lib, head, q), lib, head, q, rms)
+        ia, ib = L.query(qa), L.query(qb)
+        ra, rb = L.fetch(ia, qa.k), L.fetch(ib, qb.k)
+        assert np.array_equal(ra["ids"], refs[0]["ids"]) and np.array_equal(rb["ids"], refs[1]["ids"])
+    finally:
+        L.set_launch_shape(1 << 25, 32)
+        L.set_finalize_cover(0)
+
+
 def test_restarts_when_no_candidate_is_surely_feasible():
     """A property that is constant (its last-layer row is zero) and a box whose lower bound is that
     constant: every compound is feasible, none is surely feasible within the pass margin. The start
