@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="batched", choices=["batched", "single", "serving"])
     ap.add_argument("--queries", type=int, default=8, help="queries per batched step")
+    ap.add_argument("--subset-compounds", type=float, default=0.0,
+                    help="batched: run the step's queries on the seeded reaction subset of this many compounds "
+                         "(64 queries there, k in {10..10^5} and 8 boxes each, is the multi-query config)")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp8", "fp32"],
                     help="pass precision of the enumeration (tensor-core bf16/fp16/fp8, or fp32 CUDA cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -118,7 +121,7 @@ def linear_roofline(N, q, lib, enum_ms, clk):
             "kernel_ms_per_step": enum_ms}
 
 
-def recorded_traffic(profile: str = "k_tc_head_c2_10m.md"):
+def recorded_traffic(profile: str = "k_tc_head_c3_real.md"):
     """DRAM bytes per launch of the enumeration kernel from the committed ncu summary, when the
     kernel source is still the one the counters were taken on (sha256 of k_tc.cu + common.cuh +
     tc_sync.cuh);
@@ -324,11 +327,31 @@ def query_upload_bytes(q) -> int:
     return 4 * len(q.weights) + (4 + 8 + 8) * q.m + sub + 880  # descriptor arrays + the device query slot
 
 
-def oracle_leg(L, lib, head, qs, results, n_target, seed=3):
-    """The FP64 oracle as it stands, on every host core, over a seeded sample of small reactions:
-    each query's exact top-(k + 65) of the sample, timed (cpu_baseline), then the reaction-decomposed
-    check of the GPU's rows against it and every returned member rescored by the oracle (the
-    top-k match)."""
+def member_reactions(sizes, results, cap: float, budget: float, exclude=()):
+    """Reactions that hold returned rows (of any query), no larger than `cap` compounds, most rows
+    first, until about `budget` compounds: the reaction-decomposed check is exact on them for the
+    members themselves (result n t == the oracle's first |result n t| of t), not only for the
+    reactions' best non-members. The choice of reactions uses the rows; every expected value is
+    the oracle's."""
+    cnt = {}
+    for r in results:
+        for t in np.asarray(r["reaction"][: int(r["n"])]).tolist():
+            cnt[int(t)] = cnt.get(int(t), 0) + 1
+    cands = sorted((t for t in cnt if sizes[t] <= cap and t not in set(exclude)), key=lambda t: (-cnt[t], t))
+    chosen, n = [], 0.0
+    for t in cands:
+        if n + sizes[t] > budget:
+            continue
+        chosen.append(int(t))
+        n += float(sizes[t])
+    return chosen, int(n)
+
+
+def oracle_leg(L, lib, head, qs, results, n_target, seed=3, scope=None):
+    """The FP64 oracle as it stands, on every host core, over a seeded sample of small reactions
+    plus the small reactions that hold the most returned rows: each query's exact top-(k + 65) of
+    the sample, timed (cpu_baseline), then the reaction-decomposed check of the GPU's rows against
+    it and every returned member rescored by the oracle (the top-k match)."""
     import csl_gen
     from oracle import oracle as O
 
@@ -336,7 +359,11 @@ def oracle_leg(L, lib, head, qs, results, n_target, seed=3):
     from parity import check_members_exact, check_reaction_decomposed, decomposed_query
 
     sizes = compounds_per_reaction(lib)
-    S, nS = oracle_sample(sizes, n_target, seed)
+    if scope is not None:  # only the queries' reactions can be checked
+        sizes = np.where(np.isin(np.arange(lib.n_reactions), scope), sizes, np.inf)
+    S0, n0 = oracle_sample(sizes, n_target, seed)
+    M, nM = member_reactions(sizes, results, cap=max(n_target, 1.0), budget=n_target, exclude=S0)
+    S, nS = sorted(S0 + M), n0 + nM
     rms = np.array(list(L.info().rms)[: head.dims[-1]])
     t_or, refs = 0.0, []
     for q in qs:
@@ -357,12 +384,12 @@ def oracle_leg(L, lib, head, qs, results, n_target, seed=3):
             ok = False
         per.append(entry)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
-    sample = (f"{len(S)} of {lib.n_reactions} reactions ({nS} compounds), each of the {len(qs)} queries of a step "
-              f"enumerated exactly, {t_or:.1f} s")
+    sample = (f"{len(S)} of {lib.n_reactions} reactions ({nS} compounds: {len(S0)} drawn at random, {len(M)} "
+              f"holding returned rows), each of the {len(qs)} queries of a step enumerated exactly, {t_or:.1f} s")
     cpu = {"value": nS / t_or, "unit": "compounds/s", "cores": cores, "kind": "oracle", "sample": sample}
     match = {"passed": ok, "rule": "reaction-decomposed on the sampled reactions (exact per reaction) + every "
                                    "returned member rescored in FP64 (feasible, objective and outputs within 1e-5)",
-             "reactions": S, "sample_compounds": nS, "queries": per}
+             "reactions": S, "member_reactions": M, "sample_compounds": nS, "queries": per}
     return cpu, match
 
 
@@ -415,7 +442,8 @@ def run_reference(args):
 
 def run_config(args, lib, head, qs, N, world):
     form = "batched" if args.mode == "batched" else "single query"
-    return {"workload": f"{args.workload} {form}: {len(qs)} quer{'ies' if len(qs) > 1 else 'y'} per shared pass",
+    where = f" {N:.3g}-compound reaction subset," if args.subset_compounds > 0 else ""
+    return {"workload": f"{args.workload}{where} {form}: {len(qs)} quer{'ies' if len(qs) > 1 else 'y'} per shared pass",
             "n_compounds": int(N), "n_reactions": int(lib.n_reactions), "queries_per_step": len(qs),
             "k": [int(q.k) for q in qs], "n_constraints": [int(q.m) for q in qs],
             "head": "-".join(str(x) for x in head.dims) + f" {head.activation}",
@@ -435,26 +463,41 @@ def run_batched(args):
     world, rank, local, pg = dist_setup(args)
     t_load0 = time.perf_counter()
     lib, head, spec = csl_gen.build_workload(args.workload)
-    qs = step_queries(args, spec)
     sizes = compounds_per_reaction(lib)
-    N = float(sizes.sum())
     prec = args.precision
+    scope = None
+    if args.subset_compounds > 0:  # the multi-query form on a reaction subset: random queries only
+        scope = np.array(csl_gen.subset_prefix(lib, 0, args.subset_compounds), np.int32)
+        qs = csl_gen.queries_batched(csl_gen.load_stats(args.workload), spec["n_obj"], spec["n_prop"], args.queries,
+                                     seed=1, subset=scope, precision=prec)
+        N = float(sizes[scope].sum())  # every step scores the subset once
+    else:
+        qs = step_queries(args, spec)
+        N = float(sizes.sum())
     dev = local
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
     L = apex.Library(lib, head, precisions=("fp32", prec), device=dev, stream=stream.cuda_stream, seed=0)
     load_s = time.perf_counter() - t_load0
     if args.autotune:
-        tune = L.autotune(prec, n_queries=len(qs), k=10000, subset=np.arange(min(30, lib.n_reactions)))
+        tune = L.autotune(prec, n_queries=len(qs), k=10000,
+                          subset=scope if scope is not None else np.arange(min(30, lib.n_reactions)))
     elif N > 1e9 and len(head.dims) > 2:
         L.set_launch_shape(1 << 27, 32)  # 2^27 compounds per launch: the autotuner's choice on this library
         tune = {"chosen_chunk_compounds": 1 << 27, "how": "fixed (autotuned choice on this workload)"}
     else:
         tune = {"chosen_chunk_compounds": 1 << 25, "how": "library default"}
 
+    qstats = []  # stats of every query of the last run (fetched one after another)
+
     def run_local(lq):
         ids = [L.query(q) for q in lq]
-        return [L.fetch(i, q.k) for i, q in zip(ids, lq)]
+        out = []
+        qstats.clear()
+        for i, q in zip(ids, lq):
+            out.append(L.fetch(i, q.k))
+            qstats.append(L.stats(-1))
+        return out
 
     runner = shard.ShardedRunner(sizes, rank, world, run_local, L.n_outputs)
     n_rank = float(sizes[runner.part].sum())
@@ -574,10 +617,20 @@ def run_batched(args):
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
-        cpu, match = oracle_leg(L, lib, head, qs, res, args.oracle_compounds)
+        cpu, match = oracle_leg(L, lib, head, qs, res, args.oracle_compounds, scope=scope)
         line["topk_match_vs_fp64_oracle"] = match
         line["cpu_baseline"] = cpu
     line["queries"] = [{"k": int(q.k), "n": int(r["n"])} for q, r in zip(qs, res)]
+    if qstats:  # the runtime margin check and the candidate traffic of the last step's queries
+        line["margin_check"] = {
+            "max_pass_err_ratio": round(max(st["pass_err_ratio"] for st in qstats), 4),
+            "max_fp32_err_ratio": round(max(st["fp32_err_ratio"] for st in qstats), 4),
+            "n_margin_reruns": int(sum(st["n_margin_reruns"] for st in qstats)),
+            "n_restarts": int(sum(st["n_restarts"] for st in qstats)),
+            "n_compactions": int(sum(st["n_compactions"] for st in qstats)),
+            "max_candidates": int(max(st["n_candidates"] for st in qstats)),
+            "rule": "observed max |pass - FP32| objective and |FP32 - FP64| output over every candidate / the "
+                    "margins the pass used; a ratio above 1 reruns the query with wider margins"}
     st = last_stats[0]
     line["last_query_stats"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()
                                 if k in ("n_candidates", "n_rescored_fp64", "n_restarts", "n_margin_reruns",

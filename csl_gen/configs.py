@@ -38,10 +38,16 @@ WORKLOADS = {
     "linear_1e12": dict(sizes=[[10000, 10000, 10000]], d=1024, dims=[1024, 3], act="identity", n_obj=1, n_prop=2,
                         seed=17, k=1000, precision="fp32"),
 }
+# the first 12 reactions of c3_real (same seeds: identical synthon embeddings and head), ~4e8
+# compounds in runs as long as c3_real's: profiling-sized (tables of a few tens of MB); its query
+# recipe and output statistics are c3_real's
+WORKLOADS["c3_slice"] = dict(WORKLOADS["c3_real"], slice_of="c3_real", n_slice=12, stats="c3_real")
 
 
 def workload_sizes(name: str):
     w = WORKLOADS[name]
+    if "slice_of" in w:
+        return workload_sizes(w["slice_of"])[: w["n_slice"]]
     if "sizes" in w:
         return [list(s) for s in w["sizes"]]
     return lognormal_slot_sizes(seed=w["seed"], **w["lognormal"])

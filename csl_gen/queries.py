@@ -38,6 +38,9 @@ class Query:
 
 
 def load_stats(name: str) -> dict:
+    from .configs import WORKLOADS  # a slice of a workload shares its statistics
+
+    name = WORKLOADS.get(name, {}).get("stats", name)
     path = os.path.join(DATA_DIR, f"{name}_stats.json")
     if not os.path.exists(path):
         raise FileNotFoundError(f"{path} is missing; write it with: python oracle/make_output_stats.py {name}")
@@ -71,7 +74,7 @@ def query_single(name: str, spec: dict, stats: dict | None = None, precision: st
         lo = np.array([quantile(stats, int(i), 0.15) for i in idx])
         hi = np.array([quantile(stats, int(i), 0.85) for i in idx])
         return Query(w, idx, lo, hi, k, sub, prec)
-    if name == "c3_real":
+    if name in ("c3_real", "c3_slice"):
         idx = np.arange(n_obj, n_obj + 6, dtype=np.int32)
         hi = np.array([quantile(stats, int(i), 0.8) for i in idx])
         lo = np.full(idx.shape, -np.inf)
