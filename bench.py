@@ -300,11 +300,11 @@ def step_queries(args, spec, precision=None):
 
 
 def oracle_sample(sizes, n_target: float, seed: int, min_reactions: int = 5):
-    """A seeded sample of small reactions for the oracle: at least min_reactions reactions, drawn
-    from those no larger than max(n_target / 3, the min_reactions-th smallest), until about
-    n_target compounds."""
+    """A seeded sample of small reactions for the oracle: drawn from those no larger than
+    max(n_target / 3, the min_reactions-th smallest) and never larger than n_target, until about
+    n_target compounds (at least min_reactions reactions when that many fit)."""
     order = np.sort(sizes)
-    cap = max(n_target / 3.0, order[min(min_reactions, len(order)) - 1])
+    cap = min(max(n_target / 3.0, order[min(min_reactions, len(order)) - 1]), n_target)
     cand = np.flatnonzero(sizes <= cap)
     np.random.default_rng(seed).shuffle(cand)
     chosen, n = [], 0.0
@@ -359,6 +359,7 @@ def oracle_leg(L, lib, head, qs, results, n_target, seed=3, scope=None):
     from parity import check_members_exact, check_reaction_decomposed, decomposed_query
 
     sizes = compounds_per_reaction(lib)
+    n_target = n_target * 8.0 / max(8, len(qs))  # every query enumerates the sample: bounded total work
     if scope is not None:  # only the queries' reactions can be checked
         sizes = np.where(np.isin(np.arange(lib.n_reactions), scope), sizes, np.inf)
     S0, n0 = oracle_sample(sizes, n_target, seed)

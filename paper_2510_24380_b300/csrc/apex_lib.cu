@@ -311,6 +311,9 @@ struct apex_library {
   };
   cudaEvent_t ev_l0[kRing] = {}, ev_l1[kRing] = {}, ev_ls[kRing] = {};
   int *status_pin = nullptr;
+  // claim counter of the enumeration kernel's tail pool (zeroed before every launch that uses it)
+  unsigned long long *d_pool_ctr = nullptr;
+  bool pool_off = false;  // APEX_NO_TILE_POOL set: CTA ranges only
   // per ring entry: (count, count_compacted) of every slot after the launch's select and
   // compactions (pinned), read when the launch retires to decide the next compactions
   unsigned *cnt_pin = nullptr;
@@ -536,18 +539,40 @@ static inline const double *pass_err(const apex_library &L, int precision) {
 // inner rows again at its start and its pipeline refills) costs kRunCost more, about 2.4 tiles as
 // measured per CTA on B300 (a reaction whose outer slot has 19 synthons ran ~10 % slower per tile
 // than one with long runs, and equal tile counts left its CTAs last). Every CTA gets >= 1 tile.
-static void tc_partition(const apex_library &L, LaunchPlan &P, int grid) {
+//
+// Tail pool: with 8 queries in a launch the cost of a tile also depends on how many of its compounds
+// pass some query's objective threshold (those warps take the box tests and the candidate append),
+// which differs between reactions: on c3_slice the slowest CTA ran 17 % above the mean. So for query
+// launches of at least kPoolMinPerCta tiles per CTA the ranges cover the first (1 - kPoolFrac) of
+// the tiles, and CTAs that finish their range take the rest kPoolChunk tiles at a time (each chunk
+// starts a new run for the CTA: the pool costs about 2.4 / kPoolChunk of its tiles).
+static constexpr double kPoolFrac = 0.2;
+static constexpr int kPoolChunk = 48;
+static constexpr long long kPoolMinPerCta = 512;
+static void tc_partition(const apex_library &L, LaunchPlan &P, int grid, unsigned long long *pool_ctr) {
   P.cta_n = 0;
+  P.pool_ctr = nullptr;
+  P.pool_first = P.total_tiles;
+  P.pool_chunk = 0;
   if (grid < 2 || grid > APX_MAX_CTA || P.total_tiles < grid) return;
+  long long n_static = P.total_tiles;  // tiles covered by the CTA ranges
+  if (pool_ctr && P.mode == 0 && P.total_tiles >= kPoolMinPerCta * grid) {
+    n_static = P.total_tiles - (long long)(kPoolFrac * (double)P.total_tiles);
+    P.pool_ctr = pool_ctr;
+    P.pool_first = n_static;
+    P.pool_chunk = kPoolChunk;
+  }
   constexpr double kRunCost = 2.4;
-  std::vector<std::pair<long long, long long>> runs;  // (first launch tile, tiles)
+  std::vector<std::pair<long long, long long>> runs;  // (first launch tile, tiles), below n_static
   for (int g = 0; g < P.n_seg; ++g) {
     const Segment &sg = P.seg[g];
     const RxnPlan &p = L.rx[sg.rxn];
     const long long x0 = apx_tiles_before(p, sg.item_begin), x1 = apx_tiles_before(p, sg.item_end);
     for (long long x = x0; x < x1;) {
       const long long e = std::min(x1, (x / p.n_outer + 1) * p.n_outer);
-      runs.emplace_back(P.seg_tile_first[g] + (x - x0), e - x);
+      const long long first = P.seg_tile_first[g] + (x - x0);
+      if (first >= n_static) break;
+      runs.emplace_back(first, std::min(e - x, n_static - first));
       x = e;
     }
   }
@@ -562,13 +587,13 @@ static void tc_partition(const apex_library &L, LaunchPlan &P, int grid) {
       const double into = std::max(0.0, (double)c * per - cum - kRunCost);  // tiles into the run
       long long t = r.first + std::min(r.second, (long long)std::ceil(into));
       t = std::max(t, P.cta_first[c - 1] + 1);
-      t = std::min(t, P.total_tiles - (grid - c));
+      t = std::min(t, n_static - (grid - c));
       P.cta_first[c++] = t;
     }
     cum += kRunCost + (double)r.second;
   }
-  for (; c < grid; ++c) P.cta_first[c] = std::min(P.total_tiles - (grid - c), P.cta_first[c - 1] + 1);
-  P.cta_first[grid] = P.total_tiles;
+  for (; c < grid; ++c) P.cta_first[c] = std::min(n_static - (grid - c), P.cta_first[c - 1] + 1);
+  P.cta_first[grid] = n_static;
   P.cta_n = grid;
 }
 
@@ -578,7 +603,8 @@ static void launch_enum(apex_library &L, const LaunchPlan &P, int precision) {
   if (fmt >= 0) {  // CTAs take tile ranges of equal estimated cost
     const int grid = grid_for(L, P.total_tiles);
     LaunchPlan Q = P;
-    tc_partition(L, Q, grid);
+    tc_partition(L, Q, grid, L.pool_off ? nullptr : L.d_pool_ctr);
+    if (Q.pool_ctr) CU(cudaMemsetAsync(Q.pool_ctr, 0, sizeof(unsigned long long), L.st));
     CU(apx_launch_tc(Q, L.T_, L.d_slots, L.d_err, grid, L.st, fmt));
   } else if (L.n_layers == 1 && P.mode == 0) {  // linear head: per-synthon scalar sums (Eq. apex)
     CU(apx_launch_linear(P, L.T_, L.d_slots, L.n_sm, L.st));
@@ -1087,6 +1113,8 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
     CU(cudaMallocHost(&L->cnt_pin, sizeof(unsigned) * 2 * APEX_MAX_ACTIVE * apex_library::kRing));
     memset(L->cnt_pin, 0, sizeof(unsigned) * 2 * APEX_MAX_ACTIVE * apex_library::kRing);
     L->d_obs_slots = (unsigned *)L->dalloc(sizeof(unsigned) * (1 + APEX_MAX_OUTPUTS) * APEX_MAX_ACTIVE);
+    L->d_pool_ctr = (unsigned long long *)L->dalloc(sizeof(unsigned long long));
+    L->pool_off = getenv("APEX_NO_TILE_POOL") != nullptr;
     if (trace_on())
       for (auto &e : L->ev_tr) CU(cudaEventCreate(&e));
     L->pin(1 << 20);

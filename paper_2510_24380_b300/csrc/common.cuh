@@ -58,6 +58,12 @@ struct LaunchPlan {
   long long *dump_ids;                       // mode 2: [dump_n], row r of launch tile t at t * 128 + r,
                                              // -1 = padding row; mode 3: the input ids [dump_n]
   long long dump_base, dump_n;
+  // tensor-core kernel, tail pool: tiles [pool_first, total_tiles) are not in any CTA's range; a CTA
+  // done with its own range claims them pool_chunk at a time (atomicAdd on *pool_ctr, zeroed before
+  // the launch). pool_ctr == nullptr: no pool, the CTA ranges cover every tile.
+  unsigned long long *pool_ctr;
+  long long pool_first;
+  int pool_chunk;
   // tensor-core kernel: CTA c takes launch tiles [cta_first[c], cta_first[c + 1]) when cta_n equals
   // the launch's grid (ranges of equal estimated cost), else an equal count of tiles
   int cta_n;

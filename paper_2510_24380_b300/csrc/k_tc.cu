@@ -66,7 +66,7 @@ struct SlotParams {
 // K-quarter stages of 16 KB (one tile). FP8: W_2 64 KB, W_3 8 KB (FP16), a_1 double-buffered: two
 // tiles x two K-halves of 16 KB (128 K elements per 128-byte row), plus the per-channel
 // dequantization scales of W_2.
-#define TC_NBAR 27
+#define TC_NBAR 35
 template <int FMT>
 struct TcL {
   static constexpr bool F8 = FMT == 2;
@@ -81,7 +81,8 @@ struct TcL {
   static constexpr uint32_t BAR = QP + (uint32_t)(APEX_MAX_ACTIVE * sizeof(SlotParams));
   static constexpr uint32_t MISC = BAR + 8u * TC_NBAR;
   static constexpr uint32_t QLIST = MISC + 64u;                  // per query warp: its run's query slots
-  static constexpr uint32_t SMEM = QLIST + 4u * APEX_MAX_ACTIVE + 1024u;  // + alignment slack
+  static constexpr uint32_t RING = (QLIST + 4u * APEX_MAX_ACTIVE + 15u) & ~15u;  // 4 tail-pool ranges {a, b}
+  static constexpr uint32_t SMEM = RING + 64u + 1024u;            // + alignment slack
 };
 static_assert(sizeof(SlotParams) == 352, "SlotParams layout");
 static_assert(TcL<0>::SMEM <= 232448 && TcL<1>::SMEM <= 232448 && TcL<2>::SMEM <= 232448, "shared memory budget");
@@ -100,6 +101,9 @@ static_assert(TcL<0>::A1 % 1024 == 0 && TcL<2>::A1 % 1024 == 0 && TcL<0>::QP % 1
 #define B_DRAIN3 26  // layer-3 issuer's drain
 #define B_OFULL(r) (18 + (r))
 #define B_OEMPTY(r) (22 + (r))
+#define B_RFULL(e) (27 + (e))   // tail-pool range ring (entry e of 4): published by the loader
+#define B_REMPTY(e) (31 + (e))  // ... released by every other warp role (TC_RING_READERS arrivals)
+#define TC_RING_READERS (TC_PROD_WARPS + TC_EPI_WARPS + 2)
 
 // UMMA shared-memory descriptor: SW128 K-major, 8-row atoms 1024 B apart (SBO)
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -423,6 +427,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const long long t_begin = L.cta_n == (int)gridDim.x ? L.cta_first[blockIdx.x]
                                                       : (long long)blockIdx.x * L.total_tiles / gridDim.x;
   const long long t_end = TC_CTA_END();
+  // Tail pool (L.pool_ctr != nullptr): after its own range a CTA takes chunks of the tiles past every
+  // CTA's range, claimed by the loader warp and passed to the other roles through a 4-entry ring of
+  // ranges in shared memory (a = -1: no more). Every role walks the same sequence of ranges.
+  auto pool_next = [&](unsigned &n, long long &a, long long &b, bool whole_warp) -> bool {
+    const int e = (int)(n & 3u);
+    bool got = mbar_wait(bar(B_RFULL(e)), (n >> 2) & 1u, abort_flag, err);
+    if (whole_warp) got = __all_sync(0xffffffffu, got);  // every lane gets here: no divergent exit
+    if (!got) return false;
+    const volatile long long *ring = reinterpret_cast<const volatile long long *>(sm + LY::RING) + 2 * e;
+    a = ring[0];
+    b = ring[1];
+    if (whole_warp) __syncwarp();
+    if (!whole_warp || lane == 0) mbar_arrive(bar(B_REMPTY(e)));
+    ++n;
+    return a >= 0;
+  };
+  auto pool_publish = [&](unsigned &n, long long a, long long b) -> bool {
+    const int e = (int)(n & 3u);
+    if (!mbar_wait(bar(B_REMPTY(e)), ((n >> 2) & 1u) ^ 1u, abort_flag, err)) return false;
+    volatile long long *ring = reinterpret_cast<volatile long long *>(sm + LY::RING) + 2 * e;
+    ring[0] = a;
+    ring[1] = b;
+    mbar_arrive(bar(B_RFULL(e)));
+    ++n;
+    return true;
+  };
   if (tid == 0) {
     for (int s = 0; s < 4; ++s) {  // FP8: a K-half stage is written by the warps of two K quarters
       mbar_init(bar(B_FULL(s)), F8 ? 8 : 4);
@@ -440,6 +470,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int r = 0; r < TC_OROW_SLOTS; ++r) {
       mbar_init(bar(B_OFULL(r)), 1);
       mbar_init(bar(B_OEMPTY(r)), TC_PROD_WARPS);  // every math warp reads every outer row
+    }
+    for (int e = 0; e < 4; ++e) {
+      mbar_init(bar(B_RFULL(e)), 1);
+      mbar_init(bar(B_REMPTY(e)), TC_RING_READERS);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -527,10 +561,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t row_off = (uint32_t)(m >> 3) * 1024u + (uint32_t)(m & 7) * 128u;
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     uint32_t R[32];  // resident inner sum of the producing item (64 columns), packed bf16 pairs
-    long long tile = t_begin;
+    long long tile = t_begin, rend = t_end;  // current range of tiles
+    unsigned n_ring = 0;                       // tail-pool ranges read so far
     int left = 0;            // tiles left in the current run
     bool has_outer = false;  // per-run fields kept in registers (no per-tile global loads)
-    bool more = tile < TC_CTA_END();
+    bool more = tile < rend;
+    while (!more && L.pool_ctr && pool_next(n_ring, tile, rend, true)) more = tile < rend;
     bool need_r = more;
     bool ok = true;
     for (unsigned s = 0; ok; ++s) {
@@ -567,7 +603,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               }
             }
           } else {  // the inner slots of the tile's work item
-            const TileRun I = apx_tile_run(L, T.rx, tile, TC_CTA_END());
+            const TileRun I = apx_tile_run(L, T.rx, tile, rend);
             const RxnPlan *rp = I.rp;
             left = (int)(I.o_end - I.o_begin);
             has_outer = rp->outer_row >= 0;
@@ -660,7 +696,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         ++tile;
         if (--left == 0) {
-          more = tile < TC_CTA_END();
+          more = tile < rend;
+          while (!more && L.pool_ctr && pool_next(n_ring, tile, rend, true)) more = tile < rend;
           need_r = more;
         }
       }
@@ -730,8 +767,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (lane == 0) {
       long long j = 0;
       bool ok = true;
-      for (long long tile = t_begin; ok && tile < t_end;) {
-        const TileRun I = apx_tile_run(L, T.rx, tile, t_end);
+      long long ra = t_begin, rb = t_end;  // current range: this CTA's own, then tail-pool chunks
+      unsigned n_ring = 0;
+      for (;;) {
+      for (long long tile = ra; ok && tile < rb;) {
+        const TileRun I = apx_tile_run(L, T.rx, tile, rb);
         tile += I.o_end - I.o_begin;
         const long long orow = I.rp->outer_row;
         for (long long o = I.o_begin; o < I.o_end; ++o, ++j) {
@@ -752,6 +792,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
+      if (!ok || !L.pool_ctr) break;
+      // claim the next chunk of the tail pool (or learn that it is empty) and publish it to the
+      // other roles; the claim runs a few tiles ahead of the math warps (the outer-row ring's depth)
+      const long long a = L.pool_first + (long long)atomicAdd(L.pool_ctr, (unsigned long long)L.pool_chunk);
+      ra = a < L.total_tiles ? a : -1;
+      rb = a < L.total_tiles ? (a + L.pool_chunk < L.total_tiles ? a + L.pool_chunk : L.total_tiles) : -1;
+      if (!pool_publish(n_ring, ra, rb) || ra < 0) break;
+      }
     }
     __syncwarp();
   } else if (warp == TC_MMA_WARP) {
@@ -762,7 +810,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t a1 = sbase + LY::A1, w2 = sbase + LY::W2;
         bool ok = true;
         {
-          for (long long j = 0; j < t_end - t_begin; ++j) {  // this CTA's tiles, in order
+          long long n_tiles = t_end - t_begin, pa = 0, pb = 0;  // own range, then tail-pool ranges
+          unsigned n_ring = 0;
+          bool have = true;
+          for (long long j = 0;; ++j) {  // this CTA's tiles, in order
+            while (j == n_tiles && (have = (L.pool_ctr && pool_next(n_ring, pa, pb, false)))) n_tiles += pb - pa;
+            if (!have) break;
             const int buf = (int)(j & 1);
             if (!mbar_wait(bar(B_D2EMPTY(buf)), (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag, err)) { ok = false; break; }
             tc_fence_after();
@@ -804,7 +857,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // behind the MMA warp's layer-2 work of the next tile nor wait for the query epilogue.
     if (lane == 0 && mbar_wait(bar(B_W), 0, abort_flag, err)) {
       const uint32_t w3 = sbase + LY::W3;
-      for (long long j = 0; j < t_end - t_begin; ++j) {
+      long long n_tiles = t_end - t_begin, pa = 0, pb = 0;  // own range, then tail-pool ranges
+      unsigned n_ring = 0;
+      bool have = true;
+      for (long long j = 0;; ++j) {
+        while (j == n_tiles && (have = (L.pool_ctr && pool_next(n_ring, pa, pb, false)))) n_tiles += pb - pa;
+        if (!have) break;
         const int buf = (int)(j & 1);
         if (!mbar_wait(bar(B_A2FULL(buf)), (uint32_t)((j >> 1) & 1), abort_flag, err)) break;
         tc_fence_after();
@@ -869,8 +927,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     long long j = 0;
     bool ok = !IDS;
-    for (long long tile = t_begin; ok && tile < t_end;) {
-      const TileRun I = apx_tile_run(L, T.rx, tile, t_end);
+    long long ra = t_begin, rb = t_end;  // own range, then tail-pool ranges
+    unsigned n_ring = 0;
+    for (long long tile = ra; ok;) {
+      if (tile >= rb) {  // range done: the next tail-pool range, if any
+        if (!L.pool_ctr || !pool_next(n_ring, ra, rb, true)) break;
+        tile = ra;
+        continue;
+      }
+      const TileRun I = apx_tile_run(L, T.rx, tile, rb);
       const long long run_tile0 = tile - I.o_begin;  // launch tile of outer index o: run_tile0 + o
       // this run's query slots, as a list
       unsigned char *qlist = sm + LY::QLIST + (uint32_t)warp * APEX_MAX_ACTIVE;
