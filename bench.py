@@ -82,25 +82,34 @@ def peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
-# tanh.approx.f16x2 (one per SiLU pair) issues 7.3 times per clock per SM: CUDA-event timed over a
-# full-occupancy kernel of independent chains on a B300
-MUFU_SILU_PER_CLK_SM = 14.6
+# MUFU element rates per clock per SM, measured on a B300 with a full-occupancy kernel of independent
+# chains timed by CUDA events (per clock at the 2,032 MHz maximum SM clock, so lower bounds):
+# tanh.approx.{bf16x2,f16x2} 7.92 instructions (15.84 activations), ex2.approx.{bf16x2,f16x2} twice that
+MUFU_SILU_PER_CLK_SM = 15.84
+# share of the BF16 pass's layer-2 activations evaluated through ex2 (half the MUFU time of tanh)
+EX2_SHARE_L2_BF16 = 3.0 / 8.0
 
 
-def mufu_bound(N, head, enum_ms, clk):
-    """Second bound of the tensor-core kernel: the SiLU activations (one MUFU tanh per pair) of
-    every hidden layer, against the measured MUFU rate x 148 SMs x the sampled SM clock."""
+def mufu_bound(N, head, enum_ms, clk, precision):
+    """Second bound of the tensor-core kernel: the SiLU activations of every hidden layer on the MUFU
+    (one tanh per pair, or one ex2 at half its cost for the BF16 layer-2 share), in tanh-equivalent
+    activations, against the measured MUFU rate x 148 SMs x the sampled SM clock."""
     if head.activation != "silu":
         return None
-    acts = float(sum(head.dims[1:-1]))
+    hidden = [float(x) for x in head.dims[1:-1]]
+    acts = float(sum(hidden))
+    work = acts
+    if precision == "bf16" and len(hidden) >= 2:
+        work = acts - hidden[1] * EX2_SHARE_L2_BF16 * 0.5
     mhz = (clk or {}).get("sm_mhz") or 2032.0
-    achieved = N * acts / (enum_ms * 1e-3) / (148 * mhz * 1e6)
-    t_mufu = N * acts / MUFU_SILU_PER_CLK_SM / 148 / (mhz * 1e6)
+    achieved = N * work / (enum_ms * 1e-3) / (148 * mhz * 1e6)
+    t_mufu = N * work / MUFU_SILU_PER_CLK_SM / 148 / (mhz * 1e6)
     t_tensor = N / 128 * 2851 / 148 / (mhz * 1e6)  # 2,221 (layer 2) + ~630 (layer 3) cycles per 128-row tile
-    return {"bound": "xu", "unit": "activations/clk/SM", "achieved": achieved, "peak": MUFU_SILU_PER_CLK_SM,
-            "frac": achieved / MUFU_SILU_PER_CLK_SM, "activations_per_compound": acts,
+    return {"bound": "xu", "unit": "tanh-equivalent activations/clk/SM", "achieved": achieved,
+            "peak": MUFU_SILU_PER_CLK_SM, "frac": achieved / MUFU_SILU_PER_CLK_SM, "activations_per_compound": acts,
+            "mufu_work_per_compound": work,
             "tensor_frac_cap": t_tensor / t_mufu if t_mufu > t_tensor else 1.0,
-            "peak_kind": "measured tanh.approx.f16x2 rate x 2 elements"}
+            "peak_kind": "measured tanh.approx.bf16x2 rate x 2 elements (ex2 counted at half)"}
 
 
 def linear_roofline(N, q, lib, enum_ms, clk):
@@ -588,7 +597,7 @@ def run_batched(args):
                              f"against the {kind} burst peak {peak_b:.0f}: frac {achieved / peak_b:.3f}",
                 "frac_vs_burst": achieved / peak_b, "kernel_ms_per_step": enum_ms,
                 "launches_per_step": sv["n_enumeration_launches"] / K,
-                "mufu": mufu_bound(n_rank, head, enum_ms, clk)}
+                "mufu": mufu_bound(n_rank, head, enum_ms, clk, prec)}
     d2h = int(sum(r["n"] for r in res)) * row_bytes(L.n_outputs)
     h2d = int(sum(query_upload_bytes(q) for q in qs))
     qc = float(sum(N if q.subset is None else sizes[q.subset].sum() for q in qs))
