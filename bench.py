@@ -580,7 +580,10 @@ def run_batched(args):
     P, kind = peaks()
     K = args.steps
     enum_ms = sv["enumerate_ms"] / K
-    achieved = FLOP_PER_COMPOUND * n_rank / (enum_ms * 1e-3) / 1e12
+    # compounds the enumeration launches scored per step (the scope once per pass; more when a query
+    # had to run its pass again)
+    n_enum = sv["head_evaluations"] / K if sv["head_evaluations"] > 0 else n_rank
+    achieved = FLOP_PER_COMPOUND * n_enum / (enum_ms * 1e-3) / 1e12
     linear = len(head.dims) == 2
     peak_s = P.get("bf16_tflops_sustained", 1400.0)
     peak_b = P.get("bf16_tflops", 1800.0)
@@ -597,7 +600,8 @@ def run_batched(args):
                              f"against the {kind} burst peak {peak_b:.0f}: frac {achieved / peak_b:.3f}",
                 "frac_vs_burst": achieved / peak_b, "kernel_ms_per_step": enum_ms,
                 "launches_per_step": sv["n_enumeration_launches"] / K,
-                "mufu": mufu_bound(n_rank, head, enum_ms, clk, prec)}
+                "compounds_scored_per_step": n_enum,
+                "mufu": mufu_bound(n_enum, head, enum_ms, clk, prec)}
     d2h = int(sum(r["n"] for r in res)) * row_bytes(L.n_outputs)
     h2d = int(sum(query_upload_bytes(q) for q in qs))
     qc = float(sum(N if q.subset is None else sizes[q.subset].sum() for q in qs))

@@ -485,6 +485,16 @@ static RxnPlan plan_reaction(const apex_library &L, int t, long long target_tile
   return p;
 }
 
+// Compounds in items [ib, ie) of a reaction: 128 per tile, except in the tiles of the last inner
+// block, which hold n_inner - 128 (n_b - 1) rows each.
+static long long items_compounds(const RxnPlan &r, long long ib, long long ie) {
+  const long long t0 = apx_tiles_before(r, ib), t1 = apx_tiles_before(r, ie);
+  const long long last0 = (long long)(r.n_b - 1) * r.n_outer;  // first tile of the last inner block
+  const long long last_rows = r.n_inner - (long long)(r.n_b - 1) * APX_TILE;
+  const long long in_last = std::max(0LL, t1 - std::max(t0, last0));
+  return (t1 - t0) * APX_TILE - in_last * (APX_TILE - last_rows);
+}
+
 static DevTables upload_plans(apex_library &L) {
   RxnPlan *d_rx = (RxnPlan *)L.dalloc(sizeof(RxnPlan) * L.rx.size());
   CU(cudaMemcpy(d_rx, L.rx.data(), sizeof(RxnPlan) * L.rx.size(), cudaMemcpyHostToDevice));
@@ -2077,8 +2087,8 @@ static void pass_step(apex_library &L) {
     long long launched = 0;
     for (int p = 0; p < 5; ++p)
       for (int g = 0; g < pb[p].P.n_seg; ++g) {
-        const RxnPlan &r = L.rx[pb[p].P.seg[g].rxn];
-        launched += (pb[p].P.seg[g].item_end - pb[p].P.seg[g].item_begin) * r.L_o * APX_TILE;
+        const Segment &sg = pb[p].P.seg[g];
+        launched += items_compounds(L.rx[sg.rxn], sg.item_begin, sg.item_end);
       }
     L.head_evals += launched;
   }
@@ -2090,8 +2100,8 @@ static void pass_step(apex_library &L) {
     for (int p = 0; p < 5; ++p)
       for (int g = 0; g < pb[p].P.n_seg; ++g)
         if (pb[p].P.seg[g].qmask >> s & 1ull) {
-          const RxnPlan &r = L.rx[pb[p].P.seg[g].rxn];
-          comp += (pb[p].P.seg[g].item_end - pb[p].P.seg[g].item_begin) * r.L_o * APX_TILE;
+          const Segment &sg = pb[p].P.seg[g];
+          comp += items_compounds(L.rx[sg.rxn], sg.item_begin, sg.item_end);
         }
     q->stats.n_scored += comp;
   }
