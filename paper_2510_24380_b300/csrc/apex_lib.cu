@@ -1517,11 +1517,15 @@ static bool admit_one(apex_library &L, QueryRec *q) {
       break;
     }
   if (slot < 0) return false;
-  // candidate buffer: 2^18 entries (2^20 for scopes above 2^31 compounds, where the loose start
-  // threshold meets launches of 2^26 - 2^27 compounds) or 8k, grown 4x after an overflow
-  if (q->cap == 0)
-    q->cap = (unsigned)std::min<long long>(std::max<long long>(q->scope_n > (1LL << 31) ? 1LL << 20 : 1LL << 18, 8 * q->k),
+  // candidate buffer: 2^18 entries or 8k for scopes up to 2^28 compounds; above that, where a loose
+  // or missing start threshold meets launches of 2^26 - 2^27 compounds, 2^20 entries or 32k (a
+  // narrow box can leave fewer than k compounds surely feasible in the start sample, and then the
+  // buffer holds every admitted candidate until k sure ones exist); grown 4x after an overflow
+  if (q->cap == 0) {
+    const bool big = q->scope_n > (1LL << 28);
+    q->cap = (unsigned)std::min<long long>(std::max<long long>(big ? 1LL << 20 : 1LL << 18, (big ? 32 : 8) * q->k),
                                            1LL << 30);
+  }
   const unsigned have = L.slotbuf[slot].cap;
   if (have < q->cap) {
     const size_t need = query_bytes_for(q->cap) - query_bytes_for(have);
