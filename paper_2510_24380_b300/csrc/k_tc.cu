@@ -49,12 +49,15 @@
 __host__ __device__ constexpr uint32_t tc_d3_col(int c) { return 64u * (uint32_t)(c >> 1) + 32u + 16u * (uint32_t)(c & 1); }
 
 // Query parameters cached in shared memory for the whole launch (one entry per query slot). The
-// boxes are stored per output (several constraints on one output intersect), so the epilogue
-// tests outputs at compile-time register indices: cmask bit j = output j is constrained.
+// boxes are stored per output (several constraints on one output intersect; +-inf where an output
+// is unconstrained) as FP16 pairs, element j of pair j / 2 for output j, so that the epilogue tests
+// two outputs per packed instruction with no branch per output. Bounds are rounded so that the
+// FP16 tests never err the wrong way (tc_box_admit / tc_box_sure): the admission box outward, the
+// sure box inward and one more FP16 step inward.
 struct SlotParams {
   float w[APEX_MAX_OBJECTIVES];  // zero beyond n_obj
-  float lo_w[16], hi_w[16];      // admission box (widened by the pass margin), per output
-  float lo_s[16], hi_s[16];      // "sure" box (shrunk by the margin), per output
+  uint32_t lo_w[8], hi_w[8];     // admission box (widened by the pass margin)
+  uint32_t lo_s[8], hi_s[8];     // "sure" box (shrunk by the margin)
   float admit;
   unsigned cmask;
   int n_obj;
@@ -86,7 +89,7 @@ struct TcL {
   static constexpr uint32_t RING = (QLIST + 4u * APEX_MAX_ACTIVE + 15u) & ~15u;  // 4 tail-pool ranges {a, b}
   static constexpr uint32_t SMEM = RING + 64u + 1024u;            // + alignment slack
 };
-static_assert(sizeof(SlotParams) == 352, "SlotParams layout");
+static_assert(sizeof(SlotParams) == 224, "SlotParams layout");
 static_assert(TcL<0>::SMEM <= 232448 && TcL<1>::SMEM <= 232448 && TcL<2>::SMEM <= 232448, "shared memory budget");
 static_assert(TcL<0>::A1 % 1024 == 0 && TcL<2>::A1 % 1024 == 0 && TcL<0>::QP % 16 == 0 && TcL<2>::QP % 16 == 0,
               "alignment");
@@ -315,20 +318,74 @@ __device__ __forceinline__ float2 unpack2(uint32_t w) {
   return make_float2(lo, hi);
 }
 
+// FP16 bound rounding (bit level; x is never NaN): the largest FP16 value <= x, the smallest >= x,
+// and one FP16 step down / up.
+__device__ __forceinline__ uint16_t f16_rn(float x) {
+  uint16_t h;
+  asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(x));
+  return h;
+}
+__device__ __forceinline__ float f16_val(uint16_t h) {
+  float x;
+  asm("cvt.f32.f16 %0, %1;" : "=f"(x) : "h"(h));
+  return x;
+}
+__device__ __forceinline__ uint16_t f16_down(uint16_t h) {  // next FP16 value below (-inf stays)
+  if (h == 0x0000u) return 0x8001u;
+  if (h == 0xfc00u) return h;
+  return (h & 0x8000u) ? (uint16_t)(h + 1u) : (uint16_t)(h - 1u);
+}
+__device__ __forceinline__ uint16_t f16_up(uint16_t h) {  // next FP16 value above (+inf stays)
+  if (h == 0x8000u) return 0x0001u;
+  if (h == 0x7c00u) return h;
+  return (h & 0x8000u) ? (uint16_t)(h - 1u) : (uint16_t)(h + 1u);
+}
+__device__ __forceinline__ uint16_t f16_rd(float x) {
+  const uint16_t h = f16_rn(x);
+  return f16_val(h) > x ? f16_down(h) : h;
+}
+__device__ __forceinline__ uint16_t f16_ru(float x) {
+  const uint16_t h = f16_rn(x);
+  return f16_val(h) < x ? f16_up(h) : h;
+}
+// The row's 16 outputs as FP16 pairs (round to nearest, saturated to the finite range: both are
+// monotonic, so an output inside a box stays inside its outward-rounded FP16 image)
+__device__ __forceinline__ void tc_outputs_f16(const float (&o)[16], uint32_t (&h)[8]) {
+#pragma unroll
+  for (int n = 0; n < 8; ++n) asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(h[n]) : "f"(o[2 * n + 1]), "f"(o[2 * n]));
+}
+// Box tests on FP16 pairs: inside iff every o - lo and hi - o is >= 0, i.e. has a clear sign bit
+// (the difference of two FP16 values is zero only when they are equal, and then +0). Admission box
+// [rd(lo), ru(hi)]: every output inside [lo, hi] passes (extra passes near the bounds only add
+// candidates). Sure box [up(ru(lo)), down(rd(hi))]: an FP16 image at or above up(ru(lo)) comes from
+// an output above ru(lo) >= lo, so every output that passes is inside [lo, hi].
+__device__ __forceinline__ bool tc_box(const uint32_t (&h)[8], const uint32_t *lo, const uint32_t *hi) {
+  uint32_t neg = 0u;
+#pragma unroll
+  for (int n = 0; n < 8; n += 4) {
+    const uint4 l = *reinterpret_cast<const uint4 *>(lo + n), u = *reinterpret_cast<const uint4 *>(hi + n);
+    const uint32_t lv[4] = {l.x, l.y, l.z, l.w}, uv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint32_t a, b;
+      asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(a) : "r"(h[n + e]), "r"(lv[e]));
+      asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(b) : "r"(uv[e]), "r"(h[n + e]));
+      neg |= a | b;
+    }
+  }
+  return (neg & 0x80008000u) == 0u;
+}
+
 // Sec. 3 / Eq. apex_topk per compound (one row per lane, all 32 lanes call it): objective,
 // admission threshold, widened box (admission) and shrunk box ("sure"), then a warp-aggregated
 // append to the query's candidate buffer in global memory. Parameters come from shared memory.
 __device__ __forceinline__ void tc_apply_query_slow(const SlotParams &P, QuerySlot *Q, bool pass, float f, long long id,
                                                     const float (&o)[16]) {
-  const unsigned cm = P.cmask;
-#pragma unroll
-  for (int j = 0; j < 16; ++j)
-    if (cm & (1u << j)) pass = pass && (o[j] >= P.lo_w[j]) && (o[j] <= P.hi_w[j]);  // warp-uniform test
+  uint32_t h[8];  // the row's outputs as FP16 pairs (formed per test: cheaper than keeping them live)
+  tc_outputs_f16(o, h);
+  pass = pass && tc_box(h, P.lo_w, P.hi_w);
   if (__ballot_sync(0xffffffffu, pass) == 0u) return;  // no lane inside the widened boxes
-  bool sure = true;
-#pragma unroll
-  for (int j = 0; j < 16; ++j)
-    if (cm & (1u << j)) sure = sure && (o[j] >= P.lo_s[j]) && (o[j] <= P.hi_s[j]);
+  const bool sure = tc_box(h, P.lo_s, P.hi_s);
   const unsigned pos = apx_warp_reserve(&Q->count, pass);
   if (pass) {
     if (pos < P.cap) {
@@ -548,10 +605,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ls = fmaxf(ls, Q->lo_s[c]);
             hs = fminf(hs, Q->hi_s[c]);
           }
-        P.lo_w[lane] = lw;
-        P.hi_w[lane] = hw;
-        P.lo_s[lane] = ls;
-        P.hi_s[lane] = hs;
+        // FP16 images: admission box outward, sure box inward and one step further in (an infinite
+        // bound stays infinite)
+        const uint32_t b_lw = f16_rd(lw), b_hw = f16_ru(hw);
+        const uint32_t b_ls = ls == -INFINITY ? 0xfc00u : f16_up(f16_ru(ls));
+        const uint32_t b_hs = hs == INFINITY ? 0x7c00u : f16_down(f16_rd(hs));
+        const uint32_t p_lw = b_lw | (__shfl_down_sync(0x0000ffffu, b_lw, 1) << 16);
+        const uint32_t p_hw = b_hw | (__shfl_down_sync(0x0000ffffu, b_hw, 1) << 16);
+        const uint32_t p_ls = b_ls | (__shfl_down_sync(0x0000ffffu, b_ls, 1) << 16);
+        const uint32_t p_hs = b_hs | (__shfl_down_sync(0x0000ffffu, b_hs, 1) << 16);
+        if ((lane & 1) == 0) {
+          P.lo_w[lane >> 1] = p_lw;
+          P.hi_w[lane >> 1] = p_hw;
+          P.lo_s[lane >> 1] = p_ls;
+          P.hi_s[lane >> 1] = p_hs;
+        }
         const unsigned cm = __ballot_sync(0x0000ffffu, any);
         if (lane == 0) P.cmask = cm;
       }
