@@ -475,3 +475,42 @@ def test_library_file_round_trip(ragged, tmp_path):
             assert np.array_equal(r1["ids"], r2["ids"]) and np.array_equal(r1["objective"], r2["objective"])
     finally:
         L2.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_box_bounds_between_close_outputs_and_beyond_fp16(ragged, precision):
+    """The epilogue tests boxes on FP16 images of the outputs and bounds (admission box rounded
+    outward, sure box inward): bounds placed between the outputs of compounds far closer together
+    than an FP16 step, a band narrower than one, and finite bounds beyond the FP16 range. The
+    FP16 tests may only admit more candidates or mark fewer sure; the FP32 and FP64 rescores
+    decide, so the rows equal the oracle's outside its 1e-9 ambiguous band."""
+    lib, head, spec, L, rms = ragged
+    N = O.count(lib)
+    n_obj = spec["n_obj"]
+    ids = np.sort(np.random.default_rng(11).choice(N, 20000, replace=False))
+    o = O.score_ids(lib, head, ids)
+    p = n_obj + 1
+    v = np.sort(o[:, p])
+    mid = len(v) // 2
+    gaps = np.diff(v)
+    assert np.median(gaps) < 1e-3 * rms[p]  # neighbouring sampled outputs lie well inside one FP16 step
+    lo_b, hi_b = 0.5 * (v[mid - 1] + v[mid]), 0.5 * (v[mid + 3000] + v[mid + 3001])
+    w = np.zeros(n_obj, np.float32)
+    w[0] = 1.0
+    cases = {
+        "between_close": ([p], [lo_b], [hi_b]),
+        "band_below_fp16_step": ([p], [v[mid] - 1e-7], [v[mid] + 1e-7]),
+        "finite_beyond_fp16": ([p, p + 1], [-1e6, -7.0e4], [1e6, 7.0e4]),
+        "above_fp16_range": ([p], [7.0e4], [8.0e4]),
+    }
+    for name, (idx, lo, hi) in cases.items():
+        q = _q(w, idx, lo, hi, k=300, precision=precision)
+        ref = O.topk(lib, head, q)
+        res = L.run(q)
+        check_topk(res, ref, lib, head, q, rms)
+        if name == "above_fp16_range":
+            assert res["n"] == 0
+        if name == "band_below_fp16_step":
+            assert res["n"] == ref.n_feasible <= 300
+        if name == "finite_beyond_fp16":
+            assert ref.n_feasible == N and res["n"] == 300
