@@ -553,9 +553,12 @@ static inline const double *pass_err(const apex_library &L, int precision) {
 // Tail pool: with 8 queries in a launch the cost of a tile also depends on how many of its compounds
 // pass some query's objective threshold (those warps take the box tests and the candidate append),
 // which differs between reactions: on c3_slice the slowest CTA ran 17 % above the mean. So for query
-// launches of at least kPoolMinPerCta tiles per CTA the ranges cover the first (1 - kPoolFrac) of
-// the tiles, and CTAs that finish their range take the rest kPoolChunk tiles at a time (each chunk
-// starts a new run for the CTA: the pool costs about 2.4 / kPoolChunk of its tiles).
+// launches of more than two queries and at least kPoolMinPerCta tiles per CTA the ranges cover the
+// first (1 - kPoolFrac) of the tiles, and CTAs that finish their range take the rest kPoolChunk
+// tiles at a time (each chunk starts a new run for the CTA: the pool costs about 2.4 / kPoolChunk of
+// its tiles). With one or two queries the cost-weighted ranges alone end within a few percent of
+// each other, and the pool's extra run starts cost more than it balances (c2_10m single query:
+// 1.63 ms per launch with the pool, 1.55 ms without).
 static constexpr double kPoolFrac = 0.2;
 static constexpr int kPoolChunk = 48;
 static constexpr long long kPoolMinPerCta = 512;
@@ -566,7 +569,7 @@ static void tc_partition(const apex_library &L, LaunchPlan &P, int grid, unsigne
   P.pool_chunk = 0;
   if (grid < 2 || grid > APX_MAX_CTA || P.total_tiles < grid) return;
   long long n_static = P.total_tiles;  // tiles covered by the CTA ranges
-  if (pool_ctr && P.mode == 0 && P.total_tiles >= kPoolMinPerCta * grid) {
+  if (pool_ctr && P.mode == 0 && __builtin_popcountll(P.qmask_all) > 2 && P.total_tiles >= kPoolMinPerCta * grid) {
     n_static = P.total_tiles - (long long)(kPoolFrac * (double)P.total_tiles);
     P.pool_ctr = pool_ctr;
     P.pool_first = n_static;
@@ -1015,8 +1018,10 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
         CU(cudaMemcpy(dw + w2.size(), w3.data(), sizeof(float) * w3.size(), cudaMemcpyHostToDevice));
         for (int f = 0; f < 2; ++f) {  // 16-bit tables and images
           if (!L->tc_fmt[f]) continue;
-          void *P16 = L->dalloc(sizeof(unsigned short) * L->rows * 256);
+          // one more row of zeros (row `rows`): the outer row of reactions without an outer slot
+          void *P16 = L->dalloc(sizeof(unsigned short) * (L->rows + 1) * 256);
           CU(apx_launch_p16(P32, L->rows * 256, scale, f, P16, L->st));
+          CU(cudaMemsetAsync((unsigned short *)P16 + (size_t)L->rows * 256, 0, sizeof(unsigned short) * 256, L->st));
           unsigned char *d2 = (unsigned char *)L->dalloc(256 * 256 * 2);
           unsigned char *d3 = (unsigned char *)L->dalloc(16 * 256 * 2);
           CU(apx_launch_image(dw, 256, 256, f, d2, L->st));

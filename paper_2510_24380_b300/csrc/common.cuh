@@ -313,7 +313,8 @@ struct DevTables {
   // tensor-core path (3-layer heads with dims[1] == dims[2] == 256, <= 16 outputs). P tables and
   // W_3 images per 16-bit format: [0] = BF16, [1] = FP16 (the FP8 pass uses the FP16 ones); W_2
   // images per operand format: [0] = BF16, [1] = FP16, [2] = FP8 e4m3 with per-channel scales s2.
-  const unsigned short *P16[2];   // [n_rows x 256] 16-bit bits, scaled into the activation's input space
+  const unsigned short *P16[2];   // [n_rows + 1 x 256] 16-bit bits, scaled into the activation's input
+                                  // space; row n_rows is zero
   const unsigned char *w2img[3];  // W_2 as the SW128 K-major shared-memory image (128 KB; FP8: 64 KB)
   const unsigned char *w3img[2];  // W_3 padded to 16 rows, same layout (8 KB)
   const float *s2;                // FP8: dequantization scale of every W_2 output channel, times the

@@ -658,7 +658,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     long long tile = t_begin, rend = t_end;  // current range of tiles
     unsigned n_ring = 0;                       // tail-pool ranges read so far
     int left = 0;            // tiles left in the current run
-    bool has_outer = false;  // per-run fields kept in registers (no per-tile global loads)
     bool more = tile < rend;
     while (!more && L.pool_ctr && pool_next(n_ring, tile, rend, true)) more = tile < rend;
     bool need_r = more;
@@ -674,7 +673,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           bool row_ok;
           if constexpr (IDS) {  // every slot of the listed compound; each tile is its own run
             left = 1;
-            has_outer = false;
             const long long i = tile * APX_TILE + m;
             row_ok = i < L.dump_n;
             const long long id = row_ok ? (L.dump_ids[i] & APX_ID_MASK) : 0;
@@ -700,7 +698,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const TileRun I = apx_tile_run(L, T.rx, tile, rend);
             const RxnPlan *rp = I.rp;
             left = (int)(I.o_end - I.o_begin);
-            has_outer = rp->outer_row >= 0;
             const long long q = I.q0 + m;
             row_ok = q < rp->n_inner;
             long long rem = q;
@@ -754,7 +751,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               uint4 pv = make_uint4(0u, 0u, 0u, 0u);
-              if (has_outer) pv = *reinterpret_cast<const uint4 *>(prow + c * 16);
+              if (!IDS) pv = *reinterpret_cast<const uint4 *>(prow + c * 16);  // 1-slot reactions: the zero row
               const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
               uint32_t out[4];
 #pragma unroll
@@ -769,7 +766,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               for (int h = 0; h < 2; ++h) {
                 const int c = 2 * cc + h;
                 uint4 pv = make_uint4(0u, 0u, 0u, 0u);
-                if (has_outer) pv = *reinterpret_cast<const uint4 *>(prow + c * 16);
+                if (!IDS) pv = *reinterpret_cast<const uint4 *>(prow + c * 16);
                 const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w};
                 uint32_t out[4];
 #pragma unroll
@@ -879,16 +876,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ok = false;
             break;
           }
-          if (orow >= 0) {
-            mbar_expect_tx(bar(B_OFULL(rs)), 512u);
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 512, [%2];" ::"r"(
-                    sbase + LY::OROW + (uint32_t)rs * 512u),
-                "l"(T.P16[PF] + (orow + o) * 256), "r"(bar(B_OFULL(rs)))
-                : "memory");
-          } else {
-            mbar_arrive(bar(B_OFULL(rs)));
-          }
+          // the outer synthon's row; a reaction without an outer slot (one slot) gets the table's
+          // zero row (row n_rows), so that the math warps add a row whatever the reaction
+          const unsigned short *src = T.P16[PF] + (orow >= 0 ? orow + o : T.n_rows) * 256;
+          mbar_expect_tx(bar(B_OFULL(rs)), 512u);
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 512, [%2];" ::"r"(
+                  sbase + LY::OROW + (uint32_t)rs * 512u),
+              "l"(src), "r"(bar(B_OFULL(rs)))
+              : "memory");
         }
       }
       if (!ok || !L.pool_ctr) break;
