@@ -59,6 +59,9 @@ cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const flo
                                const unsigned char *sure, const float *tau32, float margin2, RItem *R, unsigned *n_r,
                                cudaStream_t st, const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_collect64(RItem *R, unsigned n, long long *ids64, int *pos64, unsigned *n64, cudaStream_t st);
+cudaError_t apx_launch_split_scored(const QuerySlot *Q, unsigned n_max, float *f32, unsigned char *maybe,
+                                    unsigned char *sure, long long *ids_new, int *pos_new, unsigned *n_new, int n_sm,
+                                    cudaStream_t st);
 cudaError_t apx_launch_compact(QuerySlot *Q, const float *f32, const unsigned char *maybe, const unsigned char *sure,
                                const float *tau32, const int *ok, float margin2, float eps_f, unsigned *kept,
                                unsigned n_max, int n_sm, cudaStream_t st);
@@ -886,7 +889,7 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
   int64_t N = 0;
   apex_status s = apex_count_compounds(D->n_reactions, D->n_slots, D->slot_sizes, &N);
   if (s != APEX_OK) return s;
-  if (N >= (1LL << 62)) return fail(APEX_EINVAL, "library too large (ids must stay below 2^62)");
+  if (N >= (1LL << 61)) return fail(APEX_EINVAL, "library too large (ids must stay below 2^61)");
   for (int t = 0; t < D->n_reactions; ++t)
     if (D->n_slots[t] > APEX_MAX_SLOTS) return fail(APEX_EUNSUPPORTED, "reaction %d has more than %d slots", t, APEX_MAX_SLOTS);
   if (D->precisions & ~((1u << APEX_FP32) | (1u << APEX_BF16) | (1u << APEX_FP16) | (1u << APEX_FP8)))
@@ -1963,18 +1966,23 @@ static void finish(apex_library &L, QueryRec *q, QState st, apex_status err, con
 // One step of the circular pass: a launch over the next chunk of items needed by any active
 // query (per precision), then the conditional select of the served queries.
 // In-pass FP32 compaction of query q's candidate buffer (queued behind the select that follows an
-// enumeration launch; no host wait): FP32 rescore of the buffer's entries, their FP32 decisions
-// and the k-th FP32-sure objective, then the buffer keeps only what can still reach the top-k and
-// the admission threshold rises to the FP32-certified floor (k_compact_keep / k_compact_apply).
+// enumeration launch; no host wait): FP32 rescore of the entries appended since the last
+// compaction (the ones it kept already carry their FP32 objective), their FP32 decisions and the
+// k-th FP32-sure objective, then the buffer keeps only what can still reach the top-k and the
+// admission threshold rises to the FP32-certified floor (k_compact_keep / k_compact_apply).
 static void compact_query(apex_library &L, QueryRec *q) {
   const int no = L.n_out, m = (int)q->cidx.size();
   const unsigned cover = q->cap;
   const unsigned *d_n = &L.d_slots[q->slot].count;
-  L.arena_reserve(sizeof(float) * (size_t)cover * (no + 1) + 2 * (size_t)cover + 16 * (size_t)(m + 1) + 8 * 256);
+  L.arena_reserve(sizeof(float) * (size_t)cover * (no + 1) + 2 * (size_t)cover + 12 * (size_t)cover +
+                  16 * (size_t)(m + 1) + 10 * 256);
   float *out32 = (float *)L.aget(sizeof(float) * (size_t)cover * no);
   float *f32 = (float *)L.aget(sizeof(float) * cover);
   unsigned char *maybe = (unsigned char *)L.aget(cover);
   unsigned char *sure = (unsigned char *)L.aget(cover);
+  long long *ids_new = (long long *)L.aget(sizeof(long long) * cover);
+  int *pos_new = (int *)L.aget(sizeof(int) * cover);
+  unsigned *n_new = (unsigned *)L.aget(sizeof(unsigned));
   double *dlo = (double *)L.aget(sizeof(double) * std::max(m, 1));
   double *dhi = (double *)L.aget(sizeof(double) * std::max(m, 1));
   float *d_tau = (float *)L.aget(sizeof(float));
@@ -1984,16 +1992,18 @@ static void compact_query(apex_library &L, QueryRec *q) {
     L.upload(dlo, q->lo.data(), sizeof(double) * m);
     L.upload(dhi, q->hi.data(), sizeof(double) * m);
   }
+  CU(apx_launch_split_scored(L.d_slots + q->slot, cover, f32, maybe, sure, ids_new, pos_new, n_new, L.n_sm, L.st));
   LaunchPlan dummy;
   memset(&dummy, 0, sizeof(dummy));
-  CU(apx_launch_fp32(dummy, L.T_, nullptr, q->ids, cover, out32, grid_for(L, (cover + APX_TILE - 1) / APX_TILE), L.st,
-                     L.fp32_id_tile.load(), d_n));
+  CU(apx_launch_fp32(dummy, L.T_, nullptr, ids_new, cover, out32, grid_for(L, (cover + APX_TILE - 1) / APX_TILE), L.st,
+                     L.fp32_id_tile.load(), n_new));
   const double e32f = fp32_delta_f(L, q);
   EvalArgs ea{out32, no, L.d_slots + q->slot, L.d_err32f, (float)e32f, dlo, dhi};
   ea.eps_scale = (float)q->mscale;
   ea.pass_keys = q->keys;
   ea.obs = slot_obs(L, q->slot);
-  CU(apx_launch_eval32(ea, cover, f32, maybe, sure, L.st, d_n));
+  ea.pos = pos_new;
+  CU(apx_launch_eval32(ea, cover, f32, maybe, sure, L.st, n_new));
   CU(apx_launch_kth(f32, sure, cover, q->k, d_tau, d_ok, L.st, d_n));
   CU(apx_launch_compact(L.d_slots + q->slot, f32, maybe, sure, d_tau, d_ok, (float)(2.0 * e32f * 1.0001),
                         (float)(e32f * 1.0001), kept, cover, L.n_sm, L.st));

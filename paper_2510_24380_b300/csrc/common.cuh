@@ -110,7 +110,10 @@ struct SpecArgs {
 };
 
 #define APX_UNSURE_BIT (1LL << 62)
-#define APX_ID_MASK ((1LL << 62) - 1)
+// A candidate whose key is its FP32 objective and whose FP32 outputs lie inside the box widened by
+// the FP32 margin: an in-pass compaction kept it, and the next one reuses that rescore.
+#define APX_F32_BIT (1LL << 61)
+#define APX_ID_MASK ((1LL << 61) - 1)
 
 // Kernel status word values (device-side failures; never trap).
 #define APX_ERR_TIMEOUT 1
@@ -281,6 +284,8 @@ struct EvalArgs {
   const float *pass_keys;   // [n] pass objective of every candidate (nullptr: not checked)
   unsigned *obs;            // [1 + n_out] observed maxima as float bits: [0] max |pass key - FP32
                             // objective| (here), [1 + p] max |FP32 - FP64| of output p (k_apply64)
+  const int *pos = nullptr; // [n] buffer position of out32 row i (f32 / maybe / sure / pass_keys are
+                            // indexed by it); nullptr: row i is position i
 };
 
 // One member of the result set under exact selection.

@@ -236,10 +236,11 @@ __global__ void k_eval32(EvalArgs a, long long n, float *f32, unsigned char *may
       mb = mb && v >= mlo[c] && v <= mhi[c];
       sr = sr && v >= slo[c] && v <= shi[c];
     }
-    f32[i] = f;
-    maybe[i] = mb;
-    sure[i] = sr;
-    if (a.pass_keys) dmax = fmaxf(dmax, __fsub_ru(fmaxf(a.pass_keys[i], f), fminf(a.pass_keys[i], f)));
+    const long long t = a.pos ? (long long)a.pos[i] : i;
+    f32[t] = f;
+    maybe[t] = mb;
+    sure[t] = sr;
+    if (a.pass_keys) dmax = fmaxf(dmax, __fsub_ru(fmaxf(a.pass_keys[t], f), fminf(a.pass_keys[t], f)));
   }
   if (a.obs) {  // every thread of the block reaches this point
     for (int off = 16; off > 0; off >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
@@ -303,10 +304,37 @@ __global__ void k_build_r(long long n, const long long *cand_ids, const float *f
 // exact objective is >= B: a candidate can still be a member only if its FP32 objective is >=
 // B - eps_f = tau32 - 2 eps_f and its FP32 outputs lie in the box widened by eps, and a compound
 // of a later launch only if its pass objective is >= B - delta_f. The buffer keeps the first kind
-// (pass keys unchanged; an entry becomes "sure" when it is FP32-sure) and the admission threshold
-// rises to the second, so the buffer holds about k entries plus the FP32 band after every
-// compaction, whatever the width of the pass margin (Sec. 3.3 queue with the precision pattern's
-// FP32 rescore moved into the pass).
+// (the key becomes the FP32 objective, within eps_f < delta_f of the exact one, so the selects
+// between launches keep their guarantee; an entry becomes "sure" when it is FP32-sure) and the
+// admission threshold rises to the second, so the buffer holds about k entries plus the FP32 band
+// after every compaction, whatever the width of the pass margin (Sec. 3.3 queue with the precision
+// pattern's FP32 rescore moved into the pass).
+// Entries a previous compaction kept carry APX_F32_BIT: their key is already their FP32 objective
+// and they are inside the FP32-widened box (the FP32 rescore is deterministic), so only the
+// entries appended since are rescored (k_split_scored lists them).
+// Split step: entries with APX_F32_BIT get f32 = key, maybe = 1, sure = no APX_UNSURE_BIT; the
+// others are listed (id, buffer position) for the FP32 rescore, their count -> *n_new.
+__global__ void k_split_scored(const QuerySlot *Q, unsigned n_max, float *f32, unsigned char *maybe,
+                               unsigned char *sure, long long *ids_new, int *pos_new, unsigned *n_new) {
+  const unsigned n = min(Q->count, min(Q->cap, n_max));
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned b = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < n; b += stride) {
+    const unsigned i = b + (threadIdx.x & 31);
+    const long long id = i < n ? Q->ids[i] : 0;
+    const bool scored = (i < n) && (id & APX_F32_BIT);
+    const bool fresh = (i < n) && !(id & APX_F32_BIT);
+    if (scored) {
+      f32[i] = Q->keys[i];
+      maybe[i] = 1;
+      sure[i] = (id & APX_UNSURE_BIT) ? 0 : 1;
+    }
+    const unsigned p = apx_warp_reserve(n_new, fresh);
+    if (fresh) {
+      ids_new[p] = id;
+      pos_new[p] = (int)i;
+    }
+  }
+}
 // Keep step: surviving entries -> keys2/ids2 (order not kept), their count -> *kept.
 __global__ void k_compact_keep(QuerySlot *Q, const float *f32, const unsigned char *maybe, const unsigned char *sure,
                                const float *tau32, const int *ok, float margin2, unsigned *kept, unsigned n_max) {
@@ -320,8 +348,8 @@ __global__ void k_compact_keep(QuerySlot *Q, const float *f32, const unsigned ch
     const unsigned p = apx_warp_reserve(kept, take);
     if (take) {
       const long long id = Q->ids[i];
-      Q->keys2[p] = Q->keys[i];
-      Q->ids2[p] = sure[i] ? (id & APX_ID_MASK) : id;
+      Q->keys2[p] = f32[i];
+      Q->ids2[p] = (sure[i] ? (id & ~APX_UNSURE_BIT) : id) | APX_F32_BIT;
     }
   }
 }
@@ -667,6 +695,16 @@ cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const flo
 }
 // n_max: entries the scratch arrays (f32, maybe, sure) cover; the slot's count decides how many
 // are used. kept: a device counter, zeroed here.
+cudaError_t apx_launch_split_scored(const QuerySlot *Q, unsigned n_max, float *f32, unsigned char *maybe,
+                                    unsigned char *sure, long long *ids_new, int *pos_new, unsigned *n_new, int n_sm,
+                                    cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(n_new, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = std::max(1u, std::min<unsigned>((n_max + 255) / 256, (unsigned)n_sm * 4u));
+  apx_count_launch();
+  k_split_scored<<<grid, 256, 0, st>>>(Q, n_max, f32, maybe, sure, ids_new, pos_new, n_new);
+  return cudaGetLastError();
+}
 cudaError_t apx_launch_compact(QuerySlot *Q, const float *f32, const unsigned char *maybe, const unsigned char *sure,
                                const float *tau32, const int *ok, float margin2, float eps_f, unsigned *kept,
                                unsigned n_max, int n_sm, cudaStream_t st) {
