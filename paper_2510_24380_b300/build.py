@@ -38,7 +38,9 @@ def _inputs():
 def source_hash() -> str:
     """sha256 over the names and contents of every input and the compile and link flags."""
     h = hashlib.sha256()
-    h.update(" ".join(ARCH + FLAGS).encode())
+    # the include directory by its path inside the tree, so that a copy of the tree elsewhere (the
+    # same sources) keeps its stamp
+    h.update(" ".join(ARCH + [os.path.relpath(f, ROOT) if os.path.isabs(f) else f for f in FLAGS]).encode())
     for f in _inputs():
         h.update(os.path.relpath(f, ROOT).encode())
         with open(f, "rb") as fh:
