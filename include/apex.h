@@ -54,9 +54,11 @@ typedef int32_t apex_status;
  * calibrated margins are tighter. FP8: layer 2 with e4m3 operands (activations quantized from
  * FP16, W_2 quantized per output channel with scale max|row| / 448, FP32 accumulators multiplied
  * back by the scales), layer 3 in FP16; twice the dense tensor rate on layer 2, much wider
- * margins (three mantissa bits). The candidates are
- * then rescored in FP32 and the top-k boundary band in FP64, so the returned set equals the FP64
- * top-k when the calibrated error bounds hold. APEX_FP64 is accepted by apex_score_ids only. */
+ * margins (three mantissa bits). Between the launches of a pass, a query whose candidate buffer
+ * fills up has it rescored (FP16 on the tensor cores for BF16 and FP8 passes, else FP32) and cut
+ * to what can still reach the top-k. At the end of the pass the candidates are rescored in FP32
+ * and the top-k boundary band in FP64, so the returned set equals the FP64 top-k when the
+ * calibrated error bounds hold. APEX_FP64 is accepted by apex_score_ids only. */
 #define APEX_FP32 0
 #define APEX_BF16 1
 #define APEX_FP64 2
@@ -90,7 +92,9 @@ typedef struct {
   int32_t n_objectives;         /* outputs [0, n_objectives) may carry objective weight */
   int32_t n_properties;         /* n_objectives + n_properties == dims[n_layers] */
   uint32_t precisions;          /* bits (1 << APEX_BF16), (1 << APEX_FP16), (1 << APEX_FP8) build the
-                                   tensor-core tables (FP8 also builds the FP16 ones); FP32 always */
+                                   tensor-core tables (BF16 and FP8 also build the FP16 ones: FP8
+                                   reads them, and both rescore candidates in FP16 between the
+                                   launches of a pass); FP32 always */
   uint64_t device_mem_budget;   /* bytes the library may hold on the device; 0 = unlimited */
   void *cuda_stream;            /* cudaStream_t to run on; NULL = the library creates one */
   int32_t device;               /* CUDA device ordinal */

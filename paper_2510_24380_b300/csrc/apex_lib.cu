@@ -47,7 +47,7 @@ cudaError_t apx_launch_slot_extremes(const float *P, const long long *row_first,
 cudaError_t apx_launch_image_e4m3(const float *W, const float *scale, int rows_used, int rows, void *img,
                                   cudaStream_t st);
 cudaError_t apx_launch_tc_ids(const DevTables &T, const long long *ids, long long n, float *out, int *err, int n_sm,
-                              cudaStream_t st, int fmt, QuerySlot *slots, int spec_slot);
+                              cudaStream_t st, int fmt, QuerySlot *slots, int spec_slot, const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_tc(const LaunchPlan &L, const DevTables &T, QuerySlot *slots, int *err, int grid,
                           cudaStream_t st, int fmt);
 cudaError_t apx_launch_slot_select(QuerySlot *slots, const int *slot_list, int n_slots, int mode, cudaStream_t st);
@@ -249,6 +249,7 @@ struct apex_library {
   int n_calib = 0;
   double a1_amax = 0;         // FP8: exact max |a_1| over the library (its static activation scale)
   float *d_err32f = nullptr;  // per-output FP32 margin (float) for eval32
+  float *d_err16f = nullptr;  // per-output FP16 pass margin (float): FP16 in-pass compactions
   uint64_t seed = 0;
   // engine
   std::thread worker;
@@ -753,6 +754,12 @@ static void upload_err32(apex_library &L) {
   float e32[APEX_MAX_OUTPUTS] = {0};
   for (int p = 0; p < L.n_out; ++p) e32[p] = (float)L.err32[p];
   CU(cudaMemcpy(L.d_err32f, e32, sizeof(e32), cudaMemcpyHostToDevice));
+  if (L.tc_fmt[1]) {  // rounded up: the FP32 test of an FP16 rescore must not be tighter than its margin
+    L.d_err16f = (float *)L.dalloc(sizeof(float) * APEX_MAX_OUTPUTS);
+    float e16[APEX_MAX_OUTPUTS] = {0};
+    for (int p = 0; p < L.n_out; ++p) e16[p] = std::nextafter((float)L.err16[1][p], INFINITY);
+    CU(cudaMemcpy(L.d_err16f, e16, sizeof(e16), cudaMemcpyHostToDevice));
+  }
 }
 
 // Margins saved with a library file (apex_save_library), restored instead of recalibrating.
@@ -896,7 +903,9 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
     return fail(APEX_EINVAL, "precisions: only the FP32, BF16, FP16 and FP8 bits are defined");
   const bool want_bf16 = (D->precisions >> APEX_BF16) & 1u;
   const bool want_fp8 = (D->precisions >> APEX_FP8) & 1u;
-  const bool want_fp16 = ((D->precisions >> APEX_FP16) & 1u) || want_fp8;  // the FP8 pass reads the FP16 table
+  // the FP8 pass reads the FP16 table; BF16 and FP8 passes rescore their candidates in FP16 between
+  // launches (in-pass compactions)
+  const bool want_fp16 = ((D->precisions >> APEX_FP16) & 1u) || want_fp8 || want_bf16;
   const bool tc_shape = D->n_layers == 3 && D->dims[1] == 256 && D->dims[2] == 256 && D->dims[3] <= 16;
   if ((want_bf16 || want_fp16) && !tc_shape)
     return fail(APEX_EUNSUPPORTED, "the tensor-core path needs a d -> 256 -> 256 -> <=16 head");
@@ -1475,6 +1484,20 @@ static double fp32_delta_f(const apex_library &L, const QueryRec *q) {
   for (int j = 0; j < L.n_obj; ++j) e += std::fabs((double)q->w[j]) * L.err32[j];
   return e * q->mscale;
 }
+// In-pass compactions of a BF16 or FP8 pass rescore in FP16 on the tensor cores (the id-list form
+// of the enumeration kernel): its margins are about a tenth of BF16's and it scores a candidate
+// ~30x faster than the FP32 SIMT kernel; the end-of-pass rescore stays FP32. Other passes (and
+// libraries without the FP16 tables) compact in FP32.
+static bool compact_fp16(const apex_library &L, const QueryRec *q) {
+  return L.tc_fmt[1] && L.d_err16f && (q->precision == APEX_BF16 || q->precision == APEX_FP8);
+}
+// objective margin of the compaction rescore for this query
+static double compact_delta_f(const apex_library &L, const QueryRec *q) {
+  if (!compact_fp16(L, q)) return fp32_delta_f(L, q);
+  double e = 0;
+  for (int j = 0; j < L.n_obj; ++j) e += std::fabs((double)q->w[j]) * L.err16[1][j];
+  return e * q->mscale;
+}
 
 static void start_query(apex_library &L, QueryRec *q) {
   tmark(L, 0);
@@ -1683,6 +1706,13 @@ static void fin_queue(apex_library &L, QueryRec *q, FinChain &C, unsigned cover)
   ea.eps_scale = (float)q->mscale;
   ea.pass_keys = q->keys;  // compacted with the ids by the slot's last select
   ea.obs = C.d_obs;
+  // keys an in-pass compaction rescored are held to that rescore's margin: scaled up by pass
+  // margin / compaction margin, their |key - FP32| counts in the same observed ratio
+  ea.ids = q->ids;
+  {
+    const double ec = compact_delta_f(L, q), ep = pass_delta_f(L, q);
+    ea.scored_scale = ec > 0 && ep > ec ? (float)(ep / ec) : 1.f;
+  }
   CU(apx_launch_eval32(ea, cover, f32, maybe, sure, L.st, d_n));
   C.d_tau = (float *)L.aget(sizeof(float));
   int *d_ok = (int *)L.aget(sizeof(int));
@@ -1993,12 +2023,17 @@ static void compact_query(apex_library &L, QueryRec *q) {
     L.upload(dhi, q->hi.data(), sizeof(double) * m);
   }
   CU(apx_launch_split_scored(L.d_slots + q->slot, cover, f32, maybe, sure, ids_new, pos_new, n_new, L.n_sm, L.st));
-  LaunchPlan dummy;
-  memset(&dummy, 0, sizeof(dummy));
-  CU(apx_launch_fp32(dummy, L.T_, nullptr, ids_new, cover, out32, grid_for(L, (cover + APX_TILE - 1) / APX_TILE), L.st,
-                     L.fp32_id_tile.load(), n_new));
-  const double e32f = fp32_delta_f(L, q);
-  EvalArgs ea{out32, no, L.d_slots + q->slot, L.d_err32f, (float)e32f, dlo, dhi};
+  const bool f16 = compact_fp16(L, q);
+  if (f16) {
+    CU(apx_launch_tc_ids(L.T_, ids_new, cover, out32, L.d_err, L.n_sm, L.st, 1, nullptr, -1, n_new));
+  } else {
+    LaunchPlan dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    CU(apx_launch_fp32(dummy, L.T_, nullptr, ids_new, cover, out32, grid_for(L, (cover + APX_TILE - 1) / APX_TILE),
+                       L.st, L.fp32_id_tile.load(), n_new));
+  }
+  const double e32f = compact_delta_f(L, q);  // the rescore's objective margin
+  EvalArgs ea{out32, no, L.d_slots + q->slot, f16 ? L.d_err16f : L.d_err32f, (float)e32f, dlo, dhi};
   ea.eps_scale = (float)q->mscale;
   ea.pass_keys = q->keys;
   ea.obs = slot_obs(L, q->slot);

@@ -58,6 +58,8 @@ struct LaunchPlan {
   long long *dump_ids;                       // mode 2: [dump_n], row r of launch tile t at t * 128 + r,
                                              // -1 = padding row; mode 3: the input ids [dump_n]
   long long dump_base, dump_n;
+  const unsigned *dump_n_dev;                // mode 3, optional: the list's length on the device
+                                             // (at most dump_n; the launch is sized for dump_n)
   // tensor-core kernel, tail pool: tiles [pool_first, total_tiles) are not in any CTA's range; a CTA
   // done with its own range claims them pool_chunk at a time (atomicAdd on *pool_ctr, zeroed before
   // the launch). pool_ctr == nullptr: no pool, the CTA ranges cover every tile.
@@ -110,9 +112,10 @@ struct SpecArgs {
 };
 
 #define APX_UNSURE_BIT (1LL << 62)
-// A candidate whose key is its FP32 objective and whose FP32 outputs lie inside the box widened by
-// the FP32 margin: an in-pass compaction kept it, and the next one reuses that rescore.
-#define APX_F32_BIT (1LL << 61)
+// A candidate an in-pass compaction kept: its key is the compaction's rescore of its objective (FP16
+// on the tensor cores or FP32) and those outputs lie inside the box widened by that rescore's
+// margin; the next compaction reuses it.
+#define APX_SCORED_BIT (1LL << 61)
 #define APX_ID_MASK ((1LL << 61) - 1)
 
 // Kernel status word values (device-side failures; never trap).
@@ -286,6 +289,8 @@ struct EvalArgs {
                             // objective| (here), [1 + p] max |FP32 - FP64| of output p (k_apply64)
   const int *pos = nullptr; // [n] buffer position of out32 row i (f32 / maybe / sure / pass_keys are
                             // indexed by it); nullptr: row i is position i
+  const long long *ids = nullptr;  // candidate ids: an entry with APX_SCORED_BIT has its |key - FP32|
+  float scored_scale = 1.f;        // multiplied by this (pass margin / compaction margin) in obs[0]
 };
 
 // One member of the result set under exact selection.

@@ -240,7 +240,11 @@ __global__ void k_eval32(EvalArgs a, long long n, float *f32, unsigned char *may
     f32[t] = f;
     maybe[t] = mb;
     sure[t] = sr;
-    if (a.pass_keys) dmax = fmaxf(dmax, __fsub_ru(fmaxf(a.pass_keys[t], f), fminf(a.pass_keys[t], f)));
+    if (a.pass_keys) {
+      float d = __fsub_ru(fmaxf(a.pass_keys[t], f), fminf(a.pass_keys[t], f));
+      if (a.ids && (a.ids[t] & APX_SCORED_BIT)) d = __fmul_ru(d, a.scored_scale);  // against its own margin
+      dmax = fmaxf(dmax, d);
+    }
   }
   if (a.obs) {  // every thread of the block reaches this point
     for (int off = 16; off > 0; off >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
@@ -304,15 +308,18 @@ __global__ void k_build_r(long long n, const long long *cand_ids, const float *f
 // exact objective is >= B: a candidate can still be a member only if its FP32 objective is >=
 // B - eps_f = tau32 - 2 eps_f and its FP32 outputs lie in the box widened by eps, and a compound
 // of a later launch only if its pass objective is >= B - delta_f. The buffer keeps the first kind
-// (the key becomes the FP32 objective, within eps_f < delta_f of the exact one, so the selects
-// between launches keep their guarantee; an entry becomes "sure" when it is FP32-sure) and the
+// (the key becomes the rescored objective, within eps_f <= delta_f of the exact one, so the selects
+// between launches keep their guarantee; an entry becomes "sure" when the rescore finds it sure) and the
 // admission threshold rises to the second, so the buffer holds about k entries plus the FP32 band
 // after every compaction, whatever the width of the pass margin (Sec. 3.3 queue with the precision
 // pattern's FP32 rescore moved into the pass).
-// Entries a previous compaction kept carry APX_F32_BIT: their key is already their FP32 objective
-// and they are inside the FP32-widened box (the FP32 rescore is deterministic), so only the
-// entries appended since are rescored (k_split_scored lists them).
-// Split step: entries with APX_F32_BIT get f32 = key, maybe = 1, sure = no APX_UNSURE_BIT; the
+// The rescore is FP32 (SIMT) or, when the library has its FP16 tables and the pass is BF16 or FP8,
+// FP16 on the tensor cores; eps and eps_f above are then that format's margins (the argument holds
+// for any rescore whose margin is below the pass's). Entries a previous compaction kept carry
+// APX_SCORED_BIT: their key is already their rescored objective and they are inside the widened
+// box (both rescores are deterministic), so only the entries appended since are rescored
+// (k_split_scored lists them).
+// Split step: entries with APX_SCORED_BIT get f32 = key, maybe = 1, sure = no APX_UNSURE_BIT; the
 // others are listed (id, buffer position) for the FP32 rescore, their count -> *n_new.
 __global__ void k_split_scored(const QuerySlot *Q, unsigned n_max, float *f32, unsigned char *maybe,
                                unsigned char *sure, long long *ids_new, int *pos_new, unsigned *n_new) {
@@ -321,8 +328,8 @@ __global__ void k_split_scored(const QuerySlot *Q, unsigned n_max, float *f32, u
   for (unsigned b = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); b < n; b += stride) {
     const unsigned i = b + (threadIdx.x & 31);
     const long long id = i < n ? Q->ids[i] : 0;
-    const bool scored = (i < n) && (id & APX_F32_BIT);
-    const bool fresh = (i < n) && !(id & APX_F32_BIT);
+    const bool scored = (i < n) && (id & APX_SCORED_BIT);
+    const bool fresh = (i < n) && !(id & APX_SCORED_BIT);
     if (scored) {
       f32[i] = Q->keys[i];
       maybe[i] = 1;
@@ -349,7 +356,7 @@ __global__ void k_compact_keep(QuerySlot *Q, const float *f32, const unsigned ch
     if (take) {
       const long long id = Q->ids[i];
       Q->keys2[p] = f32[i];
-      Q->ids2[p] = (sure[i] ? (id & ~APX_UNSURE_BIT) : id) | APX_F32_BIT;
+      Q->ids2[p] = (sure[i] ? (id & ~APX_UNSURE_BIT) : id) | APX_SCORED_BIT;
     }
   }
 }

@@ -501,15 +501,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   auto bar = [&](int i) { return sbase + LY::BAR + 8u * (uint32_t)i; };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // id lists: the list's length (read from the device when the launch gives it there) and its tiles
+  const long long n_ids = IDS ? (L.dump_n_dev ? min(L.dump_n, (long long)*L.dump_n_dev) : L.dump_n) : 0;
+  const long long launch_tiles = IDS ? (n_ids + APX_TILE - 1) / APX_TILE : L.total_tiles;
   // this CTA's share of the launch: tiles [t_begin, t_end), from the launch plan's cost-weighted
   // ranges when it has them (a tile that starts a run of tiles costs more), else equal counts;
   // walked by every role in the same order of runs
-#define TC_CTA_END()                                                        \
-  (L.cta_n == (int)gridDim.x ? L.cta_first[blockIdx.x + 1]                  \
-                             : (long long)(blockIdx.x + 1) * L.total_tiles / gridDim.x)
   const long long t_begin = L.cta_n == (int)gridDim.x ? L.cta_first[blockIdx.x]
-                                                      : (long long)blockIdx.x * L.total_tiles / gridDim.x;
-  const long long t_end = TC_CTA_END();
+                                                      : (long long)blockIdx.x * launch_tiles / gridDim.x;
+  const long long t_end = L.cta_n == (int)gridDim.x ? L.cta_first[blockIdx.x + 1]
+                                                    : (long long)(blockIdx.x + 1) * launch_tiles / gridDim.x;
   // Tail pool (L.pool_ctr != nullptr): after its own range a CTA takes chunks of the tiles past every
   // CTA's range, claimed by the loader warp and passed to the other roles through a 4-entry ring of
   // ranges in shared memory (a = -1: no more). Every role walks the same sequence of ranges.
@@ -674,7 +675,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if constexpr (IDS) {  // every slot of the listed compound; each tile is its own run
             left = 1;
             const long long i = tile * APX_TILE + m;
-            row_ok = i < L.dump_n;
+            row_ok = i < n_ids;
             const long long id = row_ok ? (L.dump_ids[i] & APX_ID_MASK) : 0;
             int lo = 0, hi = T.n_rx - 1;
             while (lo < hi) {
@@ -998,7 +999,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(bar(B_D2EMPTY(buf)));
         const long long i = (t_begin + j) * APX_TILE + r;
-        if (i < L.dump_n) {
+        if (i < n_ids) {
           if (L.dump_base >= 0) {  // start-threshold sample of query slot dump_base: its key
             const QuerySlot *Q = slots + L.dump_base;
             const int n_obj = Q->n_obj;
@@ -1164,7 +1165,7 @@ static cudaError_t tc_launch_ids_fmt(const LaunchPlan &L, const DevTables &T, Qu
 // the kernel applies that query slot's exact boxes and objective instead and writes one key per
 // compound into out (as unsigned: order-preserving objective bits, 0 = infeasible).
 cudaError_t apx_launch_tc_ids(const DevTables &T, const long long *ids, long long n, float *out, int *err, int n_sm,
-                              cudaStream_t st, int fmt, QuerySlot *slots, int spec_slot) {
+                              cudaStream_t st, int fmt, QuerySlot *slots, int spec_slot, const unsigned *n_dev) {
   if (n <= 0) return cudaSuccess;
   LaunchPlan L;
   memset(&L, 0, sizeof(L));
@@ -1173,6 +1174,7 @@ cudaError_t apx_launch_tc_ids(const DevTables &T, const long long *ids, long lon
   L.dump = out;
   L.dump_ids = const_cast<long long *>(ids);
   L.dump_n = n;
+  L.dump_n_dev = n_dev;
   L.dump_base = spec_slot >= 0 && slots ? spec_slot : -1;
   const int grid = (int)std::min<long long>(L.total_tiles, n_sm);
   if (fmt == 0) return tc_launch_ids_fmt<0>(L, T, slots, err, grid, st);
