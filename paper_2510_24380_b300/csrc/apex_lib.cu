@@ -55,6 +55,7 @@ cudaError_t apx_launch_eval32(const EvalArgs &a, long long n, float *f32, unsign
                               cudaStream_t st, const unsigned *n_dev = nullptr);
 cudaError_t apx_launch_kth(const float *keys, const unsigned char *flag, long long n, long long k, float *out_tau,
                            int *out_ok, cudaStream_t st, const unsigned *n_dev = nullptr);
+cudaError_t apx_launch_kth_multi(const KthJob *jobs, int n_jobs, cudaStream_t st);
 cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
                                const unsigned char *sure, const float *tau32, float margin2, RItem *R, unsigned *n_r,
                                cudaStream_t st, const unsigned *n_dev = nullptr);
@@ -1993,65 +1994,117 @@ static void finish(apex_library &L, QueryRec *q, QState st, apex_status err, con
   L.done_seq++;
 }
 
-// One step of the circular pass: a launch over the next chunk of items needed by any active
-// query (per precision), then the conditional select of the served queries.
-// In-pass FP32 compaction of query q's candidate buffer (queued behind the select that follows an
-// enumeration launch; no host wait): FP32 rescore of the entries appended since the last
-// compaction (the ones it kept already carry their FP32 objective), their FP32 decisions and the
-// k-th FP32-sure objective, then the buffer keeps only what can still reach the top-k and the
-// admission threshold rises to the FP32-certified floor (k_compact_keep / k_compact_apply).
-static void compact_query(apex_library &L, QueryRec *q) {
-  const int no = L.n_out, m = (int)q->cidx.size();
-  const unsigned cover = q->cap;
-  const unsigned *d_n = &L.d_slots[q->slot].count;
-  L.arena_reserve(sizeof(float) * (size_t)cover * (no + 1) + 2 * (size_t)cover + 12 * (size_t)cover +
-                  16 * (size_t)(m + 1) + 10 * 256);
-  float *out32 = (float *)L.aget(sizeof(float) * (size_t)cover * no);
-  float *f32 = (float *)L.aget(sizeof(float) * cover);
-  unsigned char *maybe = (unsigned char *)L.aget(cover);
-  unsigned char *sure = (unsigned char *)L.aget(cover);
-  long long *ids_new = (long long *)L.aget(sizeof(long long) * cover);
-  int *pos_new = (int *)L.aget(sizeof(int) * cover);
-  unsigned *n_new = (unsigned *)L.aget(sizeof(unsigned));
-  double *dlo = (double *)L.aget(sizeof(double) * std::max(m, 1));
-  double *dhi = (double *)L.aget(sizeof(double) * std::max(m, 1));
-  float *d_tau = (float *)L.aget(sizeof(float));
-  int *d_ok = (int *)L.aget(sizeof(int));
-  unsigned *kept = (unsigned *)L.aget(sizeof(unsigned));
-  if (m > 0) {
-    L.upload(dlo, q->lo.data(), sizeof(double) * m);
-    L.upload(dhi, q->hi.data(), sizeof(double) * m);
+// Scratch of one compaction of query q (256-byte roundings in the slack).
+static size_t compact_bytes(const apex_library &L, const QueryRec *q) {
+  const size_t cover = q->cap, no = L.n_out, m = q->cidx.size();
+  return sizeof(float) * cover * (no + 1) + 2 * cover + 12 * cover + 16 * (m + 1) + 10 * 256;
+}
+// The compactions of queries qs (every one's scratch in the arena at once): per query the split,
+// the rescore and the decisions; one launch selects every query's threshold (a CTA each); then
+// per query the keep and apply steps.
+static void compact_group(apex_library &L, const std::vector<QueryRec *> &qs) {
+  const int no = L.n_out;
+  size_t need = sizeof(KthJob) * qs.size() + 256;
+  for (QueryRec *q : qs) need += compact_bytes(L, q);
+  L.arena_reserve(need);
+  struct Tail {
+    float *f32;
+    unsigned char *maybe, *sure;
+    float *d_tau;
+    int *d_ok;
+    unsigned *kept;
+    double ecf;
+  };
+  std::vector<Tail> tails(qs.size());
+  std::vector<KthJob> jobs(qs.size());
+  for (size_t i = 0; i < qs.size(); ++i) {
+    QueryRec *q = qs[i];
+    const int m = (int)q->cidx.size();
+    const unsigned cover = q->cap;
+    float *out32 = (float *)L.aget(sizeof(float) * (size_t)cover * no);
+    float *f32 = (float *)L.aget(sizeof(float) * cover);
+    unsigned char *maybe = (unsigned char *)L.aget(cover);
+    unsigned char *sure = (unsigned char *)L.aget(cover);
+    long long *ids_new = (long long *)L.aget(sizeof(long long) * cover);
+    int *pos_new = (int *)L.aget(sizeof(int) * cover);
+    unsigned *n_new = (unsigned *)L.aget(sizeof(unsigned));
+    double *dlo = (double *)L.aget(sizeof(double) * std::max(m, 1));
+    double *dhi = (double *)L.aget(sizeof(double) * std::max(m, 1));
+    float *d_tau = (float *)L.aget(sizeof(float));
+    int *d_ok = (int *)L.aget(sizeof(int));
+    unsigned *kept = (unsigned *)L.aget(sizeof(unsigned));
+    if (m > 0) {
+      L.upload(dlo, q->lo.data(), sizeof(double) * m);
+      L.upload(dhi, q->hi.data(), sizeof(double) * m);
+    }
+    CU(apx_launch_split_scored(L.d_slots + q->slot, cover, f32, maybe, sure, ids_new, pos_new, n_new, L.n_sm, L.st));
+    const bool f16 = compact_fp16(L, q);
+    if (f16) {
+      CU(apx_launch_tc_ids(L.T_, ids_new, cover, out32, L.d_err, L.n_sm, L.st, 1, nullptr, -1, n_new));
+    } else {
+      LaunchPlan dummy;
+      memset(&dummy, 0, sizeof(dummy));
+      CU(apx_launch_fp32(dummy, L.T_, nullptr, ids_new, cover, out32, grid_for(L, (cover + APX_TILE - 1) / APX_TILE),
+                         L.st, L.fp32_id_tile.load(), n_new));
+    }
+    const double ecf = compact_delta_f(L, q);  // the rescore's objective margin
+    EvalArgs ea{out32, no, L.d_slots + q->slot, f16 ? L.d_err16f : L.d_err32f, (float)ecf, dlo, dhi};
+    ea.eps_scale = (float)q->mscale;
+    ea.pass_keys = q->keys;
+    ea.obs = slot_obs(L, q->slot);
+    ea.pos = pos_new;
+    CU(apx_launch_eval32(ea, cover, f32, maybe, sure, L.st, n_new));
+    jobs[i] = KthJob{f32, sure, (long long)cover, q->k, d_tau, d_ok, &L.d_slots[q->slot].count};
+    tails[i] = Tail{f32, maybe, sure, d_tau, d_ok, kept, ecf};
   }
-  CU(apx_launch_split_scored(L.d_slots + q->slot, cover, f32, maybe, sure, ids_new, pos_new, n_new, L.n_sm, L.st));
-  const bool f16 = compact_fp16(L, q);
-  if (f16) {
-    CU(apx_launch_tc_ids(L.T_, ids_new, cover, out32, L.d_err, L.n_sm, L.st, 1, nullptr, -1, n_new));
-  } else {
-    LaunchPlan dummy;
-    memset(&dummy, 0, sizeof(dummy));
-    CU(apx_launch_fp32(dummy, L.T_, nullptr, ids_new, cover, out32, grid_for(L, (cover + APX_TILE - 1) / APX_TILE),
-                       L.st, L.fp32_id_tile.load(), n_new));
+  KthJob *d_jobs = (KthJob *)L.aget(sizeof(KthJob) * qs.size());
+  L.upload(d_jobs, jobs.data(), sizeof(KthJob) * qs.size());
+  CU(apx_launch_kth_multi(d_jobs, (int)qs.size(), L.st));
+  for (size_t i = 0; i < qs.size(); ++i) {
+    QueryRec *q = qs[i];
+    const Tail &t = tails[i];
+    CU(apx_launch_compact(L.d_slots + q->slot, t.f32, t.maybe, t.sure, t.d_tau, t.d_ok, (float)(2.0 * t.ecf * 1.0001),
+                          (float)(t.ecf * 1.0001), t.kept, q->cap, L.n_sm, L.st));
+    q->want_compact = false;
+    q->stats.n_compactions++;
   }
-  const double e32f = compact_delta_f(L, q);  // the rescore's objective margin
-  EvalArgs ea{out32, no, L.d_slots + q->slot, f16 ? L.d_err16f : L.d_err32f, (float)e32f, dlo, dhi};
-  ea.eps_scale = (float)q->mscale;
-  ea.pass_keys = q->keys;
-  ea.obs = slot_obs(L, q->slot);
-  ea.pos = pos_new;
-  CU(apx_launch_eval32(ea, cover, f32, maybe, sure, L.st, n_new));
-  CU(apx_launch_kth(f32, sure, cover, q->k, d_tau, d_ok, L.st, d_n));
-  CU(apx_launch_compact(L.d_slots + q->slot, f32, maybe, sure, d_tau, d_ok, (float)(2.0 * e32f * 1.0001),
-                        (float)(e32f * 1.0001), kept, cover, L.n_sm, L.st));
-  q->want_compact = false;
-  q->stats.n_compactions++;
+}
+// In-pass compaction of the candidate buffers of queries qs (queued behind the select that
+// follows an enumeration launch; no host wait): the rescore (FP16 on the tensor cores or FP32) of
+// the entries appended since each query's last compaction (the ones it kept already carry their
+// rescored objective), their decisions and the k-th sure objective, then each buffer keeps only
+// what can still reach the top-k and its admission threshold rises to the certified floor
+// (k_compact_keep / k_compact_apply). Queries are grouped so that a group's scratch fits the
+// arena limit (8 GB, and the device budget when there is one).
+static void compact_queries(apex_library &L, const std::vector<QueryRec *> &qs) {
+  const size_t cap = L.budget ? std::min<size_t>(8ull << 30, std::max<size_t>(L.arena_cap, 64ull << 20)) : (8ull << 30);
+  std::vector<QueryRec *> group;
+  size_t bytes = 0;
+  for (QueryRec *q : qs) {
+    const size_t b = compact_bytes(L, q) + sizeof(KthJob) + 256;
+    if (!group.empty() && bytes + b > cap) {
+      compact_group(L, group);
+      group.clear();
+      bytes = 0;
+    }
+    group.push_back(q);
+    bytes += b;
+  }
+  if (!group.empty()) compact_group(L, group);
 }
 
+// One step of the circular pass: a launch over the next chunk of items needed by any active
+// query (per precision), then the conditional select of the served queries.
 static void pass_step(apex_library &L) {
   const double t_p0 = trace_on() ? now_ms() : 0.0;
   // compactions wanted by the launch retired last: queued before this step's launch, so they run
   // right behind the select of the launch still in flight (one launch of lag)
-  for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
-    if (L.active[s] && L.active[s]->want_compact && L.active[s]->remaining > 0) compact_query(L, L.active[s]);
+  {
+    std::vector<QueryRec *> cq;
+    for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+      if (L.active[s] && L.active[s]->want_compact && L.active[s]->remaining > 0) cq.push_back(L.active[s]);
+    if (!cq.empty()) compact_queries(L, cq);
+  }
   // a linear head costs ~100x less per compound than the MLP: larger launches. A query's first
   // launches are small and grow 4x per launch (2^24, 2^26, ...): its admission threshold is only
   // a sampled guess until the select after a launch raises it, and a large first launch at a loose

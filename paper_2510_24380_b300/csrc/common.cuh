@@ -293,6 +293,17 @@ struct EvalArgs {
   float scored_scale = 1.f;        // multiplied by this (pass margin / compaction margin) in obs[0]
 };
 
+// One selection of k_kth_multi: out_tau = the k-th largest key among flagged entries of [0, n)
+// (n clamped to *n_dev when given), -inf with out_ok = 0 when fewer than k are flagged.
+struct KthJob {
+  const float *keys;
+  const unsigned char *flag;
+  long long n, k;
+  float *out_tau;
+  int *out_ok;
+  const unsigned *n_dev;
+};
+
 // One member of the result set under exact selection.
 struct RItem {
   double s;          // best score so far (FP32 rescore, or FP64 once rescored)

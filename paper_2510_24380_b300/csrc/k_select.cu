@@ -253,8 +253,8 @@ __global__ void k_eval32(EvalArgs a, long long n, float *f32, unsigned char *may
 }
 
 // tau32 = k-th largest f32 among sure entries (one CTA)
-__global__ void __launch_bounds__(SEL_THREADS) k_kth(const float *keys, const unsigned char *flag, long long n, long long k,
-                                                     float *out_tau, int *out_ok, const unsigned *n_dev) {
+__device__ __forceinline__ void kth_block(const float *keys, const unsigned char *flag, long long n, long long k,
+                                          float *out_tau, int *out_ok, const unsigned *n_dev) {
   extern __shared__ unsigned sel_bits[];
   if (n_dev && (long long)*n_dev < n) n = *n_dev;
   unsigned bits;
@@ -270,6 +270,16 @@ __global__ void __launch_bounds__(SEL_THREADS) k_kth(const float *keys, const un
     *out_tau = ok ? apx_bits_key(bits) : -INFINITY;
     *out_ok = ok;
   }
+}
+__global__ void __launch_bounds__(SEL_THREADS) k_kth(const float *keys, const unsigned char *flag, long long n, long long k,
+                                                     float *out_tau, int *out_ok, const unsigned *n_dev) {
+  kth_block(keys, flag, n, k, out_tau, out_ok, n_dev);
+}
+// several independent selections, one CTA each (the in-pass compactions queued at one launch
+// boundary: their selects run side by side instead of one after another)
+__global__ void __launch_bounds__(SEL_THREADS) k_kth_multi(const KthJob *jobs) {
+  const KthJob J = jobs[blockIdx.x];
+  kth_block(J.keys, J.flag, J.n, J.k, J.out_tau, J.out_ok, J.n_dev);
 }
 
 // ------------------------------------------------------------------ result set R
@@ -689,6 +699,19 @@ cudaError_t apx_launch_kth(const float *keys, const unsigned char *flag, long lo
   }
   apx_count_launch();
   k_kth<<<1, SEL_THREADS, SEL_SMEM_KEYS * sizeof(unsigned), st>>>(keys, flag, n, k, out_tau, out_ok, n_dev);
+  return cudaGetLastError();
+}
+cudaError_t apx_launch_kth_multi(const KthJob *jobs, int n_jobs, cudaStream_t st) {
+  if (n_jobs <= 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_kth_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(SEL_SMEM_KEYS * sizeof(unsigned)));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  apx_count_launch();
+  k_kth_multi<<<n_jobs, SEL_THREADS, SEL_SMEM_KEYS * sizeof(unsigned), st>>>(jobs);
   return cudaGetLastError();
 }
 cudaError_t apx_launch_build_r(long long n, const long long *cand_ids, const float *f32, const unsigned char *maybe,
