@@ -203,6 +203,8 @@ struct QueryRec {
   // in-pass FP32 compaction of the candidate buffer wanted before the next launch (set when a
   // retired launch showed the buffer above the trigger)
   bool want_compact = false;
+  // candidate count after the select of the last retired launch of the current pass (0: none yet)
+  unsigned seen_count = 0;
   // results
   std::vector<long long> r_ids;
   std::vector<int> r_rxn;
@@ -666,7 +668,7 @@ static float tspan(apex_library &L, cudaEvent_t a, cudaEvent_t b) {
   return ms;
 }
 
-static unsigned fin_cover(const apex_library &L, const QueryRec *q);
+static unsigned fin_cover_base(const apex_library &L, const QueryRec *q);
 
 // Candidate count above which a query's buffer is compacted in FP32 before the next launch: about
 // what its end-of-pass finalization covers in one queued chain (so that chain rarely needs its exact
@@ -674,7 +676,7 @@ static unsigned fin_cover(const apex_library &L, const QueryRec *q);
 // feasible candidates cannot shrink its buffer much: no compaction every launch), and at most half
 // the buffer (two launches are queued before the compaction runs).
 static unsigned compact_trigger(const apex_library &L, const QueryRec *q, unsigned last_kept) {
-  const long long base = std::max<long long>(std::min<long long>(q->cap / 4, fin_cover(L, q) / 2), 2 * q->k);
+  const long long base = std::max<long long>(std::min<long long>(q->cap / 4, fin_cover_base(L, q) / 2), 2 * q->k);
   return (unsigned)std::min<long long>(std::max<long long>(base, 2LL * last_kept), q->cap / 2);
 }
 
@@ -702,6 +704,7 @@ static void retire_launch(apex_library &L) {
     if (q && q->id == sq.second) {
       q->stats.enumerate_ms += ms;
       const unsigned c = cnt[2 * sq.first], kept = cnt[2 * sq.first + 1];
+      q->seen_count = c;
       if (q->remaining > 0 && !q->want_compact && c > compact_trigger(L, q, kept)) q->want_compact = true;
     }
   }
@@ -1398,6 +1401,7 @@ static void write_slot(apex_library &L, QueryRec *q, float admit) {
   L.upload(L.d_slots + q->slot, &S, sizeof(S));
   CU(cudaMemsetAsync(slot_obs(L, q->slot), 0, sizeof(unsigned) * (1 + APEX_MAX_OUTPUTS), L.st));
   q->want_compact = false;
+  q->seen_count = 0;
 }
 
 
@@ -1637,10 +1641,20 @@ static size_t fin_pinned_bytes(const apex_library &L, const QueryRec *q, unsigne
 }
 // candidates an optimistic chain covers: the usual candidate set is a small multiple of k (at most
 // 2^20 by default: the scratch grows ~280 bytes per covered candidate)
-static unsigned fin_cover(const apex_library &L, const QueryRec *q) {
+static unsigned fin_cover_base(const apex_library &L, const QueryRec *q) {
   const long long set = L.fin_cover_set.load();
   const long long c = set > 0 ? set : std::max<long long>(4096, std::min<long long>(4 * q->k, 1LL << 20));
   return (unsigned)std::min<long long>(c, (long long)q->cap);
+}
+// ... and at least 1.5x the count the query's buffer held after the select of its last retired
+// launch (an FP16 compaction keeps a wider band than the FP32 one, so counts above 4k are common
+// at the end of a BF16 pass; a chain that does not cover the count takes the exact rerun), at most
+// 2^22 candidates
+static unsigned fin_cover(const apex_library &L, const QueryRec *q) {
+  const unsigned c = fin_cover_base(L, q);
+  if (L.fin_cover_set.load() > 0 || q->seen_count == 0) return c;
+  const long long want = std::min<long long>((long long)q->seen_count + q->seen_count / 2 + 4096, 1LL << 22);
+  return (unsigned)std::min<long long>(std::max<long long>(c, want), (long long)q->cap);
 }
 
 // One FP64 round: rescore what is pending (near a box bound, or in the boundary band of the k-th
@@ -1941,8 +1955,10 @@ static void finalize_batch(apex_library &L, const std::vector<QueryRec *> &qs, s
       redo[i] = 2;
       sbad[i] = sb;
       ovf[i] = of;
-    } else if (!queue || Ss[i].count > C[i].cover || (C[i].nr > 0 && C[i].h_cnt[2] > 0)) {
+    } else if (!queue || Ss[i].count > C[i].cover) {
       redo[i] = 1;
+    } else if (C[i].nr > 0 && C[i].h_cnt[2] > 0) {
+      redo[i] = 4;  // the chain covered every candidate, but its boundary band moved in the FP64 round
     } else {
       fin_take(L, C[i]);
       if (fin_margin_exceeded(qs[i]))
@@ -1951,6 +1967,27 @@ static void finalize_batch(apex_library &L, const std::vector<QueryRec *> &qs, s
         done[i] = 1;
     }
   }
+  // Chains whose band moved get further FP64 rounds on their own data (still in the arena and the
+  // download area), every such chain queued before one wait per round, until no band moves.
+  for (std::vector<size_t> more;;) {
+    more.clear();
+    for (size_t i = 0; i < n; ++i)
+      if (redo[i] == 4 && C[i].h_cnt[2] > 0 && C[i].rounds < 8) more.push_back(i);
+    if (more.empty()) break;
+    for (size_t i : more) {
+      fin_round(L, C[i]);
+      fin_emit(L, C[i]);
+    }
+    CU(cudaStreamSynchronize(L.st));
+  }
+  for (size_t i = 0; i < n; ++i)
+    if (redo[i] == 4) {
+      fin_take(L, C[i]);
+      if (fin_margin_exceeded(qs[i]))
+        redo[i] = 3;
+      else
+        done[i] = 1;
+    }
   for (size_t i = 0; i < n; ++i) {
     if (redo[i] == 2) {
       fin_restart(L, qs[i], Ss[i], sbad[i], ovf[i]);
