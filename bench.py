@@ -470,7 +470,9 @@ def run_config(args, lib, head, qs, N, world):
             "n_compounds": int(N), "n_reactions": int(lib.n_reactions), "queries_per_step": len(qs),
             "k": [int(q.k) for q in qs], "n_constraints": [int(q.m) for q in qs],
             "head": "-".join(str(x) for x in head.dims) + f" {head.activation}",
-            "precision": f"{args.precision} pass + fp32 boundary rescore + fp64 tie-break",
+            "precision": f"{args.precision} pass + "
+                         f"{'fp16' if args.precision in ('bf16', 'fp8') else 'fp32'} in-pass compaction rescore + "
+                         "fp32 boundary rescore + fp64 tie-break",
             "parallelism": f"reactions sharded x{world} (gather merge of <= k rows per query)" if world > 1
             else "1 GPU",
             "l2": "inputs larger than L2 (the 16-bit P table alone is 2.1 GB on c3_real) and a 512 MB write before "
