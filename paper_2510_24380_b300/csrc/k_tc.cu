@@ -379,10 +379,8 @@ __device__ __forceinline__ bool tc_box(const uint32_t (&h)[8], const uint32_t *l
 // Sec. 3 / Eq. apex_topk per compound (one row per lane, all 32 lanes call it): objective,
 // admission threshold, widened box (admission) and shrunk box ("sure"), then a warp-aggregated
 // append to the query's candidate buffer in global memory. Parameters come from shared memory.
-__device__ __forceinline__ void tc_apply_query_slow(const SlotParams &P, QuerySlot *Q, bool pass, float f, long long id,
-                                                    const float (&o)[16]) {
-  uint32_t h[8];  // the row's outputs as FP16 pairs (formed per test: cheaper than keeping them live)
-  tc_outputs_f16(o, h);
+__device__ __forceinline__ void tc_apply_query_box(const SlotParams &P, QuerySlot *Q, bool pass, float f, long long id,
+                                                   const uint32_t (&h)[8]) {
   pass = pass && tc_box(h, P.lo_w, P.hi_w);
   if (__ballot_sync(0xffffffffu, pass) == 0u) return;  // no lane inside the widened boxes
   const bool sure = tc_box(h, P.lo_s, P.hi_s);
@@ -395,6 +393,12 @@ __device__ __forceinline__ void tc_apply_query_slow(const SlotParams &P, QuerySl
       apx_note_dropped(Q, f);
     }
   }
+}
+__device__ __forceinline__ void tc_apply_query_slow(const SlotParams &P, QuerySlot *Q, bool pass, float f, long long id,
+                                                    const float (&o)[16]) {
+  uint32_t h[8];  // the row's outputs as FP16 pairs (formed per test: cheaper than keeping them live)
+  tc_outputs_f16(o, h);
+  tc_apply_query_box(P, Q, pass, f, id, h);
 }
 
 // objective of one query: its weights are zero beyond n_obj, so a fixed-length dot product serves
@@ -423,6 +427,8 @@ __device__ __forceinline__ float tc_objective(const SlotParams &P, const float (
 template <int NW>
 __device__ __forceinline__ void tc_apply_queries_n(const SlotParams *qp, QuerySlot *slots, const unsigned char *qlist,
                                                    int nq, bool valid, long long id, const float (&o)[16]) {
+  uint32_t h[8];  // the row's outputs as FP16 pairs, formed once for every query's box tests
+  tc_outputs_f16(o, h);
   for (int i = 0; i < nq; i += TC_QGROUP) {
     int sq[TC_QGROUP];
 #pragma unroll
@@ -437,7 +443,7 @@ __device__ __forceinline__ void tc_apply_queries_n(const SlotParams *qp, QuerySl
     }
 #pragma unroll
     for (int u = 0; u < TC_QGROUP; ++u)
-      if (__ballot_sync(0xffffffffu, pass[u]) != 0u) tc_apply_query_slow(qp[sq[u]], slots + sq[u], pass[u], f[u], id, o);
+      if (__ballot_sync(0xffffffffu, pass[u]) != 0u) tc_apply_query_box(qp[sq[u]], slots + sq[u], pass[u], f[u], id, h);
   }
 }
 
