@@ -3,9 +3,11 @@
 Default (no flags): the ~3e10-compound synthetic CSL `c3_real` (1,000 reactions of 2-3 slots,
 lognormal(2000) slot sizes, d = 256, 256-256-256-13 SiLU head), BF16 tensor-core head with FP32
 boundary rescore and FP64 tie-breaking, in the batched form: one step = one shared pass of the
-circular enumeration serving 8 queries submitted together through the C ABI (the workload's own
+circular enumeration serving 9 queries submitted together through the C ABI (the workload's own
 query -- objective 0, six upper bounds at the 0.8 quantile, k = 10^4 -- plus 7 with random convex
-weights over the 5 objectives, six property boxes and k in {100, 1000, 10^4}). `value` counts
+weights over the 5 objectives, six property boxes and k in {100, 1000, 10^4}, all on the whole
+library, and one more, k = 1000, restricted to the oracle's seeded sample of five small reactions
+so that the oracle check below covers one whole top-k, members included). `value` counts
 unique compounds scored per second (every compound's head evaluated once per step, whatever the
 number of queries); `query_compounds_per_s` counts sum over queries of their scopes.
 
@@ -299,13 +301,24 @@ def compounds_per_reaction(lib):
     return np.array([float(np.prod(lib.sizes_of(t).astype(np.float64))) for t in range(lib.n_reactions)])
 
 
-def step_queries(args, spec, precision=None):
+def step_queries(args, spec, precision=None, sizes=None):
+    """The step's queries. The batched form over the whole library adds one more query (the last
+    random query's objective and boxes, k = 1,000) restricted to the oracle leg's seeded sample of
+    small reactions, so that the oracle check covers one whole top-k, members included: the other
+    queries' rows lie in reactions too large to enumerate on the host. (No such query when no
+    reaction is small enough, as on c3_slice.)"""
     import csl_gen
 
     prec = precision or args.precision
     if args.mode == "single":
         return [csl_gen.query_single(args.workload, spec, precision=prec)]
-    return csl_gen.queries_step(args.workload, spec, args.queries, seed=1, precision=prec)
+    qs = csl_gen.queries_step(args.workload, spec, args.queries, seed=1, precision=prec)
+    if sizes is not None:
+        s0, _ = oracle_sample(sizes, args.oracle_compounds, seed=3)
+        if s0:  # (an empty reaction list would mean the whole library through the C ABI)
+            b = qs[-1]
+            qs.append(csl_gen.Query(b.weights, b.cons_idx, b.lo, b.hi, 1000, np.array(s0, np.int32), b.precision))
+    return qs
 
 
 def oracle_sample(sizes, n_target: float, seed: int, min_reactions: int = 5):
@@ -372,14 +385,19 @@ def oracle_leg(L, lib, head, qs, results, n_target, seed=3, scope=None, max_chec
 
     sizes = compounds_per_reaction(lib)
     nq = len(qs)
-    checked = (list(range(nq)) if nq <= max_checked else
-               sorted(np.random.default_rng(seed).choice(nq, max_checked, replace=False).tolist()))
     if scope is not None:  # only the queries' reactions can be checked
         sizes = np.where(np.isin(np.arange(lib.n_reactions), scope), sizes, np.inf)
     S0, n0 = oracle_sample(sizes, n_target, seed)
     if not S0:
         t = int(np.argmin(sizes))
         S0, n0 = [t], int(sizes[t])
+    # queries whose whole scope is sampled are always checked (cheap, and their top-k in full);
+    # of the others up to max_checked, seeded
+    inside = [i for i, q in enumerate(qs) if q.subset is not None and set(np.asarray(q.subset).tolist()) <= set(S0)]
+    rest = [i for i in range(nq) if i not in inside]
+    if len(rest) > max_checked:
+        rest = sorted(np.random.default_rng(seed).choice(rest, max_checked, replace=False).tolist())
+    checked = sorted(inside + rest)
     M, nM = member_reactions(sizes, results, cap=max(n_target, 1.0), budget=n_target, exclude=S0)
     S, nS = sorted(S0 + M), n0 + nM
     rms = np.array(list(L.info().rms)[: head.dims[-1]])
@@ -426,8 +444,8 @@ def run_reference(args):
     if rank != 0:
         return
     full, head, spec = csl_gen.build_workload(args.workload, materialize=False)
-    qs = step_queries(args, spec, precision="fp64")
     sizes = compounds_per_reaction(full)
+    qs = step_queries(args, spec, precision="fp64", sizes=sizes)
     # rate probe on the smallest reaction
     t_small = int(np.argmin(sizes))
     lib1 = full.subset_materialized([t_small])
@@ -441,8 +459,10 @@ def run_reference(args):
         S, nS = oracle_sample(sizes, rate * budget, seed=100 + i, min_reactions=1)
         lib_s = full.subset_materialized(S)
         t0 = time.perf_counter()
-        for q in qs:
-            O.topk(lib_s, head, csl_gen.Query(q.weights, q.cons_idx, q.lo, q.hi, q.k, None, "fp64"))
+        for q in qs:  # every query over the sampled reactions of its scope
+            sub = None if q.subset is None else np.flatnonzero(np.isin(S, q.subset)).astype(np.int32)
+            if sub is None or len(sub):
+                O.topk(lib_s, head, csl_gen.Query(q.weights, q.cons_idx, q.lo, q.hi, q.k, sub, "fp64"))
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             vals.append(nS / dt)
@@ -466,7 +486,11 @@ def run_reference(args):
 def run_config(args, lib, head, qs, N, world):
     form = "batched" if args.mode == "batched" else "single query"
     where = f" {N:.3g}-compound reaction subset," if args.subset_compounds > 0 else ""
-    return {"workload": f"{args.workload}{where} {form}: {len(qs)} quer{'ies' if len(qs) > 1 else 'y'} per shared pass",
+    n_sub = sum(q.subset is not None for q in qs) if args.subset_compounds <= 0 else 0
+    canary = (f" ({len(qs) - n_sub} on the whole library, {n_sub} on the oracle's seeded sample of "
+              f"{len(qs[-1].subset)} small reactions, checked in full)") if n_sub else ""
+    return {"workload": f"{args.workload}{where} {form}: {len(qs)} quer{'ies' if len(qs) > 1 else 'y'} per shared "
+                        f"pass{canary}",
             "n_compounds": int(N), "n_reactions": int(lib.n_reactions), "queries_per_step": len(qs),
             "k": [int(q.k) for q in qs], "n_constraints": [int(q.m) for q in qs],
             "head": "-".join(str(x) for x in head.dims) + f" {head.activation}",
@@ -497,7 +521,7 @@ def run_batched(args):
                                      seed=1, subset=scope, precision=prec)
         N = float(sizes[scope].sum())  # every step scores the subset once
     else:
-        qs = step_queries(args, spec)
+        qs = step_queries(args, spec, sizes=sizes)
         N = float(sizes.sum())
     dev = local
     torch.cuda.set_device(dev)

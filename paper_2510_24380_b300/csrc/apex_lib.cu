@@ -1559,8 +1559,10 @@ static bool admit_one(apex_library &L, QueryRec *q) {
   // buffer holds every admitted candidate until k sure ones exist); grown 4x after an overflow
   if (q->cap == 0) {
     const bool big = q->scope_n > (1LL << 28);
-    q->cap = (unsigned)std::min<long long>(std::max<long long>(big ? 1LL << 20 : 1LL << 18, (big ? 32 : 8) * q->k),
-                                           1LL << 30);
+    // an FP8 pass admits ~7x the band of a BF16 one (its margins): on scopes of 3e10 compounds its
+    // buffers overflowed within one launch until they held 2^26 entries (three 4x restarts)
+    const long long base = big ? (q->precision == APEX_FP8 ? 1LL << 26 : 1LL << 20) : 1LL << 18;
+    q->cap = (unsigned)std::min<long long>(std::max<long long>(base, (big ? 32 : 8) * q->k), 1LL << 30);
   }
   const unsigned have = L.slotbuf[slot].cap;
   if (have < q->cap) {
@@ -2143,14 +2145,17 @@ static void pass_step(apex_library &L) {
     if (!cq.empty()) compact_queries(L, cq);
   }
   // a linear head costs ~100x less per compound than the MLP: larger launches. A query's first
-  // launches are small and grow 4x per launch (2^24, 2^26, ...): its admission threshold is only
-  // a sampled guess until the select after a launch raises it, and a large first launch at a loose
-  // threshold would overflow its candidate buffer.
-  int fresh = 1 << 20;
-  for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
-    if (L.active[s] && L.active[s]->remaining > 0) fresh = std::min(fresh, L.active[s]->stats.n_launches);
-  const long long base_chunk = L.chunk_compounds.load() << (L.n_layers == 1 ? 8 : 0);
-  const long long chunk_compounds = fresh < 10 ? std::min(base_chunk, 1LL << (24 + 2 * fresh)) : base_chunk;
+  // launches serve it few compounds, 4x more per launch (2^24, 2^26, ...): its admission threshold
+  // is only a sampled guess until the select after a launch raises it, and a large first launch at
+  // a loose threshold would overflow its candidate buffer. The launch ends where a query it serves
+  // reaches that bound; queries it does not serve (other reactions) do not shorten it.
+  const long long chunk_compounds = L.chunk_compounds.load() << (L.n_layers == 1 ? 8 : 0);
+  long long ramp[APEX_MAX_ACTIVE];
+  for (int s = 0; s < APEX_MAX_ACTIVE; ++s) {
+    const int f = L.active[s] ? L.active[s]->stats.n_launches : 1 << 20;
+    ramp[s] = f < 10 ? std::min(chunk_compounds, 1LL << (24 + 2 * f)) : chunk_compounds;
+  }
+  std::vector<long long> served_c(APEX_MAX_ACTIVE, 0);  // compounds this launch serves each query
   // build one plan (items from the cursor) with per-precision query masks
   // indexed by pass precision (APEX_FP32, APEX_BF16, APEX_FP16, APEX_FP8; 2 unused)
   PlanBuilder pb[5] = {PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx), PlanBuilder(L.rx)};
@@ -2176,9 +2181,13 @@ static void pass_step(apex_library &L) {
     }
     long long take = e - b;
     const unsigned long long any = mask[0] | mask[1] | mask[3] | mask[4];
+    bool ramp_full = false;  // a query served here reached its first-launch bound
     if (any) {
       const long long per_item = (long long)L.rx[t].L_o * APX_TILE;
-      const long long room = std::max<long long>(1, (chunk_compounds - served_compounds + per_item - 1) / per_item);
+      long long left = chunk_compounds - served_compounds;
+      for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
+        if (any >> s & 1ull) left = std::min(left, ramp[s] - served_c[s]);
+      const long long room = std::max<long long>(1, (left + per_item - 1) / per_item);
       take = std::min(std::min(take, room), lack);
       bool ok = true;
       for (int p = 0; p < 5; ++p)
@@ -2187,12 +2196,17 @@ static void pass_step(apex_library &L) {
       for (int p = 0; p < 5; ++p)
         if (mask[p]) pb[p].add(t, b, b + take, mask[p]);
       for (int s = 0; s < APEX_MAX_ACTIVE; ++s)
-        if (any >> s & 1ull) served[s] += take;
+        if (any >> s & 1ull) {
+          served[s] += take;
+          served_c[s] += take * per_item;
+          ramp_full = ramp_full || served_c[s] >= ramp[s];
+        }
       served_compounds += take * per_item;
     }
     visited += take;
     cur += take;
     if (cur >= L.total_items) cur = 0;
+    if (ramp_full) break;
   }
   L.cursor = cur;
   std::vector<int> list;
