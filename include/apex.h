@@ -154,8 +154,9 @@ typedef struct {
    * widened (at least 2x, and at least twice the observed ratio), up to 4 times; the ratios
    * reported are those of the final run. */
   int32_t n_margin_reruns;
-  int32_t n_compactions;        /* in-pass FP32 compactions of its candidate buffer (a buffer filled
-                                   between launches is rescored in FP32 and cut to what can still
+  int32_t n_compactions;        /* in-pass compactions of its candidate buffer (a buffer filled
+                                   between launches is rescored -- FP16 on the tensor cores for
+                                   BF16 and FP8 passes, else FP32 -- and cut to what can still
                                    reach the top-k; the admission threshold rises accordingly) */
   double pass_err_ratio;
   double fp32_err_ratio;

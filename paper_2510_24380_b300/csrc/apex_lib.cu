@@ -200,7 +200,7 @@ struct QueryRec {
   // factors on the library's pass and FP32 margins for this query (raised when the runtime check at
   // finalization observed a larger error than a margin allows)
   double mscale = 1.0;
-  // in-pass FP32 compaction of the candidate buffer wanted before the next launch (set when a
+  // in-pass compaction of the candidate buffer wanted before the next launch (set when a
   // retired launch showed the buffer above the trigger)
   bool want_compact = false;
   // candidate count after the select of the last retired launch of the current pass (0: none yet)
@@ -682,7 +682,7 @@ static unsigned compact_trigger(const apex_library &L, const QueryRec *q, unsign
 
 // Retires the oldest enumeration launch in flight: waits for its status copy, raises a device-side
 // wait timeout as an error, adds the launch's duration to the queries it served, and marks for an
-// FP32 compaction the queries whose candidate buffer it left above their trigger.
+// in-pass compaction the queries whose candidate buffer it left above their trigger.
 static void retire_launch(apex_library &L) {
   apex_library::InFlight f = std::move(L.inflight.front());
   L.inflight.pop_front();

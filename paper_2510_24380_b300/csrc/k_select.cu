@@ -311,7 +311,7 @@ __global__ void k_build_r(long long n, const long long *cand_ids, const float *f
   }
 }
 
-// ------------------------------------------------------------------ in-pass FP32 compaction
+// ------------------------------------------------------------------ in-pass compaction
 // Between the launches of a pass, a query whose candidate buffer fills up has its candidates
 // rescored in FP32 (k_eval32, k_kth: tau32 = k-th largest FP32 objective among FP32-sure entries).
 // k surely feasible compounds then have exact objectives >= B = tau32 - eps_f, so the final k-th
