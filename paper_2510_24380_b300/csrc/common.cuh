@@ -89,7 +89,7 @@ struct QuerySlot {
   long long k;
   unsigned cap;
   unsigned count;     // appended entries (atomic)
-  unsigned count_compacted;  // entries kept by the last in-pass compaction (0 = none yet)
+  unsigned count_compacted;  // entries kept by the last in-pass FP32 compaction (0 = none yet)
   unsigned overflow;
   unsigned dropped_bits;  // order-preserving bits of the largest key that did not fit (0 = none)
   unsigned n_sure_above_spec;
