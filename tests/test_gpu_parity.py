@@ -396,11 +396,13 @@ def test_exact_finalization_rerun_matches(ragged):
 @pytest.mark.parametrize("precision", ["bf16", "fp8"])
 def test_in_pass_compaction_matches(ragged, precision):
     """Small launches and a small finalization cover make every query's candidate buffer pass its
-    trigger between launches: it is rescored in FP32 and cut to what can still reach the top-k, and
-    the admission threshold rises to the FP32-certified floor. The rows must equal those of the
-    default path (no compaction) and the FP64 oracle, alone and with a second query sharing the
-    launches; the pass error observed on the compacted candidates stays inside the margin. (The
-    FP16 pass, with margins ~10x tighter, keeps too few candidates here to reach the trigger.)"""
+    trigger between launches: the entries appended since the last compaction are rescored (FP16 on
+    the tensor cores for these passes), the buffer is cut to what can still reach the top-k, and the
+    admission threshold rises to the certified floor. The rows must equal those of the default path
+    (no compaction) and the FP64 oracle, alone and with a second query sharing the launches; the
+    error observed at the end of the pass (pass keys, and keys a compaction set, each against its
+    own margin) stays inside the margins. (The FP16 and FP32 passes, with margins ~10x and ~10^4x
+    tighter, keep too few candidates here to reach the trigger.)"""
     lib, head, spec, L, rms = ragged
     stats = csl_gen.load_stats("t_ragged")
     qa = csl_gen.query_single("t_ragged", spec, stats, precision=precision)
