@@ -297,6 +297,7 @@ struct apex_library {
   } slotbuf[APEX_MAX_ACTIVE];
   char *arena = nullptr;
   size_t arena_cap = 0, arena_off = 0;
+  size_t dev_total = 0;  // device memory (cudaMemGetInfo at load)
   char *pinned = nullptr;
   size_t pinned_cap = 0;
   // Pinned upload ring: every small host-to-device copy of the worker (slot parameters, slot
@@ -959,6 +960,11 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
     cudaDeviceProp prop;
     CU(cudaGetDeviceProperties(&prop, L->device));
     L->n_sm = prop.multiProcessorCount;
+    {
+      size_t fr = 0, tot = 0;
+      CU(cudaMemGetInfo(&fr, &tot));
+      L->dev_total = tot;
+    }
     if (D->cuda_stream) {
       L->st = (cudaStream_t)D->cuda_stream;
     } else {
@@ -2114,9 +2120,12 @@ static void compact_group(apex_library &L, const std::vector<QueryRec *> &qs) {
 // rescored objective), their decisions and the k-th sure objective, then each buffer keeps only
 // what can still reach the top-k and its admission threshold rises to the certified floor
 // (k_compact_keep / k_compact_apply). Queries are grouped so that a group's scratch fits the
-// arena limit (8 GB, and the device budget when there is one).
+// arena limit (below).
 static void compact_queries(apex_library &L, const std::vector<QueryRec *> &qs) {
-  const size_t cap = L.budget ? std::min<size_t>(8ull << 30, std::max<size_t>(L.arena_cap, 64ull << 20)) : (8ull << 30);
+  // without a budget: a quarter of the device, at most 48 GB and at least 8 GB (an FP8 pass over
+  // a large scope holds 2^26-entry buffers, ~4.7 GB of compaction scratch per query)
+  const size_t unbudgeted = std::max<size_t>(8ull << 30, std::min<size_t>(48ull << 30, L.dev_total / 4));
+  const size_t cap = L.budget ? std::min<size_t>(8ull << 30, std::max<size_t>(L.arena_cap, 64ull << 20)) : unbudgeted;
   std::vector<QueryRec *> group;
   size_t bytes = 0;
   for (QueryRec *q : qs) {
