@@ -122,6 +122,7 @@ __device__ bool block_kth_largest(const Src &src, long long n, long long k, unsi
 // Raises tau (k-th largest sure key) and the admission threshold tau - 2 delta_f, then keeps
 // only entries at or above the admission threshold.
 #define SEL_SMEM_KEYS 49152  // buffers up to this size are selected from shared memory (192 KB)
+#define SEL_SKIP_ABOVE (1u << 17)
 __global__ void __launch_bounds__(SEL_THREADS) k_slot_select(QuerySlot *slots, const int *slot_list, int mode) {
   QuerySlot *Q = slots + slot_list[blockIdx.x];
   extern __shared__ unsigned sel_bits[];  // SEL_SMEM_KEYS entries
@@ -129,6 +130,10 @@ __global__ void __launch_bounds__(SEL_THREADS) k_slot_select(QuerySlot *slots, c
   __shared__ unsigned n_spec;
   const unsigned n = min(*((volatile unsigned *)&Q->count), Q->cap);
   if (mode == 0 && (long long)n <= Q->k) return;
+  // Between launches, a buffer of more than SEL_SKIP_ABOVE entries whose query was already
+  // compacted is left to the next compaction: its admission floor is already the compaction's
+  // certified one, and one CTA would take milliseconds over the whole buffer (FP8 passes).
+  if (mode == 0 && n > SEL_SKIP_ABOVE && Q->count_compacted > 0) return;
   unsigned bits;
   bool found;
   if (n <= SEL_SMEM_KEYS) {
