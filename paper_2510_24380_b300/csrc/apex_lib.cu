@@ -759,7 +759,9 @@ static void upload_err32(apex_library &L) {
   float e32[APEX_MAX_OUTPUTS] = {0};
   for (int p = 0; p < L.n_out; ++p) e32[p] = (float)L.err32[p];
   CU(cudaMemcpy(L.d_err32f, e32, sizeof(e32), cudaMemcpyHostToDevice));
-  if (L.tc_fmt[1]) {  // rounded up: the FP32 test of an FP16 rescore must not be tighter than its margin
+  bool have16 = L.tc_fmt[1];  // FP16 margins calibrated (a library file of a BF16-only library saved
+  for (int p = 0; p < L.n_out; ++p) have16 = have16 && L.err16[1][p] > 0;  // before may lack them)
+  if (have16) {  // rounded up: the FP32 test of an FP16 rescore must not be tighter than its margin
     L.d_err16f = (float *)L.dalloc(sizeof(float) * APEX_MAX_OUTPUTS);
     float e16[APEX_MAX_OUTPUTS] = {0};
     for (int p = 0; p < L.n_out; ++p) e16[p] = std::nextafter((float)L.err16[1][p], INFINITY);
@@ -1156,7 +1158,12 @@ static apex_status load_impl(const apex_library_desc *D, const SavedCal *cal, ap
       for (auto &e : L->ev_tr) CU(cudaEventCreate(&e));
     L->pin(1 << 20);
     CU(cudaStreamSynchronize(L->st));
-    if (cal) {
+    // a file's margins are restored when they cover every tensor-core format the library builds
+    // (a file saved by a BF16-only library of an earlier build has no FP16 margins: recalibrate)
+    bool cal_ok = cal != nullptr;
+    for (int f = 0; f < 3 && cal_ok; ++f)
+      for (int p = 0; p < L->n_out && cal_ok; ++p) cal_ok = !L->tc_fmt[f] || cal->err16[f][p] > 0;
+    if (cal_ok) {
       L->n_calib = cal->n_calib;
       memcpy(L->err32, cal->err32, sizeof(L->err32));
       memcpy(L->err16, cal->err16, sizeof(L->err16));
