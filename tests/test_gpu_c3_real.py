@@ -7,6 +7,9 @@ the checks are those that hold at any size (Eq. apex_topk restricted to a set of
     returned member is rescored by the FP64 oracle; on the sampled reactions each result's members
     are the oracle's first |X n t| of those reactions and no better feasible compound is missing;
     the restricted query's whole top-k, members included, equals the oracle's;
+  - the workload's query alone in FP8 (e4m3 layer 2): its wide margins fill 10^5-10^6-entry
+    candidate buffers, so its pass runs in-pass compactions every launch and leaves the large
+    buffers' selects between launches to them; checked the same way;
   - raw outputs of the production enumeration kernel over one whole reaction of about 10^6
     compounds against the oracle on a seeded sample of its compounds (2e-2 absolute for BF16).
 """
@@ -26,7 +29,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def c3():
     lib, head, spec = csl_gen.build_workload("c3_real")
-    L = apex.Library(lib, head, precisions=("fp32", "bf16"), seed=0)
+    L = apex.Library(lib, head, precisions=("fp32", "bf16", "fp8"), seed=0)
     L.set_launch_shape(1 << 27, 32)  # the bench's launch shape on this library
     first = reaction_first_ids(lib)
     yield lib, head, spec, L, first
@@ -54,6 +57,19 @@ def test_batched_step_at_3e10_compounds_matches_oracle(c3):
     # the restricted query: its whole top-k against the oracle's enumeration of its 5 reactions
     q9, r9 = qs[-1], res[-1]
     check_topk(r9, O.topk(lib, head, q9), lib, head, q9, rms)
+
+
+def test_fp8_query_at_3e10_compounds_matches_oracle(c3):
+    lib, head, spec, L, first = c3
+    S = seeded_small_reactions(lib, 5, 400000, seed=6)
+    q = csl_gen.query_single("c3_real", spec, precision="fp8")
+    rms = np.array(list(L.info().rms)[: head.dims[-1]])
+    r = L.run(q)
+    st = L.stats(-1)
+    assert r["n"] == q.k and st["n_compactions"] > 0 and st["n_restarts"] == 0, st
+    assert st["pass_err_ratio"] <= 1.0 and st["fp32_err_ratio"] <= 1.0, st
+    check_members_exact(r, lib, head, q, rms)
+    check_reaction_decomposed(r, lib, head, q, S, rms)
 
 
 def test_raw_outputs_of_a_whole_reaction(c3):
