@@ -103,6 +103,22 @@ def test_load_rejects_before_touching_the_gpu(dll, case, code):
     assert len(dll.apex_last_error()) > 0
 
 
+def test_load_rejects_ids_at_or_above_2_61(dll):
+    """Candidate ids carry two flag bits above bit 60, so a library of 2^61 or more compounds is
+    refused (before U is read: the descriptor's U here holds far fewer rows than its slots)."""
+    D, keep = _desc(n_slots=[2], sizes=[3, 4], d=8, dims=[8, 4])
+    for big, code in (([2 ** 31, 2 ** 30], -1), ([2 ** 30, 2 ** 30], None)):
+        ss = np.asarray(big, np.int64)
+        keep.append(ss)
+        D.slot_sizes = ss.ctypes.data_as(C.POINTER(C.c_int64))
+        if code is None:  # 2^60 compounds: past the id check (a GPU-less box then fails later)
+            assert apex.apex_count_compounds([2], big) == 2 ** 60
+            continue
+        h = C.c_void_p()
+        assert dll.apex_load_library(C.byref(D), C.byref(h)) == code
+        assert not h.value and b"2^61" in dll.apex_last_error()
+
+
 def test_null_arguments(dll):
     h = C.c_void_p()
     assert dll.apex_load_library(None, C.byref(h)) == -1
